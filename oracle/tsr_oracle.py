@@ -1,0 +1,410 @@
+"""FP64 CPU oracle of the translucent-transfer hot path.
+
+TEST INFRASTRUCTURE ONLY.  This module is the plain, slow, obviously correct
+definition that the CUDA path is checked against.  Only the test suite, the
+package smoke check and the benchmark's CPU-baseline leg may import it; the
+product path never does.  It shares no code with the CUDA library.
+
+Everything is numpy float64 (complex128 where a complex step is taken).  Each
+function names the part of the paper it restates:
+
+  * Section 2.1, Eq. 4: Jensen's dipole diffuse reflectance R_d and the
+    polynomial Fresnel fit F_dr.
+  * Section 2.2, Eq. 5: the PCA factorisation R_d(r, sigma) ~ sum_k s_k(sigma) b_k(r)
+    from an SVD M = U S V of sampled R_d; b_k are columns of V.  Here b_k is
+    called f_k and s_k is called g_k.
+  * Section 3, Eq. 6-7: the transfer M[k,j,o] = sum_i A_i f_k(|x_o - x_i|) T[j,i].
+  * Section 3.2, Eq. 9-10 and precompute Step 2: spatial wavelet transform of
+    the transfer and truncation of its coefficients.
+  * Section 4, rendering Steps 3-5: project the material, weight the wavelet
+    transfer by s_k, inverse wavelet transform.
+
+Readings where the paper is silent or garbled (each is also listed with the
+design notes):
+  R1  sigma_t' = sigma_a + sigma_s' (printed "sigma_s + sigma_s'").
+  R2  sigma_tr = sqrt(3 sigma_a sigma_t') (printed "sqrt(3 sigma_s sigma_t')").
+  R3  the second dipole term uses 1/d_v (printed "1/d").
+  R4  z_v = z_r (1 + 4A/3); both dipole terms are added, as printed.
+  R7  the radial basis is the right singular vectors of the (material x radius)
+      sample matrix R[s, m] = R_d(r_m; sigma_s): R = U S V^T, f_k = V[:, k].
+  R8  the SVD is uncentred (the approximation has no mean term).
+  R9  sign: each f_k is flipped so its largest-magnitude entry is positive
+      (ties: lowest index).
+  R11 radius grid r_m = r_max * m / (n_r - 1), m = 0..n_r-1.
+  R12 f_k(r) is piecewise linear on that grid and zero for r > r_max; the
+      cutoff is decided on the FP32 squared distance (see ``pair_r2_fp32``).
+  R13 g_k = sum_m f_k(r_m) R_d(r_m) (plain discrete inner product).
+  R15 the self pair i = o is included.
+  R21 the spatial domain of chart d is its nu x nu grid in Morton order,
+      zero-padded to P x P, P = 2^ceil(log2 nu); poles pass through.
+  R22 the spatial wavelet is the orthonormal Haar.
+  R23 keep rule: per (k, j), the round(p * 10 P^2) largest |coefficients| of the
+      charts (ties: lower index); the two pole values are always kept.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# ----------------------------------------------------------------------------
+# Section 2.1, Eq. 4: dipole diffuse reflectance
+# ----------------------------------------------------------------------------
+
+
+def fresnel_dr(eta):
+    """Polynomial diffuse Fresnel reflectance F_dr(eta) of Section 2.1 (text after Eq. 4)."""
+    return -1.440 / (eta * eta) + 0.710 / eta + 0.668 + 0.0636 * eta
+
+
+def boundary_a(eta):
+    """A = (1 + F_dr) / (1 - F_dr) (Section 2.1)."""
+    F = fresnel_dr(eta)
+    return (1.0 + F) / (1.0 - F)
+
+
+def dipole_rd(r, sigma_a, sigma_s, eta):
+    """Eq. 4: R_d(r; sigma_a, sigma_s', eta), readings R1-R4.  Broadcasts; accepts complex."""
+    st = sigma_a + sigma_s                      # sigma_t'
+    alpha = sigma_s / st                        # alpha'
+    s_tr = np.sqrt(3.0 * sigma_a * st)          # sigma_tr
+    zr = 1.0 / st
+    zv = zr * (1.0 + 4.0 * boundary_a(eta) / 3.0)
+    dr = np.sqrt(r * r + zr * zr)
+    dv = np.sqrt(r * r + zv * zv)
+    real_term = zr * (s_tr + 1.0 / dr) * np.exp(-s_tr * dr) / (dr * dr)
+    virt_term = zv * (s_tr + 1.0 / dv) * np.exp(-s_tr * dv) / (dv * dv)
+    return alpha / (4.0 * math.pi) * (real_term + virt_term)
+
+
+def dipole_rd_partials(r, sigma_a, sigma_s, eta):
+    """Hand-derived partial derivatives of Eq. 4: (dR/dsigma_a, dR/dsigma_s', dR/deta).
+
+    With h(z) = z (s_tr + 1/d) e^{-s_tr d} / d^2, d = sqrt(r^2 + z^2):
+      dh/ds_tr = -s_tr z e^{-s_tr d} / d
+      dh/dz    = (s_tr + 1/d) e^{-s_tr d}/d^2 - (z^2/d) e^{-s_tr d} (s_tr^2/d^2 + 3 s_tr/d^3 + 3/d^4)
+    and R_d = alpha'/(4 pi) (h(z_r) + h(z_v)).
+    """
+    st = sigma_a + sigma_s
+    alpha = sigma_s / st
+    s_tr = np.sqrt(3.0 * sigma_a * st)
+    zr = 1.0 / st
+    F = fresnel_dr(eta)
+    A = (1.0 + F) / (1.0 - F)
+    c_v = 1.0 + 4.0 * A / 3.0
+    zv = zr * c_v
+
+    def h_parts(z):
+        d = np.sqrt(r * r + z * z)
+        e = np.exp(-s_tr * d)
+        h = z * (s_tr + 1.0 / d) * e / (d * d)
+        dh_ds = -s_tr * z * e / d
+        dh_dz = (s_tr + 1.0 / d) * e / (d * d) - (z * z / d) * e * (
+            s_tr * s_tr / (d * d) + 3.0 * s_tr / d ** 3 + 3.0 / d ** 4)
+        return h, dh_ds, dh_dz
+
+    hr, hr_s, hr_z = h_parts(zr)
+    hv, hv_s, hv_z = h_parts(zv)
+    pref = 1.0 / (4.0 * math.pi)
+    dalpha_da = -sigma_s / (st * st)
+    dalpha_ds = sigma_a / (st * st)
+    dstr_da = 3.0 * (st + sigma_a) / (2.0 * s_tr)
+    dstr_ds = 3.0 * sigma_a / (2.0 * s_tr)
+    dzr = -1.0 / (st * st)            # same for sigma_a and sigma_s'
+    dzv = c_v * dzr
+    dF = 2.0 * 1.440 / eta ** 3 - 0.710 / (eta * eta) + 0.0636
+    dA = 2.0 * dF / ((1.0 - F) ** 2)
+    dzv_deta = zr * 4.0 * dA / 3.0
+    hs = hr + hv
+    d_a = pref * (dalpha_da * hs + alpha * ((hr_s + hv_s) * dstr_da + hr_z * dzr + hv_z * dzv))
+    d_s = pref * (dalpha_ds * hs + alpha * ((hr_s + hv_s) * dstr_ds + hr_z * dzr + hv_z * dzv))
+    d_e = pref * alpha * hv_z * dzv_deta
+    return d_a, d_s, d_e
+
+
+# ----------------------------------------------------------------------------
+# Section 2.2, Eq. 5: PCA of sampled R_d
+# ----------------------------------------------------------------------------
+
+
+def radius_grid(n_r: int = 1024, r_max: float = 40.0) -> np.ndarray:
+    """Reading R11: r_m = r_max * m / (n_r - 1)."""
+    return r_max * np.arange(n_r, dtype=np.float64) / (n_r - 1)
+
+
+def sample_matrix(sigma_a, sigma_s, eta, n_r=1024, r_max=40.0):
+    """R[s, m] = R_d(r_m; sigma_a[s], sigma_s'[s], eta): the matrix factorised in Eq. 5."""
+    r = radius_grid(n_r, r_max)
+    sa = np.asarray(sigma_a, dtype=np.float64)[:, None]
+    ss = np.asarray(sigma_s, dtype=np.float64)[:, None]
+    return dipole_rd(r[None, :], sa, ss, eta)
+
+
+def fit_pca_basis(sigma_a, sigma_s, eta=1.3, n_r=1024, r_max=40.0, K=12):
+    """Eq. 5 and Section 2.2: radial basis f_k = k-th right singular vector of R (R7-R9).
+
+    Returns (f [K][n_r], singular values [min(S, n_r)]).  The SVD is a library
+    primitive (LAPACK via numpy).
+    """
+    R = sample_matrix(sigma_a, sigma_s, eta, n_r, r_max)
+    _, s, vt = np.linalg.svd(R, full_matrices=False)
+    f = vt[:K].copy()
+    for k in range(K):
+        m = int(np.argmax(np.abs(f[k])))
+        if f[k, m] < 0:
+            f[k] = -f[k]
+    return f, s
+
+
+def project_material(f, sigma_a, sigma_s, eta, r_max=40.0):
+    """Section 2.2 (coefficients by projection) and rendering Step 3: g_k = sum_m f_k(r_m) R_d(r_m).
+
+    sigma_a, sigma_s: (n, 3) per RGB channel; eta: (n,).  Returns g (n, 3, K).
+    """
+    K, n_r = f.shape
+    r = radius_grid(n_r, r_max)
+    sa = np.asarray(sigma_a)
+    ss = np.asarray(sigma_s)
+    eta = np.asarray(eta)
+    R = dipole_rd(r[None, None, :], sa[..., None], ss[..., None], eta[:, None, None])  # (n,3,n_r)
+    return R @ f.T
+
+
+def project_material_vjp(f, sigma_a, sigma_s, eta, dg, r_max=40.0):
+    """Reverse mode of ``project_material``: given dL/dg (n,3,K) return dL/dsigma_a (n,3), dL/dsigma_s' (n,3), dL/deta (n,)."""
+    K, n_r = f.shape
+    r = radius_grid(n_r, r_max)
+    sa = np.asarray(sigma_a)[..., None]
+    ss = np.asarray(sigma_s)[..., None]
+    et = np.asarray(eta)[:, None, None]
+    d_a, d_s, d_e = dipole_rd_partials(r[None, None, :], sa, ss, et)   # (n,3,n_r)
+    w = dg @ f                                                         # (n,3,n_r): sum_k dg_k f_k(r_m)
+    return (w * d_a).sum(-1), (w * d_s).sum(-1), (w * d_e).sum(-1).sum(-1)
+
+
+# ----------------------------------------------------------------------------
+# Section 3, Eq. 6-7: the transfer
+# ----------------------------------------------------------------------------
+
+
+def pair_r2_fp32(xo, xi):
+    """FP32 squared distance used only for the r > r_max cutoff decision (reading R12).
+
+    dx = fl(x_o - x_i) per axis, r2 = fl(fl(fl(dx^2) + fl(dy^2)) + fl(dz^2)), all
+    IEEE binary32 round-to-nearest, so the cutoff is taken in the same
+    precision on the CPU and the GPU.
+    """
+    d = (np.asarray(xo, dtype=np.float32)[..., :] - np.asarray(xi, dtype=np.float32)).astype(np.float32)
+    sq = (d * d).astype(np.float32)
+    return ((sq[..., 0] + sq[..., 1]).astype(np.float32) + sq[..., 2]).astype(np.float32)
+
+
+def basis_eval(f, r, r_max=40.0, r2_fp32=None):
+    """Reading R12: f_k(r) piecewise linear on the grid of R11, zero beyond r_max.
+
+    f: (K, n_r); r: any shape (float64).  If ``r2_fp32`` is given, the cutoff
+    is ``r2_fp32 > fl32(r_max^2)``; otherwise ``r > r_max``.
+    Returns (K,) + r.shape.
+    """
+    K, n_r = f.shape
+    dr = r_max / (n_r - 1)
+    x = np.asarray(r, dtype=np.float64) / dr
+    m = np.minimum(np.floor(x).astype(np.int64), n_r - 2)
+    m = np.maximum(m, 0)
+    t = x - m
+    val = f[:, m] * (1.0 - t) + f[:, m + 1] * t
+    if r2_fp32 is not None:
+        outside = r2_fp32 > np.float32(r_max * r_max)
+    else:
+        outside = np.asarray(r) > r_max
+    return np.where(outside, 0.0, val)
+
+
+def transfer_rows(f, pos, area, T, rows, r_max=40.0):
+    """Eq. 6-7 by brute force: M[k, j, o] = sum_i A_i f_k(|x_o - x_i|) T[j, i] for o in ``rows``.
+
+    pos: (N, 3) float32 positions (mm); area: (N,); T: (J, N).  The double sum
+    is taken one output row at a time, over every i (the self pair included).
+    Returns (K, J, len(rows)).
+    """
+    pos32 = np.asarray(pos, dtype=np.float32)
+    p64 = pos32.astype(np.float64)
+    Tw = np.asarray(T, dtype=np.float64) * np.asarray(area, dtype=np.float64)[None, :]   # T'[j,i] = A_i T[j,i]
+    K = f.shape[0]
+    out = np.empty((K, Tw.shape[0], len(rows)))
+    for q, o in enumerate(rows):
+        r = np.sqrt(((p64[o][None, :] - p64) ** 2).sum(axis=1))
+        F = basis_eval(f, r, r_max, r2_fp32=pair_r2_fp32(pos32[o][None, :], pos32))   # (K, N)
+        out[:, :, q] = F @ Tw.T
+    return out
+
+
+def transfer_full(f, pos, area, T, r_max=40.0):
+    """All rows of ``transfer_rows``."""
+    return transfer_rows(f, pos, area, T, np.arange(np.asarray(pos).shape[0]), r_max)
+
+
+# ----------------------------------------------------------------------------
+# Section 3.2, Eq. 9-10: spatial Haar over the rhombic charts
+# ----------------------------------------------------------------------------
+
+
+def chart_side(nu: int) -> int:
+    """P = 2^ceil(log2 nu): padded chart side (reading R21)."""
+    P = 1
+    while P < nu:
+        P *= 2
+    return P
+
+
+def morton_index(row, col, P):
+    """Morton (Z-order) index of (row, col) in a P x P chart: col bits even, row bits odd."""
+    row = np.asarray(row, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int64)
+    m = np.zeros(np.broadcast(row, col).shape, dtype=np.int64)
+    b = 0
+    while (1 << b) < P:
+        m |= ((col >> b) & 1) << (2 * b)
+        m |= ((row >> b) & 1) << (2 * b + 1)
+        b += 1
+    return m
+
+
+def haar_forward_1d(x):
+    """Orthonormal Haar analysis by its recursive definition (pairwise (a+b)/sqrt2, (a-b)/sqrt2).
+
+    Output order: [scaling, coarsest detail, ..., finest details (len/2)].  len(x) = 2^L.
+    """
+    x = np.asarray(x)
+    if x.shape[-1] == 1:
+        return x.copy()
+    a = (x[..., 0::2] + x[..., 1::2]) / math.sqrt(2.0)
+    d = (x[..., 0::2] - x[..., 1::2]) / math.sqrt(2.0)
+    return np.concatenate([haar_forward_1d(a), d], axis=-1)
+
+
+def haar_inverse_1d(c):
+    """Inverse of ``haar_forward_1d``."""
+    c = np.asarray(c)
+    n = c.shape[-1]
+    if n == 1:
+        return c.copy()
+    a = haar_inverse_1d(c[..., : n // 2])
+    d = c[..., n // 2:]
+    x = np.empty(c.shape, dtype=np.result_type(c, np.float64))
+    x[..., 0::2] = (a + d) / math.sqrt(2.0)
+    x[..., 1::2] = (a - d) / math.sqrt(2.0)
+    return x
+
+
+def chart_to_wavelet(X, nu):
+    """Spatial wavelet transform w_1 of Eq. 9 applied to per-vertex data X[..., N].
+
+    Chart d's nu x nu values go to Morton positions of a zero-padded P x P
+    domain and are Haar-analysed; the result has layout [..., 10 P^2 + 2] with
+    chart d at [d P^2, (d+1) P^2) and the two poles last.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    P = chart_side(nu)
+    rr, cc = np.meshgrid(np.arange(nu), np.arange(nu), indexing="ij")
+    mort = morton_index(rr, cc, P).reshape(-1)
+    lead = X.shape[:-1]
+    out = np.zeros(lead + (10 * P * P + 2,))
+    for d in range(10):
+        dom = np.zeros(lead + (P * P,))
+        dom[..., mort] = X[..., d * nu * nu:(d + 1) * nu * nu]
+        out[..., d * P * P:(d + 1) * P * P] = haar_forward_1d(dom)
+    out[..., 10 * P * P:] = X[..., 10 * nu * nu:]
+    return out
+
+
+def wavelet_to_chart(C, nu):
+    """Inverse spatial transform w_1^{-1} (Eq. 10, rendering Step 5); drops the padding."""
+    C = np.asarray(C, dtype=np.float64)
+    P = chart_side(nu)
+    rr, cc = np.meshgrid(np.arange(nu), np.arange(nu), indexing="ij")
+    mort = morton_index(rr, cc, P).reshape(-1)
+    lead = C.shape[:-1]
+    out = np.zeros(lead + (10 * nu * nu + 2,))
+    for d in range(10):
+        dom = haar_inverse_1d(C[..., d * P * P:(d + 1) * P * P])
+        out[..., d * nu * nu:(d + 1) * nu * nu] = dom[..., mort]
+    out[..., 10 * nu * nu:] = C[..., 10 * P * P:]
+    return out
+
+
+def keep_count(p: float, n_coef: int) -> int:
+    """Reading R23: n_keep = floor(p * n_coef + 0.5), clamped to [1, n_coef]."""
+    return int(min(n_coef, max(1, math.floor(p * n_coef + 0.5))))
+
+
+def select_top(Cw, nu, p):
+    """Precompute Step 2 (Section 3.2) with the top-p keep rule of reading R23.
+
+    Cw: (K, J, 10 P^2 + 2) wavelet coefficients (any float dtype; the ranking is
+    taken on |value| in that dtype).  Returns a boolean keep mask of the same
+    shape: per (k, j) the n_keep largest chart magnitudes (ties: lower index)
+    plus the two poles.
+    """
+    P = chart_side(nu)
+    n_coef = 10 * P * P
+    nk = keep_count(p, n_coef)
+    K, J, _ = Cw.shape
+    mask = np.zeros(Cw.shape, dtype=bool)
+    idx = np.arange(n_coef)
+    for k in range(K):
+        for j in range(J):
+            mag = np.abs(Cw[k, j, :n_coef])
+            order = np.lexsort((idx, -mag.astype(np.float64)))   # by -|c|, then index
+            mask[k, j, order[:nk]] = True
+    mask[:, :, n_coef:] = True
+    return mask
+
+
+# ----------------------------------------------------------------------------
+# Section 4, rendering Steps 3-5: relight and its adjoint
+# ----------------------------------------------------------------------------
+
+
+def relight(Cw_kept, nu, g, light):
+    """Rendering Steps 3-5: B[e, ch, o] = w_1^{-1}( sum_{k,j} g[e,ch,k] l_j Cw[k, j, :] ).
+
+    Cw_kept: (K, J, 10 P^2 + 2) kept wavelet coefficients (zeros where
+    discarded); g: (E, 3, K); light: (J,).  Returns (E, 3, N).
+    """
+    c = np.asarray(g, dtype=np.float64)[..., :, None] * np.asarray(light, dtype=np.float64)[None, None, None, :]
+    bw = np.einsum("eckj,kjw->ecw", c, np.asarray(Cw_kept, dtype=np.float64))
+    return wavelet_to_chart(bw, nu)
+
+
+def relight_direct(f, pos, area, T, g, light, r_max=40.0, rows=None):
+    """Uncompressed relight straight from Eq. 6: B[e,ch,o] = sum_i A_i (sum_k g_k f_k(r_oi)) E_i, E_i = sum_j l_j T[j,i]."""
+    pos32 = np.asarray(pos, dtype=np.float32)
+    p64 = pos32.astype(np.float64)
+    N = p64.shape[0]
+    rows = np.arange(N) if rows is None else rows
+    E = np.asarray(light, dtype=np.float64) @ np.asarray(T, dtype=np.float64)          # (N,)
+    AE = np.asarray(area, dtype=np.float64) * E
+    g = np.asarray(g, dtype=np.float64)
+    out = np.empty(g.shape[:2] + (len(rows),))
+    for q, o in enumerate(rows):
+        r = np.sqrt(((p64[o][None, :] - p64) ** 2).sum(axis=1))
+        F = basis_eval(f, r, r_max, r2_fp32=pair_r2_fp32(pos32[o][None, :], pos32))   # (K, N)
+        out[:, :, q] = g @ (F @ AE)
+    return out
+
+
+def relight_vjp(Cw_kept, nu, g, light, dB):
+    """Reverse mode of ``relight``: given dL/dB (E,3,N) return (dL/dg (E,3,K), dL/dl (J,)).
+
+    dL/db^w = w_1 dL/dB (w_1 is orthonormal, so the adjoint of its inverse is
+    itself), dL/dc[e,ch,k,j] = sum_w Cw[k,j,w] dL/db^w[e,ch,w],
+    dL/dg_k = sum_j l_j dL/dc_kj, dL/dl_j = sum_{e,ch,k} g_k dL/dc_kj.
+    """
+    rw = chart_to_wavelet(dB, nu)
+    dc = np.einsum("kjw,ecw->eckj", np.asarray(Cw_kept, dtype=np.float64), rw)
+    light = np.asarray(light, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    dg = dc @ light
+    dl = np.einsum("eck,eckj->j", g, dc)
+    return dg, dl
