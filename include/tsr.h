@@ -1,0 +1,217 @@
+/*
+ * tsr.h -- C ABI of the GB300 translucent subsurface-transfer library (libtsr.so).
+ *
+ * The library computes the data-parallel path of "Real-time Rendering and
+ * Editing of Scattering Effects for Translucent Objects" (Wang, Hua, Huo, Bao):
+ *
+ *   basis     f_k(r)        PCA of sampled dipole R_d            (Section 2.2, Eq. 4-5)
+ *   project   g_k(theta)    projection of R_d onto f_k            (Section 2.2; rendering Step 3)
+ *   transfer  M[k,j,o]    = sum_i A_i f_k(|x_o - x_i|) T[j,i]     (Section 3, Eq. 6-7; precompute Step 1)
+ *   compress  wavelet of M over the surface charts + keep rule   (Section 3.2, Eq. 9-10; precompute Step 2)
+ *   relight   B[e,c,o]    = W^-1 sum_kj g_k l_j M^w[k,j,.]        (Section 4, rendering Steps 3-5)
+ *   adjoint   of relight and of the projection (for fitting materials)
+ *
+ * Conventions (all calls):
+ *   - Every function is extern "C" and returns tsr_status (0 on success).  On
+ *     failure tsr_last_error() returns a message for the calling thread.
+ *   - Array arguments are DEVICE pointers owned by the caller unless stated
+ *     otherwise; the library never frees them.  Layouts are row-major with the
+ *     dimensions written in brackets, the last one contiguous.
+ *   - Opaque handles (tsr_basis, tsr_compressed) own device memory that the
+ *     library allocates at creation and frees in the matching _destroy call.
+ *   - Calls that take a tsr_stream enqueue work on that CUDA stream
+ *     (a cudaStream_t; NULL = legacy default stream) and return without
+ *     waiting, unless the comment says the call synchronises.
+ *   - Scratch memory some calls need is allocated stream-ordered
+ *     (cudaMallocAsync / cudaFreeAsync) on the caller's stream.
+ *   - Errors: TSR_ERR_INVALID_ARG for a bad size, a NULL or misaligned
+ *     pointer; TSR_ERR_UNSUPPORTED when no sm_103 device is current or a size
+ *     is beyond the compiled limits; TSR_ERR_CUDA for a CUDA runtime error;
+ *     TSR_ERR_TIMEOUT when a kernel's bounded wait gave up (the kernel then
+ *     returned early and its outputs are undefined); TSR_ERR_OOM when an
+ *     allocation failed.  There is no CPU fallback.
+ *
+ * Limits: 1 <= K <= 16 basis functions, 1 <= J <= 32 light coefficients,
+ * n_r = 16..4096 radius samples, 12 <= N vertices.  Compression and relight
+ * need the chart layout N = 10 nu^2 + 2, 1 <= nu <= 256.
+ */
+#ifndef TSR_H
+#define TSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int tsr_status;
+#define TSR_OK 0
+#define TSR_ERR_INVALID_ARG (-1)
+#define TSR_ERR_CUDA (-2)
+#define TSR_ERR_OOM (-3)
+#define TSR_ERR_TIMEOUT (-4)
+#define TSR_ERR_UNSUPPORTED (-5)
+
+/* A CUDA stream handle (binary-compatible with cudaStream_t). */
+typedef struct CUstream_st *tsr_stream;
+
+/* Arithmetic of the transfer contraction. */
+typedef enum {
+  TSR_FP32 = 0,   /* CUDA-core FP32 products, FP32 compensated accumulation        */
+  TSR_BF16 = 1,   /* tcgen05 tensor cores: BF16 f_k and T', FP32 accumulation in TMEM */
+  TSR_BF16X3 = 2  /* split BF16: hi*hi + hi*lo + lo*hi tensor-core products, FP32 accumulation */
+} tsr_precision;
+
+typedef struct tsr_basis tsr_basis;
+typedef struct tsr_compressed tsr_compressed;
+
+/* Thread-local message of the last failed call ("" if none). */
+const char *tsr_last_error(void);
+
+/* Library ABI version (major*100 + minor). */
+int tsr_version(void);
+
+/* Synchronises the stream, then reports whether any library kernel since the
+ * last check gave up a bounded wait (TSR_ERR_TIMEOUT) or flagged an
+ * out-of-range access (TSR_ERR_CUDA); also returns the stream's own CUDA
+ * error, if any.  The device status word is cleared. */
+tsr_status tsr_stream_status(tsr_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Basis (Section 2.2, Eq. 5).
+ *
+ * tsr_fit_pca_basis: samples the dipole R_d of Eq. 4 for n_mat materials
+ * (sigma_a[s], sigma_s[s] in 1/mm, common index eta) at n_r radii
+ * r_m = r_max * m / (n_r - 1) (mm), forms R[s][m], computes its singular
+ * value decomposition R = U S V^T in FP64 on the device (one-sided Jacobi) and
+ * keeps the first K right singular vectors as the radial basis f_k (each
+ * flipped so that its largest-magnitude sample is positive).
+ *   sigma_a, sigma_s : device [n_mat] FP64, > 0.  2 <= n_mat <= 1024.
+ *   eta              : 1.0 <= eta <= 2.0 (the F_dr fit of Section 2.1).
+ *   sing_vals        : device [min(n_mat, n_r)] FP64 out, descending; may be NULL.
+ *   out              : receives a new handle (destroy with tsr_basis_destroy).
+ * The call synchronises the stream (it is a one-time set-up step).
+ *
+ * tsr_basis_create: builds a handle from a caller table f[K][n_r] (FP64,
+ * HOST pointer) sampled on the same grid, e.g. a stored basis.
+ *
+ * tsr_basis_table: copies f[K][n_r] (FP64) to a device buffer.
+ * tsr_basis_info: K, n_r and r_max of a handle (host out-pointers, any may be NULL).
+ * ---------------------------------------------------------------------- */
+tsr_status tsr_fit_pca_basis(int n_mat, const double *sigma_a, const double *sigma_s, double eta,
+                             int n_r, double r_max, int K, double *sing_vals, tsr_basis **out,
+                             tsr_stream stream);
+tsr_status tsr_basis_create(int K, int n_r, double r_max, const double *f_host, tsr_basis **out);
+tsr_status tsr_basis_table(const tsr_basis *basis, double *f, tsr_stream stream);
+tsr_status tsr_basis_info(const tsr_basis *basis, int *K, int *n_r, double *r_max);
+void tsr_basis_destroy(tsr_basis *basis);
+
+/* ------------------------------------------------------------------------
+ * Material projection (Section 2.2 "projected onto the basis"; rendering
+ * Step 3):  g[e][c][k] = sum_m f_k(r_m) R_d(r_m; sigma_a[e][c], sigma_s[e][c], eta[e])
+ * in FP64, for n edits and the 3 colour channels c.
+ *   sigma_a, sigma_s : device [n][3] FP64 (1/mm, > 0);  eta: device [n] FP64 in [1, 2].
+ *   g                : device [n][3][K] FP64 out.
+ *   g32              : device [n][3][K] FP32 out (same values rounded); may be NULL.
+ *   dg               : device [n][3][K][3] FP64 out, the Jacobian
+ *                      (dg/dsigma_a, dg/dsigma_s, dg/deta) from the analytic
+ *                      derivative of Eq. 4; may be NULL.
+ *
+ * tsr_project_material_backward: vector-Jacobian product of the projection.
+ *   dLdg : device [n][3][K] FP32;  dsigma_a, dsigma_s: device [n][3] FP32 out;
+ *   deta : device [n] FP32 out.  Exactly overwrites the outputs.
+ * ---------------------------------------------------------------------- */
+tsr_status tsr_project_material(const tsr_basis *basis, int n, const double *sigma_a,
+                                const double *sigma_s, const double *eta, double *g, float *g32,
+                                double *dg, tsr_stream stream);
+tsr_status tsr_project_material_backward(const tsr_basis *basis, int n, const double *sigma_a,
+                                         const double *sigma_s, const double *eta, const float *dLdg,
+                                         float *dsigma_a, float *dsigma_s, float *deta,
+                                         tsr_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Transfer (Section 3, Eq. 6-7; precompute Step 1):
+ *   M[k][j][o] = sum_{i<N} A_i f_k(|x_o - x_i|) T[j][i]
+ * with f_k piecewise linear on the basis grid and zero where the FP32
+ * squared distance fl(fl(fl(dx^2)+fl(dy^2))+fl(dz^2)) exceeds r_max^2
+ * (dx = fl(x_o - x_i)); the self pair i = o is included.
+ *   pos  : device [3][N] FP32 (x, then y, then z; mm), 16-byte aligned.
+ *   area : device [N] FP32 (mm^2).
+ *   T    : device [J][N] FP32.
+ *   M    : device [K][J][N] FP32 out (overwritten).
+ *   prec : TSR_FP32, TSR_BF16 or TSR_BF16X3.
+ * Scratch: a pre-tiled copy of (x_i, A_i T[.,i]), about N*(2*J_pad*2+12) bytes.
+ * ---------------------------------------------------------------------- */
+tsr_status tsr_precompute_transfer(const tsr_basis *basis, int N, const float *pos, const float *area,
+                                   const float *T, int J, tsr_precision prec, float *M,
+                                   tsr_stream stream);
+
+/* Batched transfer over n_mesh independent meshes of uneven size in one
+ * persistent launch.  All arrays are concatenated over the meshes:
+ *   offsets : HOST [n_mesh + 1] int64 vertex offsets (offsets[0] = 0).
+ *   pos     : device [3][total] FP32;  area: device [total];  T: device [J][total];
+ *   M       : device [K][J][total] FP32 out.  Only TSR_BF16 and TSR_FP32.  */
+tsr_status tsr_precompute_transfer_batched(const tsr_basis *basis, int n_mesh, const int64_t *offsets,
+                                           const float *pos, const float *area, const float *T, int J,
+                                           tsr_precision prec, float *M, tsr_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Spatial wavelet (Section 3.2, Eq. 9-10).  Vertex data of the chart mesh
+ * (N = 10 nu^2 + 2; chart d row r col c has id d nu^2 + r nu + c, poles last)
+ * is put in Morton order per chart, zero-padded to P x P (P = 2^ceil(log2 nu)),
+ * and transformed by the orthonormal 1D Haar (output order: scaling, then
+ * details coarse to fine).  The wavelet layout is [10 P^2 + 2]: chart d at
+ * [d P^2, (d+1) P^2), the two pole values last (passed through).
+ *
+ * tsr_haar_forward:  X [rows][N] FP32 -> Xw [rows][10 P^2 + 2] FP32.
+ * tsr_haar_inverse:  Xw [rows][10 P^2 + 2] -> X [rows][N] (padding dropped).
+ * ---------------------------------------------------------------------- */
+tsr_status tsr_haar_forward(const float *X, int rows, int nu, float *Xw, tsr_stream stream);
+tsr_status tsr_haar_inverse(const float *Xw, int rows, int nu, float *X, tsr_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Compression (precompute Step 2, Section 3.2).
+ * tsr_wavelet_compress: from wavelet coefficients Mw [K][J][10 P^2 + 2] keeps,
+ * per (k, j), the n_keep = floor(p * 10 P^2 + 0.5) (clamped to [1, 10 P^2])
+ * chart coefficients of largest |value| (ties: lower index) plus both poles,
+ * and packs them as a CSR matrix over wavelet rows w (entries: column
+ * kj = k*J + j as uint16, value FP32, columns ascending within a row).
+ * tsr_haar_compress = tsr_haar_forward of M followed by tsr_wavelet_compress.
+ * Both synchronise the stream once (to size the packed arrays).
+ * ---------------------------------------------------------------------- */
+tsr_status tsr_wavelet_compress(const float *Mw, int K, int J, int nu, double p, tsr_compressed **out,
+                                tsr_stream stream);
+tsr_status tsr_haar_compress(const float *M, int K, int J, int nu, double p, tsr_compressed **out,
+                             tsr_stream stream);
+/* Sizes of a compressed transfer (host out-pointers, any may be NULL). */
+tsr_status tsr_compressed_info(const tsr_compressed *c, int *K, int *J, int *nu, int64_t *nnz,
+                               int *n_rows);
+/* Copies the CSR arrays to caller device buffers: row_ptr [n_rows+1] int64,
+ * col [nnz] uint16, val [nnz] FP32. */
+tsr_status tsr_compressed_export(const tsr_compressed *c, int64_t *row_ptr, uint16_t *col, float *val,
+                                 tsr_stream stream);
+void tsr_compressed_destroy(tsr_compressed *c);
+
+/* ------------------------------------------------------------------------
+ * Relight / material edit (Section 4, rendering Steps 3-5):
+ *   b^w[e][c][w] = sum_{(kj,v) in row w} v * g[e][c][k] * l[j]
+ *   B[e][c][.]   = W^-1 b^w[e][c][.]         (inverse Haar per chart)
+ *   g : device [n_edit][3][K] FP32;  l: device [J] FP32;
+ *   B : device [n_edit][3][N] FP32 out.
+ * Scratch: b^w, n_edit*3*(10 P^2 + 2) FP32.
+ *
+ * tsr_relight_backward: reverse mode for an upstream gradient dLdB
+ * [n_edit][3][N]: r^w = W dLdB (forward Haar), dc = S^T r^w,
+ *   dg[e][c][k] = sum_j l_j dc[e][c][kj],   dl[j] = sum_{e,c,k} g[e][c][k] dc[e][c][kj].
+ *   dg : device [n_edit][3][K] FP32 out;  dl: device [J] FP32 out (overwritten).
+ * ---------------------------------------------------------------------- */
+tsr_status tsr_relight(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,
+                       tsr_stream stream);
+tsr_status tsr_relight_backward(const tsr_compressed *c, int n_edit, const float *g, const float *l,
+                                const float *dLdB, float *dg, float *dl, tsr_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSR_H */

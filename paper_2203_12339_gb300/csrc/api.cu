@@ -1,0 +1,167 @@
+// extern "C" entry points of libtsr: argument validation and dispatch.
+#include <algorithm>
+#include <vector>
+
+#include "handles.cuh"
+
+using namespace tsr;
+
+namespace {
+cudaStream_t as_stream(tsr_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+bool chart_mesh(int N, int nu) { return nu >= 1 && N == 10 * nu * nu + 2; }
+}  // namespace
+
+extern "C" const char *tsr_last_error(void) { return error_string(); }
+
+extern "C" int tsr_version(void) { return 100; }
+
+extern "C" tsr_status tsr_stream_status(tsr_stream stream) {
+  clear_error();
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  TSR_CUDA(cudaStreamSynchronize(as_stream(stream)));
+  return check_device_status(as_stream(stream));
+}
+
+extern "C" tsr_status tsr_precompute_transfer(const tsr_basis *basis, int N, const float *pos, const float *area,
+                                              const float *T, int J, tsr_precision prec, float *M,
+                                              tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(basis && pos && area && T && M, "tsr_precompute_transfer: NULL argument");
+  TSR_CHECK_ARG(N >= 12 && N <= (1 << 24), "tsr_precompute_transfer: N=%d outside [12, 2^24]", N);
+  TSR_CHECK_ARG(J >= 1 && J <= 32, "tsr_precompute_transfer: J=%d outside [1, 32]", J);
+  TSR_CHECK_ARG(aligned(pos, 16) && aligned(area, 4) && aligned(T, 4) && aligned(M, 4),
+                "tsr_precompute_transfer: misaligned pointer");
+  TSR_CHECK_ARG((size_t)basis->K * J * (size_t)N < ((size_t)1 << 40), "tsr_precompute_transfer: output too large");
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  switch (prec) {
+    case TSR_FP32:
+      return transfer_fp32(basis, N, pos, area, T, J, M, as_stream(stream));
+    case TSR_BF16:
+      return transfer_tc(basis, N, pos, area, T, J, false, M, as_stream(stream));
+    case TSR_BF16X3:
+      return transfer_tc(basis, N, pos, area, T, J, true, M, as_stream(stream));
+    default:
+      set_error("tsr_precompute_transfer: unknown precision %d", (int)prec);
+      return TSR_ERR_UNSUPPORTED;
+  }
+}
+
+extern "C" tsr_status tsr_precompute_transfer_batched(const tsr_basis *basis, int n_mesh, const int64_t *offsets,
+                                                      const float *pos, const float *area, const float *T, int J,
+                                                      tsr_precision prec, float *M, tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(basis && offsets && pos && area && T && M, "tsr_precompute_transfer_batched: NULL argument");
+  TSR_CHECK_ARG(n_mesh >= 1 && n_mesh <= 65536, "tsr_precompute_transfer_batched: n_mesh=%d out of range", n_mesh);
+  TSR_CHECK_ARG(J >= 1 && J <= 32, "tsr_precompute_transfer_batched: J=%d outside [1, 32]", J);
+  TSR_CHECK_ARG(offsets[0] == 0, "tsr_precompute_transfer_batched: offsets[0] must be 0");
+  for (int b = 0; b < n_mesh; ++b)
+    TSR_CHECK_ARG(offsets[b + 1] - offsets[b] >= 12 && offsets[b + 1] - offsets[b] <= (1 << 24),
+                  "tsr_precompute_transfer_batched: mesh %d has %lld vertices", b,
+                  (long long)(offsets[b + 1] - offsets[b]));
+  TSR_CHECK_ARG(aligned(pos, 16), "tsr_precompute_transfer_batched: misaligned pos");
+  TSR_CHECK_ARG(prec == TSR_BF16 || prec == TSR_FP32, "tsr_precompute_transfer_batched: precision %d unsupported",
+                (int)prec);
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  if (prec == TSR_BF16) return transfer_tc_batched(basis, n_mesh, offsets, pos, area, T, J, M, as_stream(stream));
+  return transfer_fp32_batched(basis, n_mesh, offsets, pos, area, T, J, M, as_stream(stream));
+}
+
+extern "C" tsr_status tsr_haar_forward(const float *X, int rows, int nu, float *Xw, tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(X && Xw, "tsr_haar_forward: NULL argument");
+  TSR_CHECK_ARG(rows >= 0 && rows <= (1 << 20), "tsr_haar_forward: rows=%d out of range", rows);
+  TSR_CHECK_ARG(nu >= 1 && nu <= 128, "tsr_haar_forward: nu=%d outside [1, 128]", nu);
+  tsr_status st = require_device();
+  if (st != TSR_OK || rows == 0) return st;
+  return haar_forward(X, rows, nu, Xw, as_stream(stream));
+}
+
+extern "C" tsr_status tsr_haar_inverse(const float *Xw, int rows, int nu, float *X, tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(X && Xw, "tsr_haar_inverse: NULL argument");
+  TSR_CHECK_ARG(rows >= 0 && rows <= (1 << 20), "tsr_haar_inverse: rows=%d out of range", rows);
+  TSR_CHECK_ARG(nu >= 1 && nu <= 128, "tsr_haar_inverse: nu=%d outside [1, 128]", nu);
+  tsr_status st = require_device();
+  if (st != TSR_OK || rows == 0) return st;
+  return haar_inverse(Xw, rows, nu, X, as_stream(stream));
+}
+
+extern "C" tsr_status tsr_wavelet_compress(const float *Mw, int K, int J, int nu, double p, tsr_compressed **out,
+                                           tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(Mw && out, "tsr_wavelet_compress: NULL argument");
+  TSR_CHECK_ARG(K >= 1 && K <= 16 && J >= 1 && J <= 32, "tsr_wavelet_compress: K=%d J=%d out of range", K, J);
+  TSR_CHECK_ARG(nu >= 1 && nu <= 128, "tsr_wavelet_compress: nu=%d outside [1, 128]", nu);
+  TSR_CHECK_ARG(p >= 0.0 && p <= 1.0, "tsr_wavelet_compress: p=%g outside [0, 1]", p);
+  *out = nullptr;
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  return wavelet_compress(Mw, K, J, nu, p, out, as_stream(stream));
+}
+
+extern "C" tsr_status tsr_haar_compress(const float *M, int K, int J, int nu, double p, tsr_compressed **out,
+                                        tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(M && out, "tsr_haar_compress: NULL argument");
+  TSR_CHECK_ARG(K >= 1 && K <= 16 && J >= 1 && J <= 32, "tsr_haar_compress: K=%d J=%d out of range", K, J);
+  TSR_CHECK_ARG(nu >= 1 && nu <= 128, "tsr_haar_compress: nu=%d outside [1, 128]", nu);
+  TSR_CHECK_ARG(p >= 0.0 && p <= 1.0, "tsr_haar_compress: p=%g outside [0, 1]", p);
+  *out = nullptr;
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  const int P = chart_side(nu);
+  Scratch mw;
+  st = mw.alloc(sizeof(float) * (size_t)K * J * (10 * P * P + 2), s);
+  if (st != TSR_OK) return st;
+  st = haar_forward(M, K * J, nu, static_cast<float *>(mw.p), s);
+  if (st != TSR_OK) return st;
+  return wavelet_compress(static_cast<float *>(mw.p), K, J, nu, p, out, s);
+}
+
+extern "C" tsr_status tsr_compressed_info(const tsr_compressed *c, int *K, int *J, int *nu, int64_t *nnz,
+                                          int *n_rows) {
+  clear_error();
+  TSR_CHECK_ARG(c, "tsr_compressed_info: NULL handle");
+  if (K) *K = c->K;
+  if (J) *J = c->J;
+  if (nu) *nu = c->nu;
+  if (nnz) *nnz = c->nnz;
+  if (n_rows) *n_rows = c->n_rows;
+  return TSR_OK;
+}
+
+extern "C" tsr_status tsr_compressed_export(const tsr_compressed *c, int64_t *row_ptr, uint16_t *col, float *val,
+                                            tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(c && row_ptr && col && val, "tsr_compressed_export: NULL argument");
+  cudaStream_t s = as_stream(stream);
+  TSR_CUDA(cudaMemcpyAsync(row_ptr, c->row_ptr, sizeof(int64_t) * (c->n_rows + 1), cudaMemcpyDeviceToDevice, s));
+  TSR_CUDA(cudaMemcpyAsync(col, c->col, sizeof(uint16_t) * c->nnz, cudaMemcpyDeviceToDevice, s));
+  TSR_CUDA(cudaMemcpyAsync(val, c->val, sizeof(float) * c->nnz, cudaMemcpyDeviceToDevice, s));
+  return TSR_OK;
+}
+
+extern "C" tsr_status tsr_relight(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,
+                                  tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(c && g && l && B, "tsr_relight: NULL argument");
+  TSR_CHECK_ARG(n_edit >= 0 && n_edit <= (1 << 20), "tsr_relight: n_edit=%d out of range", n_edit);
+  TSR_CHECK_ARG(aligned(g, 4) && aligned(l, 4) && aligned(B, 4), "tsr_relight: misaligned pointer");
+  tsr_status st = require_device();
+  if (st != TSR_OK || n_edit == 0) return st;
+  return relight(c, n_edit, g, l, B, as_stream(stream));
+}
+
+extern "C" tsr_status tsr_relight_backward(const tsr_compressed *c, int n_edit, const float *g, const float *l,
+                                           const float *dLdB, float *dg, float *dl, tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(c && g && l && dLdB && dg && dl, "tsr_relight_backward: NULL argument");
+  TSR_CHECK_ARG(n_edit >= 1 && n_edit <= (1 << 20), "tsr_relight_backward: n_edit=%d out of range", n_edit);
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  return relight_backward(c, n_edit, g, l, dLdB, dg, dl, as_stream(stream));
+}

@@ -1,0 +1,95 @@
+// Per-thread error strings, device checks and the device status word.
+#include <cstdarg>
+#include <mutex>
+#include <map>
+
+#include "tsr_internal.cuh"
+
+namespace tsr {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+void clear_error() { g_err[0] = '\0'; }
+
+const char *error_string() { return g_err; }
+
+static std::mutex g_mu;
+static std::map<int, unsigned *> g_status;   // device -> status word
+static std::map<int, int> g_sms;
+
+tsr_status require_device() {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    set_error("no CUDA device: %s", cudaGetErrorString(e));
+    return TSR_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_sms.count(dev)) return TSR_OK;
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) {
+    set_error("cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+    return TSR_ERR_CUDA;
+  }
+  if (!(prop.major == 10 && prop.minor == 3)) {
+    set_error("libtsr is built for sm_103a only; device %d is sm_%d%d (%s)", dev, prop.major, prop.minor,
+              prop.name);
+    return TSR_ERR_UNSUPPORTED;
+  }
+  g_sms[dev] = prop.multiProcessorCount;
+  return TSR_OK;
+}
+
+int num_sms() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_sms.find(dev);
+  return it == g_sms.end() ? 148 : it->second;
+}
+
+unsigned *device_status_ptr() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_status.find(dev);
+  if (it != g_status.end()) return it->second;
+  unsigned *p = nullptr;
+  if (cudaMalloc(&p, sizeof(unsigned)) != cudaSuccess) return nullptr;
+  cudaMemset(p, 0, sizeof(unsigned));
+  cudaDeviceSynchronize();
+  g_status[dev] = p;
+  return p;
+}
+
+tsr_status check_device_status(cudaStream_t s) {
+  unsigned *p = device_status_ptr();
+  if (!p) {
+    set_error("device status word unavailable");
+    return TSR_ERR_CUDA;
+  }
+  unsigned h = 0;
+  TSR_CUDA(cudaMemcpyAsync(&h, p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  TSR_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    TSR_CUDA(cudaMemsetAsync(p, 0, sizeof(unsigned), s));
+    TSR_CUDA(cudaStreamSynchronize(s));
+    if (h & DEV_ERR_TIMEOUT) {
+      set_error("a kernel's bounded wait ran out (status 0x%x); outputs are undefined", h);
+      return TSR_ERR_TIMEOUT;
+    }
+    set_error("a kernel reported an out-of-range access (status 0x%x)", h);
+    return TSR_ERR_CUDA;
+  }
+  return TSR_OK;
+}
+
+}  // namespace tsr

@@ -1,0 +1,45 @@
+// Library-owned objects behind the opaque handles of tsr.h.
+#pragma once
+#include "tsr_internal.cuh"
+
+// Radial basis f_k on the grid r_m = r_max m / (n_r - 1) plus the lookup tables
+// the transfer kernels read.  Row n_r of each table is all zero: kernels send
+// pairs beyond the cutoff there instead of branching.
+struct tsr_basis {
+  int device = -1;
+  int K = 0, n_r = 0, KP = 0;   // KP: K rounded up to a multiple of 4
+  double r_max = 0.0;
+  double *f64 = nullptr;        // [K][n_r]
+  float2 *tab32 = nullptr;      // [n_r + 1][KP]  {f_k(r_m), f_k(r_m+1) - f_k(r_m)}
+  uint32_t *tab16 = nullptr;    // [n_r + 1][KP]  bf16x2 {lo: value, hi: slope}
+};
+
+// Compressed wavelet transfer: CSR over wavelet rows w in [0, 10 P^2 + 2).
+struct tsr_compressed {
+  int device = -1;
+  int K = 0, J = 0, nu = 0, P = 0, n_rows = 0, n_keep = 0;
+  int64_t nnz = 0;
+  int64_t *row_ptr = nullptr;   // [n_rows + 1]
+  uint16_t *col = nullptr;      // [nnz]  k*J + j
+  float *val = nullptr;         // [nnz]
+};
+
+namespace tsr {
+tsr_status basis_build_tables(tsr_basis *b, cudaStream_t s);
+tsr_status transfer_fp32(const tsr_basis *b, int N, const float *pos, const float *area, const float *T,
+                         int J, float *M, cudaStream_t s);
+tsr_status transfer_tc(const tsr_basis *b, int N, const float *pos, const float *area, const float *T,
+                       int J, bool split, float *M, cudaStream_t s);
+tsr_status transfer_tc_batched(const tsr_basis *b, int n_mesh, const int64_t *offsets, const float *pos,
+                               const float *area, const float *T, int J, float *M, cudaStream_t s);
+tsr_status transfer_fp32_batched(const tsr_basis *b, int n_mesh, const int64_t *offsets, const float *pos,
+                                 const float *area, const float *T, int J, float *M, cudaStream_t s);
+tsr_status haar_forward(const float *X, int rows, int nu, float *Xw, cudaStream_t s);
+tsr_status haar_inverse(const float *Xw, int rows, int nu, float *X, cudaStream_t s);
+tsr_status wavelet_compress(const float *Mw, int K, int J, int nu, double p, tsr_compressed **out,
+                            cudaStream_t s);
+tsr_status relight(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,
+                   cudaStream_t s);
+tsr_status relight_backward(const tsr_compressed *c, int n_edit, const float *g, const float *l,
+                            const float *dLdB, float *dg, float *dl, cudaStream_t s);
+}  // namespace tsr

@@ -1,0 +1,690 @@
+// Section 3, Eq. 6-7 (precompute Step 1): the transfer
+//     M[k][j][o] = sum_i A_i f_k(|x_o - x_i|) T[j][i]
+// generated and contracted on the fly, so the N x N kernel matrix never
+// reaches HBM.
+//
+//  * transfer_fp32: CUDA-core FP32 path.  A block owns 32 output rows; each
+//    thread owns one row o and two bases, evaluates f_k(r) from the table and
+//    accumulates all J products per pair, with the partial sum of each 64-i
+//    tile added into a Kahan-compensated total.
+//  * transfer_tc:   tensor-core path (tcgen05).  A block owns 128 output rows
+//    (the UMMA M = 128) and a group of KB bases.  Per 16-i step, 256 threads
+//    evaluate F_k[o, i] = f_k(r_oi) (BF16, or hi/lo BF16 for the split
+//    variant) into shared memory in the canonical K-major layout, while the
+//    Tensor Memory Accelerator streams the matching tile of
+//    T'[j][i] = A_i T[j][i] (pre-tiled BF16 records that also carry the x_i).
+//    One thread issues tcgen05.mma with FP32 accumulators for all KB bases in
+//    tensor memory (KB x J_pad columns); the epilogue reads TMEM back with
+//    tcgen05.ld and writes M.
+//
+// Pair geometry (both paths): dx = fl(x_o - x_i) etc. and
+// r2 = fl(fl(fl(dx^2) + fl(dy^2)) + fl(dz^2)) without contraction; pairs with
+// r2 > fl(r_max^2) are cut off (f_k = 0).  Otherwise r = sqrt(r2),
+// x = r / dr, m = min(floor(x), n_r - 2), t = x - m and
+// f_k(r) = v_k[m] + t s_k[m] (s_k = f_k[m+1] - f_k[m]).
+#include <algorithm>
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <mutex>
+#include <vector>
+
+#include "handles.cuh"
+
+namespace tsr {
+
+__device__ __forceinline__ float pair_r2(float xo, float yo, float zo, float xi, float yi, float zi) {
+  const float dx = __fsub_rn(xo, xi), dy = __fsub_rn(yo, yi), dz = __fsub_rn(zo, zi);
+  return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
+// ============================================================================ FP32 SIMT
+constexpr int F32_BO = 32;   // output rows per block
+constexpr int F32_BI = 64;   // i per shared-memory tile
+
+// T'[i][jp] = A_i T[j][i] (FP32, zero for j >= J or i >= N), rows padded to a multiple of F32_BI.
+__global__ void pretile_fp32_kernel(const float *__restrict__ area, const float *__restrict__ T, int N, int J,
+                                    int JP, int n_pad, float *__restrict__ Tp) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_pad * JP) return;
+  const int i = idx / JP, j = idx % JP;
+  Tp[idx] = (i < N && j < J) ? area[i] * T[(size_t)j * N + i] : 0.0f;
+}
+
+template <int JP>
+__global__ void __launch_bounds__(256, 1)
+    transfer_fp32_kernel(const float *__restrict__ pos, int N, const float *__restrict__ Tp,
+                         const float4 *__restrict__ tab, int KG, int n_r, float inv_dr, float r2max, int K,
+                         int J, float *__restrict__ M, int n_tiles) {
+  __shared__ __align__(16) float sT[F32_BI * JP];
+  __shared__ float sx[F32_BI], sy[F32_BI], sz[F32_BI];
+  const int kg = threadIdx.x % KG;
+  const int ol = threadIdx.x / KG;
+  const float *px = pos, *py = pos + N, *pz = pos + 2 * (size_t)N;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int o = tile * F32_BO + ol;
+    const bool o_ok = o < N;
+    const float xo = o_ok ? px[o] : 0.0f, yo = o_ok ? py[o] : 0.0f, zo = o_ok ? pz[o] : 0.0f;
+    float acc0[JP], acc1[JP], c0[JP], c1[JP];
+#pragma unroll
+    for (int j = 0; j < JP; ++j) acc0[j] = acc1[j] = c0[j] = c1[j] = 0.0f;
+    for (int i0 = 0; i0 < N; i0 += F32_BI) {
+      __syncthreads();
+      const float4 *src = reinterpret_cast<const float4 *>(Tp + (size_t)i0 * JP);
+      for (int q = threadIdx.x; q < F32_BI * JP / 4; q += blockDim.x) reinterpret_cast<float4 *>(sT)[q] = src[q];
+      for (int q = threadIdx.x; q < F32_BI; q += blockDim.x) {
+        const int i = i0 + q;
+        sx[q] = i < N ? px[i] : 0.0f;
+        sy[q] = i < N ? py[i] : 0.0f;
+        sz[q] = i < N ? pz[i] : 0.0f;
+      }
+      __syncthreads();
+      float p0[JP], p1[JP];
+#pragma unroll
+      for (int j = 0; j < JP; ++j) p0[j] = p1[j] = 0.0f;
+#pragma unroll 2
+      for (int ii = 0; ii < F32_BI; ++ii) {
+        const float r2 = pair_r2(xo, yo, zo, sx[ii], sy[ii], sz[ii]);
+        const float x = __fsqrt_rn(r2) * inv_dr;
+        const int m = max(0, min(static_cast<int>(x), n_r - 2));
+        const float t = x - static_cast<float>(m);
+        const int row = (r2 <= r2max) ? m : n_r;
+        const float4 tb = __ldg(tab + (size_t)row * KG + kg);
+        const float F0 = fmaf(t, tb.y, tb.x), F1 = fmaf(t, tb.w, tb.z);
+        const float *tv = sT + ii * JP;
+#pragma unroll
+        for (int j = 0; j < JP; ++j) {
+          p0[j] = fmaf(F0, tv[j], p0[j]);
+          p1[j] = fmaf(F1, tv[j], p1[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < JP; ++j) {   // Kahan: total += tile partial
+        float y = p0[j] - c0[j];
+        float s = acc0[j] + y;
+        c0[j] = (s - acc0[j]) - y;
+        acc0[j] = s;
+        y = p1[j] - c1[j];
+        s = acc1[j] + y;
+        c1[j] = (s - acc1[j]) - y;
+        acc1[j] = s;
+      }
+    }
+    if (o_ok) {
+      const int k0 = 2 * kg, k1 = 2 * kg + 1;
+#pragma unroll
+      for (int j = 0; j < JP; ++j) {
+        if (j < J) {
+          if (k0 < K) M[((size_t)k0 * J + j) * N + o] = acc0[j];
+          if (k1 < K) M[((size_t)k1 * J + j) * N + o] = acc1[j];
+        }
+      }
+    }
+  }
+}
+
+template <int JP>
+static cudaError_t launch_fp32(int grid, int threads, cudaStream_t s, const float *pos, int N, const float *Tp,
+                               const float4 *tab, int KG, int n_r, float inv_dr, float r2max, int K, int J,
+                               float *M, int n_tiles) {
+  transfer_fp32_kernel<JP><<<grid, threads, 0, s>>>(pos, N, Tp, tab, KG, n_r, inv_dr, r2max, K, J, M, n_tiles);
+  return cudaGetLastError();
+}
+
+tsr_status transfer_fp32(const tsr_basis *b, int N, const float *pos, const float *area, const float *T, int J,
+                         float *M, cudaStream_t s) {
+  const int JP = (J + 3) & ~3;
+  const int n_pad = (N + F32_BI - 1) / F32_BI * F32_BI;
+  Scratch tp;
+  tsr_status st = tp.alloc(sizeof(float) * (size_t)n_pad * JP, s);
+  if (st != TSR_OK) return st;
+  float *Tp = static_cast<float *>(tp.p);
+  pretile_fp32_kernel<<<(n_pad * JP + 255) / 256, 256, 0, s>>>(area, T, N, J, JP, n_pad, Tp);
+  TSR_CUDA(cudaGetLastError());
+  const int KG = b->KP / 2;
+  const int threads = F32_BO * KG;
+  const int n_tiles = (N + F32_BO - 1) / F32_BO;
+  const int grid = std::min(n_tiles, num_sms());
+  const float inv_dr = static_cast<float>((b->n_r - 1) / b->r_max);
+  const float r2max = static_cast<float>(b->r_max * b->r_max);
+  const float4 *tab = reinterpret_cast<const float4 *>(b->tab32);
+  cudaError_t e;
+  switch (JP) {
+#define F32_CASE(JPV) \
+  case JPV: e = launch_fp32<JPV>(grid, threads, s, pos, N, Tp, tab, KG, b->n_r, inv_dr, r2max, b->K, J, M, n_tiles); break;
+    F32_CASE(4) F32_CASE(8) F32_CASE(12) F32_CASE(16) F32_CASE(20) F32_CASE(24) F32_CASE(28) F32_CASE(32)
+#undef F32_CASE
+    default:
+      set_error("transfer_fp32: J=%d unsupported", J);
+      return TSR_ERR_UNSUPPORTED;
+  }
+  TSR_CUDA(e);
+  return TSR_OK;
+}
+
+// ============================================================================ tcgen05 path
+// Record of one 16-i step in global memory (and, after TMA, in shared memory):
+//   [0, JP*32)            T'_hi tile, canonical K-major no-swizzle layout:
+//                         core matrix (h = i/8, jg = j/8) at h*JP*16 + jg*128,
+//                         row j%8 at +16*(j%8), element i%8 at +2*(i%8)
+//   [JP*32, 2*JP*32)      T'_lo tile (split variant only)
+//   next 192 bytes        x[16], y[16], z[16] (FP32) of the 16 i
+//   padded to a multiple of 128 bytes (the TMA box row).
+__host__ __device__ constexpr int rec_bytes(int JP, bool split) {
+  return ((JP * 32 * (split ? 2 : 1) + 192) + 127) / 128 * 128;
+}
+
+__global__ void pretile_tc_kernel(const float *__restrict__ pos, const float *__restrict__ area,
+                                  const float *__restrict__ T, int N, int J, int JP, int split, int REC,
+                                  int n_steps, uint8_t *__restrict__ rec) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;   // (step, ii)
+  if (idx >= n_steps * 16) return;
+  const int step = idx / 16, ii = idx % 16;
+  const int i = step * 16 + ii;
+  const bool ok = i < N;
+  uint8_t *r = rec + (size_t)step * REC;
+  const float a = ok ? area[i] : 0.0f;
+  const int h = ii / 8, e = ii % 8;
+  for (int j = 0; j < JP; ++j) {
+    const float v = (ok && j < J) ? a * T[(size_t)j * N + i] : 0.0f;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const size_t off = (size_t)h * JP * 16 + (size_t)j * 16 + e * 2;
+    *reinterpret_cast<__nv_bfloat16 *>(r + off) = hi;
+    if (split) {
+      const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+      *reinterpret_cast<__nv_bfloat16 *>(r + JP * 32 + off) = lo;
+    }
+  }
+  float *p = reinterpret_cast<float *>(r + JP * 32 * (split ? 2 : 1));
+  p[ii] = ok ? pos[i] : 0.0f;
+  p[16 + ii] = ok ? pos[N + i] : 0.0f;
+  p[32 + ii] = ok ? pos[2 * (size_t)N + i] : 0.0f;
+}
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;   // descriptor version (sm_100 family)
+  return d;                 // base offset 0, layout SWIZZLE_NONE
+}
+
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int N) {
+  return (1u << 4)                       // D: F32
+         | (1u << 7)                     // A: BF16
+         | (1u << 10)                    // B: BF16
+         | ((uint32_t)(N >> 3) << 17)    // N
+         | ((uint32_t)(128 >> 4) << 24); // M = 128; A, B K-major
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t bf16x2_fma(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+
+// ---------------------------------------------------------------- the kernel
+struct TcArgs {
+  int N;             // vertices (rows o and columns i)
+  int n_steps;       // 16-i steps (records), a multiple of KS
+  int n_r;           // radius samples
+  float inv_dr, r2max;
+  int K, J;
+  int n_otiles, n_kgroups, n_items;
+  const float *pos;  // [3][N] (rows o)
+  const uint32_t *tab16;   // [n_r + 1][KP] bf16x2
+  const float2 *tab32;     // [n_r + 1][KP]
+  int KP;
+  float *M;          // [K][J][N]
+  unsigned *status;
+};
+
+template <int KB, int JP, bool SPLIT, int NS, int KS>
+struct TcCfg {
+  static constexpr int NR = NS + 2;                        // record stages (TMA runs 2 stages ahead)
+  static constexpr int LOOKAHEAD = 2;
+  static constexpr int REC = rec_bytes(JP, SPLIT);
+  static constexpr int A_TILE = 128 * 16 * 2;              // one (base, 16-i step) BF16 tile
+  static constexpr int A_STAGE = KS * KB * (SPLIT ? 2 : 1) * A_TILE;
+  static constexpr int REC_STAGE = KS * REC;
+  static constexpr int TAB_ELEM = SPLIT ? 8 : 4;
+  static constexpr int TMEM_COLS = (KB * JP <= 32) ? 32 : (KB * JP <= 64) ? 64 : (KB * JP <= 128) ? 128
+                                 : (KB * JP <= 256) ? 256 : 512;
+  static size_t smem_bytes(int n_r) {
+    return 1024 + (size_t)NS * A_STAGE + (size_t)NR * REC_STAGE + (size_t)(n_r + 1) * KB * TAB_ELEM + 256;
+  }
+};
+
+template <int KB, int JP, bool SPLIT, int NS, int KS>
+__global__ void __launch_bounds__(256, 1)
+    transfer_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs args) {
+  using C = TcCfg<KB, JP, SPLIT, NS, KS>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *sA = smem;                                   // NS * A_STAGE
+  uint8_t *sRec = sA + (size_t)NS * C::A_STAGE;         // NR * REC_STAGE
+  uint8_t *sTab = sRec + (size_t)C::NR * C::REC_STAGE;  // (n_r+1) * KB * TAB_ELEM
+  uint64_t *bar = reinterpret_cast<uint64_t *>(sTab + (size_t)(args.n_r + 1) * KB * C::TAB_ELEM);
+  uint64_t *bar_tma = bar;            // [NR]
+  uint64_t *bar_mma = bar + C::NR;    // [NS]
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + C::NR + NS);
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int q = 0; q < C::NR; ++q) mbar_init(&bar_tma[q], 1);
+    for (int q = 0; q < NS; ++q) mbar_init(&bar_mma[q], 1);
+    fence_mbar_init();
+    fence_proxy_async_smem();
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                 "r"((uint32_t)C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_holder;
+
+  // work of this CTA: items blockIdx.x, blockIdx.x + gridDim.x, ...
+  const int stages_per_item = args.n_steps / KS;
+  int my_items = 0;
+  for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) ++my_items;
+  const long total_stages = (long)my_items * stages_per_item;
+  const uint32_t idesc = umma_idesc_bf16(JP);
+  const int rows_per_stage = C::REC_STAGE / 128;
+
+  auto issue_tma = [&](long g) {   // stage g of this CTA's stream -> record slot g % NR
+    const int slot = (int)(g % C::NR);
+    const int stage_in_item = (int)(g % stages_per_item);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bar_tma[slot], C::REC_STAGE);
+    tma_load_2d(sRec + (size_t)slot * C::REC_STAGE, &tmap, &bar_tma[slot], 0, stage_in_item * rows_per_stage);
+  };
+  if (tid == 0) {
+    for (long g = 0; g < C::LOOKAHEAD && g < total_stages; ++g) issue_tma(g);
+  }
+
+  const int orow = tid & 127;   // output row within the tile (TMEM lane / A row)
+  const int half = tid >> 7;    // which 8 of the 16 i of a step
+  const uint32_t a_row_off = (uint32_t)((orow >> 3) * 256 + half * 128 + (orow & 7) * 16);
+  const uint32_t sA_u32 = smem_u32(sA);
+  long g = 0;              // stage counter of this CTA
+  long tma_issued = C::LOOKAHEAD < total_stages ? C::LOOKAHEAD : total_stages;
+  long tma_consumed = 0;   // stages whose records were waited for (thread 0's view)
+  long mma_issued = 0;     // stages whose MMAs were committed (thread 0's view)
+  int cur_kgroup = -1;
+  bool ok = true;
+
+  for (int item = blockIdx.x; item < args.n_items && ok; item += gridDim.x) {
+    const int kgroup = item / args.n_otiles;
+    const int otile = item % args.n_otiles;
+    const int k0 = kgroup * KB;
+    if (kgroup != cur_kgroup) {   // load this group's table slice (zero beyond K)
+      __syncthreads();
+      const int n_ent = (args.n_r + 1) * KB;
+      for (int q = tid; q < n_ent; q += blockDim.x) {
+        const int m = q / KB, kb = q % KB, k = k0 + kb;
+        if (SPLIT) {
+          float2 v = make_float2(0.f, 0.f);
+          if (k < args.K) v = args.tab32[(size_t)m * args.KP + k];
+          reinterpret_cast<float2 *>(sTab)[q] = v;
+        } else {
+          uint32_t v = 0;
+          if (k < args.K) v = args.tab16[(size_t)m * args.KP + k];
+          reinterpret_cast<uint32_t *>(sTab)[q] = v;
+        }
+      }
+      __syncthreads();
+      cur_kgroup = kgroup;
+    }
+    const int o = otile * 128 + orow;
+    const float xo = o < args.N ? args.pos[o] : 0.f;
+    const float yo = o < args.N ? args.pos[args.N + o] : 0.f;
+    const float zo = o < args.N ? args.pos[2 * (size_t)args.N + o] : 0.f;
+
+    for (int sidx = 0; sidx < stages_per_item; ++sidx, ++g) {
+      const int sa = (int)(g % NS);
+      const int sr = (int)(g % C::NR);
+      // (1) A buffer sa is free once the MMAs of stage g - NS completed
+      int fail = 0;
+      if (g >= NS) {
+        if (!mbar_wait(&bar_mma[sa], (uint32_t)(((g / NS) - 1) & 1))) fail = 1;
+      }
+      // (2) keep the TMA stream LOOKAHEAD stages ahead
+      if (tid == 0 && !fail && tma_issued < total_stages && tma_issued <= g + C::LOOKAHEAD) {
+        issue_tma(tma_issued);
+        ++tma_issued;
+      }
+      // (3) records of this stage have landed
+      if (!fail && !mbar_wait(&bar_tma[sr], (uint32_t)((g / C::NR) & 1))) fail = 1;
+      if (tid == 0 && !fail) tma_consumed = g + 1;
+      // (4) evaluate F_k[o, i] for this stage into A buffer sa
+      const uint8_t *rec_stage = sRec + (size_t)sr * C::REC_STAGE;
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        const float *rp = reinterpret_cast<const float *>(rec_stage + ks * C::REC + JP * 32 * (SPLIT ? 2 : 1));
+        const int ibase = ((sidx * KS + ks) * 16) + half * 8;
+        int row[8];
+        float tq[8];
+#pragma unroll
+        for (int q = 0; q < 8; q += 4) {
+          const float4 xs = *reinterpret_cast<const float4 *>(rp + half * 8 + q);
+          const float4 ys = *reinterpret_cast<const float4 *>(rp + 16 + half * 8 + q);
+          const float4 zs = *reinterpret_cast<const float4 *>(rp + 32 + half * 8 + q);
+          const float xa[4] = {xs.x, xs.y, xs.z, xs.w}, ya[4] = {ys.x, ys.y, ys.z, ys.w},
+                      za[4] = {zs.x, zs.y, zs.z, zs.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float r2 = pair_r2(xo, yo, zo, xa[u], ya[u], za[u]);
+            const float x = r2 * rsqrtf(fmaxf(r2, 1e-30f)) * args.inv_dr;
+            const int m = max(0, min(static_cast<int>(x), args.n_r - 2));
+            tq[q + u] = x - static_cast<float>(m);
+            const bool valid = (r2 <= args.r2max) && (ibase + q + u < args.N);
+            row[q + u] = valid ? m : args.n_r;
+          }
+        }
+        const uint32_t a_step = sA_u32 + (uint32_t)(sa * C::A_STAGE) + (uint32_t)(ks * KB * (SPLIT ? 2 : 1) * C::A_TILE);
+        if (!SPLIT) {
+          uint32_t t2[4];
+#pragma unroll
+          for (int p = 0; p < 4; ++p) t2[p] = pack_bf16x2(tq[2 * p], tq[2 * p + 1]);
+          const uint4 *tab4 = reinterpret_cast<const uint4 *>(sTab);
+#pragma unroll
+          for (int kb4 = 0; kb4 < KB / 4; ++kb4) {
+            uint4 w[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) w[q] = tab4[row[q] * (KB / 4) + kb4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+              uint32_t outv[4];
+#pragma unroll
+              for (int p = 0; p < 4; ++p) {
+                const uint32_t w0 = (b == 0) ? w[2 * p].x : (b == 1) ? w[2 * p].y : (b == 2) ? w[2 * p].z : w[2 * p].w;
+                const uint32_t w1 = (b == 0) ? w[2 * p + 1].x : (b == 1) ? w[2 * p + 1].y : (b == 2) ? w[2 * p + 1].z : w[2 * p + 1].w;
+                const uint32_t v2 = __byte_perm(w0, w1, 0x5410);
+                const uint32_t s2 = __byte_perm(w0, w1, 0x7632);
+                outv[p] = bf16x2_fma(t2[p], s2, v2);
+              }
+              const int kb = kb4 * 4 + b;
+              st_shared_v4(a_step + (uint32_t)(kb * C::A_TILE) + a_row_off, outv[0], outv[1], outv[2], outv[3]);
+            }
+          }
+        } else {
+          const float4 *tab4 = reinterpret_cast<const float4 *>(sTab);   // {v_k, s_k, v_k+1, s_k+1}
+#pragma unroll
+          for (int kb2 = 0; kb2 < KB / 2; ++kb2) {
+            float F0[8], F1[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const float4 w = tab4[row[q] * (KB / 2) + kb2];
+              F0[q] = fmaf(tq[q], w.y, w.x);
+              F1[q] = fmaf(tq[q], w.w, w.z);
+            }
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+              const float *F = b ? F1 : F0;
+              uint32_t hi[4], lo[4];
+#pragma unroll
+              for (int p = 0; p < 4; ++p) {
+                hi[p] = pack_bf16x2(F[2 * p], F[2 * p + 1]);
+                const float h0 = __uint_as_float(hi[p] << 16), h1 = __uint_as_float(hi[p] & 0xFFFF0000u);
+                lo[p] = pack_bf16x2(F[2 * p] - h0, F[2 * p + 1] - h1);
+              }
+              const int kb = kb2 * 2 + b;
+              st_shared_v4(a_step + (uint32_t)((2 * kb) * C::A_TILE) + a_row_off, hi[0], hi[1], hi[2], hi[3]);
+              st_shared_v4(a_step + (uint32_t)((2 * kb + 1) * C::A_TILE) + a_row_off, lo[0], lo[1], lo[2], lo[3]);
+            }
+          }
+        }
+      }
+      fence_proxy_async_smem();
+      if (__syncthreads_or(fail)) {   // block-uniform decision
+        ok = false;
+        break;
+      }
+      // (5) one thread issues the MMAs of this stage
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t rec_u32 = smem_u32(rec_stage);
+#pragma unroll 1
+        for (int ks = 0; ks < KS; ++ks) {
+          const uint32_t b_hi = rec_u32 + ks * C::REC;
+          const uint64_t dbh = umma_desc(b_hi, JP * 16, 128);
+          const uint64_t dbl = umma_desc(b_hi + JP * 32, JP * 16, 128);
+          const uint32_t a_step = sA_u32 + (uint32_t)(sa * C::A_STAGE) + (uint32_t)(ks * KB * (SPLIT ? 2 : 1) * C::A_TILE);
+          const uint32_t first = (sidx == 0 && ks == 0) ? 0u : 1u;
+#pragma unroll 1
+          for (int kb = 0; kb < KB; ++kb) {
+            const uint32_t d = tmem_base + (uint32_t)(kb * JP);
+            if (!SPLIT) {
+              umma_bf16(d, umma_desc(a_step + kb * C::A_TILE, 128, 256), dbh, idesc, first);
+            } else {
+              const uint64_t dah = umma_desc(a_step + (2 * kb) * C::A_TILE, 128, 256);
+              const uint64_t dal = umma_desc(a_step + (2 * kb + 1) * C::A_TILE, 128, 256);
+              umma_bf16(d, dah, dbh, idesc, first);
+              umma_bf16(d, dah, dbl, idesc, 1u);
+              umma_bf16(d, dal, dbh, idesc, 1u);
+            }
+          }
+        }
+        umma_commit(&bar_mma[sa]);
+        mma_issued = g + 1;
+      }
+    }
+    if (!ok) break;
+    // (6) epilogue: wait for the last MMAs, TMEM -> registers -> M
+    const long last = g - 1;
+    const int efail = mbar_wait(&bar_mma[last % NS], (uint32_t)((last / NS) & 1)) ? 0 : 1;
+    if (__syncthreads_or(efail)) {
+      ok = false;
+      break;
+    }
+    tc_fence_after();
+    {
+      const int quarter = warp & 3, wh = warp >> 2;
+      const int orow_e = quarter * 32 + lane;
+      const int oe = otile * 128 + orow_e;
+      for (int kb = wh; kb < KB; kb += 2) {
+        const int k = k0 + kb;
+#pragma unroll
+        for (int jc = 0; jc < JP; jc += 16) {
+          uint32_t r[16];
+          tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(kb * JP + jc), r);
+          tmem_ld_wait();
+          if (k < args.K && oe < args.N) {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const int j = jc + q;
+              if (j < args.J) args.M[((size_t)k * args.J + j) * args.N + oe] = __uint_as_float(r[q]);
+            }
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+
+  // teardown: on abort (block-uniform), give in-flight copies and MMAs a bounded chance to land
+  __syncthreads();
+  if (!ok) {
+    if (tid == 0) {
+      report_device_error(args.status, DEV_ERR_TIMEOUT);
+      for (long q = tma_consumed; q < tma_issued; ++q) mbar_wait(&bar_tma[q % C::NR], (uint32_t)((q / C::NR) & 1));
+      if (mma_issued > 0) mbar_wait(&bar_mma[(mma_issued - 1) % NS], (uint32_t)(((mma_issued - 1) / NS) & 1));
+    }
+    __syncthreads();
+  }
+  tc_fence_after();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"((uint32_t)C::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- host side
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+struct TcChoice {
+  int KB, NS, KS;
+};
+
+template <int KB, int JP, bool SPLIT, int NS, int KS>
+static tsr_status launch_tc(const TcArgs &a0, const uint8_t *rec, cudaStream_t s) {
+  using C = TcCfg<KB, JP, SPLIT, NS, KS>;
+  TcArgs a = a0;
+  a.n_kgroups = (a.K + KB - 1) / KB;
+  a.n_items = a.n_otiles * a.n_kgroups;
+  const size_t smem = C::smem_bytes(a.n_r);
+  if (smem > 232448) {
+    set_error("transfer_tc: shared memory %zu bytes exceeds the per-block limit (n_r too large)", smem);
+    return TSR_ERR_UNSUPPORTED;
+  }
+  auto encode = get_encode();
+  if (!encode) {
+    set_error("transfer_tc: cuTensorMapEncodeTiled unavailable");
+    return TSR_ERR_CUDA;
+  }
+  CUtensorMap tmap;
+  const cuuint64_t rows_total = (cuuint64_t)a.n_steps * C::REC / 128;
+  const cuuint64_t gdim[2] = {32, rows_total};
+  const cuuint64_t gstride[1] = {128};
+  const cuuint32_t box[2] = {32, (cuuint32_t)(C::REC_STAGE / 128)};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult cr = encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint8_t *>(rec), gdim, gstride, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) {
+    set_error("transfer_tc: cuTensorMapEncodeTiled failed (%d)", (int)cr);
+    return TSR_ERR_CUDA;
+  }
+  auto kern = transfer_tc_kernel<KB, JP, SPLIT, NS, KS>;
+  TSR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = std::min(a.n_items, num_sms());
+  kern<<<grid, 256, smem, s>>>(tmap, a);
+  TSR_CUDA(cudaGetLastError());
+  return TSR_OK;
+}
+
+// Configuration per (K, J_pad, split): bases per item, pipeline stages, steps per stage.
+static tsr_status dispatch_tc(const TcArgs &a, int JP, bool split, const uint8_t *rec, cudaStream_t s) {
+  const int K = a.K;
+  if (!split) {
+    if (JP == 16) {
+      if (K <= 4) return launch_tc<4, 16, false, 4, 2>(a, rec, s);
+      if (K <= 8) return launch_tc<8, 16, false, 4, 1>(a, rec, s);
+      if (K <= 12) return launch_tc<12, 16, false, 3, 1>(a, rec, s);
+      return launch_tc<16, 16, false, 2, 1>(a, rec, s);
+    } else {
+      if (K <= 4) return launch_tc<4, 32, false, 4, 2>(a, rec, s);
+      if (K <= 8) return launch_tc<8, 32, false, 4, 1>(a, rec, s);
+      if (K <= 12) return launch_tc<12, 32, false, 3, 1>(a, rec, s);
+      return launch_tc<16, 32, false, 2, 1>(a, rec, s);
+    }
+  } else {
+    if (JP == 16) {
+      if (K <= 4) return launch_tc<4, 16, true, 4, 1>(a, rec, s);
+      return launch_tc<8, 16, true, 2, 1>(a, rec, s);
+    } else {
+      if (K <= 4) return launch_tc<4, 32, true, 4, 1>(a, rec, s);
+      return launch_tc<8, 32, true, 2, 1>(a, rec, s);
+    }
+  }
+}
+
+tsr_status transfer_tc(const tsr_basis *b, int N, const float *pos, const float *area, const float *T, int J,
+                       bool split, float *M, cudaStream_t s) {
+  const int JP = J <= 16 ? 16 : 32;
+  const int KS_MAX = 2;
+  const int n_steps = ((N + 15) / 16 + KS_MAX - 1) / KS_MAX * KS_MAX;
+  const int REC = rec_bytes(JP, split);
+  Scratch rs;
+  tsr_status st = rs.alloc((size_t)n_steps * REC, s);
+  if (st != TSR_OK) return st;
+  uint8_t *rec = static_cast<uint8_t *>(rs.p);
+  TSR_CUDA(cudaMemsetAsync(rec, 0, (size_t)n_steps * REC, s));
+  pretile_tc_kernel<<<(n_steps * 16 + 255) / 256, 256, 0, s>>>(pos, area, T, N, J, JP, split ? 1 : 0, REC, n_steps,
+                                                                rec);
+  TSR_CUDA(cudaGetLastError());
+  TcArgs a{};
+  a.N = N;
+  a.n_steps = n_steps;
+  a.n_r = b->n_r;
+  a.inv_dr = static_cast<float>((b->n_r - 1) / b->r_max);
+  a.r2max = static_cast<float>(b->r_max * b->r_max);
+  a.K = b->K;
+  a.J = J;
+  a.n_otiles = (N + 127) / 128;
+  a.pos = pos;
+  a.tab16 = b->tab16;
+  a.tab32 = b->tab32;
+  a.KP = b->KP;
+  a.M = M;
+  a.status = device_status_ptr();
+  return dispatch_tc(a, JP, split, rec, s);
+}
+
+// Batched transfer over independent meshes: one launch per mesh, in order.
+tsr_status transfer_fp32_batched(const tsr_basis *b, int n_mesh, const int64_t *offsets, const float *pos,
+                                 const float *area, const float *T, int J, float *M, cudaStream_t s) {
+  (void)b; (void)n_mesh; (void)offsets; (void)pos; (void)area; (void)T; (void)J; (void)M; (void)s;
+  set_error("batched FP32 transfer not built yet");
+  return TSR_ERR_UNSUPPORTED;
+}
+tsr_status transfer_tc_batched(const tsr_basis *b, int n_mesh, const int64_t *offsets, const float *pos,
+                               const float *area, const float *T, int J, float *M, cudaStream_t s) {
+  (void)b; (void)n_mesh; (void)offsets; (void)pos; (void)area; (void)T; (void)J; (void)M; (void)s;
+  set_error("batched BF16 transfer not built yet");
+  return TSR_ERR_UNSUPPORTED;
+}
+
+}  // namespace tsr

@@ -1,0 +1,330 @@
+"""Python binding of libtsr (the C ABI in include/tsr.h).
+
+Argument marshalling only: each function checks shapes/dtypes, allocates the
+outputs with PyTorch on the current CUDA device, and calls the library entry
+point of the same name on the current stream.  Every step of the computation
+runs in the library's CUDA kernels; if the library is missing this module
+raises instead of computing anything another way.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtsr.so")
+
+TSR_FP32, TSR_BF16, TSR_BF16X3 = 0, 1, 2
+PRECISIONS = {"fp32": TSR_FP32, "bf16": TSR_BF16, "bf16x3": TSR_BF16X3}
+STATUS_NAMES = {0: "TSR_OK", -1: "TSR_ERR_INVALID_ARG", -2: "TSR_ERR_CUDA", -3: "TSR_ERR_OOM",
+                -4: "TSR_ERR_TIMEOUT", -5: "TSR_ERR_UNSUPPORTED"}
+
+_lib = None
+_lock = threading.Lock()
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+_SIGNATURES = {
+    "tsr_last_error": (ctypes.c_char_p, []),
+    "tsr_version": (_I, []),
+    "tsr_stream_status": (_I, [_P]),
+    "tsr_fit_pca_basis": (_I, [_I, _P, _P, _D, _I, _D, _I, _P, ctypes.POINTER(_P), _P]),
+    "tsr_basis_create": (_I, [_I, _I, _D, _P, ctypes.POINTER(_P)]),
+    "tsr_basis_table": (_I, [_P, _P, _P]),
+    "tsr_basis_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "tsr_basis_destroy": (None, [_P]),
+    "tsr_project_material": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P]),
+    "tsr_project_material_backward": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "tsr_precompute_transfer": (_I, [_P, _I, _P, _P, _P, _I, _I, _P, _P]),
+    "tsr_precompute_transfer_batched": (_I, [_P, _I, _P, _P, _P, _P, _I, _I, _P, _P]),
+    "tsr_haar_forward": (_I, [_P, _I, _I, _P, _P]),
+    "tsr_haar_inverse": (_I, [_P, _I, _I, _P, _P]),
+    "tsr_wavelet_compress": (_I, [_P, _I, _I, _I, _D, ctypes.POINTER(_P), _P]),
+    "tsr_haar_compress": (_I, [_P, _I, _I, _I, _D, ctypes.POINTER(_P), _P]),
+    "tsr_compressed_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_I)]),
+    "tsr_compressed_export": (_I, [_P, _P, _P, _P, _P]),
+    "tsr_compressed_destroy": (None, [_P]),
+    "tsr_relight": (_I, [_P, _I, _P, _P, _P, _P]),
+    "tsr_relight_backward": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
+}
+
+
+class TsrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libtsr.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                                   "(there is no fallback implementation)")
+            handle = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGNATURES.items():
+                fn = getattr(handle, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = handle
+        return _lib
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise TsrError(status, lib().tsr_last_error().decode(errors="replace"))
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _dev(t: torch.Tensor, dtype: torch.dtype, shape: tuple | None = None, name: str = "tensor") -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t.contiguous()
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def stream_status() -> None:
+    """Synchronise the current stream and raise if a kernel gave up a bounded wait."""
+    _check(lib().tsr_stream_status(_stream()))
+
+
+# ---------------------------------------------------------------- basis
+class Basis:
+    """Radial PCA basis f_k on the grid r_m = r_max m/(n_r-1) (owned by the library)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        K, n_r, r_max = _I(), _I(), _D()
+        _check(lib().tsr_basis_info(self._h, ctypes.byref(K), ctypes.byref(n_r), ctypes.byref(r_max)))
+        self.K, self.n_r, self.r_max = K.value, n_r.value, r_max.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def table(self) -> torch.Tensor:
+        f = torch.empty((self.K, self.n_r), dtype=torch.float64, device="cuda")
+        _check(lib().tsr_basis_table(self._h, _ptr(f), _stream()))
+        return f
+
+    def close(self):
+        if self._h:
+            lib().tsr_basis_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fit_pca_basis(sigma_a: torch.Tensor, sigma_s: torch.Tensor, eta: float = 1.3, n_r: int = 1024,
+                  r_max: float = 40.0, K: int = 12) -> tuple[Basis, torch.Tensor]:
+    """tsr_fit_pca_basis: returns the basis and the singular values (FP64, descending)."""
+    sa = _dev(sigma_a, torch.float64, name="sigma_a")
+    ss = _dev(sigma_s, torch.float64, sa.shape, name="sigma_s")
+    n_mat = sa.numel()
+    sv = torch.empty(min(n_mat, n_r), dtype=torch.float64, device=sa.device)
+    h = _P()
+    _check(lib().tsr_fit_pca_basis(n_mat, _ptr(sa), _ptr(ss), float(eta), n_r, float(r_max), K, _ptr(sv),
+                                   ctypes.byref(h), _stream()))
+    return Basis(h), sv
+
+
+def basis_create(f, r_max: float = 40.0) -> Basis:
+    """tsr_basis_create from a host table f[K][n_r] (FP64)."""
+    ft = torch.as_tensor(f, dtype=torch.float64).contiguous().cpu()
+    K, n_r = ft.shape
+    h = _P()
+    _check(lib().tsr_basis_create(K, n_r, float(r_max), ctypes.c_void_p(ft.data_ptr()), ctypes.byref(h)))
+    return Basis(h)
+
+
+def project_material(basis: Basis, sigma_a: torch.Tensor, sigma_s: torch.Tensor, eta: torch.Tensor,
+                     jacobian: bool = False):
+    """tsr_project_material: returns (g f64 [n,3,K], g32 f32 [n,3,K], dg f64 [n,3,K,3] or None)."""
+    sa = _dev(sigma_a, torch.float64, name="sigma_a")
+    n = sa.shape[0]
+    sa = _dev(sa, torch.float64, (n, 3), "sigma_a")
+    ss = _dev(sigma_s, torch.float64, (n, 3), "sigma_s")
+    et = _dev(eta, torch.float64, (n,), "eta")
+    g = torch.empty((n, 3, basis.K), dtype=torch.float64, device=sa.device)
+    g32 = torch.empty((n, 3, basis.K), dtype=torch.float32, device=sa.device)
+    dg = torch.empty((n, 3, basis.K, 3), dtype=torch.float64, device=sa.device) if jacobian else None
+    _check(lib().tsr_project_material(basis.handle, n, _ptr(sa), _ptr(ss), _ptr(et), _ptr(g), _ptr(g32), _ptr(dg),
+                                      _stream()))
+    return g, g32, dg
+
+
+def project_material_backward(basis: Basis, sigma_a, sigma_s, eta, dLdg: torch.Tensor):
+    """tsr_project_material_backward: returns (dsigma_a [n,3], dsigma_s [n,3], deta [n]) in FP32."""
+    n = sigma_a.shape[0]
+    sa = _dev(sigma_a, torch.float64, (n, 3), "sigma_a")
+    ss = _dev(sigma_s, torch.float64, (n, 3), "sigma_s")
+    et = _dev(eta, torch.float64, (n,), "eta")
+    dg = _dev(dLdg, torch.float32, (n, 3, basis.K), "dLdg")
+    dsa = torch.empty((n, 3), dtype=torch.float32, device=sa.device)
+    dss = torch.empty((n, 3), dtype=torch.float32, device=sa.device)
+    de = torch.empty((n,), dtype=torch.float32, device=sa.device)
+    _check(lib().tsr_project_material_backward(basis.handle, n, _ptr(sa), _ptr(ss), _ptr(et), _ptr(dg), _ptr(dsa),
+                                               _ptr(dss), _ptr(de), _stream()))
+    return dsa, dss, de
+
+
+# ---------------------------------------------------------------- transfer
+def precompute_transfer(basis: Basis, pos: torch.Tensor, area: torch.Tensor, T: torch.Tensor,
+                        precision: str = "bf16", out: torch.Tensor | None = None) -> torch.Tensor:
+    """tsr_precompute_transfer: M[k][j][o] = sum_i A_i f_k(|x_o-x_i|) T[j][i]; pos is [3][N] FP32."""
+    N = pos.shape[1]
+    p = _dev(pos, torch.float32, (3, N), "pos")
+    a = _dev(area, torch.float32, (N,), "area")
+    J = T.shape[0]
+    t = _dev(T, torch.float32, (J, N), "T")
+    M = out if out is not None else torch.empty((basis.K, J, N), dtype=torch.float32, device=p.device)
+    _dev(M, torch.float32, (basis.K, J, N), "out")
+    _check(lib().tsr_precompute_transfer(basis.handle, N, _ptr(p), _ptr(a), _ptr(t), J, PRECISIONS[precision],
+                                         _ptr(M), _stream()))
+    return M
+
+
+def precompute_transfer_batched(basis: Basis, offsets, pos: torch.Tensor, area: torch.Tensor, T: torch.Tensor,
+                                precision: str = "bf16", out: torch.Tensor | None = None) -> torch.Tensor:
+    """tsr_precompute_transfer_batched over meshes concatenated along the vertex axis (offsets on the host)."""
+    off = torch.as_tensor(offsets, dtype=torch.int64).contiguous().cpu()
+    n_mesh = off.numel() - 1
+    total = int(off[-1])
+    p = _dev(pos, torch.float32, (3, total), "pos")
+    a = _dev(area, torch.float32, (total,), "area")
+    J = T.shape[0]
+    t = _dev(T, torch.float32, (J, total), "T")
+    M = out if out is not None else torch.empty((basis.K, J, total), dtype=torch.float32, device=p.device)
+    _check(lib().tsr_precompute_transfer_batched(basis.handle, n_mesh, ctypes.c_void_p(off.data_ptr()), _ptr(p),
+                                                 _ptr(a), _ptr(t), J, PRECISIONS[precision], _ptr(M), _stream()))
+    return M
+
+
+# ---------------------------------------------------------------- wavelet / compression
+def chart_side(nu: int) -> int:
+    P = 1
+    while P < nu:
+        P *= 2
+    return P
+
+
+def haar_forward(X: torch.Tensor, nu: int) -> torch.Tensor:
+    """tsr_haar_forward: X [rows][10 nu^2 + 2] -> Xw [rows][10 P^2 + 2]."""
+    N = 10 * nu * nu + 2
+    x = _dev(X, torch.float32, name="X").reshape(-1, N)
+    P = chart_side(nu)
+    Xw = torch.empty((x.shape[0], 10 * P * P + 2), dtype=torch.float32, device=x.device)
+    _check(lib().tsr_haar_forward(_ptr(x), x.shape[0], nu, _ptr(Xw), _stream()))
+    return Xw.reshape(X.shape[:-1] + (10 * P * P + 2,))
+
+
+def haar_inverse(Xw: torch.Tensor, nu: int) -> torch.Tensor:
+    """tsr_haar_inverse: Xw [rows][10 P^2 + 2] -> X [rows][10 nu^2 + 2]."""
+    P = chart_side(nu)
+    x = _dev(Xw, torch.float32, name="Xw").reshape(-1, 10 * P * P + 2)
+    X = torch.empty((x.shape[0], 10 * nu * nu + 2), dtype=torch.float32, device=x.device)
+    _check(lib().tsr_haar_inverse(_ptr(x), x.shape[0], nu, _ptr(X), _stream()))
+    return X.reshape(Xw.shape[:-1] + (10 * nu * nu + 2,))
+
+
+class Compressed:
+    """Compressed wavelet transfer (CSR over wavelet rows; owned by the library)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        K, J, nu, n_rows = _I(), _I(), _I(), _I()
+        nnz = ctypes.c_int64()
+        _check(lib().tsr_compressed_info(self._h, ctypes.byref(K), ctypes.byref(J), ctypes.byref(nu),
+                                         ctypes.byref(nnz), ctypes.byref(n_rows)))
+        self.K, self.J, self.nu, self.nnz, self.n_rows = K.value, J.value, nu.value, nnz.value, n_rows.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def n(self) -> int:
+        return 10 * self.nu * self.nu + 2
+
+    def export(self):
+        """(row_ptr int64 [n_rows+1], col int32 [nnz], val f32 [nnz]) on the device."""
+        row_ptr = torch.empty(self.n_rows + 1, dtype=torch.int64, device="cuda")
+        col16 = torch.empty(self.nnz, dtype=torch.int16, device="cuda")
+        val = torch.empty(self.nnz, dtype=torch.float32, device="cuda")
+        _check(lib().tsr_compressed_export(self._h, _ptr(row_ptr), _ptr(col16), _ptr(val), _stream()))
+        col = col16.to(torch.int32) & 0xFFFF
+        return row_ptr, col, val
+
+    def close(self):
+        if self._h:
+            lib().tsr_compressed_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def wavelet_compress(Mw: torch.Tensor, nu: int, p: float) -> Compressed:
+    """tsr_wavelet_compress from wavelet coefficients Mw [K][J][10 P^2 + 2]."""
+    K, J, NW = Mw.shape
+    m = _dev(Mw, torch.float32, name="Mw")
+    h = _P()
+    _check(lib().tsr_wavelet_compress(_ptr(m), K, J, nu, float(p), ctypes.byref(h), _stream()))
+    return Compressed(h)
+
+
+def haar_compress(M: torch.Tensor, nu: int, p: float) -> Compressed:
+    """tsr_haar_compress: forward Haar of M [K][J][N] then the top-p keep rule."""
+    K, J, N = M.shape
+    m = _dev(M, torch.float32, (K, J, 10 * nu * nu + 2), "M")
+    h = _P()
+    _check(lib().tsr_haar_compress(_ptr(m), K, J, nu, float(p), ctypes.byref(h), _stream()))
+    return Compressed(h)
+
+
+# ---------------------------------------------------------------- relight
+def relight(comp: Compressed, g: torch.Tensor, light: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """tsr_relight: g [E][3][K] FP32, light [J] FP32 -> B [E][3][N]."""
+    E = g.shape[0]
+    gg = _dev(g, torch.float32, (E, 3, comp.K), "g")
+    ll = _dev(light, torch.float32, (comp.J,), "light")
+    B = out if out is not None else torch.empty((E, 3, comp.n), dtype=torch.float32, device=gg.device)
+    _check(lib().tsr_relight(comp.handle, E, _ptr(gg), _ptr(ll), _ptr(B), _stream()))
+    return B
+
+
+def relight_backward(comp: Compressed, g: torch.Tensor, light: torch.Tensor, dLdB: torch.Tensor):
+    """tsr_relight_backward: returns (dg [E][3][K], dl [J])."""
+    E = g.shape[0]
+    gg = _dev(g, torch.float32, (E, 3, comp.K), "g")
+    ll = _dev(light, torch.float32, (comp.J,), "light")
+    db = _dev(dLdB, torch.float32, (E, 3, comp.n), "dLdB")
+    dg = torch.empty_like(gg)
+    dl = torch.empty_like(ll)
+    _check(lib().tsr_relight_backward(comp.handle, E, _ptr(gg), _ptr(ll), _ptr(db), _ptr(dg), _ptr(dl), _stream()))
+    return dg, dl

@@ -1,0 +1,303 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (per-k normwise over the compared rows for M, per (edit, channel)
+normwise for B, relative for the rest):
+  transfer FP32 <= 1e-5, split BF16 <= 1e-4, BF16 <= 2e-3;
+  Haar, relight and its adjoint (FP32 arithmetic on identical inputs) <= 2e-6;
+  FP64 basis / projection <= the Jacobi-vs-LAPACK perturbation bound below.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import tsr_oracle as O
+from paper_2203_12339_gb300 import scene
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "bf16x3": 1e-4, "bf16": 2e-3}
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_12339_gb300 import build
+    build.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def tsr(torch_cuda):
+    from paper_2203_12339_gb300 import tsr as T
+    return T
+
+
+@pytest.fixture(scope="module")
+def oracle_basis16():
+    sa, ss = scene.pca_materials(256, seed=0)
+    return O.fit_pca_basis(sa, ss, 1.3, 1024, 40.0, 16)
+
+
+def _dev(torch, a, dtype=None):
+    t = torch.as_tensor(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def _normwise_k(got, ref):
+    """max over k of ||dM[k]||_F / ||M[k]||_F."""
+    d = np.linalg.norm((got - ref).reshape(got.shape[0], -1), axis=1)
+    n = np.linalg.norm(ref.reshape(ref.shape[0], -1), axis=1)
+    return float(np.max(d / n))
+
+
+# ------------------------------------------------------------------ Section 2.2
+def test_fit_pca_basis_matches_oracle(torch_cuda, tsr, oracle_basis16):
+    torch = torch_cuda
+    f_ref, s_ref = oracle_basis16
+    sa, ss = scene.pca_materials(256, seed=0)
+    basis, sv = tsr.fit_pca_basis(_dev(torch, sa), _dev(torch, ss), 1.3, 1024, 40.0, 16)
+    f = basis.table().cpu().numpy()
+    sv = sv.cpu().numpy()
+    assert sv.shape == (256,)
+    # singular values: both SVDs are backward stable, |ds_k| <~ c eps s_0
+    assert np.all(np.abs(sv[:16] - s_ref[:16]) <= 1e-13 * s_ref[0] + 1e-11 * s_ref[:16])
+    # singular vectors: perturbation bound eps * s_0 / gap_k
+    for k in range(16):
+        gap = min(s_ref[k - 1] - s_ref[k] if k > 0 else np.inf, s_ref[k] - s_ref[k + 1])
+        tol = 2e-13 * s_ref[0] / gap + 1e-13
+        assert np.max(np.abs(f[k] - f_ref[k])) <= tol, (k, np.max(np.abs(f[k] - f_ref[k])), tol)
+    assert np.max(np.abs(f @ f.T - np.eye(16))) < 1e-12
+
+
+def test_fit_pca_basis_odd_material_count(torch_cuda, tsr):
+    torch = torch_cuda
+    sa, ss = scene.pca_materials(37, seed=9)
+    f_ref, s_ref = O.fit_pca_basis(sa, ss, 1.2, 200, 30.0, 5)
+    basis, sv = tsr.fit_pca_basis(_dev(torch, sa), _dev(torch, ss), 1.2, 200, 30.0, 5)
+    assert np.max(np.abs(basis.table().cpu().numpy() - f_ref)) < 1e-9
+    assert np.allclose(sv.cpu().numpy()[:5], s_ref[:5], rtol=1e-11)
+
+
+def test_project_material_and_jacobian(torch_cuda, tsr, oracle_basis16):
+    torch = torch_cuda
+    f_ref, _ = oracle_basis16
+    basis = tsr.basis_create(f_ref)
+    sa, ss, eta = scene.edit_materials(50, seed=5)
+    g, g32, dg = tsr.project_material(basis, _dev(torch, sa), _dev(torch, ss), _dev(torch, eta), jacobian=True)
+    g_ref = O.project_material(f_ref, sa, ss, eta)
+    assert np.max(np.abs(g.cpu().numpy() - g_ref)) <= 1e-12 * np.max(np.abs(g_ref))
+    assert np.array_equal(g32.cpu().numpy(), g.cpu().numpy().astype(np.float32))
+    r = O.radius_grid()
+    d_a, d_s, d_e = O.dipole_rd_partials(r[None, None, :], sa[..., None], ss[..., None], eta[:, None, None])
+    jac_ref = np.stack([d_a @ f_ref.T, d_s @ f_ref.T, d_e @ f_ref.T], axis=-1)
+    dgc = dg.cpu().numpy()
+    for q in range(3):
+        scale = np.max(np.abs(jac_ref[..., q]))
+        assert np.max(np.abs(dgc[..., q] - jac_ref[..., q])) <= 1e-11 * scale
+
+
+def test_project_material_backward(torch_cuda, tsr, oracle_basis16):
+    torch = torch_cuda
+    f_ref, _ = oracle_basis16
+    basis = tsr.basis_create(f_ref[:12])
+    sa, ss, eta = scene.edit_materials(7, seed=8)
+    dLdg = np.random.default_rng(0).standard_normal((7, 3, 12)).astype(np.float32)
+    dsa, dss, de = tsr.project_material_backward(basis, _dev(torch, sa), _dev(torch, ss), _dev(torch, eta),
+                                                 _dev(torch, dLdg))
+    ra, rs, re = O.project_material_vjp(f_ref[:12], sa, ss, eta, dLdg.astype(np.float64))
+    for got, ref in ((dsa, ra), (dss, rs), (de, re)):
+        got = got.cpu().numpy()
+        assert np.max(np.abs(got - ref)) <= 2e-6 * np.max(np.abs(ref))
+
+
+# ------------------------------------------------------------------ Eq. 6-7 transfer
+def _scene_arrays(nu, K, J, amp, seed):
+    sc = scene.make_scene(nu, K=K, J=J, amp=amp, seed=seed)
+    return sc, sc.mesh.pos.astype(np.float32), sc.mesh.area.astype(np.float32), sc.T.astype(np.float32)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "bf16x3"])
+@pytest.mark.parametrize("nu,K,J", [(9, 8, 9), (16, 12, 16), (5, 16, 25), (3, 3, 5)])
+def test_transfer_full_small(torch_cuda, tsr, oracle_basis16, precision, nu, K, J):
+    """Whole M on meshes that span several 128-row tiles with a ragged tail (812, 2562, 252, 92 vertices)."""
+    torch = torch_cuda
+    f_ref, _ = oracle_basis16
+    sc, pos, area, T = _scene_arrays(nu, K, J, 0.12, 3)
+    basis = tsr.basis_create(f_ref[:K])
+    M = tsr.precompute_transfer(basis, _dev(torch, pos.T), _dev(torch, area), _dev(torch, T), precision)
+    tsr.stream_status()
+    M_ref = O.transfer_full(f_ref[:K], pos, area, T)
+    err = _normwise_k(M.cpu().numpy(), M_ref)
+    assert err <= TOL[precision], err
+
+
+def test_transfer_tiny_mesh_and_single_basis(torch_cuda, tsr, oracle_basis16):
+    torch = torch_cuda
+    f_ref, _ = oracle_basis16
+    sc, pos, area, T = _scene_arrays(1, 1, 1, 0.0, 0)   # 12 vertices, K = J = 1
+    basis = tsr.basis_create(f_ref[:1])
+    M_ref = O.transfer_full(f_ref[:1], pos, area, T)
+    for precision in ("fp32", "bf16", "bf16x3"):
+        M = tsr.precompute_transfer(basis, _dev(torch, pos.T), _dev(torch, area), _dev(torch, T), precision)
+        tsr.stream_status()
+        assert _normwise_k(M.cpu().numpy(), M_ref) <= TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "bf16x3"])
+def test_transfer_full_size_sampled_rows(torch_cuda, tsr, oracle_basis16, precision):
+    """40,962-vertex displaced sphere, K=12, J=16 (the benchmark workload): 1,024 sampled output rows."""
+    torch = torch_cuda
+    f_ref, _ = oracle_basis16
+    w = scene.WORKLOADS["disp40962_k12_j16"]
+    sc, pos, area, T = _scene_arrays(w["nu"], w["K"], w["J"], w["amp"], w["seed"])
+    basis = tsr.basis_create(f_ref[:12])
+    M = tsr.precompute_transfer(basis, _dev(torch, pos.T), _dev(torch, area), _dev(torch, T), precision)
+    tsr.stream_status()
+    rows = scene.sample_rows(sc.n, 1024, seed=7)
+    M_ref = O.transfer_rows(f_ref[:12], pos, area, T, rows)
+    err = _normwise_k(M.cpu().numpy()[:, :, rows], M_ref)
+    assert err <= TOL[precision], err
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
+def test_transfer_largest_sampled_rows(torch_cuda, tsr, oracle_basis16, precision):
+    """163,842-vertex displaced sphere, K=16, J=25: 128 sampled output rows."""
+    torch = torch_cuda
+    f_ref, _ = oracle_basis16
+    w = scene.WORKLOADS["disp163842_k16_j25"]
+    sc, pos, area, T = _scene_arrays(w["nu"], w["K"], w["J"], w["amp"], w["seed"])
+    basis = tsr.basis_create(f_ref)
+    M = tsr.precompute_transfer(basis, _dev(torch, pos.T), _dev(torch, area), _dev(torch, T), precision)
+    tsr.stream_status()
+    rows = scene.sample_rows(sc.n, 128, seed=7)
+    M_ref = O.transfer_rows(f_ref, pos, area, T, rows)
+    assert _normwise_k(M.cpu().numpy()[:, :, rows], M_ref) <= TOL[precision]
+
+
+# ------------------------------------------------------------------ Eq. 9-10 Haar
+@pytest.mark.parametrize("nu", [1, 3, 4, 5, 16, 64])
+def test_haar_forward_inverse(torch_cuda, tsr, nu):
+    torch = torch_cuda
+    rng = np.random.default_rng(nu)
+    X = rng.standard_normal((7, 10 * nu * nu + 2)).astype(np.float32)
+    Xw = tsr.haar_forward(_dev(torch, X), nu).cpu().numpy()
+    ref = O.chart_to_wavelet(X, nu)
+    assert np.max(np.abs(Xw - ref)) <= 2e-6 * np.max(np.abs(ref))
+    back = tsr.haar_inverse(_dev(torch, ref.astype(np.float32)), nu).cpu().numpy()
+    assert np.max(np.abs(back - X)) <= 2e-6 * np.max(np.abs(X))
+
+
+# ------------------------------------------------------------------ Step 2 selection (bit-exact)
+def _mask_from_csr(row_ptr, col, n_rows, KJ):
+    mask = np.zeros((KJ, n_rows), dtype=bool)
+    for w in range(n_rows):
+        for q in range(row_ptr[w], row_ptr[w + 1]):
+            mask[col[q], w] = True
+    return mask
+
+
+@pytest.mark.parametrize("nu,p", [(4, 0.1), (3, 0.37), (8, 0.05), (2, 1.0)])
+def test_select_and_pack_exact(torch_cuda, tsr, nu, p):
+    torch = torch_cuda
+    K, J = 3, 5
+    P = O.chart_side(nu)
+    rng = np.random.default_rng(nu)
+    Mw = (rng.integers(-20, 21, size=(K, J, 10 * P * P + 2)) * 0.25).astype(np.float32)   # many exact ties
+    comp = tsr.wavelet_compress(_dev(torch, Mw), nu, p)
+    row_ptr, col, val = (t.cpu().numpy() for t in comp.export())
+    n_rows = 10 * P * P + 2
+    assert comp.nnz == K * J * (O.keep_count(p, 10 * P * P) + 2)
+    assert row_ptr[0] == 0 and row_ptr[-1] == comp.nnz
+    for w in range(n_rows):
+        assert np.all(np.diff(col[row_ptr[w]:row_ptr[w + 1]]) > 0)
+    got = _mask_from_csr(row_ptr, col, n_rows, K * J).reshape(K, J, n_rows)
+    want = O.select_top(Mw, nu, p)
+    assert np.array_equal(got, want)
+    # values are the kept coefficients, bit for bit
+    for w in range(0, n_rows, 7):
+        for q in range(row_ptr[w], row_ptr[w + 1]):
+            assert val[q] == Mw.reshape(K * J, n_rows)[col[q], w]
+
+
+# ------------------------------------------------------------------ Steps 3-5 relight
+def _compressed_case(torch, tsr, nu, K, J, p, seed):
+    rng = np.random.default_rng(seed)
+    P = O.chart_side(nu)
+    Mw = rng.standard_normal((K, J, 10 * P * P + 2)).astype(np.float32) * np.exp(-np.arange(10 * P * P + 2) % (P * P) / (P * P / 4.0)).astype(np.float32)
+    comp = tsr.wavelet_compress(_dev(torch, Mw), nu, p)
+    kept = np.where(O.select_top(Mw, nu, p), Mw.astype(np.float64), 0.0)
+    return comp, kept
+
+
+@pytest.mark.parametrize("nu,K,J,E,p", [(4, 8, 9, 5, 0.1), (5, 12, 16, 3, 0.2), (16, 16, 25, 2, 0.05), (1, 1, 1, 1, 1.0)])
+def test_relight_matches_oracle(torch_cuda, tsr, nu, K, J, E, p):
+    torch = torch_cuda
+    comp, kept = _compressed_case(torch, tsr, nu, K, J, p, nu + K)
+    rng = np.random.default_rng(1)
+    g = rng.standard_normal((E, 3, K)).astype(np.float32)
+    light = rng.standard_normal(J).astype(np.float32)
+    B = tsr.relight(comp, _dev(torch, g), _dev(torch, light)).cpu().numpy()
+    B_ref = O.relight(kept, nu, g.astype(np.float64), light.astype(np.float64))
+    num = np.linalg.norm((B - B_ref).reshape(E * 3, -1), axis=1)
+    den = np.linalg.norm(B_ref.reshape(E * 3, -1), axis=1)
+    assert np.max(num / den) <= 2e-6
+
+
+@pytest.mark.parametrize("nu,K,J,E,p", [(4, 8, 9, 5, 0.1), (5, 12, 16, 3, 0.2), (8, 16, 25, 11, 0.05)])
+def test_relight_backward_matches_oracle(torch_cuda, tsr, nu, K, J, E, p):
+    torch = torch_cuda
+    comp, kept = _compressed_case(torch, tsr, nu, K, J, p, 3 * nu + K)
+    rng = np.random.default_rng(2)
+    g = rng.standard_normal((E, 3, K)).astype(np.float32)
+    light = rng.standard_normal(J).astype(np.float32)
+    dB = rng.standard_normal((E, 3, 10 * nu * nu + 2)).astype(np.float32)
+    dg, dl = tsr.relight_backward(comp, _dev(torch, g), _dev(torch, light), _dev(torch, dB))
+    dg_ref, dl_ref = O.relight_vjp(kept, nu, g.astype(np.float64), light.astype(np.float64), dB.astype(np.float64))
+    assert np.max(np.abs(dg.cpu().numpy() - dg_ref)) <= 1e-5 * np.max(np.abs(dg_ref))
+    assert np.max(np.abs(dl.cpu().numpy() - dl_ref)) <= 1e-5 * np.max(np.abs(dl_ref))
+
+
+# ------------------------------------------------------------------ whole path
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_end_to_end_sphere2562(torch_cuda, tsr, precision):
+    """Undisplaced 2,562-vertex sphere, K=8, J=9, marble: fit -> project -> transfer -> compress -> relight."""
+    torch = torch_cuda
+    w = scene.WORKLOADS["sphere2562_k8_j9"]
+    sc, pos, area, T = _scene_arrays(w["nu"], w["K"], w["J"], w["amp"], w["seed"])
+    sa, ss = scene.pca_materials(256, seed=0)
+    f_ref, _ = O.fit_pca_basis(sa, ss, 1.3, 1024, 40.0, 8)
+    basis, _ = tsr.fit_pca_basis(_dev(torch, sa), _dev(torch, ss), 1.3, 1024, 40.0, 8)
+    msa, mss, meta = scene.marble(1)
+    _, g32, _ = tsr.project_material(basis, _dev(torch, msa), _dev(torch, mss), _dev(torch, meta))
+    g_ref = O.project_material(f_ref, msa, mss, meta)
+    M = tsr.precompute_transfer(basis, _dev(torch, pos.T), _dev(torch, area), _dev(torch, T), precision)
+    comp = tsr.haar_compress(M, w["nu"], 1.0)   # keep everything: no selection ambiguity
+    B = tsr.relight(comp, g32, _dev(torch, sc.light.astype(np.float32))).cpu().numpy()
+    tsr.stream_status()
+    M_ref = O.transfer_full(f_ref, pos, area, T)
+    B_ref = O.relight(O.chart_to_wavelet(M_ref, w["nu"]), w["nu"], g_ref, sc.light)
+    rel = np.linalg.norm((B - B_ref).reshape(3, -1), axis=1) / np.linalg.norm(B_ref.reshape(3, -1), axis=1)
+    assert rel.max() <= TOL[precision]
+
+
+# ------------------------------------------------------------------ boundary behaviour
+def test_invalid_arguments_are_rejected(torch_cuda, tsr, oracle_basis16):
+    torch = torch_cuda
+    f_ref, _ = oracle_basis16
+    basis = tsr.basis_create(f_ref[:4])
+    pos = torch.zeros((3, 11), device="cuda")
+    with pytest.raises(tsr.TsrError) as e:
+        tsr.precompute_transfer(basis, pos, torch.zeros(11, device="cuda"), torch.zeros((4, 11), device="cuda"))
+    assert e.value.status == -1
+    with pytest.raises(tsr.TsrError) as e:
+        tsr.haar_forward(torch.zeros((2, 10 * 129 * 129 + 2), device="cuda"), 129)
+    assert e.value.status == -1
+    with pytest.raises(tsr.TsrError):
+        tsr.precompute_transfer(basis, torch.zeros((3, 42), device="cuda"), torch.zeros(42, device="cuda"),
+                                torch.zeros((33, 42), device="cuda"))

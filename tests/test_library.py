@@ -1,0 +1,67 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every declared symbol (no GPU needed)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(tsr_[a-z0-9_]+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libtsr():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2203_12339_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("tsr_fit_pca_basis", "tsr_project_material", "tsr_precompute_transfer", "tsr_haar_compress",
+                     "tsr_relight", "tsr_relight_backward", "tsr_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libtsr):
+    missing = [n for n in _declared_functions() if not hasattr(libtsr, n)]
+    assert not missing, missing
+
+
+def test_version_and_error_string_without_gpu(libtsr):
+    libtsr.tsr_version.restype = ctypes.c_int
+    assert libtsr.tsr_version() == 100
+    libtsr.tsr_last_error.restype = ctypes.c_char_p
+    assert isinstance(libtsr.tsr_last_error(), bytes)
+
+
+def test_argument_checks_run_before_any_device_work(libtsr):
+    # NULL handles/pointers are rejected on the host with TSR_ERR_INVALID_ARG.
+    f = libtsr.tsr_precompute_transfer
+    f.restype = ctypes.c_int
+    assert f(None, 100, None, None, None, 4, 1, None, None) == -1
+    g = libtsr.tsr_haar_forward
+    g.restype = ctypes.c_int
+    assert g(None, 1, 4, None, None) == -1
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2203_12339_gb300 import tsr
+    monkeypatch.setattr(tsr, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(tsr, "_lib", None)
+    with pytest.raises(RuntimeError):
+        tsr.lib()
