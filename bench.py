@@ -1,0 +1,376 @@
+"""Benchmark of the translucent-transfer hot path on the 40,962-vertex displaced sphere.
+
+One step = the per-scene path of the method on one synthetic scene:
+  project 64 material edits (Section 2.2, FP64)
+  -> transfer M[k,j,o] = sum_i A_i f_k(r_oi) T[j,i] on the BF16 tensor cores (Eq. 6-7)
+  -> spatial Haar + top-10% keep rule per (k, j) (Section 3.2, Eq. 9-10)
+  -> relight of the 64 edits (Section 4, Steps 3-5)
+  -> reverse mode of relight and projection for L = 0.5 ||B||^2.
+The PCA basis (Eq. 5) is fitted once before timing (a one-time set-up) and its
+time is reported as setup_ms.
+
+metric: transfer G pair.K.J/s = N^2 K J / step time / 1e9 (whole job, all ranks).
+Multi-GPU: every rank processes its own scene (independent problems, weak scaling);
+the only collectives are the barrier and the max of the timings.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of output rows of
+the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "disp40962_k12_j16"
+N_EDITS = 64
+KEEP = 0.10
+METRIC = "transfer G pair.K.J/s"
+UNIT = "G pair.K.J/s"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"tsr_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.remove(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic_record():
+    """DRAM bytes per transfer launch from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "transfer_tc_disp40962_traffic.json")
+    src = os.path.join(ROOT, "paper_2203_12339_gb300", "csrc", "transfer.cu")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        rec = json.load(fh)
+    with open(src, "rb") as fh:
+        sha = hashlib.sha256(fh.read()).hexdigest()
+    if rec.get("source_sha256") != sha:
+        return None
+    return rec.get("traffic_bytes_per_launch")
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2203_12339_gb300 import scene, tsr
+
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    w = scene.WORKLOADS[WORKLOAD]
+    sc = scene.make_scene(w["nu"], K=w["K"], J=w["J"], amp=w["amp"], octaves=w["octaves"], seed=w["seed"] + 100 * rank)
+    N, K, J, nu = sc.n, w["K"], w["J"], w["nu"]
+    sa_pca, ss_pca = scene.pca_materials(256, seed=0)
+    esa, ess, eeta = scene.edit_materials(N_EDITS, seed=5)
+
+    # host inputs (pinned) for the end-to-end measurement
+    h_pos = torch.tensor(sc.mesh.pos.astype(np.float32).T.copy()).pin_memory()
+    h_area = torch.tensor(sc.mesh.area.astype(np.float32)).pin_memory()
+    h_T = torch.tensor(sc.T.astype(np.float32)).pin_memory()
+    h_sa = torch.tensor(esa).pin_memory()
+    h_ss = torch.tensor(ess).pin_memory()
+    h_eta = torch.tensor(eeta).pin_memory()
+    h_light = torch.tensor(sc.light.astype(np.float32)).pin_memory()
+    h_B = torch.empty((N_EDITS, 3, N), dtype=torch.float32).pin_memory()
+    h_grads = torch.empty(N_EDITS * 7 + J, dtype=torch.float32).pin_memory()
+
+    d = {k: v.to(dev) for k, v in dict(pos=h_pos, area=h_area, T=h_T, sa=h_sa, ss=h_ss, eta=h_eta,
+                                         light=h_light).items()}
+    M = torch.empty((K, J, N), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+
+    t0 = time.perf_counter()
+    basis, _ = tsr.fit_pca_basis(torch.tensor(sa_pca, device=dev), torch.tensor(ss_pca, device=dev), 1.3, 1024,
+                                 40.0, K)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+
+    ev_tr = []
+    comp_box = [tsr.haar_compress(M, nu, KEEP)]   # handle reused by every step (tsr_haar_recompress)
+
+    def step(inp):
+        """The per-scene path; returns (B, gradient tensors)."""
+        _, g32, _ = tsr.project_material(basis, inp["sa"], inp["ss"], inp["eta"])
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tsr.precompute_transfer(basis, inp["pos"], inp["area"], inp["T"], "bf16", out=M)
+        e1.record()
+        ev_tr.append((e0, e1))
+        comp = tsr.haar_compress(M, nu, KEEP, out=comp_box[0])
+        B = tsr.relight(comp, g32, inp["light"])
+        dg, dl = tsr.relight_backward(comp, g32, inp["light"], B)          # dL/dB = B for L = 0.5 ||B||^2
+        dsa, dss, de = tsr.project_material_backward(basis, inp["sa"], inp["ss"], inp["eta"], dg)
+        return B, (dsa, dss, de, dl), comp
+
+    def step_e2e():
+        inp = {k: v.to(dev, non_blocking=True) for k, v in dict(pos=h_pos, area=h_area, T=h_T, sa=h_sa, ss=h_ss,
+                                                                 eta=h_eta, light=h_light).items()}
+        B, grads, comp = step(inp)
+        h_B.copy_(B, non_blocking=True)
+        flat = torch.cat([g.reshape(-1).float() for g in grads])
+        h_grads.copy_(flat, non_blocking=True)
+        return comp
+
+    for _ in range(args.warmup):
+        step(d)
+    torch.cuda.synchronize()
+    tsr.stream_status()
+    if world > 1:
+        dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    clocks = Clocks(local)
+    clocks.start()
+    ev_tr.clear()
+    step_ev = []
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step(d)
+        b.record(stream)
+        step_ev.append((a, b))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    tsr.stream_status()
+    ms_steps = [a.elapsed_time(b) for a, b in step_ev]
+    ms_transfer = [a.elapsed_time(b) for a, b in ev_tr]
+    ms_per_step = sum(ms_steps) / len(ms_steps)
+
+    # end-to-end through host buffers
+    e2e_ms = []
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        step_e2e()
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t) * 1e3)
+    e2e_step = sum(e2e_ms) / len(e2e_ms)
+    h2d = sum(t.numel() * t.element_size() for t in (h_pos, h_area, h_T, h_sa, h_ss, h_eta, h_light))
+    d2h = h_B.numel() * h_B.element_size() + h_grads.numel() * h_grads.element_size()
+
+    # relight frame rate: project + relight of the 64 edits from the compressed transfer
+    comp = comp_box[0]
+    fr = []
+    for _ in range(5):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        _, g32, _ = tsr.project_material(basis, d["sa"], d["ss"], d["eta"])
+        tsr.relight(comp, g32, d["light"])
+        b.record()
+        torch.cuda.synchronize()
+        fr.append(a.elapsed_time(b))
+    relight_ms = statistics.median(fr)
+
+    # the same transfer in the other precisions (BF16-TC vs split BF16 vs the FP32 CUDA-core path)
+    by_prec = {"bf16": round(statistics.mean(ms_transfer), 3)}
+    if not args.no_precision_sweep:
+        for prec in ("bf16x3", "fp32"):
+            tsr.precompute_transfer(basis, d["pos"], d["area"], d["T"], prec, out=M)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            flush.zero_()
+            a.record()
+            tsr.precompute_transfer(basis, d["pos"], d["area"], d["T"], prec, out=M)
+            b.record()
+            torch.cuda.synchronize()
+            by_prec[prec] = round(a.elapsed_time(b), 3)
+        tsr.stream_status()
+
+    if world > 1:
+        t = torch.tensor([ms_per_step, e2e_step, statistics.mean(ms_transfer)], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step, e2e_step, tr_mean = t.tolist()
+    else:
+        tr_mean = statistics.mean(ms_transfer)
+
+    units = float(N) * N * K * J
+    value = world * units / (ms_per_step * 1e-3) / 1e9
+    e2e_value = world * units / (e2e_step * 1e-3) / 1e9
+    peaks, peak_kind = _peaks()
+    achieved_tflops = 2.0 * units / (tr_mean * 1e-3) / 1e12
+    peak_tf = peaks.get("bf16_tflops_sustained", 1700.0)
+    traffic = _traffic_record()
+    kernels_per_step = 14   # project, pretile, transfer, haar fwd, select, count, scan, fill, spmm, haar inv,
+                            # haar fwd (adjoint), spmm^T, grad finish, projection backward
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic (seeded displaced icosphere, SH transfer, random materials)",
+        "config": {"workload": f"{WORKLOAD}: N={N}, K={K}, J={J}, 64 edits, top-10% Haar, BF16 tensor cores",
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "per_step": "project -> transfer(bf16) -> haar+select -> relight -> adjoint"},
+        "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": round(e2e_step, 3)},
+        "gpu_launches": kernels_per_step * args.steps,
+        "roofline": {"bound": "tensor", "achieved": round(achieved_tflops, 2), "peak": peak_tf,
+                     "unit": "TFLOP/s", "frac": round(achieved_tflops / peak_tf, 4), "traffic": traffic,
+                     "kernel": "transfer_tc_kernel (BF16 tcgen05), per launch",
+                     "peak_kind": f"bf16 sustained, {peak_kind}"},
+        "transfer_ms": round(tr_mean, 3),
+        "transfer_ms_by_precision": by_prec,
+        "relight_fps": round(1e3 / relight_ms, 1),
+        "setup_ms": round(setup_ms, 1),
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(rows=args.cpu_rows)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _cpu_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 1) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def cpu_baseline(rows: int = 192, seed: int = 7) -> dict:
+    """FP64 oracle transfer on `rows` sampled output vertices of the same workload (all i, all k, j)."""
+    from oracle import tsr_oracle as O
+    from paper_2203_12339_gb300 import scene
+    w = scene.WORKLOADS[WORKLOAD]
+    sc = scene.make_scene(w["nu"], K=w["K"], J=w["J"], amp=w["amp"], octaves=w["octaves"], seed=w["seed"])
+    sa, ss = scene.pca_materials(256, seed=0)
+    f, _ = O.fit_pca_basis(sa, ss, 1.3, 1024, 40.0, w["K"])
+    pos = sc.mesh.pos.astype(np.float32)
+    area = sc.mesh.area.astype(np.float32)
+    T = sc.T.astype(np.float32)
+    sel = scene.sample_rows(sc.n, rows, seed=seed)
+    t = time.perf_counter()
+    O.transfer_rows(f, pos, area, T, sel)
+    dt = time.perf_counter() - t
+    val = rows * sc.n * w["K"] * w["J"] / dt / 1e9
+    return {"value": round(val, 3), "unit": UNIT, "cores": _cpu_threads(), "kind": "oracle",
+            "sample": f"{rows} sampled output rows x all {sc.n} inputs, K={w['K']}, J={w['J']} (FP64 numpy); "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return
+    vals, ms = [], []
+    for _ in range(args.warmup):
+        cpu_baseline(rows=8)
+    for s in range(args.steps):
+        t = time.perf_counter()
+        r = cpu_baseline(rows=args.cpu_rows // 4 or 16, seed=100 + s)
+        ms.append((time.perf_counter() - t) * 1e3)
+        vals.append(r["value"])
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(statistics.mean(ms), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"{WORKLOAD} (oracle on sampled output rows)"},
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": _cpu_threads(), "kind": "oracle",
+                             "sample": f"{args.cpu_rows // 4 or 16} sampled output rows per step"},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-rows", type=int, default=192)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision-sweep", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

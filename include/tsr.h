@@ -178,12 +178,18 @@ tsr_status tsr_haar_inverse(const float *Xw, int rows, int nu, float *X, tsr_str
  * and packs them as a CSR matrix over wavelet rows w (entries: column
  * kj = k*J + j as uint16, value FP32, columns ascending within a row).
  * tsr_haar_compress = tsr_haar_forward of M followed by tsr_wavelet_compress.
- * Both synchronise the stream once (to size the packed arrays).
+ * The packed size is known in advance (K*J*(n_keep + 2) entries), so the
+ * handle's arrays are allocated at creation (cudaMalloc) and filled on the
+ * stream without synchronising.
+ * tsr_haar_recompress re-runs tsr_haar_compress for a new M [K][J][N] into an
+ * existing handle (same K, J, nu and keep rule): no device allocation other
+ * than stream-ordered scratch, so it suits a per-frame or per-step loop.
  * ---------------------------------------------------------------------- */
 tsr_status tsr_wavelet_compress(const float *Mw, int K, int J, int nu, double p, tsr_compressed **out,
                                 tsr_stream stream);
 tsr_status tsr_haar_compress(const float *M, int K, int J, int nu, double p, tsr_compressed **out,
                              tsr_stream stream);
+tsr_status tsr_haar_recompress(const float *M, tsr_compressed *c, tsr_stream stream);
 /* Sizes of a compressed transfer (host out-pointers, any may be NULL). */
 tsr_status tsr_compressed_info(const tsr_compressed *c, int *K, int *J, int *nu, int64_t *nnz,
                                int *n_rows);

@@ -122,6 +122,20 @@ extern "C" tsr_status tsr_haar_compress(const float *M, int K, int J, int nu, do
   return wavelet_compress(static_cast<float *>(mw.p), K, J, nu, p, out, s);
 }
 
+extern "C" tsr_status tsr_haar_recompress(const float *M, tsr_compressed *c, tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(M && c, "tsr_haar_recompress: NULL argument");
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  Scratch mw;
+  st = mw.alloc(sizeof(float) * (size_t)c->K * c->J * c->n_rows, s);
+  if (st != TSR_OK) return st;
+  st = haar_forward(M, c->K * c->J, c->nu, static_cast<float *>(mw.p), s);
+  if (st != TSR_OK) return st;
+  return wavelet_compress_into(static_cast<float *>(mw.p), c, s);
+}
+
 extern "C" tsr_status tsr_compressed_info(const tsr_compressed *c, int *K, int *J, int *nu, int64_t *nnz,
                                           int *n_rows) {
   clear_error();

@@ -38,6 +38,7 @@ tsr_status haar_forward(const float *X, int rows, int nu, float *Xw, cudaStream_
 tsr_status haar_inverse(const float *Xw, int rows, int nu, float *X, cudaStream_t s);
 tsr_status wavelet_compress(const float *Mw, int K, int J, int nu, double p, tsr_compressed **out,
                             cudaStream_t s);
+tsr_status wavelet_compress_into(const float *Mw, tsr_compressed *c, cudaStream_t s);
 tsr_status relight(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,
                    cudaStream_t s);
 tsr_status relight_backward(const tsr_compressed *c, int n_edit, const float *g, const float *l,

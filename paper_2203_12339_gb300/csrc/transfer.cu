@@ -267,9 +267,12 @@ struct TcArgs {
   int K, J;
   int n_otiles, n_kgroups, n_items;
   const float *pos;  // [3][N] (rows o)
+  const float *area; // [N]      (self pair, FP32 epilogue)
+  const float *T;    // [J][N]   (self pair, FP32 epilogue)
   const uint32_t *tab16;   // [n_r + 1][KP] bf16x2
   const float2 *tab32;     // [n_r + 1][KP]
   int KP;
+  int seg_stages;    // stages per accumulation segment (TMEM flushed to M after each)
   float *M;          // [K][J][N]
   unsigned *status;
 };
@@ -283,6 +286,9 @@ struct TcCfg {
   static constexpr int A_STAGE = KS * KB * (SPLIT ? 2 : 1) * A_TILE;
   static constexpr int REC_STAGE = KS * REC;
   static constexpr int TAB_ELEM = SPLIT ? 8 : 4;
+  static constexpr int U = KB * TAB_ELEM / 16;             // 16-byte units per table row
+  static constexpr int NGEN = 256;                         // generator threads (warps 0-7)
+  static constexpr int NTHREADS = NGEN + 32;               // + one control warp (TMA + MMA issue)
   static constexpr int TMEM_COLS = (KB * JP <= 32) ? 32 : (KB * JP <= 64) ? 64 : (KB * JP <= 128) ? 128
                                  : (KB * JP <= 256) ? 256 : 512;
   static size_t smem_bytes(int n_r) {
@@ -290,27 +296,101 @@ struct TcCfg {
   }
 };
 
+// Table rows are U 16-byte units; rotating the units of row m by m/2 (U = 4) or
+// m/4 (U = 2) spreads the rows read by one warp over all eight bank groups.
+template <int U>
+__device__ __forceinline__ int tab_unit(int m, int u) {
+  if (U == 4) return m * 4 + ((u + (m >> 1)) & 3);
+  if (U == 2) return m * 2 + ((u + (m >> 2)) & 1);
+  return m * U + u;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up as soon as another thread raised the abort flag.
+__device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+  for (uint32_t it = 0; it < TSR_WAIT_LIMIT; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+
 template <int KB, int JP, bool SPLIT, int NS, int KS>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
     transfer_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs args) {
   using C = TcCfg<KB, JP, SPLIT, NS, KS>;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // align by pointer arithmetic on the shared array (keeps the shared address space: LDS/STS, not generic)
+  uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t *sA = smem;                                   // NS * A_STAGE
   uint8_t *sRec = sA + (size_t)NS * C::A_STAGE;         // NR * REC_STAGE
   uint8_t *sTab = sRec + (size_t)C::NR * C::REC_STAGE;  // (n_r+1) * KB * TAB_ELEM
   uint64_t *bar = reinterpret_cast<uint64_t *>(sTab + (size_t)(args.n_r + 1) * KB * C::TAB_ELEM);
-  uint64_t *bar_tma = bar;            // [NR]
-  uint64_t *bar_mma = bar + C::NR;    // [NS]
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + C::NR + NS);
+  uint64_t *bar_tma = bar;                        // [NR] records landed
+  uint64_t *bar_full = bar + C::NR;               // [NS] A stage written by all generators
+  uint64_t *bar_mma = bar + C::NR + NS;           // [NS] MMAs of a stage completed
+  uint64_t *bar_tfree = bar + C::NR + 2 * NS;     // [1]  epilogue finished reading TMEM
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + C::NR + 2 * NS + 1);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
+  volatile long *tma_done = reinterpret_cast<volatile long *>(tmem_holder + 2);   // stages whose records generators saw
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
+  // Items: (k-group, 128-row tile).  Each CTA keeps one k-group, so its table
+  // slice is loaded once: CTA b takes group b % G and tiles b / G, b / G + grid / G, ...
+  const int G = args.n_kgroups;
+  const int kgroup = blockIdx.x % G;
+  const int k0 = kgroup * KB;
+  const int tile_first = blockIdx.x / G, tile_step = gridDim.x / G;
+  int my_items = 0;
+  for (int t = tile_first; t < args.n_otiles; t += tile_step) ++my_items;
+  const int stages_per_item = args.n_steps / KS;
+  const long total_stages = (long)my_items * stages_per_item;
+  const int seg_stages = args.seg_stages;
+
   if (tid == 0) {
     for (int q = 0; q < C::NR; ++q) mbar_init(&bar_tma[q], 1);
-    for (int q = 0; q < NS; ++q) mbar_init(&bar_mma[q], 1);
+    for (int q = 0; q < NS; ++q) {
+      mbar_init(&bar_full[q], C::NGEN);
+      mbar_init(&bar_mma[q], 1);
+    }
+    mbar_init(bar_tfree, C::NGEN);
+    *abort_flag = 0;
+    *tma_done = 0;
     fence_mbar_init();
     fence_proxy_async_smem();
+  }
+  // this group's table slice (zero beyond K), rows swizzled by tab_unit
+  {
+    const int n_units = (args.n_r + 1) * C::U;
+    for (int q = tid; q < n_units; q += blockDim.x) {
+      const int m = q / C::U, u = q % C::U;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      uint32_t w[4] = {0u, 0u, 0u, 0u};
+      if (!SPLIT) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int k = k0 + u * 4 + e;
+          if (k < args.K) w[e] = args.tab16[(size_t)m * args.KP + k];
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int k = k0 + u * 2 + e;
+          if (k < args.K) {
+            const float2 f = args.tab32[(size_t)m * args.KP + k];
+            w[2 * e] = __float_as_uint(f.x);
+            w[2 * e + 1] = __float_as_uint(f.y);
+          }
+        }
+      }
+      v = make_uint4(w[0], w[1], w[2], w[3]);
+      reinterpret_cast<uint4 *>(sTab)[tab_unit<C::U>(m, u)] = v;
+    }
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
@@ -322,237 +402,231 @@ __global__ void __launch_bounds__(256, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
-
-  // work of this CTA: items blockIdx.x, blockIdx.x + gridDim.x, ...
-  const int stages_per_item = args.n_steps / KS;
-  int my_items = 0;
-  for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) ++my_items;
-  const long total_stages = (long)my_items * stages_per_item;
-  const uint32_t idesc = umma_idesc_bf16(JP);
   const int rows_per_stage = C::REC_STAGE / 128;
 
-  auto issue_tma = [&](long g) {   // stage g of this CTA's stream -> record slot g % NR
-    const int slot = (int)(g % C::NR);
-    const int stage_in_item = (int)(g % stages_per_item);
-    fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&bar_tma[slot], C::REC_STAGE);
-    tma_load_2d(sRec + (size_t)slot * C::REC_STAGE, &tmap, &bar_tma[slot], 0, stage_in_item * rows_per_stage);
-  };
-  if (tid == 0) {
-    for (long g = 0; g < C::LOOKAHEAD && g < total_stages; ++g) issue_tma(g);
-  }
-
-  const int orow = tid & 127;   // output row within the tile (TMEM lane / A row)
-  const int half = tid >> 7;    // which 8 of the 16 i of a step
-  const uint32_t a_row_off = (uint32_t)((orow >> 3) * 256 + half * 128 + (orow & 7) * 16);
-  const uint32_t sA_u32 = smem_u32(sA);
-  long g = 0;              // stage counter of this CTA
-  long tma_issued = C::LOOKAHEAD < total_stages ? C::LOOKAHEAD : total_stages;
-  long tma_consumed = 0;   // stages whose records were waited for (thread 0's view)
-  long mma_issued = 0;     // stages whose MMAs were committed (thread 0's view)
-  int cur_kgroup = -1;
-  bool ok = true;
-
-  for (int item = blockIdx.x; item < args.n_items && ok; item += gridDim.x) {
-    const int kgroup = item / args.n_otiles;
-    const int otile = item % args.n_otiles;
-    const int k0 = kgroup * KB;
-    if (kgroup != cur_kgroup) {   // load this group's table slice (zero beyond K)
-      __syncthreads();
-      const int n_ent = (args.n_r + 1) * KB;
-      for (int q = tid; q < n_ent; q += blockDim.x) {
-        const int m = q / KB, kb = q % KB, k = k0 + kb;
-        if (SPLIT) {
-          float2 v = make_float2(0.f, 0.f);
-          if (k < args.K) v = args.tab32[(size_t)m * args.KP + k];
-          reinterpret_cast<float2 *>(sTab)[q] = v;
-        } else {
-          uint32_t v = 0;
-          if (k < args.K) v = args.tab16[(size_t)m * args.KP + k];
-          reinterpret_cast<uint32_t *>(sTab)[q] = v;
-        }
-      }
-      __syncthreads();
-      cur_kgroup = kgroup;
-    }
-    const int o = otile * 128 + orow;
-    const float xo = o < args.N ? args.pos[o] : 0.f;
-    const float yo = o < args.N ? args.pos[args.N + o] : 0.f;
-    const float zo = o < args.N ? args.pos[2 * (size_t)args.N + o] : 0.f;
-
-    for (int sidx = 0; sidx < stages_per_item; ++sidx, ++g) {
-      const int sa = (int)(g % NS);
-      const int sr = (int)(g % C::NR);
-      // (1) A buffer sa is free once the MMAs of stage g - NS completed
-      int fail = 0;
-      if (g >= NS) {
-        if (!mbar_wait(&bar_mma[sa], (uint32_t)(((g / NS) - 1) & 1))) fail = 1;
-      }
-      // (2) keep the TMA stream LOOKAHEAD stages ahead
-      if (tid == 0 && !fail && tma_issued < total_stages && tma_issued <= g + C::LOOKAHEAD) {
-        issue_tma(tma_issued);
-        ++tma_issued;
-      }
-      // (3) records of this stage have landed
-      if (!fail && !mbar_wait(&bar_tma[sr], (uint32_t)((g / C::NR) & 1))) fail = 1;
-      if (tid == 0 && !fail) tma_consumed = g + 1;
-      // (4) evaluate F_k[o, i] for this stage into A buffer sa
-      const uint8_t *rec_stage = sRec + (size_t)sr * C::REC_STAGE;
-#pragma unroll
-      for (int ks = 0; ks < KS; ++ks) {
-        const float *rp = reinterpret_cast<const float *>(rec_stage + ks * C::REC + JP * 32 * (SPLIT ? 2 : 1));
-        const int ibase = ((sidx * KS + ks) * 16) + half * 8;
-        int row[8];
-        float tq[8];
-#pragma unroll
-        for (int q = 0; q < 8; q += 4) {
-          const float4 xs = *reinterpret_cast<const float4 *>(rp + half * 8 + q);
-          const float4 ys = *reinterpret_cast<const float4 *>(rp + 16 + half * 8 + q);
-          const float4 zs = *reinterpret_cast<const float4 *>(rp + 32 + half * 8 + q);
-          const float xa[4] = {xs.x, xs.y, xs.z, xs.w}, ya[4] = {ys.x, ys.y, ys.z, ys.w},
-                      za[4] = {zs.x, zs.y, zs.z, zs.w};
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float r2 = pair_r2(xo, yo, zo, xa[u], ya[u], za[u]);
-            const float x = r2 * rsqrtf(fmaxf(r2, 1e-30f)) * args.inv_dr;
-            const int m = max(0, min(static_cast<int>(x), args.n_r - 2));
-            tq[q + u] = x - static_cast<float>(m);
-            const bool valid = (r2 <= args.r2max) && (ibase + q + u < args.N);
-            row[q + u] = valid ? m : args.n_r;
+  if (warp == C::NGEN / 32) {
+    // ------------------------------------------------------------ control warp
+    if (lane == 0) {
+      const uint32_t idesc = umma_idesc_bf16(JP);
+      const uint32_t sA_u32 = smem_u32(sA);
+      long issued = 0;
+      auto issue_tma = [&](long q) {
+        const int slot = (int)(q % C::NR);
+        const int stage_in_item = (int)(q % stages_per_item);
+        mbar_arrive_expect_tx(&bar_tma[slot], C::REC_STAGE);
+        tma_load_2d(sRec + (size_t)slot * C::REC_STAGE, &tmap, &bar_tma[slot], 0, stage_in_item * rows_per_stage);
+      };
+      for (; issued < C::LOOKAHEAD && issued < total_stages; ++issued) issue_tma(issued);
+      long g = 0;
+      int seg_no = 0;   // accumulation segments issued so far
+      for (int t = tile_first; t < args.n_otiles && !*abort_flag; t += tile_step) {
+        for (int sidx = 0; sidx < stages_per_item && !*abort_flag; ++sidx, ++g) {
+          const bool seg_start = (sidx % seg_stages) == 0;
+          // TMA of stage g + LOOKAHEAD reuses the slot of stage g - NS: wait for its MMAs
+          if (issued < total_stages && issued <= g + C::LOOKAHEAD) {
+            const long prev = issued - C::NR;
+            if (prev >= 0 && !wait_or_abort(&bar_mma[prev % NS], (uint32_t)((prev / NS) & 1), abort_flag)) break;
+            issue_tma(issued);
+            ++issued;
           }
-        }
-        const uint32_t a_step = sA_u32 + (uint32_t)(sa * C::A_STAGE) + (uint32_t)(ks * KB * (SPLIT ? 2 : 1) * C::A_TILE);
-        if (!SPLIT) {
-          uint32_t t2[4];
-#pragma unroll
-          for (int p = 0; p < 4; ++p) t2[p] = pack_bf16x2(tq[2 * p], tq[2 * p + 1]);
-          const uint4 *tab4 = reinterpret_cast<const uint4 *>(sTab);
-#pragma unroll
-          for (int kb4 = 0; kb4 < KB / 4; ++kb4) {
-            uint4 w[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) w[q] = tab4[row[q] * (KB / 4) + kb4];
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-              uint32_t outv[4];
-#pragma unroll
-              for (int p = 0; p < 4; ++p) {
-                const uint32_t w0 = (b == 0) ? w[2 * p].x : (b == 1) ? w[2 * p].y : (b == 2) ? w[2 * p].z : w[2 * p].w;
-                const uint32_t w1 = (b == 0) ? w[2 * p + 1].x : (b == 1) ? w[2 * p + 1].y : (b == 2) ? w[2 * p + 1].z : w[2 * p + 1].w;
-                const uint32_t v2 = __byte_perm(w0, w1, 0x5410);
-                const uint32_t s2 = __byte_perm(w0, w1, 0x7632);
-                outv[p] = bf16x2_fma(t2[p], s2, v2);
-              }
-              const int kb = kb4 * 4 + b;
-              st_shared_v4(a_step + (uint32_t)(kb * C::A_TILE) + a_row_off, outv[0], outv[1], outv[2], outv[3]);
-            }
-          }
-        } else {
-          const float4 *tab4 = reinterpret_cast<const float4 *>(sTab);   // {v_k, s_k, v_k+1, s_k+1}
-#pragma unroll
-          for (int kb2 = 0; kb2 < KB / 2; ++kb2) {
-            float F0[8], F1[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const float4 w = tab4[row[q] * (KB / 2) + kb2];
-              F0[q] = fmaf(tq[q], w.y, w.x);
-              F1[q] = fmaf(tq[q], w.w, w.z);
-            }
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-              const float *F = b ? F1 : F0;
-              uint32_t hi[4], lo[4];
-#pragma unroll
-              for (int p = 0; p < 4; ++p) {
-                hi[p] = pack_bf16x2(F[2 * p], F[2 * p + 1]);
-                const float h0 = __uint_as_float(hi[p] << 16), h1 = __uint_as_float(hi[p] & 0xFFFF0000u);
-                lo[p] = pack_bf16x2(F[2 * p] - h0, F[2 * p + 1] - h1);
-              }
-              const int kb = kb2 * 2 + b;
-              st_shared_v4(a_step + (uint32_t)((2 * kb) * C::A_TILE) + a_row_off, hi[0], hi[1], hi[2], hi[3]);
-              st_shared_v4(a_step + (uint32_t)((2 * kb + 1) * C::A_TILE) + a_row_off, lo[0], lo[1], lo[2], lo[3]);
-            }
-          }
-        }
-      }
-      fence_proxy_async_smem();
-      if (__syncthreads_or(fail)) {   // block-uniform decision
-        ok = false;
-        break;
-      }
-      // (5) one thread issues the MMAs of this stage
-      if (tid == 0) {
-        tc_fence_after();
-        const uint32_t rec_u32 = smem_u32(rec_stage);
+          const int sa = (int)(g % NS);
+          if (!wait_or_abort(&bar_full[sa], (uint32_t)((g / NS) & 1), abort_flag)) break;
+          // the epilogue of the previous segment must have read TMEM before it is overwritten
+          if (seg_start && seg_no > 0 && !wait_or_abort(bar_tfree, (uint32_t)((seg_no - 1) & 1), abort_flag)) break;
+          if (seg_start) ++seg_no;
+          tc_fence_after();
+          const uint32_t rec_u32 = smem_u32(sRec + (size_t)(g % C::NR) * C::REC_STAGE);
 #pragma unroll 1
+          for (int ks = 0; ks < KS; ++ks) {
+            const uint32_t b_hi = rec_u32 + ks * C::REC;
+            const uint64_t dbh = umma_desc(b_hi, JP * 16, 128);
+            const uint64_t dbl = umma_desc(b_hi + JP * 32, JP * 16, 128);
+            const uint32_t a_step =
+                sA_u32 + (uint32_t)(sa * C::A_STAGE) + (uint32_t)(ks * KB * (SPLIT ? 2 : 1) * C::A_TILE);
+            const uint32_t first = (seg_start && ks == 0) ? 0u : 1u;
+#pragma unroll 1
+            for (int kb = 0; kb < KB; ++kb) {
+              const uint32_t d = tmem_base + (uint32_t)(kb * JP);
+              if (!SPLIT) {
+                umma_bf16(d, umma_desc(a_step + kb * C::A_TILE, 128, 256), dbh, idesc, first);
+              } else {
+                const uint64_t dah = umma_desc(a_step + (2 * kb) * C::A_TILE, 128, 256);
+                const uint64_t dal = umma_desc(a_step + (2 * kb + 1) * C::A_TILE, 128, 256);
+                umma_bf16(d, dah, dbh, idesc, first);
+                umma_bf16(d, dah, dbl, idesc, 1u);
+                umma_bf16(d, dal, dbh, idesc, 1u);
+              }
+            }
+          }
+          umma_commit(&bar_mma[sa]);
+        }
+      }
+      if (*abort_flag) {   // let copies already issued land before the CTA exits
+        for (long q = *tma_done; q < issued; ++q) {
+          for (uint32_t it = 0; it < TSR_WAIT_LIMIT; ++it)
+            if (mbar_try_wait(&bar_tma[q % C::NR], (uint32_t)((q / C::NR) & 1))) break;
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ generator warps
+    const int orow = tid & 127;   // output row within the tile (TMEM lane / A row)
+    const int half = tid >> 7;    // which 8 of the 16 i of a step
+    const uint32_t a_row_off = (uint32_t)((orow >> 3) * 256 + half * 128 + (orow & 7) * 16);
+    const uint32_t sA_u32 = smem_u32(sA);
+    long g = 0;
+    for (int t = tile_first; t < args.n_otiles; t += tile_step) {
+      if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
+      const int o = t * 128 + orow;
+      const bool o_ok = o < args.N;
+      const float xo = o_ok ? args.pos[o] : 0.f;
+      const float yo = o_ok ? args.pos[args.N + o] : 0.f;
+      const float zo = o_ok ? args.pos[2 * (size_t)args.N + o] : 0.f;
+      bool ok = true;
+      for (int sidx = 0; sidx < stages_per_item; ++sidx, ++g) {
+        const int sa = (int)(g % NS);
+        const int sr = (int)(g % C::NR);
+        bool w_ok = true;
+        if (g >= NS) w_ok = wait_or_abort(&bar_mma[sa], (uint32_t)(((g / NS) - 1) & 1), abort_flag);
+        if (w_ok) w_ok = wait_or_abort(&bar_tma[sr], (uint32_t)((g / C::NR) & 1), abort_flag);
+        if (__any_sync(0xffffffffu, !w_ok)) {
+          ok = false;
+          break;
+        }
+        if (tid == 0) *tma_done = g + 1;
+        const uint8_t *rec_stage = sRec + (size_t)sr * C::REC_STAGE;
+#pragma unroll
         for (int ks = 0; ks < KS; ++ks) {
-          const uint32_t b_hi = rec_u32 + ks * C::REC;
-          const uint64_t dbh = umma_desc(b_hi, JP * 16, 128);
-          const uint64_t dbl = umma_desc(b_hi + JP * 32, JP * 16, 128);
-          const uint32_t a_step = sA_u32 + (uint32_t)(sa * C::A_STAGE) + (uint32_t)(ks * KB * (SPLIT ? 2 : 1) * C::A_TILE);
-          const uint32_t first = (sidx == 0 && ks == 0) ? 0u : 1u;
-#pragma unroll 1
-          for (int kb = 0; kb < KB; ++kb) {
-            const uint32_t d = tmem_base + (uint32_t)(kb * JP);
-            if (!SPLIT) {
-              umma_bf16(d, umma_desc(a_step + kb * C::A_TILE, 128, 256), dbh, idesc, first);
-            } else {
-              const uint64_t dah = umma_desc(a_step + (2 * kb) * C::A_TILE, 128, 256);
-              const uint64_t dal = umma_desc(a_step + (2 * kb + 1) * C::A_TILE, 128, 256);
-              umma_bf16(d, dah, dbh, idesc, first);
-              umma_bf16(d, dah, dbl, idesc, 1u);
-              umma_bf16(d, dal, dbh, idesc, 1u);
+          const float *rp = reinterpret_cast<const float *>(rec_stage + ks * C::REC + JP * 32 * (SPLIT ? 2 : 1));
+          const int ibase = ((sidx * KS + ks) * 16) + half * 8;
+          int row[8];
+          float tq[8];
+#pragma unroll
+          for (int q = 0; q < 8; q += 4) {
+            const float4 xs = *reinterpret_cast<const float4 *>(rp + half * 8 + q);
+            const float4 ys = *reinterpret_cast<const float4 *>(rp + 16 + half * 8 + q);
+            const float4 zs = *reinterpret_cast<const float4 *>(rp + 32 + half * 8 + q);
+            const float xa[4] = {xs.x, xs.y, xs.z, xs.w}, ya[4] = {ys.x, ys.y, ys.z, ys.w},
+                        za[4] = {zs.x, zs.y, zs.z, zs.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int i = ibase + q + u;
+              const float r2 = pair_r2(xo, yo, zo, xa[u], ya[u], za[u]);
+              const float x = r2 * rsqrtf(fmaxf(r2, 1e-30f)) * args.inv_dr;
+              const int m = max(0, min(static_cast<int>(x), args.n_r - 2));
+              tq[q + u] = x - static_cast<float>(m);
+              // the self pair i = o is added exactly in the epilogue
+              const bool valid = (r2 <= args.r2max) && (i < args.N) && (i != o);
+              row[q + u] = valid ? m : args.n_r;
+            }
+          }
+          const uint32_t a_step =
+              sA_u32 + (uint32_t)(sa * C::A_STAGE) + (uint32_t)(ks * KB * (SPLIT ? 2 : 1) * C::A_TILE);
+          if (!SPLIT) {
+            uint32_t t2[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) t2[p] = pack_bf16x2(tq[2 * p], tq[2 * p + 1]);
+            const uint4 *tab4 = reinterpret_cast<const uint4 *>(sTab);
+#pragma unroll
+            for (int kb4 = 0; kb4 < KB / 4; ++kb4) {
+              uint4 w[8];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) w[q] = tab4[tab_unit<C::U>(row[q], kb4)];
+#pragma unroll
+              for (int b = 0; b < 4; ++b) {
+                uint32_t outv[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                  const uint32_t w0 = (b == 0) ? w[2 * p].x : (b == 1) ? w[2 * p].y : (b == 2) ? w[2 * p].z : w[2 * p].w;
+                  const uint32_t w1 = (b == 0) ? w[2 * p + 1].x : (b == 1) ? w[2 * p + 1].y
+                                    : (b == 2) ? w[2 * p + 1].z : w[2 * p + 1].w;
+                  const uint32_t v2 = __byte_perm(w0, w1, 0x5410);
+                  const uint32_t s2 = __byte_perm(w0, w1, 0x7632);
+                  outv[p] = bf16x2_fma(t2[p], s2, v2);
+                }
+                const int kb = kb4 * 4 + b;
+                st_shared_v4(a_step + (uint32_t)(kb * C::A_TILE) + a_row_off, outv[0], outv[1], outv[2], outv[3]);
+              }
+            }
+          } else {
+            const float4 *tab4 = reinterpret_cast<const float4 *>(sTab);   // {v_k, s_k, v_k+1, s_k+1}
+#pragma unroll
+            for (int kb2 = 0; kb2 < KB / 2; ++kb2) {
+              float F0[8], F1[8];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const float4 w = tab4[tab_unit<C::U>(row[q], kb2)];
+                F0[q] = fmaf(tq[q], w.y, w.x);
+                F1[q] = fmaf(tq[q], w.w, w.z);
+              }
+#pragma unroll
+              for (int b = 0; b < 2; ++b) {
+                const float *F = b ? F1 : F0;
+                uint32_t hi[4], lo[4];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                  hi[p] = pack_bf16x2(F[2 * p], F[2 * p + 1]);
+                  const float h0 = __uint_as_float(hi[p] << 16), h1 = __uint_as_float(hi[p] & 0xFFFF0000u);
+                  lo[p] = pack_bf16x2(F[2 * p] - h0, F[2 * p + 1] - h1);
+                }
+                const int kb = kb2 * 2 + b;
+                st_shared_v4(a_step + (uint32_t)((2 * kb) * C::A_TILE) + a_row_off, hi[0], hi[1], hi[2], hi[3]);
+                st_shared_v4(a_step + (uint32_t)((2 * kb + 1) * C::A_TILE) + a_row_off, lo[0], lo[1], lo[2], lo[3]);
+              }
             }
           }
         }
-        umma_commit(&bar_mma[sa]);
-        mma_issued = g + 1;
-      }
-    }
-    if (!ok) break;
-    // (6) epilogue: wait for the last MMAs, TMEM -> registers -> M
-    const long last = g - 1;
-    const int efail = mbar_wait(&bar_mma[last % NS], (uint32_t)((last / NS) & 1)) ? 0 : 1;
-    if (__syncthreads_or(efail)) {
-      ok = false;
-      break;
-    }
-    tc_fence_after();
-    {
-      const int quarter = warp & 3, wh = warp >> 2;
-      const int orow_e = quarter * 32 + lane;
-      const int oe = otile * 128 + orow_e;
-      for (int kb = wh; kb < KB; kb += 2) {
-        const int k = k0 + kb;
+        fence_proxy_async_smem();
+        mbar_arrive(&bar_full[sa]);
+        if ((sidx + 1) % seg_stages != 0 && sidx + 1 != stages_per_item) continue;
+        // end of an accumulation segment: TMEM -> registers -> M.  The tensor-core
+        // FP32 accumulator is flushed every seg_stages steps and summed into M with
+        // round-to-nearest adds; the first segment also adds the self pair in FP32.
+        const int seg_in_item = sidx / seg_stages;
+        const long last = g;
+        const bool e_ok = wait_or_abort(&bar_mma[last % NS], (uint32_t)((last / NS) & 1), abort_flag);
+        if (__any_sync(0xffffffffu, !e_ok)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int quarter = warp & 3, wh = warp >> 2;
+        const int oe = t * 128 + quarter * 32 + lane;
+        const bool oe_ok = oe < args.N;
+        const float a_o = oe_ok ? args.area[oe] : 0.f;
+        for (int kb = wh; kb < KB; kb += 2) {
+          const int k = k0 + kb;
+          const float f0 = (k < args.K) ? args.tab32[k].x : 0.f;   // f_k(0)
 #pragma unroll
-        for (int jc = 0; jc < JP; jc += 16) {
-          uint32_t r[16];
-          tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(kb * JP + jc), r);
-          tmem_ld_wait();
-          if (k < args.K && oe < args.N) {
+          for (int jc = 0; jc < JP; jc += 16) {
+            uint32_t r[16];
+            tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(kb * JP + jc), r);
+            tmem_ld_wait();
+            if (k < args.K && oe_ok) {
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-              const int j = jc + q;
-              if (j < args.J) args.M[((size_t)k * args.J + j) * args.N + oe] = __uint_as_float(r[q]);
+              for (int q = 0; q < 16; ++q) {
+                const int j = jc + q;
+                if (j < args.J) {
+                  float *dst = args.M + ((size_t)k * args.J + j) * args.N + oe;
+                  if (seg_in_item == 0)
+                    *dst = __uint_as_float(r[q]) + f0 * (a_o * args.T[(size_t)j * args.N + oe]);
+                  else
+                    *dst = *dst + __uint_as_float(r[q]);
+                }
+              }
             }
           }
         }
+        tc_fence_before();
+        mbar_arrive(bar_tfree);
       }
+      if (!ok) break;
     }
-    tc_fence_before();
-    __syncthreads();
   }
 
-  // teardown: on abort (block-uniform), give in-flight copies and MMAs a bounded chance to land
   __syncthreads();
-  if (!ok) {
-    if (tid == 0) {
-      report_device_error(args.status, DEV_ERR_TIMEOUT);
-      for (long q = tma_consumed; q < tma_issued; ++q) mbar_wait(&bar_tma[q % C::NR], (uint32_t)((q / C::NR) & 1));
-      if (mma_issued > 0) mbar_wait(&bar_mma[(mma_issued - 1) % NS], (uint32_t)(((mma_issued - 1) / NS) & 1));
-    }
-    __syncthreads();
-  }
+  if (tid == 0 && *abort_flag) report_device_error(args.status, DEV_ERR_TIMEOUT);
   tc_fence_after();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"((uint32_t)C::TMEM_COLS)
@@ -582,6 +656,7 @@ template <int KB, int JP, bool SPLIT, int NS, int KS>
 static tsr_status launch_tc(const TcArgs &a0, const uint8_t *rec, cudaStream_t s) {
   using C = TcCfg<KB, JP, SPLIT, NS, KS>;
   TcArgs a = a0;
+  a.seg_stages = std::max(1, 4096 / (16 * KS));   // flush the tensor-core accumulator every 4,096 i
   a.n_kgroups = (a.K + KB - 1) / KB;
   a.n_items = a.n_otiles * a.n_kgroups;
   const size_t smem = C::smem_bytes(a.n_r);
@@ -609,8 +684,11 @@ static tsr_status launch_tc(const TcArgs &a0, const uint8_t *rec, cudaStream_t s
   }
   auto kern = transfer_tc_kernel<KB, JP, SPLIT, NS, KS>;
   TSR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int grid = std::min(a.n_items, num_sms());
-  kern<<<grid, 256, smem, s>>>(tmap, a);
+  // every CTA keeps one k-group: the grid is a multiple of the group count
+  const int G = a.n_kgroups;
+  int grid = std::min(a.n_items, num_sms());
+  grid = std::max(G, grid / G * G);
+  kern<<<grid, C::NTHREADS, smem, s>>>(tmap, a);
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }
@@ -665,6 +743,8 @@ tsr_status transfer_tc(const tsr_basis *b, int N, const float *pos, const float 
   a.J = J;
   a.n_otiles = (N + 127) / 128;
   a.pos = pos;
+  a.area = area;
+  a.T = T;
   a.tab16 = b->tab16;
   a.tab32 = b->tab32;
   a.KP = b->KP;

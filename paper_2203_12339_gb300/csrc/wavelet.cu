@@ -252,10 +252,26 @@ static int keep_count(double p, int n_coef) {
   return (int)v;
 }
 
+// Selection + packing into an existing handle (its K, J, nu and n_keep).
+tsr_status wavelet_compress_into(const float *Mw, tsr_compressed *c, cudaStream_t s) {
+  const int NW = c->n_rows, n_coef = NW - 2, KJ = c->K * c->J;
+  Scratch keep_s, cnt_s;
+  tsr_status st = keep_s.alloc((size_t)KJ * NW, s);
+  if (st == TSR_OK) st = cnt_s.alloc(sizeof(int64_t) * NW, s);
+  if (st != TSR_OK) return st;
+  uint8_t *keep = static_cast<uint8_t *>(keep_s.p);
+  int64_t *cnt = static_cast<int64_t *>(cnt_s.p);
+  select_kernel<<<KJ, 1024, 0, s>>>(Mw, n_coef, NW, c->n_keep, keep);
+  count_kernel<<<(NW + 255) / 256, 256, 0, s>>>(keep, KJ, NW, cnt);
+  scan_kernel<<<1, 1024, 0, s>>>(cnt, NW, c->row_ptr);
+  fill_kernel<<<(NW + 255) / 256, 256, 0, s>>>(Mw, keep, KJ, NW, c->row_ptr, c->col, c->val);
+  TSR_CUDA(cudaGetLastError());
+  return TSR_OK;
+}
+
 tsr_status wavelet_compress(const float *Mw, int K, int J, int nu, double p, tsr_compressed **out, cudaStream_t s) {
   const int P = chart_side(nu);
   const int n_coef = 10 * P * P, NW = n_coef + 2, KJ = K * J;
-  const int n_keep = keep_count(p, n_coef);
   tsr_compressed *c = new tsr_compressed();
   cudaGetDevice(&c->device);
   c->K = K;
@@ -263,34 +279,20 @@ tsr_status wavelet_compress(const float *Mw, int K, int J, int nu, double p, tsr
   c->nu = nu;
   c->P = P;
   c->n_rows = NW;
-  c->n_keep = n_keep;
-  c->nnz = (int64_t)KJ * (n_keep + 2);
-  Scratch keep_s, cnt_s;
-  tsr_status st = keep_s.alloc((size_t)KJ * NW, s);
-  if (st == TSR_OK) st = cnt_s.alloc(sizeof(int64_t) * NW, s);
-  cudaError_t e = cudaSuccess;
-  if (st == TSR_OK) e = cudaMalloc(&c->row_ptr, sizeof(int64_t) * (NW + 1));
-  if (st == TSR_OK && e == cudaSuccess) e = cudaMalloc(&c->col, sizeof(uint16_t) * c->nnz);
-  if (st == TSR_OK && e == cudaSuccess) e = cudaMalloc(&c->val, sizeof(float) * c->nnz);
-  if (st != TSR_OK || e != cudaSuccess) {
-    if (e != cudaSuccess) {
-      set_error("wavelet_compress: %s", cudaGetErrorString(e));
-      st = e == cudaErrorMemoryAllocation ? TSR_ERR_OOM : TSR_ERR_CUDA;
-    }
-    tsr_compressed_destroy(c);
-    return st;
-  }
-  uint8_t *keep = static_cast<uint8_t *>(keep_s.p);
-  int64_t *cnt = static_cast<int64_t *>(cnt_s.p);
-  select_kernel<<<KJ, 1024, 0, s>>>(Mw, n_coef, NW, n_keep, keep);
-  count_kernel<<<(NW + 255) / 256, 256, 0, s>>>(keep, KJ, NW, cnt);
-  scan_kernel<<<1, 1024, 0, s>>>(cnt, NW, c->row_ptr);
-  fill_kernel<<<(NW + 255) / 256, 256, 0, s>>>(Mw, keep, KJ, NW, c->row_ptr, c->col, c->val);
-  e = cudaGetLastError();
+  c->n_keep = keep_count(p, n_coef);
+  c->nnz = (int64_t)KJ * (c->n_keep + 2);
+  cudaError_t e = cudaMalloc(&c->row_ptr, sizeof(int64_t) * (NW + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&c->col, sizeof(uint16_t) * c->nnz);
+  if (e == cudaSuccess) e = cudaMalloc(&c->val, sizeof(float) * c->nnz);
   if (e != cudaSuccess) {
     set_error("wavelet_compress: %s", cudaGetErrorString(e));
     tsr_compressed_destroy(c);
-    return TSR_ERR_CUDA;
+    return e == cudaErrorMemoryAllocation ? TSR_ERR_OOM : TSR_ERR_CUDA;
+  }
+  tsr_status st = wavelet_compress_into(Mw, c, s);
+  if (st != TSR_OK) {
+    tsr_compressed_destroy(c);
+    return st;
   }
   *out = c;
   return TSR_OK;

@@ -46,6 +46,7 @@ _SIGNATURES = {
     "tsr_haar_inverse": (_I, [_P, _I, _I, _P, _P]),
     "tsr_wavelet_compress": (_I, [_P, _I, _I, _I, _D, ctypes.POINTER(_P), _P]),
     "tsr_haar_compress": (_I, [_P, _I, _I, _I, _D, ctypes.POINTER(_P), _P]),
+    "tsr_haar_recompress": (_I, [_P, _P, _P]),
     "tsr_compressed_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                                  ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_I)]),
     "tsr_compressed_export": (_I, [_P, _P, _P, _P, _P]),
@@ -298,10 +299,18 @@ def wavelet_compress(Mw: torch.Tensor, nu: int, p: float) -> Compressed:
     return Compressed(h)
 
 
-def haar_compress(M: torch.Tensor, nu: int, p: float) -> Compressed:
-    """tsr_haar_compress: forward Haar of M [K][J][N] then the top-p keep rule."""
+def haar_compress(M: torch.Tensor, nu: int, p: float, out: Compressed | None = None) -> Compressed:
+    """tsr_haar_compress: forward Haar of M [K][J][N] then the top-p keep rule.
+
+    With ``out`` (a handle of the same K, J, nu and p) the result is written into
+    it by tsr_haar_recompress, without allocating a new handle."""
     K, J, N = M.shape
     m = _dev(M, torch.float32, (K, J, 10 * nu * nu + 2), "M")
+    if out is not None:
+        if (out.K, out.J, out.nu) != (K, J, nu):
+            raise ValueError("out handle has different K, J or nu")
+        _check(lib().tsr_haar_recompress(_ptr(m), out.handle, _stream()))
+        return out
     h = _P()
     _check(lib().tsr_haar_compress(_ptr(m), K, J, nu, float(p), ctypes.byref(h), _stream()))
     return Compressed(h)
