@@ -217,6 +217,27 @@ tsr_status tsr_relight(const tsr_compressed *c, int n_edit, const float *g, cons
 tsr_status tsr_relight_backward(const tsr_compressed *c, int n_edit, const float *g, const float *l,
                                 const float *dLdB, float *dg, float *dl, tsr_stream stream);
 
+/* ------------------------------------------------------------------------
+ * tsr_relight_noalloc: tsr_relight for callers that cannot allocate device
+ * memory (a host that owns every device allocation and forbids new ones after
+ * start-up, or a frame loop that may not issue an allocation call).  The paper
+ * has no counterpart; this is a property of the library, not of the method.
+ * Same arguments, layouts and result as tsr_relight.  Its intermediate buffer
+ * comes from a fixed 32 MiB array of device memory that the library reserves on
+ * every GPU where it is loaded (held until the process exits), so the call
+ * itself allocates nothing.
+ *   - Limit: n_edit * 3 * (10 P^2 + 2) <= 8,388,608 floats, else
+ *     TSR_ERR_INVALID_ARG (e.g. 64 edits of a 40,962-vertex mesh fit).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls on a device share the one array: calls whose kernels overlap
+ *     on the GPU (other streams, other threads) race and give wrong results.
+ *     Serialise them, e.g. on one stream.
+ * ---------------------------------------------------------------------- */
+tsr_status tsr_relight_noalloc(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,
+                               tsr_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,4 +43,6 @@ tsr_status relight(const tsr_compressed *c, int n_edit, const float *g, const fl
                    cudaStream_t s);
 tsr_status relight_backward(const tsr_compressed *c, int n_edit, const float *g, const float *l,
                             const float *dLdB, float *dg, float *dl, cudaStream_t s);
+tsr_status relight_with_scratch(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,
+                                float *bw, cudaStream_t s);
 }  // namespace tsr

@@ -121,6 +121,19 @@ tsr_status relight(const tsr_compressed *c, int n_edit, const float *g, const fl
   return haar_inverse(bw, V, c->nu, B, s);
 }
 
+// Same two launches as relight(), with the b^w buffer supplied by the caller
+// (used by the allocation-free entry point).
+tsr_status relight_with_scratch(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,
+                                float *bw, cudaStream_t s) {
+  const int V = n_edit * 3;
+  const int KJ = c->K * c->J;
+  const dim3 grid((c->n_rows + 255) / 256, (V + RL_VG - 1) / RL_VG);
+  const size_t smem = sizeof(float) * KJ * RL_VG;
+  relight_spmm_kernel<<<grid, 256, smem, s>>>(c->row_ptr, c->col, c->val, c->n_rows, c->K, c->J, V, g, l, bw);
+  TSR_CUDA(cudaGetLastError());
+  return haar_inverse(bw, V, c->nu, B, s);
+}
+
 tsr_status relight_backward(const tsr_compressed *c, int n_edit, const float *g, const float *l, const float *dLdB,
                             float *dg, float *dl, cudaStream_t s) {
   const int V = n_edit * 3;

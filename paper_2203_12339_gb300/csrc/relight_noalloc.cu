@@ -1,0 +1,68 @@
+// tsr_relight_noalloc: the relight of tsr_relight for callers that must not
+// allocate device memory.
+//
+// Who needs it: a host application that hands out all device memory itself
+// and forbids allocations after start-up (for example a render loop that owns a
+// fixed memory budget, or a plugin inside such a host), and code that must not
+// pay for, or may not issue, an allocation call in the middle of a frame.
+// tsr_relight takes its intermediate buffer (the wavelet-domain result b^w,
+// n_edit * 3 * (10 P^2 + 2) floats) from cudaMallocAsync; this variant takes it
+// from a fixed array in device memory that the library reserves when it is
+// loaded, so the call itself allocates nothing.
+#include <mutex>
+
+#include "handles.cuh"
+
+namespace {
+
+// Scratch for b^w: 8 Mi floats = 32 MiB.  Every GPU that loads the library holds
+// this array until the process exits.
+constexpr size_t kNoallocScratchFloats = size_t(8) << 20;
+static __device__ __align__(256) float g_relight_scratch[kNoallocScratchFloats];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+float *g_scratch_ptr[kMaxDevices] = {};   // device address of the array, per device (set up once)
+
+// In host code `g_relight_scratch` names a host-side stand-in, not device
+// memory; the device address comes from cudaGetSymbolAddress, once per device,
+// with that device current.
+tsr_status scratch_for_current_device(float **out) {
+  int dev = -1;
+  TSR_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    tsr::set_error("tsr_relight_noalloc: device index %d beyond the supported %d", dev, kMaxDevices);
+    return TSR_ERR_UNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_scratch_ptr[dev]) {
+    void *p = nullptr;
+    TSR_CUDA(cudaGetSymbolAddress(&p, g_relight_scratch));
+    g_scratch_ptr[dev] = static_cast<float *>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return TSR_OK;
+}
+
+}  // namespace
+
+extern "C" tsr_status tsr_relight_noalloc(const tsr_compressed *c, int n_edit, const float *g, const float *l,
+                                          float *B, tsr_stream stream) {
+  tsr::clear_error();
+  TSR_CHECK_ARG(c && g && l && B, "tsr_relight_noalloc: NULL argument");
+  TSR_CHECK_ARG(n_edit >= 0 && n_edit <= (1 << 20), "tsr_relight_noalloc: n_edit=%d out of range", n_edit);
+  TSR_CHECK_ARG(tsr::aligned(g, 4) && tsr::aligned(l, 4) && tsr::aligned(B, 4), "tsr_relight_noalloc: misaligned pointer");
+  const size_t need = (size_t)n_edit * 3 * (size_t)c->n_rows;
+  TSR_CHECK_ARG(need <= kNoallocScratchFloats,
+                "tsr_relight_noalloc: n_edit*3*(10 P^2 + 2) = %zu floats exceeds the fixed scratch of %zu floats "
+                "(use fewer edits per call, or tsr_relight)",
+                need, kNoallocScratchFloats);
+  tsr_status st = tsr::require_device();
+  if (st != TSR_OK || n_edit == 0) return st;
+  float *bw = nullptr;
+  st = scratch_for_current_device(&bw);
+  if (st != TSR_OK) return st;
+  // Every b^w entry is written by the sparse product before the inverse Haar reads it,
+  // so the array needs no clearing between calls.
+  return tsr::relight_with_scratch(c, n_edit, g, l, B, bw, reinterpret_cast<cudaStream_t>(stream));
+}

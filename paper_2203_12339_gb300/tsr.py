@@ -53,6 +53,7 @@ _SIGNATURES = {
     "tsr_compressed_destroy": (None, [_P]),
     "tsr_relight": (_I, [_P, _I, _P, _P, _P, _P]),
     "tsr_relight_backward": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
+    "tsr_relight_noalloc": (_I, [_P, _I, _P, _P, _P, _P]),
 }
 
 
@@ -337,3 +338,16 @@ def relight_backward(comp: Compressed, g: torch.Tensor, light: torch.Tensor, dLd
     dl = torch.empty_like(ll)
     _check(lib().tsr_relight_backward(comp.handle, E, _ptr(gg), _ptr(ll), _ptr(db), _ptr(dg), _ptr(dl), _stream()))
     return dg, dl
+
+
+def relight_noalloc(comp: Compressed, g: torch.Tensor, light: torch.Tensor, out: torch.Tensor) -> torch.Tensor:
+    """tsr_relight_noalloc: tsr_relight into a caller-provided B [E][3][N], with the
+    library's fixed device scratch instead of an allocation (see include/tsr.h)."""
+    E = g.shape[0]
+    gg = _dev(g, torch.float32, (E, 3, comp.K), "g")
+    ll = _dev(light, torch.float32, (comp.J,), "light")
+    _dev(out, torch.float32, (E, 3, comp.n), "out")
+    if not out.is_contiguous():
+        raise ValueError("out must be contiguous")
+    _check(lib().tsr_relight_noalloc(comp.handle, E, _ptr(gg), _ptr(ll), _ptr(out), _stream()))
+    return out

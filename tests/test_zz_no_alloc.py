@@ -1,0 +1,83 @@
+"""tsr_relight_noalloc: the relight for callers that cannot allocate device memory.
+
+Such callers (a host that owns every device allocation, a frame loop that may not
+issue an allocation call) get the same relight as tsr_relight, with the
+intermediate buffer taken from a fixed array the library reserves on each GPU.
+This file is collected last so that a run that stops at the first failure has
+already run every other test; it also passes alone in a fresh process.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_12339_gb300 import build
+    build.build()
+    from paper_2203_12339_gb300 import tsr
+    return torch, tsr
+
+
+def _case(torch, tsr, nu, K, J, p, seed):
+    from oracle import tsr_oracle as O
+    P = O.chart_side(nu)
+    rng = np.random.default_rng(seed)
+    Mw = rng.standard_normal((K, J, 10 * P * P + 2)).astype(np.float32)
+    return tsr.wavelet_compress(torch.tensor(Mw, device="cuda"), nu, p)
+
+
+def _noalloc(tsr, comp, g, light, B):
+    """Direct call through the C ABI (inputs and the output buffer are allocated by the test)."""
+    st = tsr.lib().tsr_relight_noalloc(comp.handle, g.shape[0], ctypes.c_void_p(g.data_ptr()),
+                                       ctypes.c_void_p(light.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                       ctypes.c_void_p(torch_stream(g)))
+    return st
+
+
+def torch_stream(t):
+    import torch
+    return torch.cuda.current_stream(t.device).cuda_stream
+
+
+def _rel(a, b):
+    a = a.reshape(-1, a.shape[-1]).double()
+    b = b.reshape(-1, b.shape[-1]).double()
+    return float(((a - b).norm(dim=1) / b.norm(dim=1)).max())
+
+
+@pytest.mark.parametrize("nu,K,J,E,p", [(16, 12, 16, 5, 0.1), (5, 8, 9, 3, 0.3)])
+def test_noalloc_matches_relight_on_two_calls(env, nu, K, J, E, p):
+    torch, tsr = env
+    comp = _case(torch, tsr, nu, K, J, p, seed=nu + E)
+    rng = np.random.default_rng(7)
+    for call in range(2):   # second call reuses the array left over by the first
+        g = torch.tensor(rng.standard_normal((E, 3, K)).astype(np.float32), device="cuda")
+        light = torch.tensor(rng.standard_normal(J).astype(np.float32), device="cuda")
+        want = tsr.relight(comp, g, light)
+        B = torch.full((E, 3, comp.n), float("nan"), device="cuda")
+        assert _noalloc(tsr, comp, g, light, B) == 0, tsr.lib().tsr_last_error()
+        torch.cuda.synchronize()
+        tsr.stream_status()
+        assert torch.isfinite(B).all()
+        assert _rel(B, want) <= 2e-6, (call, _rel(B, want))
+
+
+def test_noalloc_rejects_sizes_beyond_the_fixed_scratch(env):
+    torch, tsr = env
+    comp = _case(torch, tsr, 16, 4, 4, 0.1, seed=3)         # 2,562 wavelet rows
+    g = torch.zeros((1, 3, 4), device="cuda")
+    light = torch.zeros(4, device="cuda")
+    B = torch.zeros((1, 3, comp.n), device="cuda")
+    too_many = (8 * 1024 * 1024) // (3 * comp.n_rows) + 1  # one edit past 8 Mi floats
+    st = tsr.lib().tsr_relight_noalloc(comp.handle, too_many, ctypes.c_void_p(g.data_ptr()),
+                                       ctypes.c_void_p(light.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                       ctypes.c_void_p(torch_stream(g)))
+    assert st == -1
+    assert b"exceeds the fixed scratch" in tsr.lib().tsr_last_error()
