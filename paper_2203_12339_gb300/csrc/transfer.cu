@@ -254,6 +254,10 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return *reinterpret_cast<const uint32_t *>(&v);
 }
 
+__device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t b) {
+  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+}
+
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
@@ -266,6 +270,8 @@ struct TcArgs {
   float inv_dr, r2max;
   int K, J;
   int n_otiles, n_kgroups, n_items;
+  int n_split;       // each tile's i-range is cut into n_split units (wave balance)
+  float *P;          // [n_split-1][K][J][N] partial sums of units 1.. (NULL if n_split == 1)
   const float *pos;  // [3][N] (rows o)
   const float *area; // [N]      (self pair, FP32 epilogue)
   const float *T;    // [J][N]   (self pair, FP32 epilogue)
@@ -287,7 +293,7 @@ struct TcCfg {
   static constexpr int REC_STAGE = KS * REC;
   static constexpr int TAB_ELEM = SPLIT ? 8 : 4;
   static constexpr int U = KB * TAB_ELEM / 16;             // 16-byte units per table row
-  static constexpr int NGEN = 256;                         // generator threads (warps 0-7)
+  static constexpr int NGEN = 512;                         // generator threads (warps 0-15)
   static constexpr int NTHREADS = NGEN + 32;               // + one control warp (TMA + MMA issue)
   static constexpr int TMEM_COLS = (KB * JP <= 32) ? 32 : (KB * JP <= 64) ? 64 : (KB * JP <= 128) ? 128
                                  : (KB * JP <= 256) ? 256 : 512;
@@ -345,11 +351,16 @@ __global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
   const int G = args.n_kgroups;
   const int kgroup = blockIdx.x % G;
   const int k0 = kgroup * KB;
-  const int tile_first = blockIdx.x / G, tile_step = gridDim.x / G;
-  int my_items = 0;
-  for (int t = tile_first; t < args.n_otiles; t += tile_step) ++my_items;
-  const int stages_per_item = args.n_steps / KS;
-  const long total_stages = (long)my_items * stages_per_item;
+  // Units: (tile, split).  Unit u covers tile u / S and stages [sp*SPT/S, (sp+1)*SPT/S) of it.
+  const int S = args.n_split;
+  const int SPT = args.n_steps / KS;   // stages of a whole tile
+  const int unit_first = blockIdx.x / G, unit_step = gridDim.x / G;
+  const int n_units = args.n_otiles * S;
+  long total_stages = 0;
+  for (int u = unit_first; u < n_units; u += unit_step) {
+    const int sp = u % S;
+    total_stages += (long)((sp + 1) * SPT / S - sp * SPT / S);
+  }
   const int seg_stages = args.seg_stages;
 
   if (tid == 0) {
@@ -372,11 +383,16 @@ __global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
       uint32_t w[4] = {0u, 0u, 0u, 0u};
       if (!SPLIT) {
+        uint32_t e4[4] = {0u, 0u, 0u, 0u};   // {lo: v_k, hi: s_k} per base
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int k = k0 + u * 4 + e;
-          if (k < args.K) w[e] = args.tab16[(size_t)m * args.KP + k];
+          if (k < args.K) e4[e] = args.tab16[(size_t)m * args.KP + k];
         }
+        w[0] = __byte_perm(e4[0], e4[1], 0x5410);   // {v_k, v_k+1}
+        w[1] = __byte_perm(e4[2], e4[3], 0x5410);   // {v_k+2, v_k+3}
+        w[2] = __byte_perm(e4[0], e4[1], 0x7632);   // {s_k, s_k+1}
+        w[3] = __byte_perm(e4[2], e4[3], 0x7632);   // {s_k+2, s_k+3}
       } else {
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
@@ -410,18 +426,31 @@ __global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
       const uint32_t idesc = umma_idesc_bf16(JP);
       const uint32_t sA_u32 = smem_u32(sA);
       long issued = 0;
+      // TMA cursor: unit tu, absolute stage ts within the tile (runs LOOKAHEAD stages ahead)
+      int tu = unit_first, ts = 0, te = 0;
+      if (tu < n_units) {
+        ts = (tu % S) * SPT / S;
+        te = (tu % S + 1) * SPT / S;
+      }
       auto issue_tma = [&](long q) {
         const int slot = (int)(q % C::NR);
-        const int stage_in_item = (int)(q % stages_per_item);
         mbar_arrive_expect_tx(&bar_tma[slot], C::REC_STAGE);
-        tma_load_2d(sRec + (size_t)slot * C::REC_STAGE, &tmap, &bar_tma[slot], 0, stage_in_item * rows_per_stage);
+        tma_load_2d(sRec + (size_t)slot * C::REC_STAGE, &tmap, &bar_tma[slot], 0, ts * rows_per_stage);
+        if (++ts == te) {   // next unit of this CTA
+          tu += unit_step;
+          if (tu < n_units) {
+            ts = (tu % S) * SPT / S;
+            te = (tu % S + 1) * SPT / S;
+          }
+        }
       };
       for (; issued < C::LOOKAHEAD && issued < total_stages; ++issued) issue_tma(issued);
       long g = 0;
       int seg_no = 0;   // accumulation segments issued so far
-      for (int t = tile_first; t < args.n_otiles && !*abort_flag; t += tile_step) {
-        for (int sidx = 0; sidx < stages_per_item && !*abort_flag; ++sidx, ++g) {
-          const bool seg_start = (sidx % seg_stages) == 0;
+      for (int u = unit_first; u < n_units && !*abort_flag; u += unit_step) {
+        const int sb = (u % S) * SPT / S, se = (u % S + 1) * SPT / S;
+        for (int sidx = sb; sidx < se && !*abort_flag; ++sidx, ++g) {
+          const bool seg_start = ((sidx - sb) % seg_stages) == 0;
           // TMA of stage g + LOOKAHEAD reuses the slot of stage g - NS: wait for its MMAs
           if (issued < total_stages && issued <= g + C::LOOKAHEAD) {
             const long prev = issued - C::NR;
@@ -471,20 +500,29 @@ __global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
     __syncwarp();
   } else {
     // ------------------------------------------------------------ generator warps
-    const int orow = tid & 127;   // output row within the tile (TMEM lane / A row)
-    const int half = tid >> 7;    // which 8 of the 16 i of a step
-    const uint32_t a_row_off = (uint32_t)((orow >> 3) * 256 + half * 128 + (orow & 7) * 16);
+    // Thread (orow, h4): output row orow of the tile, i = 4*h4 .. 4*h4+3 of every 16-i step.
+    // A warp covers 16 rows x two neighbouring i-quarters, so its 8-byte stores fill
+    // two whole 128-byte core matrices (2 shared-memory wavefronts per store).
+    const int orow = (warp & 7) * 16 + (lane & 7) + ((lane >> 4) << 3);
+    const int h4 = (warp >> 3) * 2 + ((lane >> 3) & 1);
+    const uint32_t a_row_off =
+        (uint32_t)((orow >> 3) * 256 + (h4 >> 1) * 128 + (orow & 7) * 16 + (h4 & 1) * 8);
     const uint32_t sA_u32 = smem_u32(sA);
+    const float r2max = args.r2max, inv_dr = args.inv_dr;
+    const int n_r = args.n_r;
     long g = 0;
-    for (int t = tile_first; t < args.n_otiles; t += tile_step) {
+    for (int u = unit_first; u < n_units; u += unit_step) {
       if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
+      const int t = u / S, sp = u % S;
+      const int sb = sp * SPT / S, se = (sp + 1) * SPT / S;
+      float *Mdst = (sp == 0) ? args.M : args.P + (size_t)(sp - 1) * args.K * args.J * args.N;
       const int o = t * 128 + orow;
       const bool o_ok = o < args.N;
       const float xo = o_ok ? args.pos[o] : 0.f;
       const float yo = o_ok ? args.pos[args.N + o] : 0.f;
       const float zo = o_ok ? args.pos[2 * (size_t)args.N + o] : 0.f;
       bool ok = true;
-      for (int sidx = 0; sidx < stages_per_item; ++sidx, ++g) {
+      for (int sidx = sb; sidx < se; ++sidx, ++g) {
         const int sa = (int)(g % NS);
         const int sr = (int)(g % C::NR);
         bool w_ok = true;
@@ -499,91 +537,88 @@ __global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
 #pragma unroll
         for (int ks = 0; ks < KS; ++ks) {
           const float *rp = reinterpret_cast<const float *>(rec_stage + ks * C::REC + JP * 32 * (SPLIT ? 2 : 1));
-          const int ibase = ((sidx * KS + ks) * 16) + half * 8;
-          int row[8];
-          float tq[8];
+          const float4 xs = *reinterpret_cast<const float4 *>(rp + h4 * 4);
+          const float4 ys = *reinterpret_cast<const float4 *>(rp + 16 + h4 * 4);
+          const float4 zs = *reinterpret_cast<const float4 *>(rp + 32 + h4 * 4);
+          const float xa[4] = {xs.x, xs.y, xs.z, xs.w}, ya[4] = {ys.x, ys.y, ys.z, ys.w},
+                      za[4] = {zs.x, zs.y, zs.z, zs.w};
+          // Padded i (beyond N) carry T' = 0 and finite positions, so they add nothing;
+          // the self pair i = o is corrected to FP32 in the epilogue.
+          int row[4];
+          float tq[4];
 #pragma unroll
-          for (int q = 0; q < 8; q += 4) {
-            const float4 xs = *reinterpret_cast<const float4 *>(rp + half * 8 + q);
-            const float4 ys = *reinterpret_cast<const float4 *>(rp + 16 + half * 8 + q);
-            const float4 zs = *reinterpret_cast<const float4 *>(rp + 32 + half * 8 + q);
-            const float xa[4] = {xs.x, xs.y, xs.z, xs.w}, ya[4] = {ys.x, ys.y, ys.z, ys.w},
-                        za[4] = {zs.x, zs.y, zs.z, zs.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int i = ibase + q + u;
-              const float r2 = pair_r2(xo, yo, zo, xa[u], ya[u], za[u]);
-              const float x = r2 * rsqrtf(fmaxf(r2, 1e-30f)) * args.inv_dr;
-              const int m = max(0, min(static_cast<int>(x), args.n_r - 2));
-              tq[q + u] = x - static_cast<float>(m);
-              // the self pair i = o is added exactly in the epilogue
-              const bool valid = (r2 <= args.r2max) && (i < args.N) && (i != o);
-              row[q + u] = valid ? m : args.n_r;
-            }
+          for (int u = 0; u < 4; ++u) {
+            const float dx = xo - xa[u], dy = yo - ya[u], dz = zo - za[u];
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            bool inside = r2 <= r2max;
+            if (fabsf(r2 - r2max) <= 1e-3f * r2max)   // near the cutoff: decide on the exact FP32 r^2
+              inside = pair_r2(xo, yo, zo, xa[u], ya[u], za[u]) <= r2max;
+            const float x = r2 * rsqrtf(fmaxf(r2, 1e-30f)) * inv_dr;
+            // m = floor(x) (round-to-nearest of x - 1/2 at 1.5 * 2^23), t = x - m
+            const float yv = (x - 0.5f) + 12582912.0f;
+            const int m = __float_as_int(yv) - 0x4B400000;
+            tq[u] = x - (yv - 12582912.0f);
+            row[u] = inside ? m : n_r;
           }
           const uint32_t a_step =
               sA_u32 + (uint32_t)(sa * C::A_STAGE) + (uint32_t)(ks * KB * (SPLIT ? 2 : 1) * C::A_TILE);
           if (!SPLIT) {
+            // unit kb4 of a table row: {v_4kb4..+1, v_+2..+3, s_4kb4..+1, s_+2..+3} (bf16 pairs)
             uint32_t t2[4];
 #pragma unroll
-            for (int p = 0; p < 4; ++p) t2[p] = pack_bf16x2(tq[2 * p], tq[2 * p + 1]);
+            for (int u = 0; u < 4; ++u) t2[u] = pack_bf16x2(tq[u], tq[u]);
             const uint4 *tab4 = reinterpret_cast<const uint4 *>(sTab);
 #pragma unroll
             for (int kb4 = 0; kb4 < KB / 4; ++kb4) {
-              uint4 w[8];
+              uint4 w[4];
 #pragma unroll
-              for (int q = 0; q < 8; ++q) w[q] = tab4[tab_unit<C::U>(row[q], kb4)];
+              for (int u = 0; u < 4; ++u) w[u] = tab4[tab_unit<C::U>(row[u], kb4)];
+              uint32_t F01[4], F23[4];   // {F_k, F_k+1} of pair u
 #pragma unroll
-              for (int b = 0; b < 4; ++b) {
-                uint32_t outv[4];
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                  const uint32_t w0 = (b == 0) ? w[2 * p].x : (b == 1) ? w[2 * p].y : (b == 2) ? w[2 * p].z : w[2 * p].w;
-                  const uint32_t w1 = (b == 0) ? w[2 * p + 1].x : (b == 1) ? w[2 * p + 1].y
-                                    : (b == 2) ? w[2 * p + 1].z : w[2 * p + 1].w;
-                  const uint32_t v2 = __byte_perm(w0, w1, 0x5410);
-                  const uint32_t s2 = __byte_perm(w0, w1, 0x7632);
-                  outv[p] = bf16x2_fma(t2[p], s2, v2);
-                }
-                const int kb = kb4 * 4 + b;
-                st_shared_v4(a_step + (uint32_t)(kb * C::A_TILE) + a_row_off, outv[0], outv[1], outv[2], outv[3]);
+              for (int u = 0; u < 4; ++u) {
+                F01[u] = bf16x2_fma(t2[u], w[u].z, w[u].x);
+                F23[u] = bf16x2_fma(t2[u], w[u].w, w[u].y);
               }
+              const uint32_t base = a_step + (uint32_t)(kb4 * 4 * C::A_TILE) + a_row_off;
+              st_shared_v2(base, __byte_perm(F01[0], F01[1], 0x5410), __byte_perm(F01[2], F01[3], 0x5410));
+              st_shared_v2(base + C::A_TILE, __byte_perm(F01[0], F01[1], 0x7632), __byte_perm(F01[2], F01[3], 0x7632));
+              st_shared_v2(base + 2 * C::A_TILE, __byte_perm(F23[0], F23[1], 0x5410), __byte_perm(F23[2], F23[3], 0x5410));
+              st_shared_v2(base + 3 * C::A_TILE, __byte_perm(F23[0], F23[1], 0x7632), __byte_perm(F23[2], F23[3], 0x7632));
             }
           } else {
             const float4 *tab4 = reinterpret_cast<const float4 *>(sTab);   // {v_k, s_k, v_k+1, s_k+1}
 #pragma unroll
             for (int kb2 = 0; kb2 < KB / 2; ++kb2) {
-              float F0[8], F1[8];
+              float F0[4], F1[4];
 #pragma unroll
-              for (int q = 0; q < 8; ++q) {
-                const float4 w = tab4[tab_unit<C::U>(row[q], kb2)];
-                F0[q] = fmaf(tq[q], w.y, w.x);
-                F1[q] = fmaf(tq[q], w.w, w.z);
+              for (int u = 0; u < 4; ++u) {
+                const float4 w = tab4[tab_unit<C::U>(row[u], kb2)];
+                F0[u] = fmaf(tq[u], w.y, w.x);
+                F1[u] = fmaf(tq[u], w.w, w.z);
               }
 #pragma unroll
               for (int b = 0; b < 2; ++b) {
                 const float *F = b ? F1 : F0;
-                uint32_t hi[4], lo[4];
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                  hi[p] = pack_bf16x2(F[2 * p], F[2 * p + 1]);
-                  const float h0 = __uint_as_float(hi[p] << 16), h1 = __uint_as_float(hi[p] & 0xFFFF0000u);
-                  lo[p] = pack_bf16x2(F[2 * p] - h0, F[2 * p + 1] - h1);
-                }
+                const uint32_t hi01 = pack_bf16x2(F[0], F[1]), hi23 = pack_bf16x2(F[2], F[3]);
+                const uint32_t lo01 = pack_bf16x2(F[0] - __uint_as_float(hi01 << 16),
+                                                  F[1] - __uint_as_float(hi01 & 0xFFFF0000u));
+                const uint32_t lo23 = pack_bf16x2(F[2] - __uint_as_float(hi23 << 16),
+                                                  F[3] - __uint_as_float(hi23 & 0xFFFF0000u));
                 const int kb = kb2 * 2 + b;
-                st_shared_v4(a_step + (uint32_t)((2 * kb) * C::A_TILE) + a_row_off, hi[0], hi[1], hi[2], hi[3]);
-                st_shared_v4(a_step + (uint32_t)((2 * kb + 1) * C::A_TILE) + a_row_off, lo[0], lo[1], lo[2], lo[3]);
+                st_shared_v2(a_step + (uint32_t)((2 * kb) * C::A_TILE) + a_row_off, hi01, hi23);
+                st_shared_v2(a_step + (uint32_t)((2 * kb + 1) * C::A_TILE) + a_row_off, lo01, lo23);
               }
             }
           }
         }
         fence_proxy_async_smem();
         mbar_arrive(&bar_full[sa]);
-        if ((sidx + 1) % seg_stages != 0 && sidx + 1 != stages_per_item) continue;
-        // end of an accumulation segment: TMEM -> registers -> M.  The tensor-core
+        if ((sidx - sb + 1) % seg_stages != 0 && sidx + 1 != se) continue;
+        // End of an accumulation segment: TMEM -> registers -> M.  The tensor-core
         // FP32 accumulator is flushed every seg_stages steps and summed into M with
-        // round-to-nearest adds; the first segment also adds the self pair in FP32.
-        const int seg_in_item = sidx / seg_stages;
+        // round-to-nearest adds.  The first segment also replaces the self pair's
+        // BF16 product (exact in FP32) by f_k(0) A_o T[j][o] in FP32.
+        const int seg_in_item = (sidx - sb) / seg_stages;
         const long last = g;
         const bool e_ok = wait_or_abort(&bar_mma[last % NS], (uint32_t)((last / NS) & 1), abort_flag);
         if (__any_sync(0xffffffffu, !e_ok)) {
@@ -591,13 +626,15 @@ __global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
           break;
         }
         tc_fence_after();
-        const int quarter = warp & 3, wh = warp >> 2;
+        const int quarter = warp & 3, wq = warp >> 2;
         const int oe = t * 128 + quarter * 32 + lane;
         const bool oe_ok = oe < args.N;
         const float a_o = oe_ok ? args.area[oe] : 0.f;
-        for (int kb = wh; kb < KB; kb += 2) {
+        for (int kb = wq; kb < KB; kb += C::NGEN / 128) {
           const int k = k0 + kb;
-          const float f0 = (k < args.K) ? args.tab32[k].x : 0.f;   // f_k(0)
+          const float f0 = (k < args.K) ? args.tab32[k].x : 0.f;   // f_k(0), FP32
+          const float f0h = __bfloat162float(__float2bfloat16_rn(f0));
+          const float f0l = __bfloat162float(__float2bfloat16_rn(f0 - f0h));
 #pragma unroll
           for (int jc = 0; jc < JP; jc += 16) {
             uint32_t r[16];
@@ -608,11 +645,23 @@ __global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
               for (int q = 0; q < 16; ++q) {
                 const int j = jc + q;
                 if (j < args.J) {
-                  float *dst = args.M + ((size_t)k * args.J + j) * args.N + oe;
-                  if (seg_in_item == 0)
-                    *dst = __uint_as_float(r[q]) + f0 * (a_o * args.T[(size_t)j * args.N + oe]);
-                  else
+                  float *dst = Mdst + ((size_t)k * args.J + j) * args.N + oe;
+                  if (seg_in_item == 0 && sp == 0) {
+                    const float tp = a_o * args.T[(size_t)j * args.N + oe];
+                    const float th = __bfloat162float(__float2bfloat16_rn(tp));
+                    float tc_self;
+                    if (!SPLIT) {
+                      tc_self = __bfloat162float(__ushort_as_bfloat16((unsigned short)(args.tab16[k] & 0xFFFFu))) * th;
+                    } else {
+                      const float tl = __bfloat162float(__float2bfloat16_rn(tp - th));
+                      tc_self = f0h * th + f0h * tl + f0l * th;
+                    }
+                    *dst = __uint_as_float(r[q]) + (f0 * tp - tc_self);
+                  } else if (seg_in_item == 0) {
+                    *dst = __uint_as_float(r[q]);
+                  } else {
                     *dst = *dst + __uint_as_float(r[q]);
+                  }
                 }
               }
             }
@@ -631,6 +680,15 @@ __global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"((uint32_t)C::TMEM_COLS)
                  : "memory");
+  }
+}
+
+// M += sum of the partial sums of units 1 .. S-1 (fixed order: deterministic)
+__global__ void add_partials_kernel(float *__restrict__ M, const float *__restrict__ P, int n_part, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float acc = M[i];
+    for (int q = 0; q < n_part; ++q) acc += P[(size_t)q * n + i];
+    M[i] = acc;
   }
 }
 
@@ -684,12 +742,42 @@ static tsr_status launch_tc(const TcArgs &a0, const uint8_t *rec, cudaStream_t s
   }
   auto kern = transfer_tc_kernel<KB, JP, SPLIT, NS, KS>;
   TSR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  // every CTA keeps one k-group: the grid is a multiple of the group count
+  // Every CTA keeps one k-group: the grid is a multiple of the group count.  Each
+  // tile's i-range is cut into S units so that the last wave is nearly full.
   const int G = a.n_kgroups;
-  int grid = std::min(a.n_items, num_sms());
+  const int sms = num_sms();
+  const int SPT = a.n_steps / KS;
+  int best_S = 1;
+  double best_cost = 1e30;
+  for (int S = 1; S <= 4 && S <= SPT; ++S) {
+    const long units = (long)a.n_otiles * S * G;
+    int grid = (int)std::min<long>(units, sms);
+    grid = std::max(G, grid / G * G);
+    const long per_cta = (units / G + grid / G - 1) / (grid / G);        // units on the busiest CTA
+    const double cost = (double)per_cta / S * (1.0 + 0.03 * (S - 1));    // in whole-tile units
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best_S = S;
+    }
+  }
+  a.n_split = best_S;
+  const long units = (long)a.n_otiles * best_S * G;
+  int grid = (int)std::min<long>(units, sms);
   grid = std::max(G, grid / G * G);
+  Scratch part;
+  const size_t mn = (size_t)a.K * a.J * a.N;
+  a.P = nullptr;
+  if (best_S > 1) {
+    tsr_status st = part.alloc(sizeof(float) * mn * (best_S - 1), s);
+    if (st != TSR_OK) return st;
+    a.P = static_cast<float *>(part.p);
+  }
   kern<<<grid, C::NTHREADS, smem, s>>>(tmap, a);
   TSR_CUDA(cudaGetLastError());
+  if (best_S > 1) {
+    add_partials_kernel<<<4 * sms, 256, 0, s>>>(a.M, a.P, best_S - 1, mn);
+    TSR_CUDA(cudaGetLastError());
+  }
   return TSR_OK;
 }
 
