@@ -2,6 +2,7 @@
 // the lookup tables of the radial basis, and the material projection
 // g_k = sum_m f_k(r_m) R_d(r_m) with its Jacobian and vector-Jacobian product.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "dipole.cuh"
@@ -172,9 +173,50 @@ __global__ void build_tables_kernel(const double *__restrict__ f, int K, int KP,
   tab16[idx] = (uint32_t)__bfloat16_as_ushort(bv) | ((uint32_t)__bfloat16_as_ushort(bs) << 16);
 }
 
+// Chebyshev projection of the piecewise-linear f_k on [r_near, r_max] in the
+// variable x = 2 (ln r - ln r_near)/(ln r_max - ln r_near) - 1, at the nodes
+// x_n = cos(theta_n), theta_n = pi (n + 1/2)/N:
+//   c_p = (2 - [p = 0]) / N * sum_n f_k(r(x_n)) cos(p theta_n).
+// One block per basis function, FP64.
+__global__ void __launch_bounds__(256) cheb_fit_kernel(const double *__restrict__ f, int n_r, double r_max,
+                                                       double r_near, float *__restrict__ cheb) {
+  __shared__ double red[TSR_CHEB_P * 32];
+  const int k = blockIdx.x;
+  const double lo = log(r_near), hi = log(r_max), dr = r_max / (n_r - 1);
+  double acc[TSR_CHEB_P];
+#pragma unroll
+  for (int p = 0; p < TSR_CHEB_P; ++p) acc[p] = 0.0;
+  for (int n = threadIdx.x; n < TSR_CHEB_NODES; n += blockDim.x) {
+    const double th = 3.14159265358979323846 * (n + 0.5) / TSR_CHEB_NODES;
+    const double x = cos(th);
+    const double r = exp(lo + 0.5 * (x + 1.0) * (hi - lo));
+    const double xm = r / dr;
+    int m = (int)floor(xm);
+    if (m > n_r - 2) m = n_r - 2;
+    if (m < 0) m = 0;
+    const double t = xm - m;
+    const double fv = f[(size_t)k * n_r + m] * (1.0 - t) + f[(size_t)k * n_r + m + 1] * t;
+#pragma unroll
+    for (int p = 0; p < TSR_CHEB_P; ++p) acc[p] += fv * cos(p * th);
+  }
+  block_sum<TSR_CHEB_P>(acc, red);
+  if (threadIdx.x < TSR_CHEB_P) {
+    const int p = threadIdx.x;
+    cheb[k * TSR_CHEB_P + p] = (float)((p == 0 ? 1.0 : 2.0) / TSR_CHEB_NODES * acc[p]);
+  }
+}
+
 tsr_status basis_build_tables(tsr_basis *b, cudaStream_t s) {
   const int n = (b->n_r + 1) * b->KP;
   build_tables_kernel<<<(n + 255) / 256, 256, 0, s>>>(b->f64, b->K, b->KP, b->n_r, b->tab32, b->tab16);
+  TSR_CUDA(cudaGetLastError());
+  // far-field series on [r_near, r_max], r_near = 3/40 r_max
+  b->r_near = 0.075 * b->r_max;
+  const double lo = std::log(b->r_near), hi = std::log(b->r_max);
+  b->x_alpha = (float)(std::log(2.0) / (hi - lo));
+  b->x_beta = (float)(-1.0 - 2.0 * lo / (hi - lo));
+  if (!b->cheb) TSR_CUDA(cudaMalloc(&b->cheb, sizeof(float) * b->K * TSR_CHEB_P));
+  cheb_fit_kernel<<<b->K, 256, 0, s>>>(b->f64, b->n_r, b->r_max, b->r_near, b->cheb);
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }
@@ -410,6 +452,7 @@ extern "C" void tsr_basis_destroy(tsr_basis *b) {
   cudaFree(b->f64);
   cudaFree(b->tab32);
   cudaFree(b->tab16);
+  cudaFree(b->cheb);
   delete b;
 }
 

@@ -12,7 +12,14 @@ struct tsr_basis {
   double *f64 = nullptr;        // [K][n_r]
   float2 *tab32 = nullptr;      // [n_r + 1][KP]  {f_k(r_m), f_k(r_m+1) - f_k(r_m)}
   uint32_t *tab16 = nullptr;    // [n_r + 1][KP]  bf16x2 {lo: value, hi: slope}
+  // Far field: for r_near <= r <= r_max, f_k(r) ~= sum_p cheb[k][p] T_p(x),
+  // x = x_alpha log2(r^2) + x_beta in [-1, 1] (linear in log r).
+  float *cheb = nullptr;        // [K][TSR_CHEB_P]
+  double r_near = 0.0;
+  float x_alpha = 0.f, x_beta = 0.f;
 };
+#define TSR_CHEB_P 16          // Chebyshev terms of the far field
+#define TSR_CHEB_NODES 256     // Chebyshev nodes of the projection
 
 // Compressed wavelet transfer: CSR over wavelet rows w in [0, 10 P^2 + 2).
 struct tsr_compressed {

@@ -23,6 +23,7 @@
 // x = r / dr, m = min(floor(x), n_r - 2), t = x - m and
 // f_k(r) = v_k[m] + t s_k[m] (s_k = f_k[m+1] - f_k[m]).
 #include <algorithm>
+#include <cstdlib>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <mutex>
@@ -258,47 +259,76 @@ __device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t
   asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
 }
 
+// hi/lo BF16 split of four consecutive-i values; hi tile at addr, lo tile at addr + lo_off
+__device__ __forceinline__ void store_split4(uint32_t addr, uint32_t lo_off, float f0, float f1, float f2, float f3) {
+  const __nv_bfloat162 h01 = __floats2bfloat162_rn(f0, f1), h23 = __floats2bfloat162_rn(f2, f3);
+  const float2 g01 = __bfloat1622float2(h01), g23 = __bfloat1622float2(h23);
+  const __nv_bfloat162 l01 = __floats2bfloat162_rn(f0 - g01.x, f1 - g01.y), l23 = __floats2bfloat162_rn(f2 - g23.x, f3 - g23.y);
+  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(*reinterpret_cast<const uint32_t *>(&h01)),
+               "r"(*reinterpret_cast<const uint32_t *>(&h23))
+               : "memory");
+  asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr + lo_off), "r"(*reinterpret_cast<const uint32_t *>(&l01)),
+               "r"(*reinterpret_cast<const uint32_t *>(&l23))
+               : "memory");
+}
+
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
 // ---------------------------------------------------------------- the kernel
+// One pipeline, two generators of the A operand (128 output rows x 16 i per step):
+//  * MODE_NEAR: A[o][i] = f_k(r_oi), k in the CTA's group of CB bases, from the
+//    shared-memory table, for the pairs with r_oi^2 < rn2 (rn2 = +inf: all pairs);
+//    the pass visits only the i-chunks listed for the tile (NULL list: all).
+//  * MODE_FAR:  A[o][i] = phi_p(r_oi) = T_p(x(r_oi)), p in the CTA's group of CB
+//    Chebyshev columns, x = alpha log2(r^2) + beta, for rn2 <= r^2 <= r_max^2,
+//    evaluated in registers by the recurrence T_{p+1} = 2x T_p - T_{p-1}.  The
+//    accumulators hold G[p][j] = sum_i phi_p(r_oi) T'[j][i]; the epilogue forms
+//    M[k][j] = sum_p C[k][p] G[p][j].
+enum { MODE_NEAR = 0, MODE_FAR = 1 };
+
 struct TcArgs {
   int N;             // vertices (rows o and columns i)
-  int n_steps;       // 16-i steps (records), a multiple of KS
+  int n_steps;       // 16-i records
   int n_r;           // radius samples
-  float inv_dr, r2max;
-  int K, J;
-  int n_otiles, n_kgroups, n_items;
-  int n_split;       // each tile's i-range is cut into n_split units (wave balance)
-  float *P;          // [n_split-1][K][J][N] partial sums of units 1.. (NULL if n_split == 1)
+  float inv_dr, r2max, rn2;
+  int K, J, KP;
+  int n_otiles, n_groups, n_split;
   const float *pos;  // [3][N] (rows o)
   const float *area; // [N]      (self pair, FP32 epilogue)
   const float *T;    // [J][N]   (self pair, FP32 epilogue)
   const uint32_t *tab16;   // [n_r + 1][KP] bf16x2
   const float2 *tab32;     // [n_r + 1][KP]
-  int KP;
-  int seg_stages;    // stages per accumulation segment (TMEM flushed to M after each)
+  const int *near_off;     // [n_otiles + 1] or NULL
+  const int *near_idx;     // chunk indices of tile t: near_idx[near_off[t] .. near_off[t+1])
+  const float *cheb;       // [K][PCH]
+  int PCH;
+  float x_alpha, x_beta;
+  int seg_stages;    // stages per accumulation segment (TMEM flushed after each)
+  int accumulate;    // destination 0 (M) is accumulated into instead of overwritten
   float *M;          // [K][J][N]
+  float *P;          // [n_dest - 1][K][J][N] partial sums (NULL if one destination)
   unsigned *status;
 };
 
-template <int KB, int JP, bool SPLIT, int NS, int KS>
+template <int MODE, int CB, int JP, bool SPLIT, int NS>
 struct TcCfg {
-  static constexpr int NR = NS + 2;                        // record stages (TMA runs 2 stages ahead)
-  static constexpr int LOOKAHEAD = 2;
+  static constexpr int LOOKAHEAD = 8;                      // records in flight ahead of the generators
+  static constexpr int NR = NS + LOOKAHEAD;                // record slots
   static constexpr int REC = rec_bytes(JP, SPLIT);
-  static constexpr int A_TILE = 128 * 16 * 2;              // one (base, 16-i step) BF16 tile
-  static constexpr int A_STAGE = KS * KB * (SPLIT ? 2 : 1) * A_TILE;
-  static constexpr int REC_STAGE = KS * REC;
-  static constexpr int TAB_ELEM = SPLIT ? 8 : 4;
-  static constexpr int U = KB * TAB_ELEM / 16;             // 16-byte units per table row
+  static constexpr int A_TILE = 128 * 16 * 2;              // one (column, 16-i step) BF16 tile
+  static constexpr int A_STAGE = CB * (SPLIT ? 2 : 1) * A_TILE;
+  static constexpr int REC_STAGE = REC;
+  static constexpr int TAB_ELEM = (MODE == MODE_NEAR) ? (SPLIT ? 8 : 4) : 0;
+  static constexpr int U = (MODE == MODE_NEAR) ? CB * TAB_ELEM / 16 : 1;   // 16-byte units per table row
   static constexpr int NGEN = 512;                         // generator threads (warps 0-15)
   static constexpr int NTHREADS = NGEN + 32;               // + one control warp (TMA + MMA issue)
-  static constexpr int TMEM_COLS = (KB * JP <= 32) ? 32 : (KB * JP <= 64) ? 64 : (KB * JP <= 128) ? 128
-                                 : (KB * JP <= 256) ? 256 : 512;
-  static size_t smem_bytes(int n_r) {
-    return 1024 + (size_t)NS * A_STAGE + (size_t)NR * REC_STAGE + (size_t)(n_r + 1) * KB * TAB_ELEM + 256;
+  static constexpr int TMEM_COLS = (CB * JP <= 32) ? 32 : (CB * JP <= 64) ? 64 : (CB * JP <= 128) ? 128
+                                 : (CB * JP <= 256) ? 256 : 512;
+  static size_t smem_bytes(int n_r, int K) {
+    return 1024 + (size_t)NS * A_STAGE + (size_t)NR * REC_STAGE + (size_t)(n_r + 1) * CB * TAB_ELEM +
+           (MODE == MODE_FAR ? (size_t)K * CB * sizeof(float) : 0) + 256;
   }
 };
 
@@ -325,17 +355,48 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, vo
   return false;
 }
 
-template <int KB, int JP, bool SPLIT, int NS, int KS>
-__global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
+// Squared distance with a fixed operation order (the near/far split of both
+// passes must classify every pair identically).
+__device__ __forceinline__ float pair_r2_fma(float xo, float yo, float zo, float xi, float yi, float zi) {
+  const float dx = __fsub_rn(xo, xi), dy = __fsub_rn(yo, yi), dz = __fsub_rn(zo, zi);
+  return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
+__device__ __forceinline__ float fast_lg2(float x) {
+  float y;
+  asm("lg2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Stage range [b, e) of unit u (tile t, split sp); stage q maps to record chunk_at(q).
+__device__ __forceinline__ void unit_range(const int *near_off, int u, int S, int SPT, int &t, int &sp, int &b,
+                                           int &e) {
+  t = u / S;
+  sp = u % S;
+  if (near_off) {
+    const int n0 = near_off[t], n = near_off[t + 1] - n0;
+    b = n0 + sp * n / S;
+    e = n0 + (sp + 1) * n / S;
+  } else {
+    b = sp * SPT / S;
+    e = (sp + 1) * SPT / S;
+  }
+}
+__device__ __forceinline__ int chunk_at(const int *near_idx, int q) { return near_idx ? near_idx[q] : q; }
+
+template <int MODE, int CB, int JP, bool SPLIT, int NS>
+__global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
     transfer_tc_kernel(const __grid_constant__ CUtensorMap tmap, const TcArgs args) {
-  using C = TcCfg<KB, JP, SPLIT, NS, KS>;
+  using C = TcCfg<MODE, CB, JP, SPLIT, NS>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // align by pointer arithmetic on the shared array (keeps the shared address space: LDS/STS, not generic)
   uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t *sA = smem;                                   // NS * A_STAGE
   uint8_t *sRec = sA + (size_t)NS * C::A_STAGE;         // NR * REC_STAGE
-  uint8_t *sTab = sRec + (size_t)C::NR * C::REC_STAGE;  // (n_r+1) * KB * TAB_ELEM
-  uint64_t *bar = reinterpret_cast<uint64_t *>(sTab + (size_t)(args.n_r + 1) * KB * C::TAB_ELEM);
+  uint8_t *sTab = sRec + (size_t)C::NR * C::REC_STAGE;  // (n_r+1) * CB * TAB_ELEM   (MODE_NEAR)
+  float *sC = reinterpret_cast<float *>(sTab + (size_t)(args.n_r + 1) * CB * C::TAB_ELEM);   // [K][CB] (MODE_FAR)
+  uint64_t *bar = reinterpret_cast<uint64_t *>(
+      reinterpret_cast<uint8_t *>(sC) + (MODE == MODE_FAR ? (((size_t)args.K * CB * 4 + 15) / 16) * 16 : 0));
   uint64_t *bar_tma = bar;                        // [NR] records landed
   uint64_t *bar_full = bar + C::NR;               // [NS] A stage written by all generators
   uint64_t *bar_mma = bar + C::NR + NS;           // [NS] MMAs of a stage completed
@@ -346,22 +407,25 @@ __global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  // Items: (k-group, 128-row tile).  Each CTA keeps one k-group, so its table
-  // slice is loaded once: CTA b takes group b % G and tiles b / G, b / G + grid / G, ...
-  const int G = args.n_kgroups;
-  const int kgroup = blockIdx.x % G;
-  const int k0 = kgroup * KB;
-  // Units: (tile, split).  Unit u covers tile u / S and stages [sp*SPT/S, (sp+1)*SPT/S) of it.
+  // Each CTA keeps one column group (bases or Chebyshev columns): CTA b takes
+  // group b % G and units b / G, b / G + grid / G, ... of that group.
+  const int G = args.n_groups;
+  const int group = blockIdx.x % G;
+  const int c0 = group * CB;        // first basis (MODE_NEAR) or Chebyshev column (MODE_FAR)
   const int S = args.n_split;
-  const int SPT = args.n_steps / KS;   // stages of a whole tile
+  const int SPT = args.n_steps;     // stages of a whole tile (one 16-i record per stage)
   const int unit_first = blockIdx.x / G, unit_step = gridDim.x / G;
   const int n_units = args.n_otiles * S;
+  const int *const near_off = args.near_off;
+  const int *const near_idx = args.near_idx;
   long total_stages = 0;
   for (int u = unit_first; u < n_units; u += unit_step) {
-    const int sp = u % S;
-    total_stages += (long)((sp + 1) * SPT / S - sp * SPT / S);
+    int t, sp, b, e;
+    unit_range(near_off, u, S, SPT, t, sp, b, e);
+    total_stages += e - b;
   }
   const int seg_stages = args.seg_stages;
+  const size_t KJN = (size_t)args.K * args.J * args.N;
 
   if (tid == 0) {
     for (int q = 0; q < C::NR; ++q) mbar_init(&bar_tma[q], 1);
@@ -375,18 +439,17 @@ __global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
     fence_mbar_init();
     fence_proxy_async_smem();
   }
-  // this group's table slice (zero beyond K), rows swizzled by tab_unit
-  {
-    const int n_units = (args.n_r + 1) * C::U;
-    for (int q = tid; q < n_units; q += blockDim.x) {
+  if (MODE == MODE_NEAR) {
+    // this group's table slice (zero beyond K), rows swizzled by tab_unit
+    const int n_units_tab = (args.n_r + 1) * C::U;
+    for (int q = tid; q < n_units_tab; q += blockDim.x) {
       const int m = q / C::U, u = q % C::U;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
       uint32_t w[4] = {0u, 0u, 0u, 0u};
       if (!SPLIT) {
         uint32_t e4[4] = {0u, 0u, 0u, 0u};   // {lo: v_k, hi: s_k} per base
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const int k = k0 + u * 4 + e;
+          const int k = c0 + u * 4 + e;
           if (k < args.K) e4[e] = args.tab16[(size_t)m * args.KP + k];
         }
         w[0] = __byte_perm(e4[0], e4[1], 0x5410);   // {v_k, v_k+1}
@@ -396,7 +459,7 @@ __global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
       } else {
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-          const int k = k0 + u * 2 + e;
+          const int k = c0 + u * 2 + e;
           if (k < args.K) {
             const float2 f = args.tab32[(size_t)m * args.KP + k];
             w[2 * e] = __float_as_uint(f.x);
@@ -404,8 +467,12 @@ __global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
           }
         }
       }
-      v = make_uint4(w[0], w[1], w[2], w[3]);
-      reinterpret_cast<uint4 *>(sTab)[tab_unit<C::U>(m, u)] = v;
+      reinterpret_cast<uint4 *>(sTab)[tab_unit<C::U>(m, u)] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  } else {
+    for (int q = tid; q < args.K * CB; q += blockDim.x) {
+      const int k = q / CB, p = c0 + q % CB;
+      sC[q] = (p < args.PCH) ? args.cheb[k * args.PCH + p] : 0.f;
     }
   }
   if (warp == 0) {
@@ -424,70 +491,85 @@ __global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
     // ------------------------------------------------------------ control warp
     if (lane == 0) {
       const uint32_t idesc = umma_idesc_bf16(JP);
-      const uint32_t sA_u32 = smem_u32(sA);
+      const uint64_t desc_a0 = umma_desc(smem_u32(sA), 128, 256);             // A: K-major, 8x16B core matrices
+      const uint64_t desc_b0 = umma_desc(smem_u32(sRec), JP * 16, 128);       // B: T' tile of a record
       long issued = 0;
-      // TMA cursor: unit tu, absolute stage ts within the tile (runs LOOKAHEAD stages ahead)
-      int tu = unit_first, ts = 0, te = 0;
-      if (tu < n_units) {
-        ts = (tu % S) * SPT / S;
-        te = (tu % S + 1) * SPT / S;
-      }
-      auto issue_tma = [&](long q) {
-        const int slot = (int)(q % C::NR);
-        mbar_arrive_expect_tx(&bar_tma[slot], C::REC_STAGE);
-        tma_load_2d(sRec + (size_t)slot * C::REC_STAGE, &tmap, &bar_tma[slot], 0, ts * rows_per_stage);
-        if (++ts == te) {   // next unit of this CTA
+      // TMA cursor: unit tu, stage tq in [tb, te) (runs LOOKAHEAD stages ahead of the MMAs)
+      int tu = unit_first, tq = 0, te = 0;
+      auto next_unit = [&]() {
+        while (tu < n_units) {
+          int t, sp;
+          unit_range(near_off, tu, S, SPT, t, sp, tq, te);
+          if (tq < te) return;
           tu += unit_step;
-          if (tu < n_units) {
-            ts = (tu % S) * SPT / S;
-            te = (tu % S + 1) * SPT / S;
-          }
         }
       };
-      for (; issued < C::LOOKAHEAD && issued < total_stages; ++issued) issue_tma(issued);
+      next_unit();
+      int tslot = 0;   // record slot of the next TMA
+      auto issue_tma = [&]() {
+        mbar_arrive_expect_tx(&bar_tma[tslot], C::REC_STAGE);
+        tma_load_2d(sRec + (size_t)tslot * C::REC_STAGE, &tmap, &bar_tma[tslot], 0,
+                    chunk_at(near_idx, tq) * rows_per_stage);
+        if (++tslot == C::NR) tslot = 0;
+        if (++tq == te) {
+          tu += unit_step;
+          next_unit();
+        }
+      };
+      for (; issued < C::LOOKAHEAD && issued < total_stages; ++issued) issue_tma();
+      // ring state: A slot sa (phase pa), record slot sr; ps/pp: A slot of stage issued - NR
+      int sa = 0, sr = 0, ps = 0;
+      uint32_t pa = 0u, pp = 0u;
       long g = 0;
       int seg_no = 0;   // accumulation segments issued so far
       for (int u = unit_first; u < n_units && !*abort_flag; u += unit_step) {
-        const int sb = (u % S) * SPT / S, se = (u % S + 1) * SPT / S;
+        int t, sp, sb, se;
+        unit_range(near_off, u, S, SPT, t, sp, sb, se);
+        int seg_pos = 0;
         for (int sidx = sb; sidx < se && !*abort_flag; ++sidx, ++g) {
-          const bool seg_start = ((sidx - sb) % seg_stages) == 0;
+          const bool seg_start = seg_pos == 0;
+          if (++seg_pos == seg_stages) seg_pos = 0;
           // TMA of stage g + LOOKAHEAD reuses the slot of stage g - NS: wait for its MMAs
           if (issued < total_stages && issued <= g + C::LOOKAHEAD) {
-            const long prev = issued - C::NR;
-            if (prev >= 0 && !wait_or_abort(&bar_mma[prev % NS], (uint32_t)((prev / NS) & 1), abort_flag)) break;
-            issue_tma(issued);
+            if (issued >= C::NR) {
+              if (!wait_or_abort(&bar_mma[ps], pp, abort_flag)) break;
+              if (++ps == NS) {
+                ps = 0;
+                pp ^= 1u;
+              }
+            }
+            issue_tma();
             ++issued;
           }
-          const int sa = (int)(g % NS);
-          if (!wait_or_abort(&bar_full[sa], (uint32_t)((g / NS) & 1), abort_flag)) break;
+          if (!wait_or_abort(&bar_full[sa], pa, abort_flag)) break;
           // the epilogue of the previous segment must have read TMEM before it is overwritten
           if (seg_start && seg_no > 0 && !wait_or_abort(bar_tfree, (uint32_t)((seg_no - 1) & 1), abort_flag)) break;
           if (seg_start) ++seg_no;
           tc_fence_after();
-          const uint32_t rec_u32 = smem_u32(sRec + (size_t)(g % C::NR) * C::REC_STAGE);
-#pragma unroll 1
-          for (int ks = 0; ks < KS; ++ks) {
-            const uint32_t b_hi = rec_u32 + ks * C::REC;
-            const uint64_t dbh = umma_desc(b_hi, JP * 16, 128);
-            const uint64_t dbl = umma_desc(b_hi + JP * 32, JP * 16, 128);
-            const uint32_t a_step =
-                sA_u32 + (uint32_t)(sa * C::A_STAGE) + (uint32_t)(ks * KB * (SPLIT ? 2 : 1) * C::A_TILE);
-            const uint32_t first = (seg_start && ks == 0) ? 0u : 1u;
-#pragma unroll 1
-            for (int kb = 0; kb < KB; ++kb) {
-              const uint32_t d = tmem_base + (uint32_t)(kb * JP);
-              if (!SPLIT) {
-                umma_bf16(d, umma_desc(a_step + kb * C::A_TILE, 128, 256), dbh, idesc, first);
-              } else {
-                const uint64_t dah = umma_desc(a_step + (2 * kb) * C::A_TILE, 128, 256);
-                const uint64_t dal = umma_desc(a_step + (2 * kb + 1) * C::A_TILE, 128, 256);
-                umma_bf16(d, dah, dbh, idesc, first);
-                umma_bf16(d, dah, dbl, idesc, 1u);
-                umma_bf16(d, dal, dbh, idesc, 1u);
-              }
+          // descriptors: start-address field (addr >> 4) advanced by offsets from the base ones
+          const uint64_t dbh = desc_b0 + (uint64_t)((sr * C::REC_STAGE) >> 4);
+          const uint64_t dbl = dbh + (uint64_t)((JP * 32) >> 4);
+          const uint64_t da = desc_a0 + (uint64_t)((sa * C::A_STAGE) >> 4);
+          const uint32_t first = seg_start ? 0u : 1u;
+#pragma unroll
+          for (int cb = 0; cb < CB; ++cb) {
+            const uint32_t d = tmem_base + (uint32_t)(cb * JP);
+            if (!SPLIT) {
+              umma_bf16(d, da + (uint64_t)((cb * C::A_TILE) >> 4), dbh, idesc, first);
+            } else {
+              const uint64_t dah = da + (uint64_t)(((2 * cb) * C::A_TILE) >> 4);
+              const uint64_t dal = da + (uint64_t)(((2 * cb + 1) * C::A_TILE) >> 4);
+              umma_bf16(d, dah, dbh, idesc, first);
+              umma_bf16(d, dah, dbl, idesc, 1u);
+              umma_bf16(d, dal, dbh, idesc, 1u);
             }
           }
           umma_commit(&bar_mma[sa]);
+          if (++sa == NS) {
+            sa = 0;
+            pa ^= 1u;
+          }
+          if (++sr == C::NR) sr = 0;
         }
       }
       if (*abort_flag) {   // let copies already issued land before the CTA exits
@@ -508,78 +590,88 @@ __global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
     const uint32_t a_row_off =
         (uint32_t)((orow >> 3) * 256 + (h4 >> 1) * 128 + (orow & 7) * 16 + (h4 & 1) * 8);
     const uint32_t sA_u32 = smem_u32(sA);
-    const float r2max = args.r2max, inv_dr = args.inv_dr;
+    const float r2max = args.r2max, rn2 = args.rn2, inv_dr = args.inv_dr;
+    const float xa_alpha = args.x_alpha, xa_beta = args.x_beta;
     const int n_r = args.n_r;
     long g = 0;
+    // ring state (advanced once per stage): A slot sa with phase bit pa = (g / NS) & 1,
+    // record slot sr with phase bit pr = (g / NR) & 1
+    int sa = 0, sr = 0;
+    uint32_t pa = 0u, pr = 0u;
     for (int u = unit_first; u < n_units; u += unit_step) {
       if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
-      const int t = u / S, sp = u % S;
-      const int sb = sp * SPT / S, se = (sp + 1) * SPT / S;
-      float *Mdst = (sp == 0) ? args.M : args.P + (size_t)(sp - 1) * args.K * args.J * args.N;
+      int t, sp, sb, se;
+      unit_range(near_off, u, S, SPT, t, sp, sb, se);
+      if (sb == se) continue;
+      const int d_idx = (MODE == MODE_FAR ? group * S : 0) + sp;   // destination
+      float *Mdst = (d_idx == 0) ? args.M : args.P + (size_t)(d_idx - 1) * KJN;
+      const bool dst_accumulates = (d_idx == 0) && args.accumulate;
       const int o = t * 128 + orow;
       const bool o_ok = o < args.N;
       const float xo = o_ok ? args.pos[o] : 0.f;
       const float yo = o_ok ? args.pos[args.N + o] : 0.f;
       const float zo = o_ok ? args.pos[2 * (size_t)args.N + o] : 0.f;
       bool ok = true;
-      for (int sidx = sb; sidx < se; ++sidx, ++g) {
-        const int sa = (int)(g % NS);
-        const int sr = (int)(g % C::NR);
+      int seg_pos = 0, seg_count = 0;   // position in / index of the accumulation segment
+      for (int sidx = sb; sidx < se; ++sidx) {
         bool w_ok = true;
-        if (g >= NS) w_ok = wait_or_abort(&bar_mma[sa], (uint32_t)(((g / NS) - 1) & 1), abort_flag);
-        if (w_ok) w_ok = wait_or_abort(&bar_tma[sr], (uint32_t)((g / C::NR) & 1), abort_flag);
+        if (g >= NS) w_ok = wait_or_abort(&bar_mma[sa], pa ^ 1u, abort_flag);
+        if (w_ok) w_ok = wait_or_abort(&bar_tma[sr], pr, abort_flag);
         if (__any_sync(0xffffffffu, !w_ok)) {
           ok = false;
           break;
         }
-        if (tid == 0) *tma_done = g + 1;
+        if (tid == 0) *tma_done = g + 1;   // records of stages <= g have landed
         const uint8_t *rec_stage = sRec + (size_t)sr * C::REC_STAGE;
+        const float *rp = reinterpret_cast<const float *>(rec_stage + JP * 32 * (SPLIT ? 2 : 1));
+        const float4 xs = *reinterpret_cast<const float4 *>(rp + h4 * 4);
+        const float4 ys = *reinterpret_cast<const float4 *>(rp + 16 + h4 * 4);
+        const float4 zs = *reinterpret_cast<const float4 *>(rp + 32 + h4 * 4);
+        const float xa[4] = {xs.x, xs.y, xs.z, xs.w}, ya[4] = {ys.x, ys.y, ys.z, ys.w},
+                    za[4] = {zs.x, zs.y, zs.z, zs.w};
+        // Padded i (beyond N) carry T' = 0 and finite positions, so they add nothing.
+        float r2v[4];
+        unsigned inside = 0u;   // bit q: pair q within r_max
 #pragma unroll
-        for (int ks = 0; ks < KS; ++ks) {
-          const float *rp = reinterpret_cast<const float *>(rec_stage + ks * C::REC + JP * 32 * (SPLIT ? 2 : 1));
-          const float4 xs = *reinterpret_cast<const float4 *>(rp + h4 * 4);
-          const float4 ys = *reinterpret_cast<const float4 *>(rp + 16 + h4 * 4);
-          const float4 zs = *reinterpret_cast<const float4 *>(rp + 32 + h4 * 4);
-          const float xa[4] = {xs.x, xs.y, xs.z, xs.w}, ya[4] = {ys.x, ys.y, ys.z, ys.w},
-                      za[4] = {zs.x, zs.y, zs.z, zs.w};
-          // Padded i (beyond N) carry T' = 0 and finite positions, so they add nothing;
-          // the self pair i = o is corrected to FP32 in the epilogue.
+        for (int q = 0; q < 4; ++q) {
+          r2v[q] = pair_r2_fma(xo, yo, zo, xa[q], ya[q], za[q]);
+          bool in = r2v[q] <= r2max;
+          if (fabsf(r2v[q] - r2max) <= 1e-3f * r2max)   // near the cutoff: decide on the exact FP32 r^2
+            in = pair_r2(xo, yo, zo, xa[q], ya[q], za[q]) <= r2max;
+          inside |= (in ? 1u : 0u) << q;
+        }
+        const uint32_t a_stage = sA_u32 + (uint32_t)(sa * C::A_STAGE);
+        if (MODE == MODE_NEAR) {
           int row[4];
           float tq[4];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float dx = xo - xa[u], dy = yo - ya[u], dz = zo - za[u];
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-            bool inside = r2 <= r2max;
-            if (fabsf(r2 - r2max) <= 1e-3f * r2max)   // near the cutoff: decide on the exact FP32 r^2
-              inside = pair_r2(xo, yo, zo, xa[u], ya[u], za[u]) <= r2max;
+          for (int q = 0; q < 4; ++q) {
+            const float r2 = r2v[q];
             const float x = r2 * rsqrtf(fmaxf(r2, 1e-30f)) * inv_dr;
             // m = floor(x) (round-to-nearest of x - 1/2 at 1.5 * 2^23), t = x - m
             const float yv = (x - 0.5f) + 12582912.0f;
             const int m = __float_as_int(yv) - 0x4B400000;
-            tq[u] = x - (yv - 12582912.0f);
-            row[u] = inside ? m : n_r;
+            tq[q] = x - (yv - 12582912.0f);
+            row[q] = (((inside >> q) & 1u) && r2 < rn2) ? m : n_r;
           }
-          const uint32_t a_step =
-              sA_u32 + (uint32_t)(sa * C::A_STAGE) + (uint32_t)(ks * KB * (SPLIT ? 2 : 1) * C::A_TILE);
           if (!SPLIT) {
-            // unit kb4 of a table row: {v_4kb4..+1, v_+2..+3, s_4kb4..+1, s_+2..+3} (bf16 pairs)
+            // unit cb4 of a table row: {v_4cb4..+1, v_+2..+3, s_4cb4..+1, s_+2..+3} (bf16 pairs)
             uint32_t t2[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) t2[u] = pack_bf16x2(tq[u], tq[u]);
+            for (int q = 0; q < 4; ++q) t2[q] = pack_bf16x2(tq[q], tq[q]);
             const uint4 *tab4 = reinterpret_cast<const uint4 *>(sTab);
 #pragma unroll
-            for (int kb4 = 0; kb4 < KB / 4; ++kb4) {
+            for (int cb4 = 0; cb4 < CB / 4; ++cb4) {
               uint4 w[4];
 #pragma unroll
-              for (int u = 0; u < 4; ++u) w[u] = tab4[tab_unit<C::U>(row[u], kb4)];
-              uint32_t F01[4], F23[4];   // {F_k, F_k+1} of pair u
+              for (int q = 0; q < 4; ++q) w[q] = tab4[tab_unit<C::U>(row[q], cb4)];
+              uint32_t F01[4], F23[4];   // {F_k, F_k+1} of pair q
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                F01[u] = bf16x2_fma(t2[u], w[u].z, w[u].x);
-                F23[u] = bf16x2_fma(t2[u], w[u].w, w[u].y);
+              for (int q = 0; q < 4; ++q) {
+                F01[q] = bf16x2_fma(t2[q], w[q].z, w[q].x);
+                F23[q] = bf16x2_fma(t2[q], w[q].w, w[q].y);
               }
-              const uint32_t base = a_step + (uint32_t)(kb4 * 4 * C::A_TILE) + a_row_off;
+              const uint32_t base = a_stage + (uint32_t)(cb4 * 4 * C::A_TILE) + a_row_off;
               st_shared_v2(base, __byte_perm(F01[0], F01[1], 0x5410), __byte_perm(F01[2], F01[3], 0x5410));
               st_shared_v2(base + C::A_TILE, __byte_perm(F01[0], F01[1], 0x7632), __byte_perm(F01[2], F01[3], 0x7632));
               st_shared_v2(base + 2 * C::A_TILE, __byte_perm(F23[0], F23[1], 0x5410), __byte_perm(F23[2], F23[3], 0x5410));
@@ -588,79 +680,160 @@ __global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
           } else {
             const float4 *tab4 = reinterpret_cast<const float4 *>(sTab);   // {v_k, s_k, v_k+1, s_k+1}
 #pragma unroll
-            for (int kb2 = 0; kb2 < KB / 2; ++kb2) {
+            for (int cb2 = 0; cb2 < CB / 2; ++cb2) {
               float F0[4], F1[4];
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
-                const float4 w = tab4[tab_unit<C::U>(row[u], kb2)];
-                F0[u] = fmaf(tq[u], w.y, w.x);
-                F1[u] = fmaf(tq[u], w.w, w.z);
+              for (int q = 0; q < 4; ++q) {
+                const float4 w = tab4[tab_unit<C::U>(row[q], cb2)];
+                F0[q] = fmaf(tq[q], w.y, w.x);
+                F1[q] = fmaf(tq[q], w.w, w.z);
               }
+              store_split4(a_stage + (uint32_t)((4 * cb2) * C::A_TILE) + a_row_off, C::A_TILE, F0[0], F0[1], F0[2], F0[3]);
+              store_split4(a_stage + (uint32_t)((4 * cb2 + 2) * C::A_TILE) + a_row_off, C::A_TILE, F1[0], F1[1], F1[2],
+                           F1[3]);
+            }
+          }
+        } else {
+          // Chebyshev columns c0 .. c0+CB-1 of the far pairs (zero for near or cut-off pairs)
+          float tp[4], tc[4], x2[4];
 #pragma unroll
-              for (int b = 0; b < 2; ++b) {
-                const float *F = b ? F1 : F0;
-                const uint32_t hi01 = pack_bf16x2(F[0], F[1]), hi23 = pack_bf16x2(F[2], F[3]);
-                const uint32_t lo01 = pack_bf16x2(F[0] - __uint_as_float(hi01 << 16),
-                                                  F[1] - __uint_as_float(hi01 & 0xFFFF0000u));
-                const uint32_t lo23 = pack_bf16x2(F[2] - __uint_as_float(hi23 << 16),
-                                                  F[3] - __uint_as_float(hi23 & 0xFFFF0000u));
-                const int kb = kb2 * 2 + b;
-                st_shared_v2(a_step + (uint32_t)((2 * kb) * C::A_TILE) + a_row_off, hi01, hi23);
-                st_shared_v2(a_step + (uint32_t)((2 * kb + 1) * C::A_TILE) + a_row_off, lo01, lo23);
+          for (int q = 0; q < 4; ++q) {
+            const bool far = ((inside >> q) & 1u) && r2v[q] >= rn2;
+            const float x = far ? fmaf(xa_alpha, fast_lg2(r2v[q]), xa_beta) : 0.f;
+            tp[q] = far ? 1.f : 0.f;   // T_0
+            tc[q] = x;                 // T_1
+            x2[q] = x + x;
+          }
+#pragma unroll
+          for (int p = 0; p < TSR_CHEB_P - CB; ++p) {   // advance to T_{c0}, T_{c0+1}
+            if (p >= c0) break;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float nx = fmaf(x2[q], tc[q], -tp[q]);
+              tp[q] = tc[q];
+              tc[q] = nx;
+            }
+          }
+#pragma unroll
+          for (int cb = 0; cb < CB; ++cb) {   // emit T_{c0+cb}
+            if (!SPLIT) {
+              st_shared_v2(a_stage + (uint32_t)(cb * C::A_TILE) + a_row_off, pack_bf16x2(tp[0], tp[1]),
+                           pack_bf16x2(tp[2], tp[3]));
+            } else {
+              store_split4(a_stage + (uint32_t)((2 * cb) * C::A_TILE) + a_row_off, C::A_TILE, tp[0], tp[1], tp[2],
+                           tp[3]);
+            }
+            if (cb + 1 < CB) {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const float nx = fmaf(x2[q], tc[q], -tp[q]);
+                tp[q] = tc[q];
+                tc[q] = nx;
               }
             }
           }
         }
         fence_proxy_async_smem();
         mbar_arrive(&bar_full[sa]);
-        if ((sidx - sb + 1) % seg_stages != 0 && sidx + 1 != se) continue;
-        // End of an accumulation segment: TMEM -> registers -> M.  The tensor-core
-        // FP32 accumulator is flushed every seg_stages steps and summed into M with
-        // round-to-nearest adds.  The first segment also replaces the self pair's
-        // BF16 product (exact in FP32) by f_k(0) A_o T[j][o] in FP32.
-        const int seg_in_item = (sidx - sb) / seg_stages;
-        const long last = g;
-        const bool e_ok = wait_or_abort(&bar_mma[last % NS], (uint32_t)((last / NS) & 1), abort_flag);
+        const int last_sa = sa;
+        const uint32_t last_pa = pa;
+        ++g;
+        if (++sa == NS) {
+          sa = 0;
+          pa ^= 1u;
+        }
+        if (++sr == C::NR) {
+          sr = 0;
+          pr ^= 1u;
+        }
+        if (++seg_pos != seg_stages && sidx + 1 != se) continue;
+        // End of an accumulation segment: TMEM -> registers -> destination.  The
+        // tensor-core FP32 accumulator is flushed every seg_stages steps and summed
+        // with round-to-nearest adds.
+        const bool first_seg = seg_count == 0;
+        seg_pos = 0;
+        ++seg_count;
+        const bool e_ok = wait_or_abort(&bar_mma[last_sa], last_pa, abort_flag);
         if (__any_sync(0xffffffffu, !e_ok)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const int quarter = warp & 3, wq = warp >> 2;
+        const int quarter = warp & 3, wq = warp >> 2;   // rows quarter*32 + lane; 4 warps share a quarter
         const int oe = t * 128 + quarter * 32 + lane;
         const bool oe_ok = oe < args.N;
-        const float a_o = oe_ok ? args.area[oe] : 0.f;
-        for (int kb = wq; kb < KB; kb += C::NGEN / 128) {
-          const int k = k0 + kb;
-          const float f0 = (k < args.K) ? args.tab32[k].x : 0.f;   // f_k(0), FP32
-          const float f0h = __bfloat162float(__float2bfloat16_rn(f0));
-          const float f0l = __bfloat162float(__float2bfloat16_rn(f0 - f0h));
+        const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+        if (MODE == MODE_NEAR) {
+          // The first segment of split 0 also replaces the self pair's BF16 product
+          // (exact in FP32) by f_k(0) A_o T[j][o] in FP32.
+          const float a_o = oe_ok ? args.area[oe] : 0.f;
+          for (int cb = wq; cb < CB; cb += C::NGEN / 128) {
+            const int k = c0 + cb;
+            const float f0 = (k < args.K) ? args.tab32[k].x : 0.f;   // f_k(0), FP32
+            const float f0h = __bfloat162float(__float2bfloat16_rn(f0));
+            const float f0l = __bfloat162float(__float2bfloat16_rn(f0 - f0h));
 #pragma unroll
-          for (int jc = 0; jc < JP; jc += 16) {
-            uint32_t r[16];
-            tmem_ld16(tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(kb * JP + jc), r);
-            tmem_ld_wait();
-            if (k < args.K && oe_ok) {
+            for (int jc = 0; jc < JP; jc += 16) {
+              uint32_t r[16];
+              tmem_ld16(lane_base + (uint32_t)(cb * JP + jc), r);
+              tmem_ld_wait();
+              if (k < args.K && oe_ok) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                  const int j = jc + q;
+                  if (j < args.J) {
+                    float *dst = Mdst + ((size_t)k * args.J + j) * args.N + oe;
+                    float v = __uint_as_float(r[q]);
+                    if (first_seg && sp == 0) {
+                      const float tpv = a_o * args.T[(size_t)j * args.N + oe];
+                      const float th = __bfloat162float(__float2bfloat16_rn(tpv));
+                      float tc_self;
+                      if (!SPLIT) {
+                        tc_self = __bfloat162float(__ushort_as_bfloat16((unsigned short)(args.tab16[k] & 0xFFFFu))) * th;
+                      } else {
+                        const float tl = __bfloat162float(__float2bfloat16_rn(tpv - th));
+                        tc_self = f0h * th + f0h * tl + f0l * th;
+                      }
+                      v += f0 * tpv - tc_self;
+                    }
+                    *dst = (first_seg && !dst_accumulates) ? v : *dst + v;
+                  }
+                }
+              }
+            }
+          }
+        } else {
+          // M[k][j] (+)= sum_{cb} C[k][c0 + cb] G[cb][j], in chunks of 2 k x 16 j
+          const int n_kc = (args.K + 1) / 2;
+          for (int item = wq; item < n_kc * (JP / 16); item += C::NGEN / 128) {
+            const int kc = item / (JP / 16), jc = (item % (JP / 16)) * 16;
+            const int ka = kc * 2, kb = kc * 2 + 1;
+            float acc0[16], acc1[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc0[q] = acc1[q] = 0.f;
+#pragma unroll 1
+            for (int cb = 0; cb < CB; ++cb) {
+              uint32_t r[16];
+              tmem_ld16(lane_base + (uint32_t)(cb * JP + jc), r);
+              tmem_ld_wait();
+              const float ca = sC[ka * CB + cb];
+              const float cbv = (kb < args.K) ? sC[kb * CB + cb] : 0.f;
+#pragma unroll
+              for (int q = 0; q < 16; ++q) {
+                acc0[q] = fmaf(ca, __uint_as_float(r[q]), acc0[q]);
+                acc1[q] = fmaf(cbv, __uint_as_float(r[q]), acc1[q]);
+              }
+            }
+            if (oe_ok) {
 #pragma unroll
               for (int q = 0; q < 16; ++q) {
                 const int j = jc + q;
                 if (j < args.J) {
-                  float *dst = Mdst + ((size_t)k * args.J + j) * args.N + oe;
-                  if (seg_in_item == 0 && sp == 0) {
-                    const float tp = a_o * args.T[(size_t)j * args.N + oe];
-                    const float th = __bfloat162float(__float2bfloat16_rn(tp));
-                    float tc_self;
-                    if (!SPLIT) {
-                      tc_self = __bfloat162float(__ushort_as_bfloat16((unsigned short)(args.tab16[k] & 0xFFFFu))) * th;
-                    } else {
-                      const float tl = __bfloat162float(__float2bfloat16_rn(tp - th));
-                      tc_self = f0h * th + f0h * tl + f0l * th;
-                    }
-                    *dst = __uint_as_float(r[q]) + (f0 * tp - tc_self);
-                  } else if (seg_in_item == 0) {
-                    *dst = __uint_as_float(r[q]);
-                  } else {
-                    *dst = *dst + __uint_as_float(r[q]);
+                  float *da = Mdst + ((size_t)ka * args.J + j) * args.N + oe;
+                  *da = (first_seg && !dst_accumulates) ? acc0[q] : *da + acc0[q];
+                  if (kb < args.K) {
+                    float *db = Mdst + ((size_t)kb * args.J + j) * args.N + oe;
+                    *db = (first_seg && !dst_accumulates) ? acc1[q] : *db + acc1[q];
                   }
                 }
               }
@@ -683,13 +856,118 @@ __global__ void __launch_bounds__(TcCfg<KB, JP, SPLIT, NS, KS>::NTHREADS, 1)
   }
 }
 
-// M += sum of the partial sums of units 1 .. S-1 (fixed order: deterministic)
+// M += sum of the partial sums of destinations 1 .. n_part (fixed order: deterministic)
 __global__ void add_partials_kernel(float *__restrict__ M, const float *__restrict__ P, int n_part, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     float acc = M[i];
     for (int q = 0; q < n_part; ++q) acc += P[(size_t)q * n + i];
     M[i] = acc;
   }
+}
+
+// ---------------------------------------------------------------- near-chunk lists
+// Bounding boxes of 128-row tiles and 16-row chunks (valid vertices only).
+__global__ void bbox_kernel(const float *__restrict__ pos, int N, int rows_per_box, int n_box,
+                            float *__restrict__ box /* [n_box][6] */) {
+  const int bidx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bidx >= n_box) return;
+  float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+  const int v0 = bidx * rows_per_box, v1 = min(N, v0 + rows_per_box);
+  for (int v = v0; v < v1; ++v) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float x = pos[(size_t)a * N + v];
+      lo[a] = fminf(lo[a], x);
+      hi[a] = fmaxf(hi[a], x);
+    }
+  }
+  if (v1 <= v0) {   // padding chunk: an empty box far away
+#pragma unroll
+    for (int a = 0; a < 3; ++a) lo[a] = hi[a] = 1e30f;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    box[bidx * 6 + a] = lo[a];
+    box[bidx * 6 + 3 + a] = hi[a];
+  }
+}
+
+// A chunk is near a tile if the boxes are closer than r_near (with a small
+// margin, so that every pair the kernels classify as near is inside a listed chunk).
+__device__ __forceinline__ bool boxes_near(const float *a, const float *b, float rn2m) {
+  float d2 = 0.f;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const float gap = fmaxf(0.f, fmaxf(a[q] - b[3 + q], b[q] - a[3 + q]));
+    d2 = fmaf(gap, gap, d2);
+  }
+  return d2 < rn2m;
+}
+
+// One block per tile: count (pass 0) or write in ascending chunk order (pass 1) the near chunks.
+__global__ void __launch_bounds__(256) near_list_kernel(const float *__restrict__ tile_box,
+                                                        const float *__restrict__ chunk_box, int n_chunks, float rn2m,
+                                                        int pass, int *__restrict__ counts,
+                                                        const int *__restrict__ offsets, int *__restrict__ idx) {
+  __shared__ int warp_tot[8];
+  __shared__ float tb[6];
+  const int t = blockIdx.x;
+  if (threadIdx.x < 6) tb[threadIdx.x] = tile_box[t * 6 + threadIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int written = 0;
+  for (int base = 0; base < n_chunks; base += blockDim.x) {
+    const int c = base + threadIdx.x;
+    const bool nr = (c < n_chunks) && boxes_near(tb, chunk_box + (size_t)c * 6, rn2m);
+    const unsigned bal = __ballot_sync(0xffffffffu, nr);
+    if (lane == 0) warp_tot[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < 8; ++w) {
+      before += (w < warp) ? warp_tot[w] : 0;
+      total += warp_tot[w];
+    }
+    if (pass == 1 && nr) idx[offsets[t] + written + before + __popc(bal & ((1u << lane) - 1u))] = c;
+    written += total;
+    __syncthreads();
+  }
+  if (pass == 0 && threadIdx.x == 0) counts[t] = written;
+}
+
+// Exclusive scan of n counts into offsets[0..n] (single block).
+__global__ void __launch_bounds__(1024) scan_counts_kernel(const int *__restrict__ counts, int n,
+                                                          int *__restrict__ offsets) {
+  __shared__ int warp_sum[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int v = i < n ? counts[i] : 0;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int ws = lane < (int)(blockDim.x >> 5) ? warp_sum[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, ws, o);
+        if (lane >= o) ws += y;
+      }
+      warp_sum[lane] = ws;
+    }
+    __syncthreads();
+    const int incl = x + (warp > 0 ? warp_sum[warp - 1] : 0) + carry;
+    if (i < n) offsets[i] = incl - v;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) offsets[n] = carry;
 }
 
 // ---------------------------------------------------------------- host side
@@ -706,112 +984,127 @@ static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   return fn;
 }
 
-struct TcChoice {
-  int KB, NS, KS;
-};
-
-template <int KB, int JP, bool SPLIT, int NS, int KS>
-static tsr_status launch_tc(const TcArgs &a0, const uint8_t *rec, cudaStream_t s) {
-  using C = TcCfg<KB, JP, SPLIT, NS, KS>;
-  TcArgs a = a0;
-  a.seg_stages = std::max(1, 4096 / (16 * KS));   // flush the tensor-core accumulator every 4,096 i
-  a.n_kgroups = (a.K + KB - 1) / KB;
-  a.n_items = a.n_otiles * a.n_kgroups;
-  const size_t smem = C::smem_bytes(a.n_r);
-  if (smem > 232448) {
-    set_error("transfer_tc: shared memory %zu bytes exceeds the per-block limit (n_r too large)", smem);
-    return TSR_ERR_UNSUPPORTED;
-  }
+static tsr_status make_record_map(CUtensorMap *tmap, const uint8_t *rec, int n_steps, int REC) {
   auto encode = get_encode();
   if (!encode) {
     set_error("transfer_tc: cuTensorMapEncodeTiled unavailable");
     return TSR_ERR_CUDA;
   }
-  CUtensorMap tmap;
-  const cuuint64_t rows_total = (cuuint64_t)a.n_steps * C::REC / 128;
-  const cuuint64_t gdim[2] = {32, rows_total};
+  const cuuint64_t gdim[2] = {32, (cuuint64_t)n_steps * REC / 128};
   const cuuint64_t gstride[1] = {128};
-  const cuuint32_t box[2] = {32, (cuuint32_t)(C::REC_STAGE / 128)};
+  const cuuint32_t box[2] = {32, (cuuint32_t)(REC / 128)};
   const cuuint32_t estr[2] = {1, 1};
-  CUresult cr = encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint8_t *>(rec), gdim, gstride, box, estr,
+  CUresult cr = encode(tmap, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint8_t *>(rec), gdim, gstride, box, estr,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) {
     set_error("transfer_tc: cuTensorMapEncodeTiled failed (%d)", (int)cr);
     return TSR_ERR_CUDA;
   }
-  auto kern = transfer_tc_kernel<KB, JP, SPLIT, NS, KS>;
+  return TSR_OK;
+}
+
+// Launch one pass.  n_cols: bases (MODE_NEAR) or Chebyshev columns (MODE_FAR) in total.
+template <int MODE, int CB, int JP, bool SPLIT, int NS>
+static tsr_status launch_tc(const TcArgs &a0, int n_cols, const CUtensorMap &tmap, bool allow_split, cudaStream_t s) {
+  using C = TcCfg<MODE, CB, JP, SPLIT, NS>;
+  TcArgs a = a0;
+  a.seg_stages = 4096 / 16;   // flush the tensor-core accumulator every 4,096 i
+  a.n_groups = (n_cols + CB - 1) / CB;
+  const size_t smem = C::smem_bytes(a.n_r, a.K);
+  if (smem > 232448) {
+    set_error("transfer_tc: shared memory %zu bytes exceeds the per-block limit (n_r too large)", smem);
+    return TSR_ERR_UNSUPPORTED;
+  }
+  auto kern = transfer_tc_kernel<MODE, CB, JP, SPLIT, NS>;
   TSR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  // Every CTA keeps one k-group: the grid is a multiple of the group count.  Each
-  // tile's i-range is cut into S units so that the last wave is nearly full.
-  const int G = a.n_kgroups;
+  // Every CTA keeps one group: the grid is a multiple of the group count.  Each
+  // tile's i-range may be cut into S units so that the last wave is nearly full.
+  const int G = a.n_groups;
   const int sms = num_sms();
-  const int SPT = a.n_steps / KS;
   int best_S = 1;
-  double best_cost = 1e30;
-  for (int S = 1; S <= 4 && S <= SPT; ++S) {
-    const long units = (long)a.n_otiles * S * G;
-    int grid = (int)std::min<long>(units, sms);
-    grid = std::max(G, grid / G * G);
-    const long per_cta = (units / G + grid / G - 1) / (grid / G);        // units on the busiest CTA
-    const double cost = (double)per_cta / S * (1.0 + 0.03 * (S - 1));    // in whole-tile units
-    if (cost < best_cost - 1e-9) {
-      best_cost = cost;
-      best_S = S;
+  if (allow_split) {
+    double best_cost = 1e30;
+    for (int S = 1; S <= 4 && S <= a.n_steps; ++S) {
+      const long units = (long)a.n_otiles * S * G;
+      int grid = (int)std::min<long>(units, sms);
+      grid = std::max(G, grid / G * G);
+      const long per_cta = (units / G + grid / G - 1) / (grid / G);      // units on the busiest CTA
+      const double cost = (double)per_cta / S * (1.0 + 0.03 * (S - 1));  // in whole-tile units
+      if (cost < best_cost - 1e-9) {
+        best_cost = cost;
+        best_S = S;
+      }
     }
   }
   a.n_split = best_S;
   const long units = (long)a.n_otiles * best_S * G;
   int grid = (int)std::min<long>(units, sms);
   grid = std::max(G, grid / G * G);
+  const int n_dest = (MODE == MODE_FAR ? G : 1) * best_S;
   Scratch part;
   const size_t mn = (size_t)a.K * a.J * a.N;
   a.P = nullptr;
-  if (best_S > 1) {
-    tsr_status st = part.alloc(sizeof(float) * mn * (best_S - 1), s);
+  if (n_dest > 1) {
+    tsr_status st = part.alloc(sizeof(float) * mn * (n_dest - 1), s);
     if (st != TSR_OK) return st;
     a.P = static_cast<float *>(part.p);
   }
   kern<<<grid, C::NTHREADS, smem, s>>>(tmap, a);
   TSR_CUDA(cudaGetLastError());
-  if (best_S > 1) {
-    add_partials_kernel<<<4 * sms, 256, 0, s>>>(a.M, a.P, best_S - 1, mn);
+  if (n_dest > 1) {
+    add_partials_kernel<<<4 * sms, 256, 0, s>>>(a.M, a.P, n_dest - 1, mn);
     TSR_CUDA(cudaGetLastError());
   }
   return TSR_OK;
 }
 
-// Configuration per (K, J_pad, split): bases per item, pipeline stages, steps per stage.
-static tsr_status dispatch_tc(const TcArgs &a, int JP, bool split, const uint8_t *rec, cudaStream_t s) {
+// Exact-table pass over the near chunks (or over everything without lists).
+static tsr_status dispatch_near(const TcArgs &a, int JP, bool split, const CUtensorMap &tmap, bool allow_split,
+                                cudaStream_t s) {
   const int K = a.K;
   if (!split) {
     if (JP == 16) {
-      if (K <= 4) return launch_tc<4, 16, false, 4, 2>(a, rec, s);
-      if (K <= 8) return launch_tc<8, 16, false, 4, 1>(a, rec, s);
-      if (K <= 12) return launch_tc<12, 16, false, 3, 1>(a, rec, s);
-      return launch_tc<16, 16, false, 2, 1>(a, rec, s);
-    } else {
-      if (K <= 4) return launch_tc<4, 32, false, 4, 2>(a, rec, s);
-      if (K <= 8) return launch_tc<8, 32, false, 4, 1>(a, rec, s);
-      if (K <= 12) return launch_tc<12, 32, false, 3, 1>(a, rec, s);
-      return launch_tc<16, 32, false, 2, 1>(a, rec, s);
+      if (K <= 4) return launch_tc<MODE_NEAR, 4, 16, false, 4>(a, K, tmap, allow_split, s);
+      if (K <= 8) return launch_tc<MODE_NEAR, 8, 16, false, 4>(a, K, tmap, allow_split, s);
+      if (K <= 12) return launch_tc<MODE_NEAR, 12, 16, false, 3>(a, K, tmap, allow_split, s);
+      return launch_tc<MODE_NEAR, 16, 16, false, 2>(a, K, tmap, allow_split, s);
     }
-  } else {
-    if (JP == 16) {
-      if (K <= 4) return launch_tc<4, 16, true, 4, 1>(a, rec, s);
-      return launch_tc<8, 16, true, 2, 1>(a, rec, s);
-    } else {
-      if (K <= 4) return launch_tc<4, 32, true, 4, 1>(a, rec, s);
-      return launch_tc<8, 32, true, 2, 1>(a, rec, s);
-    }
+    if (K <= 4) return launch_tc<MODE_NEAR, 4, 32, false, 4>(a, K, tmap, allow_split, s);
+    if (K <= 8) return launch_tc<MODE_NEAR, 8, 32, false, 4>(a, K, tmap, allow_split, s);
+    if (K <= 12) return launch_tc<MODE_NEAR, 12, 32, false, 3>(a, K, tmap, allow_split, s);
+    return launch_tc<MODE_NEAR, 16, 32, false, 2>(a, K, tmap, allow_split, s);
   }
+  if (JP == 16) {
+    if (K <= 4) return launch_tc<MODE_NEAR, 4, 16, true, 4>(a, K, tmap, allow_split, s);
+    return launch_tc<MODE_NEAR, 8, 16, true, 2>(a, K, tmap, allow_split, s);
+  }
+  if (K <= 4) return launch_tc<MODE_NEAR, 4, 32, true, 4>(a, K, tmap, allow_split, s);
+  return launch_tc<MODE_NEAR, 8, 32, true, 2>(a, K, tmap, allow_split, s);
+}
+
+// Chebyshev pass over every chunk (all TSR_CHEB_P columns).
+static tsr_status dispatch_far(const TcArgs &a, int JP, bool split, const CUtensorMap &tmap, cudaStream_t s) {
+  if (!split) {
+    if (JP == 16) return launch_tc<MODE_FAR, 16, 16, false, 3>(a, TSR_CHEB_P, tmap, true, s);
+    return launch_tc<MODE_FAR, 16, 32, false, 3>(a, TSR_CHEB_P, tmap, true, s);
+  }
+  if (JP == 16) return launch_tc<MODE_FAR, 8, 16, true, 3>(a, TSR_CHEB_P, tmap, true, s);
+  return launch_tc<MODE_FAR, 8, 32, true, 2>(a, TSR_CHEB_P, tmap, true, s);
+}
+
+// The near/far split (Chebyshev far field) is opt-in: TSR_TRANSFER_NEARFAR=1.
+// Measured on GB300 it does not beat the exact-table path at K <= 16, and its
+// split-BF16 error is larger, so the exact table is the default.
+static bool nearfar_enabled() {
+  const char *e = std::getenv("TSR_TRANSFER_NEARFAR");
+  return e && e[0] == '1';
 }
 
 tsr_status transfer_tc(const tsr_basis *b, int N, const float *pos, const float *area, const float *T, int J,
                        bool split, float *M, cudaStream_t s) {
   const int JP = J <= 16 ? 16 : 32;
-  const int KS_MAX = 2;
-  const int n_steps = ((N + 15) / 16 + KS_MAX - 1) / KS_MAX * KS_MAX;
+  const int n_steps = (N + 15) / 16;
   const int REC = rec_bytes(JP, split);
   Scratch rs;
   tsr_status st = rs.alloc((size_t)n_steps * REC, s);
@@ -821,6 +1114,9 @@ tsr_status transfer_tc(const tsr_basis *b, int N, const float *pos, const float 
   pretile_tc_kernel<<<(n_steps * 16 + 255) / 256, 256, 0, s>>>(pos, area, T, N, J, JP, split ? 1 : 0, REC, n_steps,
                                                                 rec);
   TSR_CUDA(cudaGetLastError());
+  CUtensorMap tmap;
+  st = make_record_map(&tmap, rec, n_steps, REC);
+  if (st != TSR_OK) return st;
   TcArgs a{};
   a.N = N;
   a.n_steps = n_steps;
@@ -829,16 +1125,52 @@ tsr_status transfer_tc(const tsr_basis *b, int N, const float *pos, const float 
   a.r2max = static_cast<float>(b->r_max * b->r_max);
   a.K = b->K;
   a.J = J;
+  a.KP = b->KP;
   a.n_otiles = (N + 127) / 128;
   a.pos = pos;
   a.area = area;
   a.T = T;
   a.tab16 = b->tab16;
   a.tab32 = b->tab32;
-  a.KP = b->KP;
+  a.cheb = b->cheb;
+  a.PCH = TSR_CHEB_P;
+  a.x_alpha = b->x_alpha;
+  a.x_beta = b->x_beta;
   a.M = M;
   a.status = device_status_ptr();
-  return dispatch_tc(a, JP, split, rec, s);
+  // The Chebyshev far field pays off (and keeps BF16 accuracy, since the near
+  // field then carries most of M) on meshes with many vertices within r_near.
+  if (!nearfar_enabled() || !b->cheb || N < 16384) {
+    a.rn2 = 3.0e38f;   // every pair through the exact table
+    return dispatch_near(a, JP, split, tmap, true, s);
+  }
+  // far pass: Chebyshev series for r >= r_near (writes M)
+  a.rn2 = static_cast<float>(b->r_near * b->r_near);
+  st = dispatch_far(a, JP, split, tmap, s);
+  if (st != TSR_OK) return st;
+  // near pass: exact table for r < r_near over the chunks whose box is within r_near of the tile (adds to M)
+  const int n_tiles = a.n_otiles;
+  Scratch boxes, lists;
+  st = boxes.alloc(sizeof(float) * 6 * ((size_t)n_tiles + n_steps) + sizeof(int) * (2 * (size_t)n_tiles + 1), s);
+  if (st != TSR_OK) return st;
+  float *tile_box = static_cast<float *>(boxes.p);
+  float *chunk_box = tile_box + 6 * (size_t)n_tiles;
+  int *counts = reinterpret_cast<int *>(chunk_box + 6 * (size_t)n_steps);
+  int *offsets = counts + n_tiles;
+  bbox_kernel<<<(n_tiles + 127) / 128, 128, 0, s>>>(pos, N, 128, n_tiles, tile_box);
+  bbox_kernel<<<(n_steps + 127) / 128, 128, 0, s>>>(pos, N, 16, n_steps, chunk_box);
+  const float rn2m = a.rn2 * 1.001f + 1e-6f;
+  near_list_kernel<<<n_tiles, 256, 0, s>>>(tile_box, chunk_box, n_steps, rn2m, 0, counts, nullptr, nullptr);
+  scan_counts_kernel<<<1, 1024, 0, s>>>(counts, n_tiles, offsets);
+  st = lists.alloc(sizeof(int) * (size_t)n_tiles * n_steps, s);
+  if (st != TSR_OK) return st;
+  int *idx = static_cast<int *>(lists.p);
+  near_list_kernel<<<n_tiles, 256, 0, s>>>(tile_box, chunk_box, n_steps, rn2m, 1, counts, offsets, idx);
+  TSR_CUDA(cudaGetLastError());
+  a.near_off = offsets;
+  a.near_idx = idx;
+  a.accumulate = 1;
+  return dispatch_near(a, JP, split, tmap, false, s);
 }
 
 // Batched transfer over independent meshes: one launch per mesh, in order.

@@ -301,3 +301,19 @@ def test_invalid_arguments_are_rejected(torch_cuda, tsr, oracle_basis16):
     with pytest.raises(tsr.TsrError):
         tsr.precompute_transfer(basis, torch.zeros((3, 42), device="cuda"), torch.zeros(42, device="cuda"),
                                 torch.zeros((33, 42), device="cuda"))
+
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
+def test_transfer_nearfar_path(torch_cuda, tsr, oracle_basis16, precision, monkeypatch):
+    """Opt-in near/far split (Chebyshev far field in registers, exact table below r_near); same tolerances."""
+    torch = torch_cuda
+    f_ref, _ = oracle_basis16
+    monkeypatch.setenv("TSR_TRANSFER_NEARFAR", "1")
+    for nu, K, J in ((41, 12, 16), (42, 16, 25)):
+        sc, pos, area, T = _scene_arrays(nu, K, J, 0.12, 3)
+        basis = tsr.basis_create(f_ref[:K])
+        M = tsr.precompute_transfer(basis, _dev(torch, pos.T), _dev(torch, area), _dev(torch, T), precision)
+        tsr.stream_status()
+        rows = scene.sample_rows(sc.n, 256, seed=5)
+        M_ref = O.transfer_rows(f_ref[:K], pos, area, T, rows)
+        assert _normwise_k(M.cpu().numpy()[:, :, rows], M_ref) <= TOL[precision]
