@@ -119,6 +119,22 @@ def _traffic_record():
     return rec.get("traffic_bytes_per_launch")
 
 
+def reduce_max(values, world, device=None):
+    """Max over ranks of a few timings (the only collective of the benchmark)."""
+    if world <= 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def weak_scaling_value(units_per_rank: float, world: int, ms: float) -> float:
+    """Whole-job throughput in G units/s: every rank processed units_per_rank in ms (the max over ranks)."""
+    return world * units_per_rank / (ms * 1e-3) / 1e9
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -198,6 +214,7 @@ def run_gpu(args):
     ev_tr.clear()
     step_ev = []
     torch.cuda.synchronize()
+    launches0 = tsr.kernel_launches()
     for _ in range(args.steps):
         flush.zero_()
         a = torch.cuda.Event(enable_timing=True)
@@ -207,6 +224,7 @@ def run_gpu(args):
         b.record(stream)
         step_ev.append((a, b))
     torch.cuda.synchronize()
+    launches = tsr.kernel_launches() - launches0
     clk = clocks.stop()
     tsr.stream_status()
     ms_steps = [a.elapsed_time(b) for a, b in step_ev]
@@ -255,22 +273,14 @@ def run_gpu(args):
             by_prec[prec] = round(a.elapsed_time(b), 3)
         tsr.stream_status()
 
-    if world > 1:
-        t = torch.tensor([ms_per_step, e2e_step, statistics.mean(ms_transfer)], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_per_step, e2e_step, tr_mean = t.tolist()
-    else:
-        tr_mean = statistics.mean(ms_transfer)
-
+    ms_per_step, e2e_step, tr_mean = reduce_max([ms_per_step, e2e_step, statistics.mean(ms_transfer)], world, dev)
     units = float(N) * N * K * J
-    value = world * units / (ms_per_step * 1e-3) / 1e9
-    e2e_value = world * units / (e2e_step * 1e-3) / 1e9
+    value = weak_scaling_value(units, world, ms_per_step)
+    e2e_value = weak_scaling_value(units, world, e2e_step)
     peaks, peak_kind = _peaks()
     achieved_tflops = 2.0 * units / (tr_mean * 1e-3) / 1e12
     peak_tf = peaks.get("bf16_tflops_sustained", 1700.0)
     traffic = _traffic_record()
-    kernels_per_step = 14   # project, pretile, transfer, haar fwd, select, count, scan, fill, spmm, haar inv,
-                            # haar fwd (adjoint), spmm^T, grad finish, projection backward
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
@@ -281,7 +291,7 @@ def run_gpu(args):
                    "per_step": "project -> transfer(bf16) -> haar+select -> relight -> adjoint"},
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": round(e2e_step, 3)},
-        "gpu_launches": kernels_per_step * args.steps,
+        "gpu_launches": launches,
         "roofline": {"bound": "tensor", "achieved": round(achieved_tflops, 2), "peak": peak_tf,
                      "unit": "TFLOP/s", "frac": round(achieved_tflops / peak_tf, 4), "traffic": traffic,
                      "kernel": "transfer_tc_kernel (BF16 tcgen05), per launch",

@@ -72,6 +72,18 @@ const char *tsr_last_error(void);
 /* Library ABI version (major*100 + minor). */
 int tsr_version(void);
 
+/* Number of kernel launches the library has made in this process (all
+ * threads and devices); a diagnostic for counting launches in a region. */
+uint64_t tsr_kernel_launches(void);
+
+/* Diagnostic of the failure path: launches one block that waits, with at most
+ * `limit` (1..1e6) polls, on an mbarrier phase that nothing completes.  The
+ * wait gives up, the kernel records a timeout in the device status word and
+ * returns; the following tsr_stream_status reports TSR_ERR_TIMEOUT and the
+ * context stays usable.  The same bounded waits guard every pipeline barrier
+ * of the transfer kernels. */
+tsr_status tsr_selftest_bounded_wait(unsigned limit, tsr_stream stream);
+
 /* Synchronises the stream, then reports whether any library kernel since the
  * last check gave up a bounded wait (TSR_ERR_TIMEOUT) or flagged an
  * out-of-range access (TSR_ERR_CUDA); also returns the stream's own CUDA

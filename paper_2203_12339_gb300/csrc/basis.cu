@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(256) cheb_fit_kernel(const double *__restrict_
 
 tsr_status basis_build_tables(tsr_basis *b, cudaStream_t s) {
   const int n = (b->n_r + 1) * b->KP;
-  build_tables_kernel<<<(n + 255) / 256, 256, 0, s>>>(b->f64, b->K, b->KP, b->n_r, b->tab32, b->tab16);
+  build_tables_kernel<<<(n + 255) / 256, 256, 0, s>>>(b->f64, b->K, b->KP, b->n_r, b->tab32, b->tab16); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   // far-field series on [r_near, r_max], r_near = 3/40 r_max
   b->r_near = 0.075 * b->r_max;
@@ -216,7 +216,7 @@ tsr_status basis_build_tables(tsr_basis *b, cudaStream_t s) {
   b->x_alpha = (float)(std::log(2.0) / (hi - lo));
   b->x_beta = (float)(-1.0 - 2.0 * lo / (hi - lo));
   if (!b->cheb) TSR_CUDA(cudaMalloc(&b->cheb, sizeof(float) * b->K * TSR_CHEB_P));
-  cheb_fit_kernel<<<b->K, 256, 0, s>>>(b->f64, b->n_r, b->r_max, b->r_near, b->cheb);
+  cheb_fit_kernel<<<b->K, 256, 0, s>>>(b->f64, b->n_r, b->r_max, b->r_near, b->cheb); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }
@@ -358,14 +358,16 @@ extern "C" tsr_status tsr_fit_pca_basis(int n_mat, const double *sigma_a, const 
   FIT_CUDA(cudaMalloc(&col_of_rank, sizeof(int) * n_cols));
   FIT_CUDA(cudaMalloc(&rot, sizeof(unsigned)));
 
-  jacobi_build_kernel<<<n_cols, 256, 0, s>>>(sigma_a, sigma_s, eta, n_mat, n_cols, n_r, dr, A);
+  jacobi_build_kernel<<<n_cols, 256, 0, s>>>(sigma_a, sigma_s, eta, n_mat, n_cols, n_r, dr, A); ::tsr::count_launch();
   FIT_CUDA(cudaGetLastError());
   const double tol = 1e-14;
   bool converged = false;
   for (int sweep = 0; sweep < 60 && !converged; ++sweep) {
     FIT_CUDA(cudaMemsetAsync(rot, 0, sizeof(unsigned), s));
-    for (int r = 0; r < n_cols - 1; ++r)
+    for (int r = 0; r < n_cols - 1; ++r) {
       jacobi_round_kernel<<<n_cols / 2, 256, 0, s>>>(A, n_cols, n_r, r, tol, rot);
+      ::tsr::count_launch();
+    }
     FIT_CUDA(cudaGetLastError());
     unsigned h = 0;
     FIT_CUDA(cudaMemcpyAsync(&h, rot, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
@@ -378,8 +380,8 @@ extern "C" tsr_status tsr_fit_pca_basis(int n_mat, const double *sigma_a, const 
   }
   const int n_sv = std::min(n_mat, n_r);
   jacobi_rank_kernel<<<1, 1024, sizeof(double) * n_cols, s>>>(A, n_cols, n_r, n_sv, norms, col_of_rank,
-                                                                sing_vals);
-  jacobi_emit_kernel<<<K, 256, 0, s>>>(A, norms, col_of_rank, n_r, b->f64);
+                                                                sing_vals); ::tsr::count_launch();
+  jacobi_emit_kernel<<<K, 256, 0, s>>>(A, norms, col_of_rank, n_r, b->f64); ::tsr::count_launch();
   FIT_CUDA(cudaGetLastError());
   st = basis_build_tables(b, s);
   if (st != TSR_OK) return fail(st);
@@ -473,6 +475,7 @@ extern "C" tsr_status tsr_project_material(const tsr_basis *basis, int n, const 
   else
     project_kernel<false><<<n * 3, 256, 0, s>>>(basis->f64, basis->K, basis->n_r, dr, sigma_a, sigma_s, eta,
                                                 g, g32, nullptr);
+  ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }
@@ -491,7 +494,7 @@ extern "C" tsr_status tsr_project_material_backward(const tsr_basis *basis, int 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const double dr = basis->r_max / (basis->n_r - 1);
   project_backward_kernel<<<n, 256, 0, s>>>(basis->f64, basis->K, basis->n_r, dr, sigma_a, sigma_s, eta, dLdg,
-                                            dsigma_a, dsigma_s, deta);
+                                            dsigma_a, dsigma_s, deta); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }

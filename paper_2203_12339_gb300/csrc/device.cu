@@ -1,4 +1,5 @@
 // Per-thread error strings, device checks and the device status word.
+#include <atomic>
 #include <cstdarg>
 #include <mutex>
 #include <map>
@@ -19,6 +20,10 @@ void set_error(const char *fmt, ...) {
 void clear_error() { g_err[0] = '\0'; }
 
 const char *error_string() { return g_err; }
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launches() { return g_launches.load(std::memory_order_relaxed); }
 
 static std::mutex g_mu;
 static std::map<int, unsigned *> g_status;   // device -> status word
@@ -93,3 +98,5 @@ tsr_status check_device_status(cudaStream_t s) {
 }
 
 }  // namespace tsr
+
+extern "C" uint64_t tsr_kernel_launches(void) { return (uint64_t)tsr::launches(); }

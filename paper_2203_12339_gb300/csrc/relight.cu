@@ -116,7 +116,7 @@ tsr_status relight(const tsr_compressed *c, int n_edit, const float *g, const fl
   float *bw = static_cast<float *>(bw_s.p);
   const dim3 grid((c->n_rows + 255) / 256, (V + RL_VG - 1) / RL_VG);
   const size_t smem = sizeof(float) * KJ * RL_VG;
-  relight_spmm_kernel<<<grid, 256, smem, s>>>(c->row_ptr, c->col, c->val, c->n_rows, c->K, c->J, V, g, l, bw);
+  relight_spmm_kernel<<<grid, 256, smem, s>>>(c->row_ptr, c->col, c->val, c->n_rows, c->K, c->J, V, g, l, bw); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return haar_inverse(bw, V, c->nu, B, s);
 }
@@ -129,7 +129,7 @@ tsr_status relight_with_scratch(const tsr_compressed *c, int n_edit, const float
   const int KJ = c->K * c->J;
   const dim3 grid((c->n_rows + 255) / 256, (V + RL_VG - 1) / RL_VG);
   const size_t smem = sizeof(float) * KJ * RL_VG;
-  relight_spmm_kernel<<<grid, 256, smem, s>>>(c->row_ptr, c->col, c->val, c->n_rows, c->K, c->J, V, g, l, bw);
+  relight_spmm_kernel<<<grid, 256, smem, s>>>(c->row_ptr, c->col, c->val, c->n_rows, c->K, c->J, V, g, l, bw); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return haar_inverse(bw, V, c->nu, B, s);
 }
@@ -149,8 +149,8 @@ tsr_status relight_backward(const tsr_compressed *c, int n_edit, const float *g,
   TSR_CUDA(cudaMemsetAsync(dc, 0, sizeof(float) * (size_t)V * KJ, s));
   const dim3 grid((c->n_rows + 255) / 256, (V + RL_VG - 1) / RL_VG);
   const size_t smem = sizeof(float) * KJ * RL_VG;
-  relight_spmm_t_kernel<<<grid, 256, smem, s>>>(c->row_ptr, c->col, c->val, c->n_rows, KJ, V, rw, dc);
-  relight_grad_finish_kernel<<<1, 1024, 0, s>>>(dc, c->K, c->J, V, g, l, dg, dl);
+  relight_spmm_t_kernel<<<grid, 256, smem, s>>>(c->row_ptr, c->col, c->val, c->n_rows, KJ, V, rw, dc); ::tsr::count_launch();
+  relight_grad_finish_kernel<<<1, 1024, 0, s>>>(dc, c->K, c->J, V, g, l, dg, dl); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }

@@ -127,7 +127,7 @@ template <int JP>
 static cudaError_t launch_fp32(int grid, int threads, cudaStream_t s, const float *pos, int N, const float *Tp,
                                const float4 *tab, int KG, int n_r, float inv_dr, float r2max, int K, int J,
                                float *M, int n_tiles) {
-  transfer_fp32_kernel<JP><<<grid, threads, 0, s>>>(pos, N, Tp, tab, KG, n_r, inv_dr, r2max, K, J, M, n_tiles);
+  transfer_fp32_kernel<JP><<<grid, threads, 0, s>>>(pos, N, Tp, tab, KG, n_r, inv_dr, r2max, K, J, M, n_tiles); ::tsr::count_launch();
   return cudaGetLastError();
 }
 
@@ -139,7 +139,7 @@ tsr_status transfer_fp32(const tsr_basis *b, int N, const float *pos, const floa
   tsr_status st = tp.alloc(sizeof(float) * (size_t)n_pad * JP, s);
   if (st != TSR_OK) return st;
   float *Tp = static_cast<float *>(tp.p);
-  pretile_fp32_kernel<<<(n_pad * JP + 255) / 256, 256, 0, s>>>(area, T, N, J, JP, n_pad, Tp);
+  pretile_fp32_kernel<<<(n_pad * JP + 255) / 256, 256, 0, s>>>(area, T, N, J, JP, n_pad, Tp); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   const int KG = b->KP / 2;
   const int threads = F32_BO * KG;
@@ -1050,10 +1050,10 @@ static tsr_status launch_tc(const TcArgs &a0, int n_cols, const CUtensorMap &tma
     if (st != TSR_OK) return st;
     a.P = static_cast<float *>(part.p);
   }
-  kern<<<grid, C::NTHREADS, smem, s>>>(tmap, a);
+  kern<<<grid, C::NTHREADS, smem, s>>>(tmap, a); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   if (n_dest > 1) {
-    add_partials_kernel<<<4 * sms, 256, 0, s>>>(a.M, a.P, n_dest - 1, mn);
+    add_partials_kernel<<<4 * sms, 256, 0, s>>>(a.M, a.P, n_dest - 1, mn); ::tsr::count_launch();
     TSR_CUDA(cudaGetLastError());
   }
   return TSR_OK;
@@ -1112,7 +1112,7 @@ tsr_status transfer_tc(const tsr_basis *b, int N, const float *pos, const float 
   uint8_t *rec = static_cast<uint8_t *>(rs.p);
   TSR_CUDA(cudaMemsetAsync(rec, 0, (size_t)n_steps * REC, s));
   pretile_tc_kernel<<<(n_steps * 16 + 255) / 256, 256, 0, s>>>(pos, area, T, N, J, JP, split ? 1 : 0, REC, n_steps,
-                                                                rec);
+                                                                rec); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   CUtensorMap tmap;
   st = make_record_map(&tmap, rec, n_steps, REC);
@@ -1157,15 +1157,15 @@ tsr_status transfer_tc(const tsr_basis *b, int N, const float *pos, const float 
   float *chunk_box = tile_box + 6 * (size_t)n_tiles;
   int *counts = reinterpret_cast<int *>(chunk_box + 6 * (size_t)n_steps);
   int *offsets = counts + n_tiles;
-  bbox_kernel<<<(n_tiles + 127) / 128, 128, 0, s>>>(pos, N, 128, n_tiles, tile_box);
-  bbox_kernel<<<(n_steps + 127) / 128, 128, 0, s>>>(pos, N, 16, n_steps, chunk_box);
+  bbox_kernel<<<(n_tiles + 127) / 128, 128, 0, s>>>(pos, N, 128, n_tiles, tile_box); ::tsr::count_launch();
+  bbox_kernel<<<(n_steps + 127) / 128, 128, 0, s>>>(pos, N, 16, n_steps, chunk_box); ::tsr::count_launch();
   const float rn2m = a.rn2 * 1.001f + 1e-6f;
-  near_list_kernel<<<n_tiles, 256, 0, s>>>(tile_box, chunk_box, n_steps, rn2m, 0, counts, nullptr, nullptr);
-  scan_counts_kernel<<<1, 1024, 0, s>>>(counts, n_tiles, offsets);
+  near_list_kernel<<<n_tiles, 256, 0, s>>>(tile_box, chunk_box, n_steps, rn2m, 0, counts, nullptr, nullptr); ::tsr::count_launch();
+  scan_counts_kernel<<<1, 1024, 0, s>>>(counts, n_tiles, offsets); ::tsr::count_launch();
   st = lists.alloc(sizeof(int) * (size_t)n_tiles * n_steps, s);
   if (st != TSR_OK) return st;
   int *idx = static_cast<int *>(lists.p);
-  near_list_kernel<<<n_tiles, 256, 0, s>>>(tile_box, chunk_box, n_steps, rn2m, 1, counts, offsets, idx);
+  near_list_kernel<<<n_tiles, 256, 0, s>>>(tile_box, chunk_box, n_steps, rn2m, 1, counts, offsets, idx); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   a.near_off = offsets;
   a.near_idx = idx;

@@ -39,6 +39,9 @@ enum : unsigned { DEV_ERR_TIMEOUT = 1u, DEV_ERR_BOUNDS = 2u };
 tsr_status check_device_status(cudaStream_t s);   // synchronises s
 unsigned *device_status_ptr();                     // device address of the word (current device)
 
+// Count of kernel launches made by the library (all threads, all devices).
+void count_launch();
+
 // Verifies that the current device is an sm_103 part (the only compiled target).
 tsr_status require_device();
 int num_sms();

@@ -100,7 +100,7 @@ tsr_status haar_forward(const float *X, int rows, int nu, float *Xw, cudaStream_
   const int N = 10 * nu * nu + 2, NW = 10 * P * P + 2;
   const size_t smem = sizeof(float) * (size_t)P * P * 2;
   TSR_CUDA(cudaFuncSetAttribute(haar_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  haar_forward_kernel<<<rows * 10, haar_threads(P * P), smem, s>>>(X, nu, P, bits, N, NW, Xw);
+  haar_forward_kernel<<<rows * 10, haar_threads(P * P), smem, s>>>(X, nu, P, bits, N, NW, Xw); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }
@@ -110,7 +110,7 @@ tsr_status haar_inverse(const float *Xw, int rows, int nu, float *X, cudaStream_
   const int N = 10 * nu * nu + 2, NW = 10 * P * P + 2;
   const size_t smem = sizeof(float) * (size_t)P * P * 2;
   TSR_CUDA(cudaFuncSetAttribute(haar_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  haar_inverse_kernel<<<rows * 10, haar_threads(P * P), smem, s>>>(Xw, nu, P, bits, N, NW, X);
+  haar_inverse_kernel<<<rows * 10, haar_threads(P * P), smem, s>>>(Xw, nu, P, bits, N, NW, X); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }
@@ -261,10 +261,10 @@ tsr_status wavelet_compress_into(const float *Mw, tsr_compressed *c, cudaStream_
   if (st != TSR_OK) return st;
   uint8_t *keep = static_cast<uint8_t *>(keep_s.p);
   int64_t *cnt = static_cast<int64_t *>(cnt_s.p);
-  select_kernel<<<KJ, 1024, 0, s>>>(Mw, n_coef, NW, c->n_keep, keep);
-  count_kernel<<<(NW + 255) / 256, 256, 0, s>>>(keep, KJ, NW, cnt);
-  scan_kernel<<<1, 1024, 0, s>>>(cnt, NW, c->row_ptr);
-  fill_kernel<<<(NW + 255) / 256, 256, 0, s>>>(Mw, keep, KJ, NW, c->row_ptr, c->col, c->val);
+  select_kernel<<<KJ, 1024, 0, s>>>(Mw, n_coef, NW, c->n_keep, keep); ::tsr::count_launch();
+  count_kernel<<<(NW + 255) / 256, 256, 0, s>>>(keep, KJ, NW, cnt); ::tsr::count_launch();
+  scan_kernel<<<1, 1024, 0, s>>>(cnt, NW, c->row_ptr); ::tsr::count_launch();
+  fill_kernel<<<(NW + 255) / 256, 256, 0, s>>>(Mw, keep, KJ, NW, c->row_ptr, c->col, c->val); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }

@@ -33,6 +33,8 @@ _SIGNATURES = {
     "tsr_last_error": (ctypes.c_char_p, []),
     "tsr_version": (_I, []),
     "tsr_stream_status": (_I, [_P]),
+    "tsr_kernel_launches": (ctypes.c_uint64, []),
+    "tsr_selftest_bounded_wait": (_I, [ctypes.c_uint, _P]),
     "tsr_fit_pca_basis": (_I, [_I, _P, _P, _D, _I, _D, _I, _P, ctypes.POINTER(_P), _P]),
     "tsr_basis_create": (_I, [_I, _I, _D, _P, ctypes.POINTER(_P)]),
     "tsr_basis_table": (_I, [_P, _P, _P]),
@@ -106,6 +108,16 @@ def _ptr(t: torch.Tensor | None):
 def stream_status() -> None:
     """Synchronise the current stream and raise if a kernel gave up a bounded wait."""
     _check(lib().tsr_stream_status(_stream()))
+
+
+def kernel_launches() -> int:
+    """Kernel launches made by the library so far in this process."""
+    return int(lib().tsr_kernel_launches())
+
+
+def selftest_bounded_wait(limit: int = 1000) -> None:
+    """Run the bounded-wait diagnostic kernel (a wait that nothing ends); see include/tsr.h."""
+    _check(lib().tsr_selftest_bounded_wait(int(limit), _stream()))
 
 
 # ---------------------------------------------------------------- basis
