@@ -29,6 +29,10 @@ struct tsr_compressed {
   int64_t *row_ptr = nullptr;   // [n_rows + 1]
   uint16_t *col = nullptr;      // [nnz]  k*J + j
   float *val = nullptr;         // [nnz]
+  // The same entries by column: column kj holds exactly n_keep + 2 entries
+  // (ascending wavelet row), used by the reverse mode.
+  int32_t *cidx = nullptr;      // [K*J][n_keep + 2] wavelet rows
+  float *cval = nullptr;        // [K*J][n_keep + 2]
 };
 
 namespace tsr {

@@ -56,33 +56,39 @@ __global__ void __launch_bounds__(256) relight_spmm_kernel(const int64_t *__rest
     if (v0 + vv < V) bw[(size_t)(v0 + vv) * n_rows + w] = acc[vv];
 }
 
-// dc[v][kj] += sum_w S[w][kj] r^w[v][w]; per-block partials in shared memory.
-__global__ void __launch_bounds__(256) relight_spmm_t_kernel(const int64_t *__restrict__ row_ptr,
-                                                            const uint16_t *__restrict__ col,
-                                                            const float *__restrict__ val, int n_rows, int KJ, int V,
-                                                            const float *__restrict__ rw, float *__restrict__ dc) {
-  extern __shared__ float part[];   // [KJ][RL_VG]
+// dc[v][kj] = sum over the n_keep+2 entries (w, val) of column kj of val * r^w[v][w]:
+// one block per (kj, group of RL_VG vectors), no atomics.
+__global__ void __launch_bounds__(256) relight_colgather_kernel(const int32_t *__restrict__ cidx,
+                                                               const float *__restrict__ cval, int ncol, int n_rows,
+                                                               int KJ, int V, const float *__restrict__ rw,
+                                                               float *__restrict__ dc) {
+  __shared__ float red[RL_VG][8];
+  const int kj = blockIdx.x;
   const int v0 = blockIdx.y * RL_VG;
-  for (int q = threadIdx.x; q < KJ * RL_VG; q += blockDim.x) part[q] = 0.0f;
-  __syncthreads();
-  const int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w < n_rows) {
-    float r[RL_VG];
+  float acc[RL_VG];
 #pragma unroll
-    for (int vv = 0; vv < RL_VG; ++vv) r[vv] = (v0 + vv < V) ? rw[(size_t)(v0 + vv) * n_rows + w] : 0.0f;
-    const int64_t p1 = row_ptr[w + 1];
-    for (int64_t p = row_ptr[w]; p < p1; ++p) {
-      const float a = val[p];
-      float *pr = part + (int)col[p] * RL_VG;
+  for (int vv = 0; vv < RL_VG; ++vv) acc[vv] = 0.0f;
+  const int32_t *ci = cidx + (size_t)kj * ncol;
+  const float *cv = cval + (size_t)kj * ncol;
+  for (int q = threadIdx.x; q < ncol; q += blockDim.x) {
+    const int w = ci[q];
+    const float a = cv[q];
 #pragma unroll
-      for (int vv = 0; vv < RL_VG; ++vv)
-        if (r[vv] != 0.0f) atomicAdd(pr + vv, a * r[vv]);
-    }
+    for (int vv = 0; vv < RL_VG; ++vv)
+      if (v0 + vv < V) acc[vv] = fmaf(a, rw[(size_t)(v0 + vv) * n_rows + w], acc[vv]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int vv = 0; vv < RL_VG; ++vv) {
+    float x = acc[vv];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[vv][warp] = x;
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < KJ * RL_VG; q += blockDim.x) {
-    const int kj = q / RL_VG, vv = q % RL_VG, v = v0 + vv;
-    if (v < V && part[q] != 0.0f) atomicAdd(&dc[(size_t)v * KJ + kj], part[q]);
+  if (threadIdx.x < RL_VG && v0 + threadIdx.x < V) {
+    float x = 0.0f;
+    for (int w8 = 0; w8 < 8; ++w8) x += red[threadIdx.x][w8];
+    dc[(size_t)(v0 + threadIdx.x) * KJ + kj] = x;
   }
 }
 
@@ -146,10 +152,8 @@ tsr_status relight_backward(const tsr_compressed *c, int n_edit, const float *g,
   float *dc = static_cast<float *>(dc_s.p);
   st = haar_forward(dLdB, V, c->nu, rw, s);
   if (st != TSR_OK) return st;
-  TSR_CUDA(cudaMemsetAsync(dc, 0, sizeof(float) * (size_t)V * KJ, s));
-  const dim3 grid((c->n_rows + 255) / 256, (V + RL_VG - 1) / RL_VG);
-  const size_t smem = sizeof(float) * KJ * RL_VG;
-  relight_spmm_t_kernel<<<grid, 256, smem, s>>>(c->row_ptr, c->col, c->val, c->n_rows, KJ, V, rw, dc); ::tsr::count_launch();
+  const dim3 grid(KJ, (V + RL_VG - 1) / RL_VG);
+  relight_colgather_kernel<<<grid, 256, 0, s>>>(c->cidx, c->cval, c->n_keep + 2, c->n_rows, KJ, V, rw, dc); ::tsr::count_launch();
   relight_grad_finish_kernel<<<1, 1024, 0, s>>>(dc, c->K, c->J, V, g, l, dg, dl); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;

@@ -187,6 +187,37 @@ __global__ void __launch_bounds__(1024) select_kernel(const float *__restrict__ 
   }
 }
 
+// Column view: block per kj compacts its kept rows in ascending order.
+__global__ void __launch_bounds__(1024) pack_columns_kernel(const float *__restrict__ Mw,
+                                                           const uint8_t *__restrict__ keep, int NW, int ncol,
+                                                           int32_t *__restrict__ cidx, float *__restrict__ cval) {
+  __shared__ unsigned warp_tot[32];
+  const int kj = blockIdx.x;
+  const uint8_t *kp = keep + (size_t)kj * NW;
+  const float *c = Mw + (size_t)kj * NW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned written = 0;
+  for (int base = 0; base < NW; base += blockDim.x) {
+    const int w = base + threadIdx.x;
+    const bool k = (w < NW) && kp[w];
+    const unsigned bal = __ballot_sync(0xffffffffu, k);
+    if (lane == 0) warp_tot[warp] = __popc(bal);
+    __syncthreads();
+    unsigned before = 0, total = 0;
+    for (int q = 0; q < nw; ++q) {
+      before += (q < warp) ? warp_tot[q] : 0u;
+      total += warp_tot[q];
+    }
+    const unsigned pos = written + before + __popc(bal & ((1u << lane) - 1u));
+    if (k && pos < (unsigned)ncol) {
+      cidx[(size_t)kj * ncol + pos] = w;
+      cval[(size_t)kj * ncol + pos] = c[w];
+    }
+    written += total;
+    __syncthreads();
+  }
+}
+
 // entries per wavelet row w (over all kj)
 __global__ void count_kernel(const uint8_t *__restrict__ keep, int KJ, int NW, int64_t *__restrict__ cnt) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
@@ -265,6 +296,7 @@ tsr_status wavelet_compress_into(const float *Mw, tsr_compressed *c, cudaStream_
   count_kernel<<<(NW + 255) / 256, 256, 0, s>>>(keep, KJ, NW, cnt); ::tsr::count_launch();
   scan_kernel<<<1, 1024, 0, s>>>(cnt, NW, c->row_ptr); ::tsr::count_launch();
   fill_kernel<<<(NW + 255) / 256, 256, 0, s>>>(Mw, keep, KJ, NW, c->row_ptr, c->col, c->val); ::tsr::count_launch();
+  pack_columns_kernel<<<KJ, 1024, 0, s>>>(Mw, keep, NW, c->n_keep + 2, c->cidx, c->cval); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }
@@ -284,6 +316,8 @@ tsr_status wavelet_compress(const float *Mw, int K, int J, int nu, double p, tsr
   cudaError_t e = cudaMalloc(&c->row_ptr, sizeof(int64_t) * (NW + 1));
   if (e == cudaSuccess) e = cudaMalloc(&c->col, sizeof(uint16_t) * c->nnz);
   if (e == cudaSuccess) e = cudaMalloc(&c->val, sizeof(float) * c->nnz);
+  if (e == cudaSuccess) e = cudaMalloc(&c->cidx, sizeof(int32_t) * c->nnz);
+  if (e == cudaSuccess) e = cudaMalloc(&c->cval, sizeof(float) * c->nnz);
   if (e != cudaSuccess) {
     set_error("wavelet_compress: %s", cudaGetErrorString(e));
     tsr_compressed_destroy(c);
@@ -305,5 +339,7 @@ extern "C" void tsr_compressed_destroy(tsr_compressed *c) {
   cudaFree(c->row_ptr);
   cudaFree(c->col);
   cudaFree(c->val);
+  cudaFree(c->cidx);
+  cudaFree(c->cval);
   delete c;
 }
