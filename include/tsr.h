@@ -159,14 +159,37 @@ tsr_status tsr_precompute_transfer(const tsr_basis *basis, int N, const float *p
                                    const float *T, int J, tsr_precision prec, float *M,
                                    tsr_stream stream);
 
-/* Batched transfer over n_mesh independent meshes of uneven size in one
- * persistent launch.  All arrays are concatenated over the meshes:
- *   offsets : HOST [n_mesh + 1] int64 vertex offsets (offsets[0] = 0).
+/* Batched transfer over n_mesh independent meshes of uneven size (Eq. 6-7 per
+ * mesh; pairs never cross meshes).  All arrays are concatenated over the meshes:
+ *   offsets : HOST [n_mesh + 1] int64 vertex offsets (offsets[0] = 0; 12 <= each mesh <= 2^24).
  *   pos     : device [3][total] FP32;  area: device [total];  T: device [J][total];
- *   M       : device [K][J][total] FP32 out.  Only TSR_BF16 and TSR_FP32.  */
+ *   M       : device [K][J][total] FP32 out.  Only TSR_BF16 and TSR_FP32.
+ * TSR_BF16 runs one persistent launch over the (mesh, 128-row tile) units in
+ * longest-first order; TSR_FP32 runs one launch per mesh.
+ *
+ * tsr_precompute_transfer_batched synchronises the stream (it builds and frees
+ * a plan).  For repeated or graph-captured use, build a plan once:
+ *   tsr_batch_plan_create   uploads the unit and mesh tables (synchronous);
+ *   tsr_batch_plan_autotune times each tile configuration (bases per CTA group)
+ *                           on the caller's data, keeps the fastest, returns its
+ *                           time in *best_ms (synchronises; outside any capture);
+ *   tsr_precompute_transfer_plan enqueues the transfer only (kernels and
+ *                           stream-ordered scratch), so it may be captured in a
+ *                           CUDA graph;
+ *   tsr_batch_plan_info     units and chosen bases per group (0 = default);
+ *   tsr_batch_plan_destroy. */
 tsr_status tsr_precompute_transfer_batched(const tsr_basis *basis, int n_mesh, const int64_t *offsets,
                                            const float *pos, const float *area, const float *T, int J,
                                            tsr_precision prec, float *M, tsr_stream stream);
+typedef struct tsr_batch_plan tsr_batch_plan;
+tsr_status tsr_batch_plan_create(const tsr_basis *basis, int n_mesh, const int64_t *offsets, int J,
+                                 tsr_precision prec, tsr_batch_plan **out);
+tsr_status tsr_batch_plan_autotune(tsr_batch_plan *plan, const float *pos, const float *area, const float *T,
+                                   float *M, tsr_stream stream, float *best_ms);
+tsr_status tsr_precompute_transfer_plan(const tsr_batch_plan *plan, const float *pos, const float *area,
+                                        const float *T, float *M, tsr_stream stream);
+tsr_status tsr_batch_plan_info(const tsr_batch_plan *plan, int *n_units, int *kb);
+void tsr_batch_plan_destroy(tsr_batch_plan *plan);
 
 /* ------------------------------------------------------------------------
  * Spatial wavelet (Section 3.2, Eq. 9-10).  Vertex data of the chart mesh

@@ -179,3 +179,53 @@ extern "C" tsr_status tsr_relight_backward(const tsr_compressed *c, int n_edit, 
   if (st != TSR_OK) return st;
   return relight_backward(c, n_edit, g, l, dLdB, dg, dl, as_stream(stream));
 }
+
+extern "C" tsr_status tsr_batch_plan_create(const tsr_basis *basis, int n_mesh, const int64_t *offsets, int J,
+                                            tsr_precision prec, tsr_batch_plan **out) {
+  clear_error();
+  TSR_CHECK_ARG(basis && offsets && out, "tsr_batch_plan_create: NULL argument");
+  TSR_CHECK_ARG(n_mesh >= 1 && n_mesh <= 65536, "tsr_batch_plan_create: n_mesh=%d out of range", n_mesh);
+  TSR_CHECK_ARG(J >= 1 && J <= 32, "tsr_batch_plan_create: J=%d outside [1, 32]", J);
+  TSR_CHECK_ARG(offsets[0] == 0, "tsr_batch_plan_create: offsets[0] must be 0");
+  for (int b = 0; b < n_mesh; ++b)
+    TSR_CHECK_ARG(offsets[b + 1] - offsets[b] >= 12 && offsets[b + 1] - offsets[b] <= (1 << 24),
+                  "tsr_batch_plan_create: mesh %d has %lld vertices", b, (long long)(offsets[b + 1] - offsets[b]));
+  TSR_CHECK_ARG(prec == TSR_BF16 || prec == TSR_FP32, "tsr_batch_plan_create: precision %d unsupported", (int)prec);
+  *out = nullptr;
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  return batch_plan_create(basis, n_mesh, offsets, J, (int)prec, out);
+}
+
+extern "C" tsr_status tsr_precompute_transfer_plan(const tsr_batch_plan *plan, const float *pos, const float *area,
+                                                   const float *T, float *M, tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(plan && pos && area && T && M, "tsr_precompute_transfer_plan: NULL argument");
+  TSR_CHECK_ARG(aligned(pos, 16), "tsr_precompute_transfer_plan: misaligned pos");
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  return batch_plan_run(plan, pos, area, T, M, as_stream(stream));
+}
+
+extern "C" tsr_status tsr_batch_plan_autotune(tsr_batch_plan *plan, const float *pos, const float *area,
+                                              const float *T, float *M, tsr_stream stream, float *best_ms) {
+  clear_error();
+  TSR_CHECK_ARG(plan && pos && area && T && M, "tsr_batch_plan_autotune: NULL argument");
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  return batch_plan_autotune(plan, pos, area, T, M, as_stream(stream), best_ms);
+}
+
+extern "C" tsr_status tsr_batch_plan_info(const tsr_batch_plan *plan, int *n_units, int *kb) {
+  clear_error();
+  TSR_CHECK_ARG(plan, "tsr_batch_plan_info: NULL plan");
+  if (n_units) *n_units = plan->n_units;
+  if (kb) *kb = plan->kb;
+  return TSR_OK;
+}
+
+extern "C" void tsr_batch_plan_destroy(tsr_batch_plan *plan) {
+  if (!plan) return;
+  cudaFree(plan->tables);
+  delete plan;
+}

@@ -1,5 +1,7 @@
 // Library-owned objects behind the opaque handles of tsr.h.
 #pragma once
+#include <vector>
+
 #include "tsr_internal.cuh"
 
 // Radial basis f_k on the grid r_m = r_max m / (n_r - 1) plus the lookup tables
@@ -35,10 +37,32 @@ struct tsr_compressed {
   float *cval = nullptr;        // [K*J][n_keep + 2]
 };
 
+// Batched-transfer plan: unit and mesh tables on the device (built once, outside
+// any stream capture) and the chosen tile configuration.
+struct tsr_batch_plan {
+  int device = -1;
+  const tsr_basis *basis = nullptr;
+  int n_mesh = 0, J = 0, total_steps = 0, n_units = 0;
+  long long total = 0;
+  int prec = 1;                 // tsr_precision
+  int kb = 0;                   // bases per CTA group (0: default for K)
+  std::vector<int64_t> offsets; // host copy
+  void *tables = nullptr;       // device: units | voff | N | soff
+  int4 *d_units = nullptr;
+  long long *d_voff = nullptr;
+  int *d_N = nullptr, *d_soff = nullptr;
+};
+
 namespace tsr {
+tsr_status batch_plan_create(const tsr_basis *b, int n_mesh, const int64_t *offsets, int J, int prec,
+                             tsr_batch_plan **out);
+tsr_status batch_plan_run(const tsr_batch_plan *p, const float *pos, const float *area, const float *T, float *M,
+                          cudaStream_t s);
+tsr_status batch_plan_autotune(tsr_batch_plan *p, const float *pos, const float *area, const float *T, float *M,
+                               cudaStream_t s, float *best_ms);
 tsr_status basis_build_tables(tsr_basis *b, cudaStream_t s);
 tsr_status transfer_fp32(const tsr_basis *b, int N, const float *pos, const float *area, const float *T,
-                         int J, float *M, cudaStream_t s);
+                         int J, float *M, cudaStream_t s, long long stride = 0);
 tsr_status transfer_tc(const tsr_basis *b, int N, const float *pos, const float *area, const float *T,
                        int J, bool split, float *M, cudaStream_t s);
 tsr_status transfer_tc_batched(const tsr_basis *b, int n_mesh, const int64_t *offsets, const float *pos,

@@ -43,24 +43,24 @@ constexpr int F32_BO = 32;   // output rows per block
 constexpr int F32_BI = 64;   // i per shared-memory tile
 
 // T'[i][jp] = A_i T[j][i] (FP32, zero for j >= J or i >= N), rows padded to a multiple of F32_BI.
-__global__ void pretile_fp32_kernel(const float *__restrict__ area, const float *__restrict__ T, int N, int J,
-                                    int JP, int n_pad, float *__restrict__ Tp) {
+__global__ void pretile_fp32_kernel(const float *__restrict__ area, const float *__restrict__ T, int N, long long stride,
+                                    int J, int JP, int n_pad, float *__restrict__ Tp) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n_pad * JP) return;
   const int i = idx / JP, j = idx % JP;
-  Tp[idx] = (i < N && j < J) ? area[i] * T[(size_t)j * N + i] : 0.0f;
+  Tp[idx] = (i < N && j < J) ? area[i] * T[(size_t)j * stride + i] : 0.0f;
 }
 
 template <int JP>
 __global__ void __launch_bounds__(256, 1)
-    transfer_fp32_kernel(const float *__restrict__ pos, int N, const float *__restrict__ Tp,
+    transfer_fp32_kernel(const float *__restrict__ pos, int N, long long stride, const float *__restrict__ Tp,
                          const float4 *__restrict__ tab, int KG, int n_r, float inv_dr, float r2max, int K,
                          int J, float *__restrict__ M, int n_tiles) {
   __shared__ __align__(16) float sT[F32_BI * JP];
   __shared__ float sx[F32_BI], sy[F32_BI], sz[F32_BI];
   const int kg = threadIdx.x % KG;
   const int ol = threadIdx.x / KG;
-  const float *px = pos, *py = pos + N, *pz = pos + 2 * (size_t)N;
+  const float *px = pos, *py = pos + stride, *pz = pos + 2 * stride;
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     const int o = tile * F32_BO + ol;
     const bool o_ok = o < N;
@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
       for (int j = 0; j < JP; ++j) {
         if (j < J) {
-          if (k0 < K) M[((size_t)k0 * J + j) * N + o] = acc0[j];
-          if (k1 < K) M[((size_t)k1 * J + j) * N + o] = acc1[j];
+          if (k0 < K) M[((size_t)k0 * J + j) * stride + o] = acc0[j];
+          if (k1 < K) M[((size_t)k1 * J + j) * stride + o] = acc1[j];
         }
       }
     }
@@ -124,22 +124,23 @@ __global__ void __launch_bounds__(256, 1)
 }
 
 template <int JP>
-static cudaError_t launch_fp32(int grid, int threads, cudaStream_t s, const float *pos, int N, const float *Tp,
-                               const float4 *tab, int KG, int n_r, float inv_dr, float r2max, int K, int J,
-                               float *M, int n_tiles) {
-  transfer_fp32_kernel<JP><<<grid, threads, 0, s>>>(pos, N, Tp, tab, KG, n_r, inv_dr, r2max, K, J, M, n_tiles); ::tsr::count_launch();
+static cudaError_t launch_fp32(int grid, int threads, cudaStream_t s, const float *pos, int N, long long stride,
+                               const float *Tp, const float4 *tab, int KG, int n_r, float inv_dr, float r2max, int K,
+                               int J, float *M, int n_tiles) {
+  transfer_fp32_kernel<JP><<<grid, threads, 0, s>>>(pos, N, stride, Tp, tab, KG, n_r, inv_dr, r2max, K, J, M, n_tiles); ::tsr::count_launch();
   return cudaGetLastError();
 }
 
 tsr_status transfer_fp32(const tsr_basis *b, int N, const float *pos, const float *area, const float *T, int J,
-                         float *M, cudaStream_t s) {
+                         float *M, cudaStream_t s, long long stride) {
+  if (stride <= 0) stride = N;
   const int JP = (J + 3) & ~3;
   const int n_pad = (N + F32_BI - 1) / F32_BI * F32_BI;
   Scratch tp;
   tsr_status st = tp.alloc(sizeof(float) * (size_t)n_pad * JP, s);
   if (st != TSR_OK) return st;
   float *Tp = static_cast<float *>(tp.p);
-  pretile_fp32_kernel<<<(n_pad * JP + 255) / 256, 256, 0, s>>>(area, T, N, J, JP, n_pad, Tp); ::tsr::count_launch();
+  pretile_fp32_kernel<<<(n_pad * JP + 255) / 256, 256, 0, s>>>(area, T, N, stride, J, JP, n_pad, Tp); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   const int KG = b->KP / 2;
   const int threads = F32_BO * KG;
@@ -151,7 +152,7 @@ tsr_status transfer_fp32(const tsr_basis *b, int N, const float *pos, const floa
   cudaError_t e;
   switch (JP) {
 #define F32_CASE(JPV) \
-  case JPV: e = launch_fp32<JPV>(grid, threads, s, pos, N, Tp, tab, KG, b->n_r, inv_dr, r2max, b->K, J, M, n_tiles); break;
+  case JPV: e = launch_fp32<JPV>(grid, threads, s, pos, N, stride, Tp, tab, KG, b->n_r, inv_dr, r2max, b->K, J, M, n_tiles); break;
     F32_CASE(4) F32_CASE(8) F32_CASE(12) F32_CASE(16) F32_CASE(20) F32_CASE(24) F32_CASE(28) F32_CASE(32)
 #undef F32_CASE
     default:
@@ -174,19 +175,16 @@ __host__ __device__ constexpr int rec_bytes(int JP, bool split) {
   return ((JP * 32 * (split ? 2 : 1) + 192) + 127) / 128 * 128;
 }
 
-__global__ void pretile_tc_kernel(const float *__restrict__ pos, const float *__restrict__ area,
-                                  const float *__restrict__ T, int N, int J, int JP, int split, int REC,
-                                  int n_steps, uint8_t *__restrict__ rec) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;   // (step, ii)
-  if (idx >= n_steps * 16) return;
-  const int step = idx / 16, ii = idx % 16;
-  const int i = step * 16 + ii;
-  const bool ok = i < N;
+// Writes entry ii of record `step` for vertex i of a mesh whose arrays start at
+// vertex 0 of `pos`/`area`/`T` with row stride `stride` (ok = false: padding).
+__device__ __forceinline__ void pretile_entry(const float *__restrict__ pos, const float *__restrict__ area,
+                                              const float *__restrict__ T, long long stride, int J, int JP, int split,
+                                              int REC, int step, int ii, int i, bool ok, uint8_t *__restrict__ rec) {
   uint8_t *r = rec + (size_t)step * REC;
   const float a = ok ? area[i] : 0.0f;
   const int h = ii / 8, e = ii % 8;
   for (int j = 0; j < JP; ++j) {
-    const float v = (ok && j < J) ? a * T[(size_t)j * N + i] : 0.0f;
+    const float v = (ok && j < J) ? a * T[(size_t)j * stride + i] : 0.0f;
     const __nv_bfloat16 hi = __float2bfloat16_rn(v);
     const size_t off = (size_t)h * JP * 16 + (size_t)j * 16 + e * 2;
     *reinterpret_cast<__nv_bfloat16 *>(r + off) = hi;
@@ -197,8 +195,37 @@ __global__ void pretile_tc_kernel(const float *__restrict__ pos, const float *__
   }
   float *p = reinterpret_cast<float *>(r + JP * 32 * (split ? 2 : 1));
   p[ii] = ok ? pos[i] : 0.0f;
-  p[16 + ii] = ok ? pos[N + i] : 0.0f;
-  p[32 + ii] = ok ? pos[2 * (size_t)N + i] : 0.0f;
+  p[16 + ii] = ok ? pos[stride + i] : 0.0f;
+  p[32 + ii] = ok ? pos[2 * stride + i] : 0.0f;
+}
+
+__global__ void pretile_tc_kernel(const float *__restrict__ pos, const float *__restrict__ area,
+                                  const float *__restrict__ T, int N, int J, int JP, int split, int REC,
+                                  int n_steps, uint8_t *__restrict__ rec) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;   // (step, ii)
+  if (idx >= n_steps * 16) return;
+  const int step = idx / 16, ii = idx % 16;
+  const int i = step * 16 + ii;
+  pretile_entry(pos, area, T, N, J, JP, split, REC, step, ii, i, i < N, rec);
+}
+
+// Records of concatenated meshes: mesh b owns records [mesh_soff[b], mesh_soff[b+1]).
+__global__ void pretile_tc_batched_kernel(const float *__restrict__ pos, const float *__restrict__ area,
+                                          const float *__restrict__ T, long long stride, int J, int JP, int split,
+                                          int REC, int n_steps, const int *__restrict__ mesh_soff, int n_mesh,
+                                          const int *__restrict__ mesh_N, const long long *__restrict__ mesh_voff,
+                                          uint8_t *__restrict__ rec) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n_steps * 16) return;
+  const int step = idx / 16, ii = idx % 16;
+  int lo = 0, hi = n_mesh;   // mesh_soff[lo] <= step < mesh_soff[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (mesh_soff[mid] <= step) lo = mid; else hi = mid;
+  }
+  const int i = (step - mesh_soff[lo]) * 16 + ii;
+  const long long v = mesh_voff[lo];
+  pretile_entry(pos + v, area + v, T + v, stride, J, JP, split, REC, step, ii, i, i < mesh_N[lo], rec);
 }
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -310,6 +337,22 @@ struct TcArgs {
   float *M;          // [K][J][N]
   float *P;          // [n_dest - 1][K][J][N] partial sums (NULL if one destination)
   unsigned *status;
+  // Batched meshes (units != NULL): arrays are concatenated along the vertex axis
+  // with row stride `stride`; unit u = (mesh, tile, split, splits of that mesh).
+  const int4 *units;
+  int n_units_total;
+  const int *mesh_N;
+  const long long *mesh_voff;   // first vertex of each mesh
+  const int *mesh_soff;         // first record of each mesh
+  long long stride;             // total vertices (= N for one mesh)
+};
+
+// Everything a CTA needs to know about one unit of work.
+struct Unit {
+  int t, sp, sb, se;   // tile, split, stage range [sb, se)
+  int Nb;              // vertices of the unit's mesh
+  long long voff;      // first vertex of the mesh
+  int soff;            // first record of the mesh
 };
 
 template <int MODE, int CB, int JP, bool SPLIT, int NS>
@@ -368,21 +411,42 @@ __device__ __forceinline__ float fast_lg2(float x) {
   return y;
 }
 
-// Stage range [b, e) of unit u (tile t, split sp); stage q maps to record chunk_at(q).
-__device__ __forceinline__ void unit_range(const int *near_off, int u, int S, int SPT, int &t, int &sp, int &b,
-                                           int &e) {
-  t = u / S;
-  sp = u % S;
-  if (near_off) {
-    const int n0 = near_off[t], n = near_off[t + 1] - n0;
-    b = n0 + sp * n / S;
-    e = n0 + (sp + 1) * n / S;
-  } else {
-    b = sp * SPT / S;
-    e = (sp + 1) * SPT / S;
+// Decodes unit u.  One mesh: u = tile * S + split, stages over all records (or
+// over the tile's near-chunk list); batched: the unit table.
+__device__ __forceinline__ Unit decode_unit(int u, int S, int SPT, int N, const int *near_off, const int4 *units,
+                                            const int *mesh_N, const long long *mesh_voff, const int *mesh_soff) {
+  Unit r;
+  if (units) {
+    const int4 d = units[u];
+    r.t = d.y;
+    r.sp = d.z;
+    r.Nb = mesh_N[d.x];
+    r.voff = mesh_voff[d.x];
+    r.soff = mesh_soff[d.x];
+    const int spt = (r.Nb + 15) / 16;
+    r.sb = d.z * spt / d.w;
+    r.se = (d.z + 1) * spt / d.w;
+    return r;
   }
+  r.t = u / S;
+  r.sp = u % S;
+  r.Nb = N;
+  r.voff = 0;
+  r.soff = 0;
+  if (near_off) {
+    const int n0 = near_off[r.t], n = near_off[r.t + 1] - n0;
+    r.sb = n0 + r.sp * n / S;
+    r.se = n0 + (r.sp + 1) * n / S;
+  } else {
+    r.sb = r.sp * SPT / S;
+    r.se = (r.sp + 1) * SPT / S;
+  }
+  return r;
 }
-__device__ __forceinline__ int chunk_at(const int *near_idx, int q) { return near_idx ? near_idx[q] : q; }
+// record holding stage q of a unit
+__device__ __forceinline__ int chunk_at(const int *near_idx, int q, int soff) {
+  return soff + (near_idx ? near_idx[q] : q);
+}
 
 template <int MODE, int CB, int JP, bool SPLIT, int NS>
 __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
@@ -415,17 +479,22 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
   const int S = args.n_split;
   const int SPT = args.n_steps;     // stages of a whole tile (one 16-i record per stage)
   const int unit_first = blockIdx.x / G, unit_step = gridDim.x / G;
-  const int n_units = args.n_otiles * S;
+  const int n_units = args.units ? args.n_units_total : args.n_otiles * S;
   const int *const near_off = args.near_off;
   const int *const near_idx = args.near_idx;
+  const int4 *const units = args.units;
+  const int *const mesh_N = args.mesh_N;
+  const long long *const mesh_voff = args.mesh_voff;
+  const int *const mesh_soff = args.mesh_soff;
+  const long long stride = args.stride;
+#define TSR_UNIT(u) decode_unit((u), S, SPT, args.N, near_off, units, mesh_N, mesh_voff, mesh_soff)
   long total_stages = 0;
   for (int u = unit_first; u < n_units; u += unit_step) {
-    int t, sp, b, e;
-    unit_range(near_off, u, S, SPT, t, sp, b, e);
-    total_stages += e - b;
+    const Unit un = TSR_UNIT(u);
+    total_stages += un.se - un.sb;
   }
   const int seg_stages = args.seg_stages;
-  const size_t KJN = (size_t)args.K * args.J * args.N;
+  const size_t KJN = (size_t)args.K * args.J * (size_t)stride;
 
   if (tid == 0) {
     for (int q = 0; q < C::NR; ++q) mbar_init(&bar_tma[q], 1);
@@ -495,11 +564,13 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
       const uint64_t desc_b0 = umma_desc(smem_u32(sRec), JP * 16, 128);       // B: T' tile of a record
       long issued = 0;
       // TMA cursor: unit tu, stage tq in [tb, te) (runs LOOKAHEAD stages ahead of the MMAs)
-      int tu = unit_first, tq = 0, te = 0;
+      int tu = unit_first, tq = 0, te = 0, tsoff = 0;
       auto next_unit = [&]() {
         while (tu < n_units) {
-          int t, sp;
-          unit_range(near_off, tu, S, SPT, t, sp, tq, te);
+          const Unit un = TSR_UNIT(tu);
+          tq = un.sb;
+          te = un.se;
+          tsoff = un.soff;
           if (tq < te) return;
           tu += unit_step;
         }
@@ -509,7 +580,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
       auto issue_tma = [&]() {
         mbar_arrive_expect_tx(&bar_tma[tslot], C::REC_STAGE);
         tma_load_2d(sRec + (size_t)tslot * C::REC_STAGE, &tmap, &bar_tma[tslot], 0,
-                    chunk_at(near_idx, tq) * rows_per_stage);
+                    chunk_at(near_idx, tq, tsoff) * rows_per_stage);
         if (++tslot == C::NR) tslot = 0;
         if (++tq == te) {
           tu += unit_step;
@@ -523,8 +594,8 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
       long g = 0;
       int seg_no = 0;   // accumulation segments issued so far
       for (int u = unit_first; u < n_units && !*abort_flag; u += unit_step) {
-        int t, sp, sb, se;
-        unit_range(near_off, u, S, SPT, t, sp, sb, se);
+        const Unit un = TSR_UNIT(u);
+        const int sb = un.sb, se = un.se;
         int seg_pos = 0;
         for (int sidx = sb; sidx < se && !*abort_flag; ++sidx, ++g) {
           const bool seg_start = seg_pos == 0;
@@ -600,17 +671,19 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
     uint32_t pa = 0u, pr = 0u;
     for (int u = unit_first; u < n_units; u += unit_step) {
       if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
-      int t, sp, sb, se;
-      unit_range(near_off, u, S, SPT, t, sp, sb, se);
+      const Unit un = TSR_UNIT(u);
+      const int t = un.t, sp = un.sp, sb = un.sb, se = un.se, Nb = un.Nb;
       if (sb == se) continue;
       const int d_idx = (MODE == MODE_FAR ? group * S : 0) + sp;   // destination
-      float *Mdst = (d_idx == 0) ? args.M : args.P + (size_t)(d_idx - 1) * KJN;
+      // destination base shifted to the unit's mesh (rows voff .. voff + Nb - 1)
+      float *Mdst = ((d_idx == 0) ? args.M : args.P + (size_t)(d_idx - 1) * KJN) + un.voff;
       const bool dst_accumulates = (d_idx == 0) && args.accumulate;
       const int o = t * 128 + orow;
-      const bool o_ok = o < args.N;
-      const float xo = o_ok ? args.pos[o] : 0.f;
-      const float yo = o_ok ? args.pos[args.N + o] : 0.f;
-      const float zo = o_ok ? args.pos[2 * (size_t)args.N + o] : 0.f;
+      const bool o_ok = o < Nb;
+      const float *pos_m = args.pos + un.voff;
+      const float xo = o_ok ? pos_m[o] : 0.f;
+      const float yo = o_ok ? pos_m[stride + o] : 0.f;
+      const float zo = o_ok ? pos_m[2 * stride + o] : 0.f;
       bool ok = true;
       int seg_pos = 0, seg_count = 0;   // position in / index of the accumulation segment
       for (int sidx = sb; sidx < se; ++sidx) {
@@ -761,12 +834,12 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
         tc_fence_after();
         const int quarter = warp & 3, wq = warp >> 2;   // rows quarter*32 + lane; 4 warps share a quarter
         const int oe = t * 128 + quarter * 32 + lane;
-        const bool oe_ok = oe < args.N;
+        const bool oe_ok = oe < Nb;
         const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
         if (MODE == MODE_NEAR) {
           // The first segment of split 0 also replaces the self pair's BF16 product
           // (exact in FP32) by f_k(0) A_o T[j][o] in FP32.
-          const float a_o = oe_ok ? args.area[oe] : 0.f;
+          const float a_o = oe_ok ? args.area[un.voff + oe] : 0.f;
           for (int cb = wq; cb < CB; cb += C::NGEN / 128) {
             const int k = c0 + cb;
             const float f0 = (k < args.K) ? args.tab32[k].x : 0.f;   // f_k(0), FP32
@@ -782,10 +855,10 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
                 for (int q = 0; q < 16; ++q) {
                   const int j = jc + q;
                   if (j < args.J) {
-                    float *dst = Mdst + ((size_t)k * args.J + j) * args.N + oe;
+                    float *dst = Mdst + ((size_t)k * args.J + j) * stride + oe;
                     float v = __uint_as_float(r[q]);
                     if (first_seg && sp == 0) {
-                      const float tpv = a_o * args.T[(size_t)j * args.N + oe];
+                      const float tpv = a_o * args.T[(size_t)j * stride + un.voff + oe];
                       const float th = __bfloat162float(__float2bfloat16_rn(tpv));
                       float tc_self;
                       if (!SPLIT) {
@@ -829,10 +902,10 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
               for (int q = 0; q < 16; ++q) {
                 const int j = jc + q;
                 if (j < args.J) {
-                  float *da = Mdst + ((size_t)ka * args.J + j) * args.N + oe;
+                  float *da = Mdst + ((size_t)ka * args.J + j) * stride + oe;
                   *da = (first_seg && !dst_accumulates) ? acc0[q] : *da + acc0[q];
                   if (kb < args.K) {
-                    float *db = Mdst + ((size_t)kb * args.J + j) * args.N + oe;
+                    float *db = Mdst + ((size_t)kb * args.J + j) * stride + oe;
                     *db = (first_seg && !dst_accumulates) ? acc1[q] : *db + acc1[q];
                   }
                 }
@@ -1038,12 +1111,12 @@ static tsr_status launch_tc(const TcArgs &a0, int n_cols, const CUtensorMap &tma
     }
   }
   a.n_split = best_S;
-  const long units = (long)a.n_otiles * best_S * G;
+  const long units = (a.units ? (long)a.n_units_total : (long)a.n_otiles * best_S) * G;
   int grid = (int)std::min<long>(units, sms);
   grid = std::max(G, grid / G * G);
   const int n_dest = (MODE == MODE_FAR ? G : 1) * best_S;
   Scratch part;
-  const size_t mn = (size_t)a.K * a.J * a.N;
+  const size_t mn = (size_t)a.K * a.J * (size_t)a.stride;
   a.P = nullptr;
   if (n_dest > 1) {
     tsr_status st = part.alloc(sizeof(float) * mn * (n_dest - 1), s);
@@ -1060,19 +1133,21 @@ static tsr_status launch_tc(const TcArgs &a0, int n_cols, const CUtensorMap &tma
 }
 
 // Exact-table pass over the near chunks (or over everything without lists).
+// kb: bases per CTA group (4, 8, 12 or 16; 0 = the smallest group holding all K).
 static tsr_status dispatch_near(const TcArgs &a, int JP, bool split, const CUtensorMap &tmap, bool allow_split,
-                                cudaStream_t s) {
+                                cudaStream_t s, int kb = 0) {
   const int K = a.K;
   if (!split) {
+    const int g = kb ? kb : (K <= 4 ? 4 : K <= 8 ? 8 : K <= 12 ? 12 : 16);
     if (JP == 16) {
-      if (K <= 4) return launch_tc<MODE_NEAR, 4, 16, false, 4>(a, K, tmap, allow_split, s);
-      if (K <= 8) return launch_tc<MODE_NEAR, 8, 16, false, 4>(a, K, tmap, allow_split, s);
-      if (K <= 12) return launch_tc<MODE_NEAR, 12, 16, false, 3>(a, K, tmap, allow_split, s);
+      if (g == 4) return launch_tc<MODE_NEAR, 4, 16, false, 4>(a, K, tmap, allow_split, s);
+      if (g == 8) return launch_tc<MODE_NEAR, 8, 16, false, 4>(a, K, tmap, allow_split, s);
+      if (g == 12) return launch_tc<MODE_NEAR, 12, 16, false, 3>(a, K, tmap, allow_split, s);
       return launch_tc<MODE_NEAR, 16, 16, false, 2>(a, K, tmap, allow_split, s);
     }
-    if (K <= 4) return launch_tc<MODE_NEAR, 4, 32, false, 4>(a, K, tmap, allow_split, s);
-    if (K <= 8) return launch_tc<MODE_NEAR, 8, 32, false, 4>(a, K, tmap, allow_split, s);
-    if (K <= 12) return launch_tc<MODE_NEAR, 12, 32, false, 3>(a, K, tmap, allow_split, s);
+    if (g == 4) return launch_tc<MODE_NEAR, 4, 32, false, 4>(a, K, tmap, allow_split, s);
+    if (g == 8) return launch_tc<MODE_NEAR, 8, 32, false, 4>(a, K, tmap, allow_split, s);
+    if (g == 12) return launch_tc<MODE_NEAR, 12, 32, false, 3>(a, K, tmap, allow_split, s);
     return launch_tc<MODE_NEAR, 16, 32, false, 2>(a, K, tmap, allow_split, s);
   }
   if (JP == 16) {
@@ -1138,6 +1213,7 @@ tsr_status transfer_tc(const tsr_basis *b, int N, const float *pos, const float 
   a.x_beta = b->x_beta;
   a.M = M;
   a.status = device_status_ptr();
+  a.stride = N;
   // The Chebyshev far field pays off (and keeps BF16 accuracy, since the near
   // field then carries most of M) on meshes with many vertices within r_near.
   if (!nearfar_enabled() || !b->cheb || N < 16384) {
@@ -1173,18 +1249,172 @@ tsr_status transfer_tc(const tsr_basis *b, int N, const float *pos, const float 
   return dispatch_near(a, JP, split, tmap, false, s);
 }
 
-// Batched transfer over independent meshes: one launch per mesh, in order.
-tsr_status transfer_fp32_batched(const tsr_basis *b, int n_mesh, const int64_t *offsets, const float *pos,
-                                 const float *area, const float *T, int J, float *M, cudaStream_t s) {
-  (void)b; (void)n_mesh; (void)offsets; (void)pos; (void)area; (void)T; (void)J; (void)M; (void)s;
-  set_error("batched FP32 transfer not built yet");
-  return TSR_ERR_UNSUPPORTED;
+// Batched transfer over independent meshes of uneven size: one persistent launch
+// whose units are the (mesh, 128-row tile) pairs in longest-first order, each CTA
+// taking every grid-th unit (so every CTA gets a similar mix of long and short
+// units).  The plan holds the unit and mesh tables on the device; running it only
+// enqueues kernels and stream-ordered scratch, so it can be captured in a CUDA graph.
+tsr_status batch_plan_create(const tsr_basis *b, int n_mesh, const int64_t *offsets, int J, int prec,
+                             tsr_batch_plan **out) {
+  tsr_batch_plan *p = new tsr_batch_plan();
+  cudaGetDevice(&p->device);
+  p->basis = b;
+  p->n_mesh = n_mesh;
+  p->J = J;
+  p->prec = prec;
+  p->offsets.assign(offsets, offsets + n_mesh + 1);
+  p->total = offsets[n_mesh];
+  std::vector<int> Nm(n_mesh), soff(n_mesh + 1, 0);
+  std::vector<long long> voff(n_mesh);
+  for (int m = 0; m < n_mesh; ++m) {
+    Nm[m] = (int)(offsets[m + 1] - offsets[m]);
+    voff[m] = offsets[m];
+    soff[m + 1] = soff[m] + (Nm[m] + 15) / 16;
+  }
+  p->total_steps = soff[n_mesh];
+  std::vector<int4> units;
+  for (int m = 0; m < n_mesh; ++m)
+    for (int t = 0; t < (Nm[m] + 127) / 128; ++t) units.push_back(make_int4(m, t, 0, 1));
+  std::stable_sort(units.begin(), units.end(), [&](const int4 &x, const int4 &y) { return Nm[x.x] > Nm[y.x]; });
+  p->n_units = (int)units.size();
+  const size_t b_units = sizeof(int4) * units.size(), b_voff = sizeof(long long) * n_mesh, b_N = sizeof(int) * n_mesh,
+               b_soff = sizeof(int) * (n_mesh + 1);
+  cudaError_t e = cudaMalloc(&p->tables, b_units + b_voff + b_N + b_soff + 64);
+  if (e == cudaSuccess) {
+    uint8_t *t = static_cast<uint8_t *>(p->tables);
+    p->d_units = reinterpret_cast<int4 *>(t);
+    p->d_voff = reinterpret_cast<long long *>(t + b_units);
+    p->d_N = reinterpret_cast<int *>(t + b_units + b_voff);
+    p->d_soff = p->d_N + n_mesh;
+    e = cudaMemcpy(p->d_units, units.data(), b_units, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_voff, voff.data(), b_voff, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_N, Nm.data(), b_N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_soff, soff.data(), b_soff, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    set_error("tsr_batch_plan_create: %s", cudaGetErrorString(e));
+    cudaFree(p->tables);
+    delete p;
+    return e == cudaErrorMemoryAllocation ? TSR_ERR_OOM : TSR_ERR_CUDA;
+  }
+  *out = p;
+  return TSR_OK;
 }
+
+tsr_status batch_plan_run(const tsr_batch_plan *p, const float *pos, const float *area, const float *T, float *M,
+                          cudaStream_t s) {
+  const tsr_basis *b = p->basis;
+  if (p->prec == TSR_FP32) return transfer_fp32_batched(b, p->n_mesh, p->offsets.data(), pos, area, T, p->J, M, s);
+  const int J = p->J;
+  const int JP = J <= 16 ? 16 : 32;
+  const int REC = rec_bytes(JP, false);
+  Scratch rs;
+  tsr_status st = rs.alloc((size_t)p->total_steps * REC, s);
+  if (st != TSR_OK) return st;
+  uint8_t *rec = static_cast<uint8_t *>(rs.p);
+  TSR_CUDA(cudaMemsetAsync(rec, 0, (size_t)p->total_steps * REC, s));
+  pretile_tc_batched_kernel<<<(p->total_steps * 16 + 255) / 256, 256, 0, s>>>(
+      pos, area, T, p->total, J, JP, 0, REC, p->total_steps, p->d_soff, p->n_mesh, p->d_N, p->d_voff, rec);
+  ::tsr::count_launch();
+  TSR_CUDA(cudaGetLastError());
+  CUtensorMap tmap;
+  st = make_record_map(&tmap, rec, p->total_steps, REC);
+  if (st != TSR_OK) return st;
+  TcArgs a{};
+  a.N = 0;
+  a.n_steps = 1;
+  a.n_r = b->n_r;
+  a.inv_dr = static_cast<float>((b->n_r - 1) / b->r_max);
+  a.r2max = static_cast<float>(b->r_max * b->r_max);
+  a.rn2 = 3.0e38f;
+  a.K = b->K;
+  a.J = J;
+  a.KP = b->KP;
+  a.n_otiles = 0;
+  a.pos = pos;
+  a.area = area;
+  a.T = T;
+  a.tab16 = b->tab16;
+  a.tab32 = b->tab32;
+  a.M = M;
+  a.status = device_status_ptr();
+  a.units = p->d_units;
+  a.n_units_total = p->n_units;
+  a.mesh_N = p->d_N;
+  a.mesh_voff = p->d_voff;
+  a.mesh_soff = p->d_soff;
+  a.stride = p->total;
+  return dispatch_near(a, JP, false, tmap, false, s, p->kb);
+}
+
+// Times every tile configuration (bases per CTA group) once on the caller's data and
+// keeps the fastest in the plan.  Synchronises the stream; not for use inside a capture.
+tsr_status batch_plan_autotune(tsr_batch_plan *p, const float *pos, const float *area, const float *T, float *M,
+                               cudaStream_t s, float *best_ms) {
+  if (p->prec == TSR_FP32) {
+    if (best_ms) *best_ms = 0.f;
+    return TSR_OK;
+  }
+  const std::vector<int> cands = {4, 8, 12, 16};   // bases per CTA group (groups = K / group, rounded up)
+  cudaEvent_t e0, e1;
+  TSR_CUDA(cudaEventCreate(&e0));
+  TSR_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_kb = 0;
+  for (int kb : cands) {
+    p->kb = kb;
+    tsr_status st = batch_plan_run(p, pos, area, T, M, s);   // warm
+    if (st == TSR_OK) {
+      TSR_CUDA(cudaEventRecord(e0, s));
+      st = batch_plan_run(p, pos, area, T, M, s);
+      TSR_CUDA(cudaEventRecord(e1, s));
+    }
+    if (st != TSR_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return st;
+    }
+    TSR_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    TSR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      best_kb = kb;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->kb = best_kb;
+  if (best_ms) *best_ms = best;
+  return TSR_OK;
+}
+
 tsr_status transfer_tc_batched(const tsr_basis *b, int n_mesh, const int64_t *offsets, const float *pos,
                                const float *area, const float *T, int J, float *M, cudaStream_t s) {
-  (void)b; (void)n_mesh; (void)offsets; (void)pos; (void)area; (void)T; (void)J; (void)M; (void)s;
-  set_error("batched BF16 transfer not built yet");
-  return TSR_ERR_UNSUPPORTED;
+  tsr_batch_plan *p = nullptr;
+  tsr_status st = batch_plan_create(b, n_mesh, offsets, J, TSR_BF16, &p);
+  if (st != TSR_OK) return st;
+  st = batch_plan_run(p, pos, area, T, M, s);
+  const cudaError_t e = cudaStreamSynchronize(s);   // the plan's tables are freed below
+  cudaFree(p->tables);
+  delete p;
+  if (st == TSR_OK && e != cudaSuccess) {
+    set_error("transfer_tc_batched: %s", cudaGetErrorString(e));
+    st = TSR_ERR_CUDA;
+  }
+  return st;
+}
+
+// FP32 batched: one launch per mesh on the strided concatenated arrays.
+tsr_status transfer_fp32_batched(const tsr_basis *b, int n_mesh, const int64_t *offsets, const float *pos,
+                                 const float *area, const float *T, int J, float *M, cudaStream_t s) {
+  const long long total = offsets[n_mesh];
+  for (int m = 0; m < n_mesh; ++m) {
+    const long long v = offsets[m];
+    const tsr_status st = transfer_fp32(b, (int)(offsets[m + 1] - v), pos + v, area + v, T + v, J, M + v, s, total);
+    if (st != TSR_OK) return st;
+  }
+  return TSR_OK;
 }
 
 }  // namespace tsr

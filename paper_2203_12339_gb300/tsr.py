@@ -44,6 +44,11 @@ _SIGNATURES = {
     "tsr_project_material_backward": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
     "tsr_precompute_transfer": (_I, [_P, _I, _P, _P, _P, _I, _I, _P, _P]),
     "tsr_precompute_transfer_batched": (_I, [_P, _I, _P, _P, _P, _P, _I, _I, _P, _P]),
+    "tsr_batch_plan_create": (_I, [_P, _I, _P, _I, _I, ctypes.POINTER(_P)]),
+    "tsr_batch_plan_autotune": (_I, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_float)]),
+    "tsr_precompute_transfer_plan": (_I, [_P, _P, _P, _P, _P, _P]),
+    "tsr_batch_plan_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "tsr_batch_plan_destroy": (None, [_P]),
     "tsr_haar_forward": (_I, [_P, _I, _I, _P, _P]),
     "tsr_haar_inverse": (_I, [_P, _I, _I, _P, _P]),
     "tsr_wavelet_compress": (_I, [_P, _I, _I, _I, _D, ctypes.POINTER(_P), _P]),
@@ -234,6 +239,56 @@ def precompute_transfer_batched(basis: Basis, offsets, pos: torch.Tensor, area: 
     _check(lib().tsr_precompute_transfer_batched(basis.handle, n_mesh, ctypes.c_void_p(off.data_ptr()), _ptr(p),
                                                  _ptr(a), _ptr(t), J, PRECISIONS[precision], _ptr(M), _stream()))
     return M
+
+
+class BatchPlan:
+    """Plan of a batched transfer (unit and mesh tables on the device; owned by the library)."""
+
+    def __init__(self, basis: Basis, offsets, J: int, precision: str = "bf16"):
+        self.offsets = torch.as_tensor(offsets, dtype=torch.int64).contiguous().cpu()
+        self.basis, self.J = basis, J
+        self.total = int(self.offsets[-1])
+        h = _P()
+        _check(lib().tsr_batch_plan_create(basis.handle, self.offsets.numel() - 1, ctypes.c_void_p(self.offsets.data_ptr()),
+                                           J, PRECISIONS[precision], ctypes.byref(h)))
+        self._h = h
+
+    def _args(self, pos, area, T, out):
+        p = _dev(pos, torch.float32, (3, self.total), "pos")
+        a = _dev(area, torch.float32, (self.total,), "area")
+        t = _dev(T, torch.float32, (self.J, self.total), "T")
+        M = out if out is not None else torch.empty((self.basis.K, self.J, self.total), dtype=torch.float32,
+                                                    device=p.device)
+        return p, a, t, M
+
+    def autotune(self, pos, area, T, out=None) -> float:
+        """tsr_batch_plan_autotune: returns the best time (ms) and keeps that tile configuration."""
+        p, a, t, M = self._args(pos, area, T, out)
+        best = ctypes.c_float()
+        _check(lib().tsr_batch_plan_autotune(self._h, _ptr(p), _ptr(a), _ptr(t), _ptr(M), _stream(), ctypes.byref(best)))
+        return best.value
+
+    def run(self, pos, area, T, out=None) -> torch.Tensor:
+        """tsr_precompute_transfer_plan (enqueue only; capturable in a CUDA graph)."""
+        p, a, t, M = self._args(pos, area, T, out)
+        _check(lib().tsr_precompute_transfer_plan(self._h, _ptr(p), _ptr(a), _ptr(t), _ptr(M), _stream()))
+        return M
+
+    def info(self):
+        n, kb = _I(), _I()
+        _check(lib().tsr_batch_plan_info(self._h, ctypes.byref(n), ctypes.byref(kb)))
+        return {"units": n.value, "bases_per_group": kb.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tsr_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------- wavelet / compression
