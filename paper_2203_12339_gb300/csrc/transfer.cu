@@ -255,6 +255,22 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t 
       : "memory");
 }
 
+// Same MMA with the A operand read from tensor memory (M = 128 lanes x 8 columns per K = 16 step).
+__device__ __forceinline__ void umma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                             uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, uint32_t a, uint32_t b) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(a), "r"(b) : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -313,7 +329,10 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 //    evaluated in registers by the recurrence T_{p+1} = 2x T_p - T_{p-1}.  The
 //    accumulators hold G[p][j] = sum_i phi_p(r_oi) T'[j][i]; the epilogue forms
 //    M[k][j] = sum_p C[k][p] G[p][j].
-enum { MODE_NEAR = 0, MODE_FAR = 1 };
+enum { MODE_NEAR = 0, MODE_FAR = 1, MODE_NEAR_TMEM = 2 };
+// MODE_NEAR_TMEM: the MODE_NEAR generator writing the A operand to tensor memory
+// (tcgen05.st) instead of shared memory; the MMA reads A from TMEM.  Warp w then
+// owns TMEM lanes (rows) 32 (w mod 4) .. +31 and i-quarter w / 4 of every step.
 
 struct TcArgs {
   int N;             // vertices (rows o and columns i)
@@ -360,15 +379,21 @@ struct TcCfg {
   static constexpr int LOOKAHEAD = 8;                      // records in flight ahead of the generators
   static constexpr int NR = NS + LOOKAHEAD;                // record slots
   static constexpr int REC = rec_bytes(JP, SPLIT);
+  static constexpr bool ATMEM = (MODE == MODE_NEAR_TMEM);
+  static constexpr bool TABLE = (MODE == MODE_NEAR || MODE == MODE_NEAR_TMEM);
   static constexpr int A_TILE = 128 * 16 * 2;              // one (column, 16-i step) BF16 tile
-  static constexpr int A_STAGE = CB * (SPLIT ? 2 : 1) * A_TILE;
+  static constexpr int A_STAGE = ATMEM ? 0 : CB * (SPLIT ? 2 : 1) * A_TILE;
   static constexpr int REC_STAGE = REC;
-  static constexpr int TAB_ELEM = (MODE == MODE_NEAR) ? (SPLIT ? 8 : 4) : 0;
-  static constexpr int U = (MODE == MODE_NEAR) ? CB * TAB_ELEM / 16 : 1;   // 16-byte units per table row
+  static constexpr int TAB_ELEM = TABLE ? (SPLIT ? 8 : 4) : 0;
+  static constexpr int U = TABLE ? CB * TAB_ELEM / 16 : 1;   // 16-byte units per table row
   static constexpr int NGEN = 512;                         // generator threads (warps 0-15)
   static constexpr int NTHREADS = NGEN + 32;               // + one control warp (TMA + MMA issue)
-  static constexpr int TMEM_COLS = (CB * JP <= 32) ? 32 : (CB * JP <= 64) ? 64 : (CB * JP <= 128) ? 128
-                                 : (CB * JP <= 256) ? 256 : 512;
+  static constexpr int ACC_COLS = CB * JP;                 // FP32 accumulators
+  static constexpr int A_COLS = ATMEM ? CB * 8 : 0;        // A tile of one stage in TMEM (16 BF16 per row = 8 columns)
+  static constexpr int USED_COLS = ACC_COLS + NS * A_COLS;
+  static constexpr int TMEM_COLS = (USED_COLS <= 32) ? 32 : (USED_COLS <= 64) ? 64 : (USED_COLS <= 128) ? 128
+                                 : (USED_COLS <= 256) ? 256 : 512;
+  static_assert(USED_COLS <= 512, "tensor memory holds 512 columns");
   static size_t smem_bytes(int n_r, int K) {
     return 1024 + (size_t)NS * A_STAGE + (size_t)NR * REC_STAGE + (size_t)(n_r + 1) * CB * TAB_ELEM +
            (MODE == MODE_FAR ? (size_t)K * CB * sizeof(float) : 0) + 256;
@@ -508,7 +533,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
     fence_mbar_init();
     fence_proxy_async_smem();
   }
-  if (MODE == MODE_NEAR) {
+  if (C::TABLE) {
     // this group's table slice (zero beyond K), rows swizzled by tab_unit
     const int n_units_tab = (args.n_r + 1) * C::U;
     for (int q = tid; q < n_units_tab; q += blockDim.x) {
@@ -625,7 +650,9 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
 #pragma unroll
           for (int cb = 0; cb < CB; ++cb) {
             const uint32_t d = tmem_base + (uint32_t)(cb * JP);
-            if (!SPLIT) {
+            if (C::ATMEM) {
+              umma_bf16_ta(d, tmem_base + (uint32_t)(C::ACC_COLS + sa * C::A_COLS + cb * 8), dbh, idesc, first);
+            } else if (!SPLIT) {
               umma_bf16(d, da + (uint64_t)((cb * C::A_TILE) >> 4), dbh, idesc, first);
             } else {
               const uint64_t dah = da + (uint64_t)(((2 * cb) * C::A_TILE) >> 4);
@@ -656,8 +683,9 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
     // Thread (orow, h4): output row orow of the tile, i = 4*h4 .. 4*h4+3 of every 16-i step.
     // A warp covers 16 rows x two neighbouring i-quarters, so its 8-byte stores fill
     // two whole 128-byte core matrices (2 shared-memory wavefronts per store).
-    const int orow = (warp & 7) * 16 + (lane & 7) + ((lane >> 4) << 3);
-    const int h4 = (warp >> 3) * 2 + ((lane >> 3) & 1);
+    const int orow = C::ATMEM ? (warp & 3) * 32 + lane : (warp & 7) * 16 + (lane & 7) + ((lane >> 4) << 3);
+    const int h4 = C::ATMEM ? (warp >> 2) : (warp >> 3) * 2 + ((lane >> 3) & 1);
+    const uint32_t a_tmem_row = tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(C::ACC_COLS + 2 * h4);
     const uint32_t a_row_off =
         (uint32_t)((orow >> 3) * 256 + (h4 >> 1) * 128 + (orow & 7) * 16 + (h4 & 1) * 8);
     const uint32_t sA_u32 = smem_u32(sA);
@@ -695,6 +723,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
           break;
         }
         if (tid == 0) *tma_done = g + 1;   // records of stages <= g have landed
+        if (C::ATMEM) tc_fence_after();    // the MMAs that read this A slot have completed
         const uint8_t *rec_stage = sRec + (size_t)sr * C::REC_STAGE;
         const float *rp = reinterpret_cast<const float *>(rec_stage + JP * 32 * (SPLIT ? 2 : 1));
         const float4 xs = *reinterpret_cast<const float4 *>(rp + h4 * 4);
@@ -714,7 +743,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
           inside |= (in ? 1u : 0u) << q;
         }
         const uint32_t a_stage = sA_u32 + (uint32_t)(sa * C::A_STAGE);
-        if (MODE == MODE_NEAR) {
+        if (C::TABLE) {
           int row[4];
           float tq[4];
 #pragma unroll
@@ -744,11 +773,20 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
                 F01[q] = bf16x2_fma(t2[q], w[q].z, w[q].x);
                 F23[q] = bf16x2_fma(t2[q], w[q].w, w[q].y);
               }
-              const uint32_t base = a_stage + (uint32_t)(cb4 * 4 * C::A_TILE) + a_row_off;
-              st_shared_v2(base, __byte_perm(F01[0], F01[1], 0x5410), __byte_perm(F01[2], F01[3], 0x5410));
-              st_shared_v2(base + C::A_TILE, __byte_perm(F01[0], F01[1], 0x7632), __byte_perm(F01[2], F01[3], 0x7632));
-              st_shared_v2(base + 2 * C::A_TILE, __byte_perm(F23[0], F23[1], 0x5410), __byte_perm(F23[2], F23[3], 0x5410));
-              st_shared_v2(base + 3 * C::A_TILE, __byte_perm(F23[0], F23[1], 0x7632), __byte_perm(F23[2], F23[3], 0x7632));
+              if (C::ATMEM) {
+                // columns 2 h4, 2 h4 + 1 of base (4 cb4 + b)'s 8-column A tile in slot sa
+                const uint32_t ta = a_tmem_row + (uint32_t)(sa * C::A_COLS + cb4 * 32);
+                tmem_st2(ta, __byte_perm(F01[0], F01[1], 0x5410), __byte_perm(F01[2], F01[3], 0x5410));
+                tmem_st2(ta + 8, __byte_perm(F01[0], F01[1], 0x7632), __byte_perm(F01[2], F01[3], 0x7632));
+                tmem_st2(ta + 16, __byte_perm(F23[0], F23[1], 0x5410), __byte_perm(F23[2], F23[3], 0x5410));
+                tmem_st2(ta + 24, __byte_perm(F23[0], F23[1], 0x7632), __byte_perm(F23[2], F23[3], 0x7632));
+              } else {
+                const uint32_t base = a_stage + (uint32_t)(cb4 * 4 * C::A_TILE) + a_row_off;
+                st_shared_v2(base, __byte_perm(F01[0], F01[1], 0x5410), __byte_perm(F01[2], F01[3], 0x5410));
+                st_shared_v2(base + C::A_TILE, __byte_perm(F01[0], F01[1], 0x7632), __byte_perm(F01[2], F01[3], 0x7632));
+                st_shared_v2(base + 2 * C::A_TILE, __byte_perm(F23[0], F23[1], 0x5410), __byte_perm(F23[2], F23[3], 0x5410));
+                st_shared_v2(base + 3 * C::A_TILE, __byte_perm(F23[0], F23[1], 0x7632), __byte_perm(F23[2], F23[3], 0x7632));
+              }
             }
           } else {
             const float4 *tab4 = reinterpret_cast<const float4 *>(sTab);   // {v_k, s_k, v_k+1, s_k+1}
@@ -806,7 +844,12 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
             }
           }
         }
-        fence_proxy_async_smem();
+        if (C::ATMEM) {
+          tmem_st_wait();     // this thread's A columns are written ...
+          tc_fence_before();  // ... and ordered before the barrier the MMA issuer waits on
+        } else {
+          fence_proxy_async_smem();
+        }
         mbar_arrive(&bar_full[sa]);
         const int last_sa = sa;
         const uint32_t last_pa = pa;
@@ -836,7 +879,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
         const int oe = t * 128 + quarter * 32 + lane;
         const bool oe_ok = oe < Nb;
         const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
-        if (MODE == MODE_NEAR) {
+        if (C::TABLE) {
           // The first segment of split 0 also replaces the self pair's BF16 product
           // (exact in FP32) by f_k(0) A_o T[j][o] in FP32.
           const float a_o = oe_ok ? args.area[un.voff + oe] : 0.f;
@@ -1134,9 +1177,29 @@ static tsr_status launch_tc(const TcArgs &a0, int n_cols, const CUtensorMap &tma
 
 // Exact-table pass over the near chunks (or over everything without lists).
 // kb: bases per CTA group (4, 8, 12 or 16; 0 = the smallest group holding all K).
+static bool atmem_enabled() {
+  const char *e = std::getenv("TSR_TRANSFER_ATMEM");   // "0": A operand staged in shared memory
+  return !(e && e[0] == '0');
+}
+
 static tsr_status dispatch_near(const TcArgs &a, int JP, bool split, const CUtensorMap &tmap, bool allow_split,
-                                cudaStream_t s, int kb = 0) {
+                                cudaStream_t s, int kb = 0, int atmem = -1) {
   const int K = a.K;
+  if (atmem < 0) atmem = atmem_enabled() ? 1 : 0;
+  // A in tensor memory when the bases of a group and 2..4 A stages fit in 512 columns
+  // next to the accumulators without splitting K further than the default grouping
+  // (with J_pad = 32 only K <= 8 does; more groups would recompute every r).
+  if (!split && atmem && (JP == 16 || (kb ? kb : K) <= 8)) {
+    const int g = kb ? kb : (K <= 4 ? 4 : K <= 8 ? 8 : K <= 12 ? 12 : 16);
+    if (JP == 16) {
+      if (g == 4) return launch_tc<MODE_NEAR_TMEM, 4, 16, false, 4>(a, K, tmap, allow_split, s);
+      if (g == 8) return launch_tc<MODE_NEAR_TMEM, 8, 16, false, 4>(a, K, tmap, allow_split, s);
+      if (g == 12) return launch_tc<MODE_NEAR_TMEM, 12, 16, false, 3>(a, K, tmap, allow_split, s);
+      return launch_tc<MODE_NEAR_TMEM, 16, 16, false, 2>(a, K, tmap, allow_split, s);
+    }
+    if (g == 4) return launch_tc<MODE_NEAR_TMEM, 4, 32, false, 4>(a, K, tmap, allow_split, s);
+    return launch_tc<MODE_NEAR_TMEM, 8, 32, false, 3>(a, K, tmap, allow_split, s);
+  }
   if (!split) {
     const int g = kb ? kb : (K <= 4 ? 4 : K <= 8 ? 8 : K <= 12 ? 12 : 16);
     if (JP == 16) {
