@@ -322,24 +322,38 @@ def _cpu_threads() -> int:
     return os.cpu_count() or 1
 
 
-def cpu_baseline(rows: int = 192, seed: int = 7) -> dict:
+class _OracleCase:
+    """The benchmark workload prepared once for the FP64 CPU oracle (scene, fitted basis)."""
+
+    def __init__(self):
+        from oracle import tsr_oracle as O
+        from paper_2203_12339_gb300 import scene
+        self.O, self.scene = O, scene
+        self.w = w = scene.WORKLOADS[WORKLOAD]
+        sc = scene.make_scene(w["nu"], K=w["K"], J=w["J"], amp=w["amp"], octaves=w["octaves"], seed=w["seed"])
+        sa, ss = scene.pca_materials(256, seed=0)
+        self.f, _ = O.fit_pca_basis(sa, ss, 1.3, 1024, 40.0, w["K"])
+        self.n = sc.n
+        self.pos = sc.mesh.pos.astype(np.float32)
+        self.area = sc.mesh.area.astype(np.float32)
+        self.T = sc.T.astype(np.float32)
+
+    def run(self, rows: int, seed: int) -> tuple[float, float]:
+        """Oracle transfer on `rows` sampled output vertices (all i, all k, j): (G pair.K.J/s, seconds)."""
+        sel = self.scene.sample_rows(self.n, rows, seed=seed)
+        t = time.perf_counter()
+        self.O.transfer_rows(self.f, self.pos, self.area, self.T, sel)
+        dt = time.perf_counter() - t
+        return rows * self.n * self.w["K"] * self.w["J"] / dt / 1e9, dt
+
+
+def cpu_baseline(rows: int = 3072, seed: int = 7) -> dict:
     """FP64 oracle transfer on `rows` sampled output vertices of the same workload (all i, all k, j)."""
-    from oracle import tsr_oracle as O
-    from paper_2203_12339_gb300 import scene
-    w = scene.WORKLOADS[WORKLOAD]
-    sc = scene.make_scene(w["nu"], K=w["K"], J=w["J"], amp=w["amp"], octaves=w["octaves"], seed=w["seed"])
-    sa, ss = scene.pca_materials(256, seed=0)
-    f, _ = O.fit_pca_basis(sa, ss, 1.3, 1024, 40.0, w["K"])
-    pos = sc.mesh.pos.astype(np.float32)
-    area = sc.mesh.area.astype(np.float32)
-    T = sc.T.astype(np.float32)
-    sel = scene.sample_rows(sc.n, rows, seed=seed)
-    t = time.perf_counter()
-    O.transfer_rows(f, pos, area, T, sel)
-    dt = time.perf_counter() - t
-    val = rows * sc.n * w["K"] * w["J"] / dt / 1e9
+    case = _OracleCase()
+    val, dt = case.run(rows, seed)
+    w = case.w
     return {"value": round(val, 3), "unit": UNIT, "cores": _cpu_threads(), "kind": "oracle",
-            "sample": f"{rows} sampled output rows x all {sc.n} inputs, K={w['K']}, J={w['J']} (FP64 numpy); "
+            "sample": f"{rows} sampled output rows x all {case.n} inputs, K={w['K']}, J={w['J']} (FP64 numpy); "
                       f"{dt:.1f} s"}
 
 
@@ -347,21 +361,21 @@ def run_reference(args):
     rank, world, _ = _dist_env()
     if rank != 0:
         return
+    case = _OracleCase()
     vals, ms = [], []
-    for _ in range(args.warmup):
-        cpu_baseline(rows=8)
+    for s in range(args.warmup):
+        case.run(8, seed=50 + s)
     for s in range(args.steps):
-        t = time.perf_counter()
-        r = cpu_baseline(rows=args.cpu_rows // 4 or 16, seed=100 + s)
-        ms.append((time.perf_counter() - t) * 1e3)
-        vals.append(r["value"])
+        v, dt = case.run(args.ref_rows, seed=100 + s)
+        ms.append(dt * 1e3)
+        vals.append(v)
     value = statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(statistics.mean(ms), 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": f"{WORKLOAD} (oracle on sampled output rows)"},
             "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": _cpu_threads(), "kind": "oracle",
-                             "sample": f"{args.cpu_rows // 4 or 16} sampled output rows per step"},
+                             "sample": f"{args.ref_rows} sampled output rows x all {case.n} inputs per step"},
             "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -372,7 +386,8 @@ def main():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--cpu-rows", type=int, default=192)
+    ap.add_argument("--cpu-rows", type=int, default=3072, help="oracle sample of the cpu_baseline leg (~10 s)")
+    ap.add_argument("--ref-rows", type=int, default=64, help="oracle sample per step of --impl reference")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-sweep", action="store_true")
     args = ap.parse_args()

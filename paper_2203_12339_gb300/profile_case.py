@@ -1,0 +1,44 @@
+"""A single transfer precompute on a seeded displaced icosphere, sized for a profiler capture.
+
+    python -m paper_2203_12339_gb300.profile_case --nu 48 --K 12 --J 16 --precision bf16
+
+The basis is fitted on the device from the seeded PCA materials (n_r = 1024, r_max = 40 mm,
+eta = 1.3, Section 3.2), the scene is the icosphere of the benchmark recipe with 10 nu^2 + 2
+vertices.  Every step runs through the C-ABI library; nothing here computes on the host.
+"""
+import argparse
+
+import numpy as np
+import torch
+
+from . import scene, tsr
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--nu", type=int, default=48)
+    ap.add_argument("--K", type=int, default=12)
+    ap.add_argument("--J", type=int, default=16)
+    ap.add_argument("--amp", type=float, default=0.1)
+    ap.add_argument("--octaves", type=int, default=3)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--precision", default="bf16", help="comma-separated list of bf16, bf16x3, fp32")
+    ap.add_argument("--repeat", type=int, default=1)
+    a = ap.parse_args(argv)
+    sa, ss = scene.pca_materials(256, seed=0)
+    basis, _ = tsr.fit_pca_basis(torch.tensor(sa, device="cuda"), torch.tensor(ss, device="cuda"), 1.3, 1024, 40.0,
+                                 a.K)
+    sc = scene.make_scene(a.nu, K=a.K, J=a.J, amp=a.amp, octaves=a.octaves, seed=a.seed)
+    pos = torch.tensor(np.ascontiguousarray(sc.mesh.pos.astype(np.float32).T), device="cuda")
+    area = torch.tensor(sc.mesh.area.astype(np.float32), device="cuda")
+    T = torch.tensor(sc.T.astype(np.float32), device="cuda")
+    for prec in a.precision.split(","):
+        for _ in range(a.repeat):
+            tsr.precompute_transfer(basis, pos, area, T, prec)
+    torch.cuda.synchronize()
+    tsr.stream_status()
+    print(f"ok: N={sc.n} K={a.K} J={a.J} precision={a.precision}")
+
+
+if __name__ == "__main__":
+    main()
