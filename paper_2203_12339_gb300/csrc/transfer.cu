@@ -246,23 +246,35 @@ __host__ __device__ constexpr uint32_t umma_idesc_bf16(int N) {
          | ((uint32_t)(128 >> 4) << 24); // M = 128; A, B K-major
 }
 
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+
+
+// Warp-collective forms: every lane of the warp executes them with the same
+// operands, and the lane chosen by elect.sync issues the instruction.
+__device__ __forceinline__ void umma_bf16_elect(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                                uint32_t acc) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\t"
+      "{\n\t.reg .pred p, e;\n\t"
+      "elect.sync _|e, 0xffffffff;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
-
-// Same MMA with the A operand read from tensor memory (M = 128 lanes x 8 columns per K = 16 step).
-__device__ __forceinline__ void umma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
-                                             uint32_t acc) {
+__device__ __forceinline__ void umma_bf16_ta_elect(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                                   uint32_t acc) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\t"
+      "{\n\t.reg .pred p, e;\n\t"
+      "elect.sync _|e, 0xffffffff;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
       "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit_elect(uint64_t *bar) {
+  asm volatile(
+      "{\n\t.reg .pred e;\n\t"
+      "elect.sync _|e, 0xffffffff;\n\t"
+      "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(smem_u32(bar))
       : "memory");
 }
 
@@ -271,10 +283,6 @@ __device__ __forceinline__ void tmem_st2(uint32_t taddr, uint32_t a, uint32_t b)
 }
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void umma_commit(uint64_t *bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -583,98 +591,122 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
 
   if (warp == C::NGEN / 32) {
     // ------------------------------------------------------------ control warp
-    if (lane == 0) {
-      const uint32_t idesc = umma_idesc_bf16(JP);
-      const uint64_t desc_a0 = umma_desc(smem_u32(sA), 128, 256);             // A: K-major, 8x16B core matrices
-      const uint64_t desc_b0 = umma_desc(smem_u32(sRec), JP * 16, 128);       // B: T' tile of a record
-      long issued = 0;
-      // TMA cursor: unit tu, stage tq in [tb, te) (runs LOOKAHEAD stages ahead of the MMAs)
-      int tu = unit_first, tq = 0, te = 0, tsoff = 0;
-      auto next_unit = [&]() {
-        while (tu < n_units) {
-          const Unit un = TSR_UNIT(tu);
-          tq = un.sb;
-          te = un.se;
-          tsoff = un.soff;
-          if (tq < te) return;
-          tu += unit_step;
-        }
-      };
-      next_unit();
-      int tslot = 0;   // record slot of the next TMA
-      auto issue_tma = [&]() {
+    // All 32 lanes run the loop on warp-uniform state, so the MMA operands stay in
+    // uniform registers; one elected lane issues each TMA, MMA and commit.  (An
+    // issue loop run by one lane alone costs about twice the tensor core's own
+    // ~47 cycles per M = 128 MMA.)
+    const uint32_t idesc = umma_idesc_bf16(JP);
+    const uint64_t desc_a0 = umma_desc(smem_u32(sA), 128, 256);             // A: K-major, 8x16B core matrices
+    const uint64_t desc_b0 = umma_desc(smem_u32(sRec), JP * 16, 128);       // B: T' tile of a record
+    long issued = 0;
+    // TMA cursor: unit tu, stage tq in [tb, te) (runs LOOKAHEAD stages ahead of the MMAs)
+    int tu = unit_first, tq = 0, te = 0, tsoff = 0;
+    auto next_unit = [&]() {
+      while (tu < n_units) {
+        const Unit un = TSR_UNIT(tu);
+        tq = un.sb;
+        te = un.se;
+        tsoff = un.soff;
+        if (tq < te) return;
+        tu += unit_step;
+      }
+    };
+    next_unit();
+    int tslot = 0;   // record slot of the next TMA
+    auto issue_tma = [&]() {
+      if (lane == 0) {
         mbar_arrive_expect_tx(&bar_tma[tslot], C::REC_STAGE);
         tma_load_2d(sRec + (size_t)tslot * C::REC_STAGE, &tmap, &bar_tma[tslot], 0,
                     chunk_at(near_idx, tq, tsoff) * rows_per_stage);
-        if (++tslot == C::NR) tslot = 0;
-        if (++tq == te) {
-          tu += unit_step;
-          next_unit();
-        }
-      };
-      for (; issued < C::LOOKAHEAD && issued < total_stages; ++issued) issue_tma();
-      // ring state: A slot sa (phase pa), record slot sr; ps/pp: A slot of stage issued - NR
-      int sa = 0, sr = 0, ps = 0;
-      uint32_t pa = 0u, pp = 0u;
-      long g = 0;
-      int seg_no = 0;   // accumulation segments issued so far
-      for (int u = unit_first; u < n_units && !*abort_flag; u += unit_step) {
-        const Unit un = TSR_UNIT(u);
-        const int sb = un.sb, se = un.se;
-        int seg_pos = 0;
-        for (int sidx = sb; sidx < se && !*abort_flag; ++sidx, ++g) {
-          const bool seg_start = seg_pos == 0;
-          if (++seg_pos == seg_stages) seg_pos = 0;
-          // TMA of stage g + LOOKAHEAD reuses the slot of stage g - NS: wait for its MMAs
-          if (issued < total_stages && issued <= g + C::LOOKAHEAD) {
-            if (issued >= C::NR) {
-              if (!wait_or_abort(&bar_mma[ps], pp, abort_flag)) break;
-              if (++ps == NS) {
-                ps = 0;
-                pp ^= 1u;
-              }
-            }
-            issue_tma();
-            ++issued;
-          }
-          if (!wait_or_abort(&bar_full[sa], pa, abort_flag)) break;
-          // the epilogue of the previous segment must have read TMEM before it is overwritten
-          if (seg_start && seg_no > 0 && !wait_or_abort(bar_tfree, (uint32_t)((seg_no - 1) & 1), abort_flag)) break;
-          if (seg_start) ++seg_no;
-          tc_fence_after();
-          // descriptors: start-address field (addr >> 4) advanced by offsets from the base ones
-          const uint64_t dbh = desc_b0 + (uint64_t)((sr * C::REC_STAGE) >> 4);
-          const uint64_t dbl = dbh + (uint64_t)((JP * 32) >> 4);
-          const uint64_t da = desc_a0 + (uint64_t)((sa * C::A_STAGE) >> 4);
-          const uint32_t first = seg_start ? 0u : 1u;
-#pragma unroll
-          for (int cb = 0; cb < CB; ++cb) {
-            const uint32_t d = tmem_base + (uint32_t)(cb * JP);
-            if (C::ATMEM) {
-              umma_bf16_ta(d, tmem_base + (uint32_t)(C::ACC_COLS + sa * C::A_COLS + cb * 8), dbh, idesc, first);
-            } else if (!SPLIT) {
-              umma_bf16(d, da + (uint64_t)((cb * C::A_TILE) >> 4), dbh, idesc, first);
-            } else {
-              const uint64_t dah = da + (uint64_t)(((2 * cb) * C::A_TILE) >> 4);
-              const uint64_t dal = da + (uint64_t)(((2 * cb + 1) * C::A_TILE) >> 4);
-              umma_bf16(d, dah, dbh, idesc, first);
-              umma_bf16(d, dah, dbl, idesc, 1u);
-              umma_bf16(d, dal, dbh, idesc, 1u);
-            }
-          }
-          umma_commit(&bar_mma[sa]);
-          if (++sa == NS) {
-            sa = 0;
-            pa ^= 1u;
-          }
-          if (++sr == C::NR) sr = 0;
-        }
       }
-      if (*abort_flag) {   // let copies already issued land before the CTA exits
-        for (long q = *tma_done; q < issued; ++q) {
-          for (uint32_t it = 0; it < TSR_WAIT_LIMIT; ++it)
-            if (mbar_try_wait(&bar_tma[q % C::NR], (uint32_t)((q / C::NR) & 1))) break;
+      __syncwarp();
+      if (++tslot == C::NR) tslot = 0;
+      if (++tq == te) {
+        tu += unit_step;
+        next_unit();
+      }
+    };
+    // every lane waits (and acquires); the outcome is made warp-uniform
+    auto wait_warp = [&](uint64_t *b, uint32_t parity) {
+      return __all_sync(0xffffffffu, wait_or_abort(b, parity, abort_flag));
+    };
+    for (; issued < C::LOOKAHEAD && issued < total_stages; ++issued) issue_tma();
+    // ring state: A slot sa (phase pa), record slot sr; ps/pp: A slot of stage issued - NR
+    int sa = 0, sr = 0, ps = 0;
+    uint32_t pa = 0u, pp = 0u;
+    long g = 0;
+    int seg_no = 0;   // accumulation segments issued so far
+    bool run = true;
+    for (int u = unit_first; u < n_units && run; u += unit_step) {
+      const Unit un = TSR_UNIT(u);
+      const int sb = un.sb, se = un.se;
+      int seg_pos = 0;
+      for (int sidx = sb; sidx < se; ++sidx, ++g) {
+        if (__any_sync(0xffffffffu, *abort_flag != 0)) {
+          run = false;
+          break;
         }
+        const bool seg_start = seg_pos == 0;
+        if (++seg_pos == seg_stages) seg_pos = 0;
+        // TMA of stage g + LOOKAHEAD reuses the slot of stage g - NS: wait for its MMAs
+        if (issued < total_stages && issued <= g + C::LOOKAHEAD) {
+          if (issued >= C::NR) {
+            if (!wait_warp(&bar_mma[ps], pp)) {
+              run = false;
+              break;
+            }
+            if (++ps == NS) {
+              ps = 0;
+              pp ^= 1u;
+            }
+          }
+          issue_tma();
+          ++issued;
+        }
+        if (!wait_warp(&bar_full[sa], pa)) {
+          run = false;
+          break;
+        }
+        // the epilogue of the previous segment must have read TMEM before it is overwritten
+        if (seg_start && seg_no > 0 && !wait_warp(bar_tfree, (uint32_t)((seg_no - 1) & 1))) {
+          run = false;
+          break;
+        }
+        if (seg_start) ++seg_no;
+        tc_fence_after();
+        // descriptors: start-address field (addr >> 4) advanced by offsets from the base ones
+        const uint64_t dbh = desc_b0 + (uint64_t)((sr * C::REC_STAGE) >> 4);
+        const uint64_t dbl = dbh + (uint64_t)((JP * 32) >> 4);
+        const uint64_t da = desc_a0 + (uint64_t)((sa * C::A_STAGE) >> 4);
+        const uint32_t first = seg_start ? 0u : 1u;
+#pragma unroll
+        for (int cb = 0; cb < CB; ++cb) {
+          const uint32_t d = tmem_base + (uint32_t)(cb * JP);
+          if (C::ATMEM) {
+            umma_bf16_ta_elect(d, tmem_base + (uint32_t)(C::ACC_COLS + sa * C::A_COLS + cb * 8), dbh, idesc, first);
+          } else if (!SPLIT) {
+            umma_bf16_elect(d, da + (uint64_t)((cb * C::A_TILE) >> 4), dbh, idesc, first);
+          } else {
+            const uint64_t dah = da + (uint64_t)(((2 * cb) * C::A_TILE) >> 4);
+            const uint64_t dal = da + (uint64_t)(((2 * cb + 1) * C::A_TILE) >> 4);
+            umma_bf16_elect(d, dah, dbh, idesc, first);
+            umma_bf16_elect(d, dah, dbl, idesc, 1u);
+            umma_bf16_elect(d, dal, dbh, idesc, 1u);
+          }
+        }
+        umma_commit_elect(&bar_mma[sa]);
+        if (++sa == NS) {
+          sa = 0;
+          pa ^= 1u;
+        }
+        if (++sr == C::NR) sr = 0;
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && *abort_flag) {   // let copies already issued land before the CTA exits
+      for (long q = *tma_done; q < issued; ++q) {
+        for (uint32_t it = 0; it < TSR_WAIT_LIMIT; ++it)
+          if (mbar_try_wait(&bar_tma[q % C::NR], (uint32_t)((q / C::NR) & 1))) break;
       }
     }
     __syncwarp();
