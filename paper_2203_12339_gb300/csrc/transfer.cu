@@ -23,6 +23,7 @@
 // x = r / dr, m = min(floor(x), n_r - 2), t = x - m and
 // f_k(r) = v_k[m] + t s_k[m] (s_k = f_k[m+1] - f_k[m]).
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -347,6 +348,7 @@ struct TcArgs {
   int n_steps;       // 16-i records
   int n_r;           // radius samples
   float inv_dr, r2max, rn2;
+  float r2lim;       // largest r^2 of a table pair: min(r2max, the float below rn2)
   int K, J, KP;
   int n_otiles, n_groups, n_split;
   const float *pos;  // [3][N] (rows o)
@@ -431,11 +433,11 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, vo
   return false;
 }
 
-// Squared distance with a fixed operation order (the near/far split of both
-// passes must classify every pair identically).
-__device__ __forceinline__ float pair_r2_fma(float xo, float yo, float zo, float xi, float yi, float zi) {
-  const float dx = __fsub_rn(xo, xi), dy = __fsub_rn(yo, yi), dz = __fsub_rn(zo, zi);
-  return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 __device__ __forceinline__ float fast_lg2(float x) {
@@ -721,7 +723,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
     const uint32_t a_row_off =
         (uint32_t)((orow >> 3) * 256 + (h4 >> 1) * 128 + (orow & 7) * 16 + (h4 & 1) * 8);
     const uint32_t sA_u32 = smem_u32(sA);
-    const float r2max = args.r2max, rn2 = args.rn2, inv_dr = args.inv_dr;
+    const float r2max = args.r2max, rn2 = args.rn2, r2lim = args.r2lim, inv_dr2 = args.inv_dr * args.inv_dr;
     const float xa_alpha = args.x_alpha, xa_beta = args.x_beta;
     const int n_r = args.n_r;
     long g = 0;
@@ -764,16 +766,11 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
         const float xa[4] = {xs.x, xs.y, xs.z, xs.w}, ya[4] = {ys.x, ys.y, ys.z, ys.w},
                     za[4] = {zs.x, zs.y, zs.z, zs.w};
         // Padded i (beyond N) carry T' = 0 and finite positions, so they add nothing.
+        // r^2 in the exact FP32 order of the definition: the cutoff and the near/far
+        // split are decided on the same value the reference computes.
         float r2v[4];
-        unsigned inside = 0u;   // bit q: pair q within r_max
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          r2v[q] = pair_r2_fma(xo, yo, zo, xa[q], ya[q], za[q]);
-          bool in = r2v[q] <= r2max;
-          if (fabsf(r2v[q] - r2max) <= 1e-3f * r2max)   // near the cutoff: decide on the exact FP32 r^2
-            in = pair_r2(xo, yo, zo, xa[q], ya[q], za[q]) <= r2max;
-          inside |= (in ? 1u : 0u) << q;
-        }
+        for (int q = 0; q < 4; ++q) r2v[q] = pair_r2(xo, yo, zo, xa[q], ya[q], za[q]);
         const uint32_t a_stage = sA_u32 + (uint32_t)(sa * C::A_STAGE);
         if (C::TABLE) {
           int row[4];
@@ -781,12 +778,10 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const float r2 = r2v[q];
-            const float x = r2 * rsqrtf(fmaxf(r2, 1e-30f)) * inv_dr;
-            // m = floor(x) (round-to-nearest of x - 1/2 at 1.5 * 2^23), t = x - m
-            const float yv = (x - 0.5f) + 12582912.0f;
-            const int m = __float_as_int(yv) - 0x4B400000;
-            tq[q] = x - (yv - 12582912.0f);
-            row[q] = (((inside >> q) & 1u) && r2 < rn2) ? m : n_r;
+            const float x = sqrt_approx(r2 * inv_dr2);   // r / dr
+            const int m = __float2int_rd(x);
+            tq[q] = x - __int2float_rn(m);
+            row[q] = (r2 <= r2lim) ? m : n_r;            // r2lim: r^2 <= r_max^2 and r^2 < r_near^2
           }
           if (!SPLIT) {
             // unit cb4 of a table row: {v_4cb4..+1, v_+2..+3, s_4cb4..+1, s_+2..+3} (bf16 pairs)
@@ -841,7 +836,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
           float tp[4], tc[4], x2[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const bool far = ((inside >> q) & 1u) && r2v[q] >= rn2;
+            const bool far = r2v[q] <= r2max && r2v[q] >= rn2;
             const float x = far ? fmaf(xa_alpha, fast_lg2(r2v[q]), xa_beta) : 0.f;
             tp[q] = far ? 1.f : 0.f;   // T_0
             tc[q] = x;                 // T_1
@@ -1157,6 +1152,7 @@ template <int MODE, int CB, int JP, bool SPLIT, int NS>
 static tsr_status launch_tc(const TcArgs &a0, int n_cols, const CUtensorMap &tmap, bool allow_split, cudaStream_t s) {
   using C = TcCfg<MODE, CB, JP, SPLIT, NS>;
   TcArgs a = a0;
+  a.r2lim = std::min(a.r2max, std::nextafter(a.rn2, 0.0f));   // r^2 <= r2lim  <=>  r^2 <= r2max and r^2 < rn2
   a.seg_stages = 4096 / 16;   // flush the tensor-core accumulator every 4,096 i
   a.n_groups = (n_cols + CB - 1) / CB;
   const size_t smem = C::smem_bytes(a.n_r, a.K);
