@@ -119,6 +119,18 @@ def _traffic_record():
     return rec.get("traffic_bytes_per_launch")
 
 
+def _smem_roofline(gather_bytes: float, ms: float, peaks: dict) -> dict:
+    """Shared-memory gather roofline of the transfer kernel (algorithmic table bytes per launch / time)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = 128.0 * sms * mhz * 1e6 / 1e12
+    achieved = gather_bytes / (ms * 1e-3) / 1e12
+    return {"bound": "smem", "achieved": round(achieved, 2), "peak": round(peak, 2), "unit": "TB/s",
+            "frac": round(achieved / peak, 4), "bytes_per_pair": "4 K (BF16 value + slope per basis)",
+            "peak_kind": f"derived: 128 B/clk/SM x {sms} SMs x {mhz:.0f} MHz"}
+
+
 def reduce_max(values, world, device=None):
     """Max over ranks of a few timings (the only collective of the benchmark)."""
     if world <= 1:
@@ -296,6 +308,10 @@ def run_gpu(args):
                      "unit": "TFLOP/s", "frac": round(achieved_tflops / peak_tf, 4), "traffic": traffic,
                      "kernel": "transfer_tc_kernel (BF16 tcgen05), per launch",
                      "peak_kind": f"bf16 sustained, {peak_kind}"},
+        # The bound that binds this kernel: per pair it gathers {value, slope} (BF16) of every
+        # basis from a data-dependent row of the shared-memory table, 4 K bytes.  Peak: 128 B per
+        # clock per SM (32 banks x 4 B) x SMs x the maximum SM clock.
+        "smem_roofline": _smem_roofline(N * float(N) * 4 * K, tr_mean, peaks),
         "transfer_ms": round(tr_mean, 3),
         "transfer_ms_by_precision": by_prec,
         "relight_fps": round(1e3 / relight_ms, 1),
