@@ -365,6 +365,13 @@ struct TcArgs {
   int accumulate;    // destination 0 (M) is accumulated into instead of overwritten
   float *M;          // [K][J][N]
   float *P;          // [n_dest - 1][K][J][N] partial sums (NULL if one destination)
+  // Stream-K split (streamk_P > 0, one mesh, no near lists): CTA p of its group takes
+  // the stages [p T / P, (p+1) T / P) of the tile-major stage space (T = n_otiles n_steps).
+  // The piece of a tile that starts at its first stage writes M; a piece that starts
+  // inside a tile (only the first piece of a CTA) writes the CTA's slot, which a fix-up
+  // kernel adds to M in CTA order.
+  int streamk_P;
+  float *slots;      // [G][P][K][J][128]
   unsigned *status;
   // Batched meshes (units != NULL): arrays are concatenated along the vertex axis
   // with row stride `stride`; unit u = (mesh, tile, split, splits of that mesh).
@@ -513,8 +520,24 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
   const int c0 = group * CB;        // first basis (MODE_NEAR) or Chebyshev column (MODE_FAR)
   const int S = args.n_split;
   const int SPT = args.n_steps;     // stages of a whole tile (one 16-i record per stage)
-  const int unit_first = blockIdx.x / G, unit_step = gridDim.x / G;
-  const int n_units = args.units ? args.n_units_total : args.n_otiles * S;
+  const int SKP = args.streamk_P;
+  const int cta_in_group = blockIdx.x / G;
+  long long sk0 = 0, sk1 = 0;   // stream-K stage range of this CTA
+  int sk_t0 = 0;                // its first tile
+  int unit_first, unit_step, n_units;
+  if (SKP > 0) {
+    const long long T_st = (long long)args.n_otiles * SPT;
+    sk0 = T_st * cta_in_group / SKP;
+    sk1 = T_st * (cta_in_group + 1) / SKP;
+    sk_t0 = (int)(sk0 / SPT);
+    unit_first = 0;
+    unit_step = 1;
+    n_units = sk1 > sk0 ? (int)((sk1 - 1) / SPT) - sk_t0 + 1 : 0;
+  } else {
+    unit_first = cta_in_group;
+    unit_step = gridDim.x / G;
+    n_units = args.units ? args.n_units_total : args.n_otiles * S;
+  }
   const int *const near_off = args.near_off;
   const int *const near_idx = args.near_idx;
   const int4 *const units = args.units;
@@ -522,7 +545,21 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
   const long long *const mesh_voff = args.mesh_voff;
   const int *const mesh_soff = args.mesh_soff;
   const long long stride = args.stride;
-#define TSR_UNIT(u) decode_unit((u), S, SPT, args.N, near_off, units, mesh_N, mesh_voff, mesh_soff)
+  // stream-K: piece u of this CTA's stage range (sp = 1: starts inside its tile -> slot)
+  auto streamk_unit = [&](int u) {
+    Unit r;
+    r.t = sk_t0 + u;
+    const long long base = (long long)r.t * SPT;
+    r.sb = (int)((sk0 > base ? sk0 : base) - base);
+    r.se = (int)((sk1 < base + SPT ? sk1 : base + SPT) - base);
+    r.sp = r.sb > 0 ? 1 : 0;
+    r.Nb = args.N;
+    r.voff = 0;
+    r.soff = 0;
+    return r;
+  };
+#define TSR_UNIT(u) \
+  (SKP > 0 ? streamk_unit(u) : decode_unit((u), S, SPT, args.N, near_off, units, mesh_N, mesh_voff, mesh_soff))
   long total_stages = 0;
   for (int u = unit_first; u < n_units; u += unit_step) {
     const Unit un = TSR_UNIT(u);
@@ -736,10 +773,20 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
       const Unit un = TSR_UNIT(u);
       const int t = un.t, sp = un.sp, sb = un.sb, se = un.se, Nb = un.Nb;
       if (sb == se) continue;
-      const int d_idx = (MODE == MODE_FAR ? group * S : 0) + sp;   // destination
+      const int d_idx = (MODE == MODE_FAR ? group * S : 0) + sp;   // destination (equal splits)
       // destination base shifted to the unit's mesh (rows voff .. voff + Nb - 1)
-      float *Mdst = ((d_idx == 0) ? args.M : args.P + (size_t)(d_idx - 1) * KJN) + un.voff;
-      const bool dst_accumulates = (d_idx == 0) && args.accumulate;
+      // destination of this unit: element (k, j, row r of the tile) at dbase + (k J + j) dld + r
+      const bool to_M = SKP > 0 ? sp == 0 : d_idx == 0;
+      float *dbase;
+      long long dld;
+      if (SKP > 0 && sp != 0) {
+        dbase = args.slots + (size_t)(group * SKP + cta_in_group) * args.K * args.J * 128;
+        dld = 128;
+      } else {
+        dbase = ((d_idx == 0) ? args.M : args.P + (size_t)(d_idx - 1) * KJN) + un.voff + (size_t)t * 128;
+        dld = stride;
+      }
+      const bool dst_accumulates = to_M && args.accumulate;
       const int o = t * 128 + orow;
       const bool o_ok = o < Nb;
       const float *pos_m = args.pos + un.voff;
@@ -925,9 +972,9 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
                 for (int q = 0; q < 16; ++q) {
                   const int j = jc + q;
                   if (j < args.J) {
-                    float *dst = Mdst + ((size_t)k * args.J + j) * stride + oe;
+                    float *dst = dbase + ((size_t)k * args.J + j) * dld + (oe - t * 128);
                     float v = __uint_as_float(r[q]);
-                    if (first_seg && sp == 0) {
+                    if (first_seg && to_M) {
                       const float tpv = a_o * args.T[(size_t)j * stride + un.voff + oe];
                       const float th = __bfloat162float(__float2bfloat16_rn(tpv));
                       float tc_self;
@@ -972,10 +1019,10 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
               for (int q = 0; q < 16; ++q) {
                 const int j = jc + q;
                 if (j < args.J) {
-                  float *da = Mdst + ((size_t)ka * args.J + j) * stride + oe;
+                  float *da = dbase + ((size_t)ka * args.J + j) * dld + (oe - t * 128);
                   *da = (first_seg && !dst_accumulates) ? acc0[q] : *da + acc0[q];
                   if (kb < args.K) {
-                    float *db = Mdst + ((size_t)kb * args.J + j) * stride + oe;
+                    float *db = dbase + ((size_t)kb * args.J + j) * dld + (oe - t * 128);
                     *db = (first_seg && !dst_accumulates) ? acc1[q] : *db + acc1[q];
                   }
                 }
@@ -1005,6 +1052,34 @@ __global__ void add_partials_kernel(float *__restrict__ M, const float *__restri
     float acc = M[i];
     for (int q = 0; q < n_part; ++q) acc += P[(size_t)q * n + i];
     M[i] = acc;
+  }
+}
+
+// Stream-K fix-up: block (g, p) leads when CTA p's stage range starts inside a tile and
+// CTA p - 1's does not start inside the same tile; it adds the slots p, p+1, ... of that
+// tile (in CTA order) to M for the bases of group g.
+__global__ void streamk_fixup_kernel(float *__restrict__ M, const float *__restrict__ slots, int n_tiles, int SPT,
+                                     int P, int CB, int K, int J, int N, long long stride) {
+  const int g = blockIdx.x / P, p = blockIdx.x % P;
+  const long long T_st = (long long)n_tiles * SPT;
+  const long long s0 = T_st * p / P;
+  if (s0 % SPT == 0) return;
+  const long long t = s0 / SPT;
+  if (p > 0 && T_st * (p - 1) / P > t * SPT) return;
+  int p_end = p + 1;
+  while (p_end < P && T_st * p_end / P < (t + 1) * SPT) ++p_end;
+  const int k0 = g * CB, k1 = min(K, k0 + CB);
+  const long long left = (long long)N - t * 128;
+  const int rows = left < 128 ? (int)left : 128;
+  const int n_el = (k1 - k0) * J * 128;
+  for (int e = threadIdx.x; e < n_el; e += blockDim.x) {
+    const int row = e % 128, kj = e / 128;
+    if (row >= rows) continue;
+    const int k = k0 + kj / J, j = kj % J;
+    float *dst = M + ((size_t)k * J + j) * stride + t * 128 + row;
+    float acc = *dst;
+    for (int q = p; q < p_end; ++q) acc += slots[(((size_t)(g * P + q) * K + k) * J + j) * 128 + row];
+    *dst = acc;
   }
 }
 
@@ -1185,6 +1260,21 @@ static tsr_status launch_tc(const TcArgs &a0, int n_cols, const CUtensorMap &tma
   const long units = (a.units ? (long)a.n_units_total : (long)a.n_otiles * best_S) * G;
   int grid = (int)std::min<long>(units, sms);
   grid = std::max(G, grid / G * G);
+  // Stream-K for one mesh over all its records (table modes): equal stage ranges per CTA.
+  const bool streamk = allow_split && MODE != MODE_FAR && !a.units && !a.near_off;
+  Scratch slots;
+  if (streamk) {
+    const long long T_st = (long long)a.n_otiles * a.n_steps;
+    int P = std::max(1, sms / G);
+    P = (int)std::min<long long>(P, std::max<long long>(1, T_st / 64));   // at least 64 stages per CTA
+    a.streamk_P = P;
+    a.n_split = 1;
+    best_S = 1;
+    grid = G * P;
+    tsr_status st = slots.alloc(sizeof(float) * (size_t)G * P * a.K * a.J * 128, s);
+    if (st != TSR_OK) return st;
+    a.slots = static_cast<float *>(slots.p);
+  }
   const int n_dest = (MODE == MODE_FAR ? G : 1) * best_S;
   Scratch part;
   const size_t mn = (size_t)a.K * a.J * (size_t)a.stride;
@@ -1196,6 +1286,12 @@ static tsr_status launch_tc(const TcArgs &a0, int n_cols, const CUtensorMap &tma
   }
   kern<<<grid, C::NTHREADS, smem, s>>>(tmap, a); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
+  if (streamk) {
+    streamk_fixup_kernel<<<G * a.streamk_P, 256, 0, s>>>(a.M, a.slots, a.n_otiles, a.n_steps, a.streamk_P, CB, a.K,
+                                                          a.J, a.N, a.stride);
+    ::tsr::count_launch();
+    TSR_CUDA(cudaGetLastError());
+  }
   if (n_dest > 1) {
     add_partials_kernel<<<4 * sms, 256, 0, s>>>(a.M, a.P, n_dest - 1, mn); ::tsr::count_launch();
     TSR_CUDA(cudaGetLastError());
