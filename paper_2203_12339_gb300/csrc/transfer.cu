@@ -1072,14 +1072,30 @@ __global__ void streamk_fixup_kernel(float *__restrict__ M, const float *__restr
   const long long left = (long long)N - t * 128;
   const int rows = left < 128 ? (int)left : 128;
   const int n_el = (k1 - k0) * J * 128;
-  for (int e = threadIdx.x; e < n_el; e += blockDim.x) {
-    const int row = e % 128, kj = e / 128;
-    if (row >= rows) continue;
-    const int k = k0 + kj / J, j = kj % J;
-    float *dst = M + ((size_t)k * J + j) * stride + t * 128 + row;
-    float acc = *dst;
-    for (int q = p; q < p_end; ++q) acc += slots[(((size_t)(g * P + q) * K + k) * J + j) * 128 + row];
-    *dst = acc;
+  constexpr int U = 4;   // elements per thread in flight
+  for (int e0 = threadIdx.x; e0 < n_el; e0 += U * blockDim.x) {
+    float acc[U];
+    float *dst[U];
+    size_t soff[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      const int row = e % 128, kj = e / 128;
+      const bool ok = e < n_el && row < rows;
+      const int k = k0 + kj / J, j = kj % J;
+      dst[u] = ok ? M + ((size_t)k * J + j) * stride + t * 128 + row : nullptr;
+      soff[u] = ((size_t)k * J + j) * 128 + row;
+      acc[u] = ok ? *dst[u] : 0.f;
+    }
+    for (int q = p; q < p_end; ++q) {
+      const float *sl = slots + (size_t)(g * P + q) * K * J * 128;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (dst[u]) acc[u] += sl[soff[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (dst[u]) *dst[u] = acc[u];
   }
 }
 
@@ -1287,7 +1303,7 @@ static tsr_status launch_tc(const TcArgs &a0, int n_cols, const CUtensorMap &tma
   kern<<<grid, C::NTHREADS, smem, s>>>(tmap, a); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   if (streamk) {
-    streamk_fixup_kernel<<<G * a.streamk_P, 256, 0, s>>>(a.M, a.slots, a.n_otiles, a.n_steps, a.streamk_P, CB, a.K,
+    streamk_fixup_kernel<<<G * a.streamk_P, 1024, 0, s>>>(a.M, a.slots, a.n_otiles, a.n_steps, a.streamk_P, CB, a.K,
                                                           a.J, a.N, a.stride);
     ::tsr::count_launch();
     TSR_CUDA(cudaGetLastError());

@@ -116,158 +116,264 @@ tsr_status haar_inverse(const float *Xw, int rows, int nu, float *X, cudaStream_
 }
 
 // ---------------------------------------------------------------- top-p selection
+// Exclusive scan of one value per thread across a block of SEL_NT threads; `total`
+// receives the block sum.  wsum: SEL_NT / 32 shared words.
+constexpr int SEL_NT = 512;
+__device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned *wsum, unsigned &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned v = lane < SEL_NT / 32 ? wsum[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane < SEL_NT / 32) wsum[lane] = v;
+  }
+  __syncthreads();
+  const unsigned excl = incl - x + (warp > 0 ? wsum[warp - 1] : 0u);
+  total = wsum[SEL_NT / 32 - 1];
+  __syncthreads();
+  return excl;
+}
+
 // One block per (k, j) row.  Radix select (4 x 8 bits) of the n_keep-th largest
-// |c| over the chart coefficients, then a block scan in index order that keeps
-// every larger value and the first (n_keep - #larger) values equal to it.
-__global__ void __launch_bounds__(1024) select_kernel(const float *__restrict__ Mw, int n_coef, int NW, int n_keep,
-                                                     uint8_t *__restrict__ keep) {
+// |c| over the chart coefficients (histograms with warp-aggregated shared atomics:
+// lanes holding the same digit add once; four independent loads per thread in
+// flight), then, in index order, the keep flags and the column list: every larger
+// value, and the first (n_keep - #larger) values equal to it.  Both poles are kept
+// and end the column list.
+__global__ void __launch_bounds__(SEL_NT) select_kernel(const float *__restrict__ Mw, int n_coef, int NW, int n_keep,
+                                                       uint8_t *__restrict__ keep, int32_t *__restrict__ cidx,
+                                                       float *__restrict__ cval) {
   __shared__ unsigned hist[256];
-  __shared__ unsigned s_sel, s_cum;
-  __shared__ unsigned warp_tot[32];
+  __shared__ unsigned s_sel, s_cum, s_eq;
+  __shared__ unsigned wsum[SEL_NT / 32];
   const int rowi = blockIdx.x;
   const float *c = Mw + (size_t)rowi * NW;
   uint8_t *kp = keep + (size_t)rowi * NW;
-  unsigned prefix = 0, mask = 0, remaining = (unsigned)n_keep;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned prefix = 0, mask = 0, remaining = (unsigned)n_keep, n_eq = 0;
   for (int shift = 24; shift >= 0; shift -= 8) {
-    for (int q = threadIdx.x; q < 256; q += blockDim.x) hist[q] = 0;
+    for (int q = threadIdx.x; q < 256; q += SEL_NT) hist[q] = 0;
     __syncthreads();
-    for (int w = threadIdx.x; w < n_coef; w += blockDim.x) {
-      const unsigned u = __float_as_uint(c[w]) & 0x7FFFFFFFu;
-      if ((u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
+    for (int base = 0; base < n_coef; base += 4 * SEL_NT) {
+      unsigned u[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int w = base + q * SEL_NT + threadIdx.x;
+        u[q] = (w < n_coef) ? (__float_as_uint(c[w]) & 0x7FFFFFFFu) : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int w = base + q * SEL_NT + threadIdx.x;
+        const bool in = (w < n_coef) && ((u[q] & mask) == prefix);
+        const unsigned digit = in ? ((u[q] >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, digit);
+        if (in && lane == __ffs(peers) - 1) atomicAdd(&hist[digit], (unsigned)__popc(peers));
+      }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned cum = 0;
-      int sel = 0;
-      for (int dgt = 255; dgt >= 0; --dgt) {
-        if (cum + hist[dgt] >= remaining) {
-          sel = dgt;
-          break;
-        }
-        cum += hist[dgt];
+    if (warp == 0) {
+      // lane l holds digits 255 - 8 l down to 248 - 8 l; a scan from the top finds the
+      // digit where the running count reaches `remaining` (the histogram holds >= remaining)
+      unsigned h[8], sum = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        h[q] = hist[255 - 8 * lane - q];
+        sum += h[q];
       }
-      s_sel = (unsigned)sel;
-      s_cum = cum;
+      unsigned incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const unsigned hit = __ballot_sync(0xffffffffu, incl >= remaining);
+      if (hit != 0u && lane == __ffs(hit) - 1) {
+        unsigned cum = incl - sum;
+        int q = 0;
+        for (; q < 7; ++q) {
+          if (cum + h[q] >= remaining) break;
+          cum += h[q];
+        }
+        s_sel = (unsigned)(255 - 8 * lane - q);
+        s_cum = cum;
+        s_eq = h[q];
+      }
     }
     __syncthreads();
     remaining -= s_cum;
     prefix |= s_sel << shift;
     mask |= 255u << shift;
+    n_eq = s_eq;
     __syncthreads();
   }
-  // prefix = key of the n_keep-th largest; keep `remaining` of the equal keys (lowest index first)
+  // prefix = key of the n_keep-th largest; keep `remaining` of its n_eq equal keys (lowest index first)
   const unsigned tau = prefix;
-  unsigned taken_before = 0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int base = 0; base < n_coef; base += blockDim.x) {
-    const int w = base + threadIdx.x;
-    unsigned u = 0;
-    if (w < n_coef) u = __float_as_uint(c[w]) & 0x7FFFFFFFu;
-    const bool eq = (w < n_coef) && (u == tau);
-    const unsigned bal = __ballot_sync(0xffffffffu, eq);
-    const unsigned before_in_warp = __popc(bal & ((1u << lane) - 1u));
-    if (lane == 0) warp_tot[warp] = __popc(bal);
-    __syncthreads();
-    unsigned before_warps = 0, total = 0;
-    for (int q = 0; q < nw; ++q) {
-      const unsigned v = warp_tot[q];
-      if (q < warp) before_warps += v;
-      total += v;
+  const bool all_eq = remaining >= n_eq;
+  const int ncol = n_keep + 2;
+  int32_t *ci = cidx + (size_t)rowi * ncol;
+  float *cv = cval + (size_t)rowi * ncol;
+  unsigned written = 0, eq_seen = 0;
+  for (int base = 0; base < n_coef; base += 8 * SEL_NT) {
+    const int w0 = base + 8 * threadIdx.x;
+    float v[8];
+    unsigned u[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      v[q] = (w0 + q < n_coef) ? c[w0 + q] : 0.f;
+      u[q] = __float_as_uint(v[q]) & 0x7FFFFFFFu;
     }
-    if (w < n_coef) {
-      const bool keepit = (u > tau) || (eq && (taken_before + before_warps + before_in_warp) < remaining);
-      kp[w] = keepit ? 1 : 0;
+    unsigned er = 0, eq_tot = 0;
+    if (!all_eq) {
+      unsigned neq = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) neq += (w0 + q < n_coef && u[q] == tau) ? 1u : 0u;
+      er = eq_seen + block_excl_scan(neq, wsum, eq_tot);
     }
-    taken_before += total;
-    __syncthreads();
+    unsigned kmask = 0, nk = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      bool k = false;
+      if (w0 + q < n_coef) {
+        if (u[q] > tau) {
+          k = true;
+        } else if (u[q] == tau) {
+          k = all_eq || er < remaining;
+          ++er;
+        }
+      }
+      kmask |= (k ? 1u : 0u) << q;
+      nk += k ? 1u : 0u;
+    }
+    unsigned k_tot;
+    unsigned pos = written + block_excl_scan(nk, wsum, k_tot);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (w0 + q < n_coef) kp[w0 + q] = (uint8_t)((kmask >> q) & 1u);
+      if (((kmask >> q) & 1u) && pos < (unsigned)n_keep) {
+        ci[pos] = w0 + q;
+        cv[pos] = v[q];
+        ++pos;
+      }
+    }
+    written += k_tot;
+    eq_seen += eq_tot;
   }
   if (threadIdx.x == 0) {
     kp[n_coef] = 1;
     kp[n_coef + 1] = 1;
+    ci[n_keep] = n_coef;
+    cv[n_keep] = c[n_coef];
+    ci[n_keep + 1] = n_coef + 1;
+    cv[n_keep + 1] = c[n_coef + 1];
   }
 }
 
-// Column view: block per kj compacts its kept rows in ascending order.
-__global__ void __launch_bounds__(1024) pack_columns_kernel(const float *__restrict__ Mw,
-                                                           const uint8_t *__restrict__ keep, int NW, int ncol,
-                                                           int32_t *__restrict__ cidx, float *__restrict__ cval) {
-  __shared__ unsigned warp_tot[32];
-  const int kj = blockIdx.x;
-  const uint8_t *kp = keep + (size_t)kj * NW;
-  const float *c = Mw + (size_t)kj * NW;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  unsigned written = 0;
-  for (int base = 0; base < NW; base += blockDim.x) {
-    const int w = base + threadIdx.x;
-    const bool k = (w < NW) && kp[w];
-    const unsigned bal = __ballot_sync(0xffffffffu, k);
-    if (lane == 0) warp_tot[warp] = __popc(bal);
-    __syncthreads();
-    unsigned before = 0, total = 0;
-    for (int q = 0; q < nw; ++q) {
-      before += (q < warp) ? warp_tot[q] : 0u;
-      total += warp_tot[q];
-    }
-    const unsigned pos = written + before + __popc(bal & ((1u << lane) - 1u));
-    if (k && pos < (unsigned)ncol) {
-      cidx[(size_t)kj * ncol + pos] = w;
-      cval[(size_t)kj * ncol + pos] = c[w];
-    }
-    written += total;
-    __syncthreads();
-  }
-}
-
-// entries per wavelet row w (over all kj)
-__global__ void count_kernel(const uint8_t *__restrict__ keep, int KJ, int NW, int64_t *__restrict__ cnt) {
-  const int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= NW) return;
-  int64_t n = 0;
-  for (int kj = 0; kj < KJ; ++kj) n += keep[(size_t)kj * NW + w];
-  cnt[w] = n;
-}
-
-// exclusive scan of cnt[0..n) into row_ptr[0..n] (single block; n is a few 1e5)
-__global__ void __launch_bounds__(1024) scan_kernel(const int64_t *__restrict__ cnt, int n, int64_t *__restrict__ row_ptr) {
-  __shared__ int64_t warp_sum[32];
-  __shared__ int64_t carry;
-  if (threadIdx.x == 0) carry = 0;
+// CSR by wavelet row, in three launches over tiles of 32 rows:
+//  count: warp q sums the rows' flags of kj = q, q + 8, ... (32 consecutive bytes per
+//         load); the tile's total goes to tsum[tile];
+//  scan:  exclusive scan of the tile totals (one block);
+//  fill:  warp q owns the kj chunk [q KJ / 8, (q+1) KJ / 8); row offsets come from the
+//         tile offset and a scan of the 32 row counts, the warp writes its entries
+//         (kj ascending within each row) and row_ptr.
+constexpr int ROW_TILE = 32;
+__global__ void __launch_bounds__(256) count_kernel(const uint8_t *__restrict__ keep, int KJ, int NW,
+                                                    int64_t *__restrict__ tsum) {
+  __shared__ int part[8][ROW_TILE];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = blockIdx.x * ROW_TILE + lane;
+  int n = 0;
+  if (w < NW)
+    for (int kj = warp; kj < KJ; kj += 8) n += keep[(size_t)kj * NW + w];
+  part[warp][lane] = n;
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int base = 0; base < n; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const int64_t v = i < n ? cnt[i] : 0;
-    int64_t x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sum[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      int64_t ws = lane < (int)(blockDim.x >> 5) ? warp_sum[lane] : 0;
-      for (int o = 1; o < 32; o <<= 1) {
-        const int64_t y = __shfl_up_sync(0xffffffffu, ws, o);
-        if (lane >= o) ws += y;
-      }
-      warp_sum[lane] = ws;
-    }
-    __syncthreads();
-    const int64_t incl = x + (warp > 0 ? warp_sum[warp - 1] : 0) + carry;
-    if (i < n) row_ptr[i] = incl - v;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry = incl;
-    __syncthreads();
+  if (warp == 0) {
+    int t = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += part[q][lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) tsum[blockIdx.x] = t;
   }
-  if (threadIdx.x == 0) row_ptr[n] = carry;
 }
 
-__global__ void fill_kernel(const float *__restrict__ Mw, const uint8_t *__restrict__ keep, int KJ, int NW,
-                            const int64_t *__restrict__ row_ptr, uint16_t *__restrict__ col, float *__restrict__ val) {
-  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+// exclusive scan of v[0..n) in place; v[n] = total (single block; n = tiles, a few thousand)
+__global__ void __launch_bounds__(1024) scan_kernel(int64_t *__restrict__ v, int n) {
+  __shared__ int64_t warp_sum[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int b = min(n, (int)threadIdx.x * per), e = min(n, b + per);
+  int64_t sum = 0;
+  for (int i = b; i < e; ++i) sum += v[i];
+  int64_t x = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t ws = lane < (int)(blockDim.x >> 5) ? warp_sum[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, ws, o);
+      if (lane >= o) ws += y;
+    }
+    warp_sum[lane] = ws;
+  }
+  __syncthreads();
+  int64_t run = x - sum + (warp > 0 ? warp_sum[warp - 1] : 0);
+  for (int i = b; i < e; ++i) {
+    const int64_t c = v[i];
+    v[i] = run;
+    run += c;
+  }
+  if (threadIdx.x == blockDim.x - 1) v[n] = run;
+}
+
+__global__ void __launch_bounds__(256) fill_kernel(const float *__restrict__ Mw, const uint8_t *__restrict__ keep,
+                                                   int KJ, int NW, const int64_t *__restrict__ toff,
+                                                   int64_t *__restrict__ row_ptr, uint16_t *__restrict__ col,
+                                                   float *__restrict__ val) {
+  __shared__ int part[8][ROW_TILE];
+  __shared__ int64_t rbase[ROW_TILE];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = blockIdx.x * ROW_TILE + lane;
+  const int kb = warp * KJ / 8, ke = (warp + 1) * KJ / 8;
+  int n = 0;
+  if (w < NW)
+    for (int kj = kb; kj < ke; ++kj) n += keep[(size_t)kj * NW + w];
+  part[warp][lane] = n;
+  __syncthreads();
+  if (warp == 0) {
+    int t = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += part[q][lane];
+    int incl = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int64_t rb = toff[blockIdx.x] + (incl - t);
+    rbase[lane] = rb;
+    if (w < NW) row_ptr[w] = rb;
+    if (w == NW - 1) row_ptr[NW] = rb + t;
+  }
+  __syncthreads();
   if (w >= NW) return;
-  int64_t p = row_ptr[w];
-  for (int kj = 0; kj < KJ; ++kj) {
+  int64_t p = rbase[lane];
+  for (int q = 0; q < warp; ++q) p += part[q][lane];
+  for (int kj = kb; kj < ke; ++kj) {
     if (keep[(size_t)kj * NW + w]) {
       col[p] = (uint16_t)kj;
       val[p] = Mw[(size_t)kj * NW + w];
@@ -288,15 +394,15 @@ tsr_status wavelet_compress_into(const float *Mw, tsr_compressed *c, cudaStream_
   const int NW = c->n_rows, n_coef = NW - 2, KJ = c->K * c->J;
   Scratch keep_s, cnt_s;
   tsr_status st = keep_s.alloc((size_t)KJ * NW, s);
-  if (st == TSR_OK) st = cnt_s.alloc(sizeof(int64_t) * NW, s);
+  if (st == TSR_OK) st = cnt_s.alloc(sizeof(int64_t) * ((NW + ROW_TILE - 1) / ROW_TILE + 1), s);
   if (st != TSR_OK) return st;
   uint8_t *keep = static_cast<uint8_t *>(keep_s.p);
   int64_t *cnt = static_cast<int64_t *>(cnt_s.p);
-  select_kernel<<<KJ, 1024, 0, s>>>(Mw, n_coef, NW, c->n_keep, keep); ::tsr::count_launch();
-  count_kernel<<<(NW + 255) / 256, 256, 0, s>>>(keep, KJ, NW, cnt); ::tsr::count_launch();
-  scan_kernel<<<1, 1024, 0, s>>>(cnt, NW, c->row_ptr); ::tsr::count_launch();
-  fill_kernel<<<(NW + 255) / 256, 256, 0, s>>>(Mw, keep, KJ, NW, c->row_ptr, c->col, c->val); ::tsr::count_launch();
-  pack_columns_kernel<<<KJ, 1024, 0, s>>>(Mw, keep, NW, c->n_keep + 2, c->cidx, c->cval); ::tsr::count_launch();
+  const int row_tiles = (NW + ROW_TILE - 1) / ROW_TILE;
+  select_kernel<<<KJ, SEL_NT, 0, s>>>(Mw, n_coef, NW, c->n_keep, keep, c->cidx, c->cval); ::tsr::count_launch();
+  count_kernel<<<row_tiles, 256, 0, s>>>(keep, KJ, NW, cnt); ::tsr::count_launch();
+  scan_kernel<<<1, 1024, 0, s>>>(cnt, row_tiles); ::tsr::count_launch();
+  fill_kernel<<<row_tiles, 256, 0, s>>>(Mw, keep, KJ, NW, cnt, c->row_ptr, c->col, c->val); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }
