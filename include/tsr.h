@@ -238,13 +238,18 @@ void tsr_compressed_destroy(tsr_compressed *c);
  * Relight / material edit (Section 4, rendering Steps 3-5):
  *   b^w[e][c][w] = sum_{(kj,v) in row w} v * g[e][c][k] * l[j]
  *   B[e][c][.]   = W^-1 b^w[e][c][.]         (inverse Haar per chart)
- *   g : device [n_edit][3][K] FP32;  l: device [J] FP32;
+ *   g : device [n_edit][3][K] FP32;  l: device [J] FP32 (one light for all edits);
  *   B : device [n_edit][3][N] FP32 out.
- * Scratch: b^w, n_edit*3*(10 P^2 + 2) FP32.
+ * Evaluated with the light contracted first (the same B by linearity):
+ *   Y[k][w] = sum_j S[w][kj] l[j],  Z[k] = W^-1 Y[k],  B[e][c] = sum_k g[e][c][k] Z[k],
+ * so the kept coefficients are read once per call, whatever n_edit.
+ * Scratch: Y and Z, K*(10 P^2 + 2 + N) FP32.
  *
  * tsr_relight_backward: reverse mode for an upstream gradient dLdB
- * [n_edit][3][N]: r^w = W dLdB (forward Haar), dc = S^T r^w,
- *   dg[e][c][k] = sum_j l_j dc[e][c][kj],   dl[j] = sum_{e,c,k} g[e][c][k] dc[e][c][kj].
+ * [n_edit][3][N] (r^w = W dLdB, dc = S^T r^w, dg = sum_j l_j dc, dl = sum g dc),
+ * evaluated as
+ *   dg[e][c][k] = <dLdB[e][c], Z[k]>,
+ *   dl[j] = sum_k sum_w S[w][kj] (W Q[k])[w],  Q[k] = sum_{e,c} g[e][c][k] dLdB[e][c].
  *   dg : device [n_edit][3][K] FP32 out;  dl: device [J] FP32 out (overwritten).
  * ---------------------------------------------------------------------- */
 tsr_status tsr_relight(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,
@@ -261,8 +266,9 @@ tsr_status tsr_relight_backward(const tsr_compressed *c, int n_edit, const float
  * comes from a fixed 32 MiB array of device memory that the library reserves on
  * every GPU where it is loaded (held until the process exits), so the call
  * itself allocates nothing.
- *   - Limit: n_edit * 3 * (10 P^2 + 2) <= 8,388,608 floats, else
- *     TSR_ERR_INVALID_ARG (e.g. 64 edits of a 40,962-vertex mesh fit).
+ *   - Limit: K * (10 P^2 + 2 + N) <= 8,388,608 floats, else TSR_ERR_INVALID_ARG
+ *     (the largest case the library accepts, K = 16 on nu = 128, needs 5.2 Mi;
+ *     the number of edits does not enter).
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.

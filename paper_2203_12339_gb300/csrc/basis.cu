@@ -272,35 +272,38 @@ __global__ void __launch_bounds__(256) project_kernel(const double *__restrict__
   }
 }
 
-// One block per edit: dL/dtheta = sum_k dL/dg_k dg_k/dtheta over the three channels.
+// One block per (edit, channel): dL/dtheta = sum_k dL/dg_k dg_k/dtheta.  The
+// eta part of each channel goes to de_part[e][c]; project_eta_finish_kernel adds
+// the three channels of an edit in order.
 __global__ void __launch_bounds__(256) project_backward_kernel(
     const double *__restrict__ f, int K, int n_r, double dr, const double *__restrict__ sa,
     const double *__restrict__ ss, const double *__restrict__ eta, const float *__restrict__ dLdg,
-    float *__restrict__ dsa, float *__restrict__ dss, float *__restrict__ deta) {
+    float *__restrict__ dsa, float *__restrict__ dss, double *__restrict__ de_part) {
   __shared__ double red[3 * 32];
-  const int e = blockIdx.x;
-  double de_total = 0.0;
-  for (int ch = 0; ch < 3; ++ch) {
-    const DipoleMaterial mat = dipole_material(sa[e * 3 + ch], ss[e * 3 + ch], eta[e]);
-    const float *w = dLdg + (size_t)(e * 3 + ch) * K;
-    double v[3] = {0.0, 0.0, 0.0};
-    for (int m = threadIdx.x; m < n_r; m += blockDim.x) {
-      double wm = 0.0;
-      for (int k = 0; k < K; ++k) wm += (double)w[k] * f[(size_t)k * n_r + m];
-      double R, dRa, dRs, dRe;
-      dipole_rd_grad(dr * m, mat, R, dRa, dRs, dRe);
-      v[0] += wm * dRa;
-      v[1] += wm * dRs;
-      v[2] += wm * dRe;
-    }
-    block_sum<3>(v, red);
-    if (threadIdx.x == 0) {
-      dsa[e * 3 + ch] = (float)v[0];
-      dss[e * 3 + ch] = (float)v[1];
-    }
-    de_total += v[2];
+  const int e = blockIdx.x / 3, ch = blockIdx.x % 3;
+  const DipoleMaterial mat = dipole_material(sa[e * 3 + ch], ss[e * 3 + ch], eta[e]);
+  const float *w = dLdg + (size_t)(e * 3 + ch) * K;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int m = threadIdx.x; m < n_r; m += blockDim.x) {
+    double wm = 0.0;
+    for (int k = 0; k < K; ++k) wm += (double)w[k] * f[(size_t)k * n_r + m];
+    double R, dRa, dRs, dRe;
+    dipole_rd_grad(dr * m, mat, R, dRa, dRs, dRe);
+    v[0] += wm * dRa;
+    v[1] += wm * dRs;
+    v[2] += wm * dRe;
   }
-  if (threadIdx.x == 0) deta[e] = (float)de_total;
+  block_sum<3>(v, red);
+  if (threadIdx.x == 0) {
+    dsa[e * 3 + ch] = (float)v[0];
+    dss[e * 3 + ch] = (float)v[1];
+    de_part[e * 3 + ch] = v[2];
+  }
+}
+
+__global__ void project_eta_finish_kernel(const double *__restrict__ de_part, int n, float *__restrict__ deta) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) deta[e] = (float)((de_part[e * 3] + de_part[e * 3 + 1]) + de_part[e * 3 + 2]);
 }
 
 }  // namespace tsr
@@ -493,8 +496,13 @@ extern "C" tsr_status tsr_project_material_backward(const tsr_basis *basis, int 
   if (n == 0) return TSR_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const double dr = basis->r_max / (basis->n_r - 1);
-  project_backward_kernel<<<n, 256, 0, s>>>(basis->f64, basis->K, basis->n_r, dr, sigma_a, sigma_s, eta, dLdg,
-                                            dsigma_a, dsigma_s, deta); ::tsr::count_launch();
+  Scratch de_s;
+  st = de_s.alloc(sizeof(double) * 3 * (size_t)n, s);
+  if (st != TSR_OK) return st;
+  double *de_part = static_cast<double *>(de_s.p);
+  project_backward_kernel<<<n * 3, 256, 0, s>>>(basis->f64, basis->K, basis->n_r, dr, sigma_a, sigma_s, eta, dLdg,
+                                                dsigma_a, dsigma_s, de_part); ::tsr::count_launch();
+  project_eta_finish_kernel<<<(n + 255) / 256, 256, 0, s>>>(de_part, n, deta); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }

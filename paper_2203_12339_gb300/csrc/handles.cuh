@@ -78,6 +78,8 @@ tsr_status relight(const tsr_compressed *c, int n_edit, const float *g, const fl
                    cudaStream_t s);
 tsr_status relight_backward(const tsr_compressed *c, int n_edit, const float *g, const float *l,
                             const float *dLdB, float *dg, float *dl, cudaStream_t s);
+// Floats of caller-provided scratch relight_with_scratch needs: K (10 P^2 + 2 + N).
+size_t relight_scratch_floats(const tsr_compressed *c);
 tsr_status relight_with_scratch(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,
-                                float *bw, cudaStream_t s);
+                                float *scratch, cudaStream_t s);
 }  // namespace tsr

@@ -1,160 +1,281 @@
 // Section 4, rendering Steps 3-5: relight / material edit from the compressed
 // wavelet transfer, and its reverse mode.
 //
-// Forward, per vector v = (edit e, channel c):
-//   c_v[kj]  = g[e][c][k] * l[j]                       (Steps 3-4 weights)
-//   b^w_v[w] = sum over the kept entries (kj, val) of row w of val * c_v[kj]
-//   B_v      = w_1^{-1} b^w_v                           (Step 5, inverse Haar per chart)
-// Reverse, for an upstream gradient dL/dB:
-//   r^w_v    = w_1 dL/dB_v          (w_1 is orthonormal: the adjoint of w_1^{-1} is w_1)
-//   dc_v[kj] = sum_w S[w][kj] r^w_v[w]
-//   dg[e][c][k] = sum_j l_j dc_v[kj],   dl[j] = sum_{v,k} g_v[k] dc_v[kj].
+// Steps 3-5 give, per vector v = (edit e, channel c) of a call,
+//   c_v[kj] = g[e][c][k] * l[j],   b^w_v = S c_v,   B_v = w_1^{-1} b^w_v.
+// All vectors of a call share the light l, so c_v factorises and the same B is
+// reached by contracting the light first (the Haar transform is linear):
+//   Y[k][w] = sum_j S[w][kj] l[j]          one pass over the kept entries
+//   Z[k]    = w_1^{-1} Y[k]                K inverse Haar transforms
+//   B_v     = sum_k g_v[k] Z[k]            a K-term combination per output value
+// The compressed transfer is read once per call whatever the number of edits,
+// and the per-edit work is K multiply-adds per vertex.
+//
+// Reverse, for an upstream gradient dL/dB (w_1 is orthonormal, so the adjoint of
+// w_1^{-1} is w_1):
+//   dg_v[k] = <dL/dB_v, Z[k]>
+//   Q[k]    = sum_v g_v[k] dL/dB_v,   R[k] = w_1 Q[k]
+//   dl[j]   = sum_k sum_w S[w][kj] R[k][w]
 #include <algorithm>
 
 #include "handles.cuh"
 
 namespace tsr {
 
-constexpr int RL_VG = 8;   // vectors per block
+constexpr int RL_KMAX = 16;   // bases (the library's K limit)
 
-// b^w[v][w] for a group of RL_VG vectors; one thread per wavelet row.
-__global__ void __launch_bounds__(256) relight_spmm_kernel(const int64_t *__restrict__ row_ptr,
-                                                          const uint16_t *__restrict__ col,
-                                                          const float *__restrict__ val, int n_rows, int K, int J,
-                                                          int V, const float *__restrict__ g,
-                                                          const float *__restrict__ l, float *__restrict__ bw) {
-  extern __shared__ float cw[];   // [KJ][RL_VG]
-  const int KJ = K * J;
-  const int v0 = blockIdx.y * RL_VG;
-  for (int q = threadIdx.x; q < KJ * RL_VG; q += blockDim.x) {
-    const int kj = q / RL_VG, vv = q % RL_VG, v = v0 + vv;
-    const int k = kj / J, j = kj % J;
-    cw[q] = (v < V) ? g[(size_t)v * K + k] * l[j] : 0.0f;
-  }
+// Y[k][w] for every wavelet row w, a warp per row: lane q takes entry q (then
+// q + 32, ...) of the row, which is sorted by kj, so the entries of basis k form a
+// run; a segmented scan over the lanes sums each run and the run's last lane adds
+// it to Y[k][w] (Y is zeroed first).
+__global__ void __launch_bounds__(256) relight_y_kernel(const int64_t *__restrict__ row_ptr,
+                                                       const uint16_t *__restrict__ col,
+                                                       const float *__restrict__ val, int n_rows, int J,
+                                                       const float *__restrict__ l, float *__restrict__ Y) {
+  __shared__ float ls[32];
+  if (threadIdx.x < J) ls[threadIdx.x] = l[threadIdx.x];
   __syncthreads();
-  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w >= n_rows) return;
-  float acc[RL_VG];
+  const int64_t p0 = row_ptr[w], pe = row_ptr[w + 1];
+  for (int64_t base = p0; base < pe; base += 32) {
+    const int64_t p = base + lane;
+    const bool in = p < pe;
+    const int kj = in ? (int)col[p] : 0;
+    const int k = in ? kj / J : -1 - lane;   // inactive lanes: keys of their own
+    float x = in ? val[p] * ls[kj - (kj / J) * J] : 0.0f;
 #pragma unroll
-  for (int vv = 0; vv < RL_VG; ++vv) acc[vv] = 0.0f;
-  const int64_t p1 = row_ptr[w + 1];
-  for (int64_t p = row_ptr[w]; p < p1; ++p) {
-    const float a = val[p];
-    const float4 *cr = reinterpret_cast<const float4 *>(cw + (int)col[p] * RL_VG);
-    const float4 c0 = cr[0], c1 = cr[1];
-    acc[0] = fmaf(a, c0.x, acc[0]);
-    acc[1] = fmaf(a, c0.y, acc[1]);
-    acc[2] = fmaf(a, c0.z, acc[2]);
-    acc[3] = fmaf(a, c0.w, acc[3]);
-    acc[4] = fmaf(a, c1.x, acc[4]);
-    acc[5] = fmaf(a, c1.y, acc[5]);
-    acc[6] = fmaf(a, c1.z, acc[6]);
-    acc[7] = fmaf(a, c1.w, acc[7]);
+    for (int o = 1; o < 32; o <<= 1) {
+      const float y = __shfl_up_sync(0xffffffffu, x, o);
+      const int ky = __shfl_up_sync(0xffffffffu, k, o);
+      if (lane >= o && ky == k) x += y;
+    }
+    const int k_next = __shfl_down_sync(0xffffffffu, k, 1);
+    if (in && (lane == 31 || k_next != k)) Y[(size_t)k * n_rows + w] += x;
   }
-#pragma unroll
-  for (int vv = 0; vv < RL_VG; ++vv)
-    if (v0 + vv < V) bw[(size_t)(v0 + vv) * n_rows + w] = acc[vv];
 }
 
-// dc[v][kj] = sum over the n_keep+2 entries (w, val) of column kj of val * r^w[v][w]:
-// one block per (kj, group of RL_VG vectors), no atomics.
-__global__ void __launch_bounds__(256) relight_colgather_kernel(const int32_t *__restrict__ cidx,
-                                                               const float *__restrict__ cval, int ncol, int n_rows,
-                                                               int KJ, int V, const float *__restrict__ rw,
-                                                               float *__restrict__ dc) {
-  __shared__ float red[RL_VG][8];
-  const int kj = blockIdx.x;
-  const int v0 = blockIdx.y * RL_VG;
-  float acc[RL_VG];
+// B[v][o] = sum_k g[v][k] Z[k][o]: a thread per output vertex o and a chunk of RL_VB vectors.
+constexpr int RL_VB = 32;
+__global__ void __launch_bounds__(256) relight_combine_kernel(const float *__restrict__ Z, int N, int K, int V,
+                                                             const float *__restrict__ g, float *__restrict__ B) {
+  __shared__ float gs[RL_VB * RL_KMAX];
+  const int v0 = blockIdx.y * RL_VB;
+  for (int q = threadIdx.x; q < RL_VB * K; q += blockDim.x) {
+    const int vv = q / K, k = q % K;
+    gs[vv * RL_KMAX + k] = (v0 + vv < V) ? g[(size_t)(v0 + vv) * K + k] : 0.0f;
+  }
+  __syncthreads();
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= N) return;
+  float z[RL_KMAX];
 #pragma unroll
-  for (int vv = 0; vv < RL_VG; ++vv) acc[vv] = 0.0f;
-  const int32_t *ci = cidx + (size_t)kj * ncol;
-  const float *cv = cval + (size_t)kj * ncol;
-  for (int q = threadIdx.x; q < ncol; q += blockDim.x) {
-    const int w = ci[q];
-    const float a = cv[q];
+  for (int k = 0; k < RL_KMAX; ++k) z[k] = (k < K) ? Z[(size_t)k * N + o] : 0.0f;
+  const int vn = min(RL_VB, V - v0);
+  for (int vv = 0; vv < vn; ++vv) {
+    const float *gv = gs + vv * RL_KMAX;
+    float b = 0.0f;
 #pragma unroll
-    for (int vv = 0; vv < RL_VG; ++vv)
-      if (v0 + vv < V) acc[vv] = fmaf(a, rw[(size_t)(v0 + vv) * n_rows + w], acc[vv]);
+    for (int k = 0; k < RL_KMAX; ++k)
+      if (k < K) b = fmaf(gv[k], z[k], b);
+    B[(size_t)(v0 + vv) * N + o] = b;
+  }
+}
+
+// dg partials: block (vector group of RL_GV, o-split s) forms sum over its o-range of
+// dL/dB[v][o] Z[k][o] for its vectors; part[s][v][k].
+constexpr int RL_GV = 4;
+constexpr int RL_OSPLIT = 8;
+__global__ void __launch_bounds__(256) relight_dg_kernel(const float *__restrict__ dLdB, const float *__restrict__ Z,
+                                                        int N, int K, int V, float *__restrict__ part) {
+  __shared__ float red[RL_GV * RL_KMAX][8];
+  const int v0 = blockIdx.x * RL_GV;
+  const int s = blockIdx.y;
+  const int ob = (int)((long long)N * s / RL_OSPLIT), oe = (int)((long long)N * (s + 1) / RL_OSPLIT);
+  float acc[RL_GV][RL_KMAX];
+#pragma unroll
+  for (int a = 0; a < RL_GV; ++a)
+#pragma unroll
+    for (int k = 0; k < RL_KMAX; ++k) acc[a][k] = 0.0f;
+  for (int o = ob + threadIdx.x; o < oe; o += blockDim.x) {
+    float z[RL_KMAX];
+#pragma unroll
+    for (int k = 0; k < RL_KMAX; ++k) z[k] = (k < K) ? Z[(size_t)k * N + o] : 0.0f;
+#pragma unroll
+    for (int a = 0; a < RL_GV; ++a) {
+      const float d = (v0 + a < V) ? dLdB[(size_t)(v0 + a) * N + o] : 0.0f;
+#pragma unroll
+      for (int k = 0; k < RL_KMAX; ++k) acc[a][k] = fmaf(d, z[k], acc[a][k]);
+    }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int vv = 0; vv < RL_VG; ++vv) {
-    float x = acc[vv];
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) red[vv][warp] = x;
-  }
+  for (int a = 0; a < RL_GV; ++a)
+#pragma unroll
+    for (int k = 0; k < RL_KMAX; ++k) {
+      float x = acc[a][k];
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) red[a * RL_KMAX + k][warp] = x;
+    }
   __syncthreads();
-  if (threadIdx.x < RL_VG && v0 + threadIdx.x < V) {
-    float x = 0.0f;
-    for (int w8 = 0; w8 < 8; ++w8) x += red[threadIdx.x][w8];
-    dc[(size_t)(v0 + threadIdx.x) * KJ + kj] = x;
+  if (threadIdx.x < RL_GV * RL_KMAX) {
+    const int a = threadIdx.x / RL_KMAX, k = threadIdx.x % RL_KMAX;
+    if (v0 + a < V && k < K) {
+      float x = 0.0f;
+      for (int q = 0; q < 8; ++q) x += red[threadIdx.x][q];
+      part[((size_t)s * V + v0 + a) * K + k] = x;
+    }
   }
 }
 
-// dg[v][k] = sum_j l_j dc[v][kj];  dl[j] = sum_{v,k} g[v][k] dc[v][kj]  (single block)
-__global__ void __launch_bounds__(1024) relight_grad_finish_kernel(const float *__restrict__ dc, int K, int J, int V,
-                                                                  const float *__restrict__ g,
-                                                                  const float *__restrict__ l, float *__restrict__ dg,
-                                                                  float *__restrict__ dl) {
+// Q[k][o] = sum_v g[v][k] dL/dB[v][o], in RL_QS vector chunks (blockIdx.y) for
+// parallelism: a thread per vertex writes its chunk's partial Qp[chunk][k][o]; the
+// chunks are added in order by relight_qsum_kernel.
+constexpr int RL_QS = 4;
+__global__ void __launch_bounds__(256) relight_q_kernel(const float *__restrict__ dLdB, int N, int K, int V,
+                                                       const float *__restrict__ g, float *__restrict__ Qp) {
+  __shared__ float gs[64 * RL_KMAX];
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int vb = (int)((long long)V * blockIdx.y / RL_QS), ve = (int)((long long)V * (blockIdx.y + 1) / RL_QS);
+  float q[RL_KMAX];
+#pragma unroll
+  for (int k = 0; k < RL_KMAX; ++k) q[k] = 0.0f;
+  for (int v0 = vb; v0 < ve; v0 += 64) {
+    const int vn = min(64, ve - v0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < 64 * K; t += blockDim.x) {
+      const int vv = t / K, k = t % K;
+      gs[vv * RL_KMAX + k] = (vv < vn) ? g[(size_t)(v0 + vv) * K + k] : 0.0f;
+    }
+    __syncthreads();
+    if (o < N) {
+      int vv = 0;
+      for (; vv + 4 <= vn; vv += 4) {   // four independent loads in flight
+        float d[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) d[a] = dLdB[(size_t)(v0 + vv + a) * N + o];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int k = 0; k < RL_KMAX; ++k) q[k] = fmaf(gs[(vv + a) * RL_KMAX + k], d[a], q[k]);
+      }
+      for (; vv < vn; ++vv) {
+        const float d = dLdB[(size_t)(v0 + vv) * N + o];
+#pragma unroll
+        for (int k = 0; k < RL_KMAX; ++k) q[k] = fmaf(gs[vv * RL_KMAX + k], d, q[k]);
+      }
+    }
+  }
+  if (o < N)
+    for (int k = 0; k < K; ++k) Qp[((size_t)blockIdx.y * K + k) * N + o] = q[k];
+}
+
+__global__ void relight_qsum_kernel(const float *__restrict__ Qp, size_t n, float *__restrict__ Q) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float x = Qp[i];
+#pragma unroll
+    for (int c = 1; c < RL_QS; ++c) x += Qp[(size_t)c * n + i];
+    Q[i] = x;
+  }
+}
+
+// colsum[kj] = sum over the n_keep + 2 entries (w, val) of column kj of val * R[k][w]: a block per kj.
+__global__ void __launch_bounds__(256) relight_colsum_kernel(const int32_t *__restrict__ cidx,
+                                                            const float *__restrict__ cval, int ncol, int n_rows,
+                                                            int J, const float *__restrict__ R,
+                                                            float *__restrict__ colsum) {
+  __shared__ float red[8];
+  const int kj = blockIdx.x, k = kj / J;
+  const int32_t *ci = cidx + (size_t)kj * ncol;
+  const float *cv = cval + (size_t)kj * ncol;
+  const float *Rk = R + (size_t)k * n_rows;
+  float acc = 0.0f;
+  for (int q = threadIdx.x; q < ncol; q += blockDim.x) acc = fmaf(cv[q], Rk[ci[q]], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float x = 0.0f;
+    for (int w8 = 0; w8 < 8; ++w8) x += red[w8];
+    colsum[kj] = x;
+  }
+}
+
+// dg[v][k] = sum_s part[s][v][k];  dl[j] = sum_k colsum[k J + j]   (one block)
+__global__ void __launch_bounds__(1024) relight_grad_finish_kernel(const float *__restrict__ part, int V, int K,
+                                                                  int J, const float *__restrict__ colsum,
+                                                                  float *__restrict__ dg, float *__restrict__ dl) {
   for (int q = threadIdx.x; q < V * K; q += blockDim.x) {
-    const int v = q / K, k = q % K;
-    float s = 0.0f;
-    for (int j = 0; j < J; ++j) s = fmaf(l[j], dc[((size_t)v * K + k) * J + j], s);
-    dg[q] = s;
+    float x = 0.0f;
+    for (int s = 0; s < RL_OSPLIT; ++s) x += part[(size_t)s * V * K + q];
+    dg[q] = x;
   }
-  // dl: one warp per j, lanes over (v, k)
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = warp; j < J; j += nw) {
-    float s = 0.0f;
-    for (int q = lane; q < V * K; q += 32) s = fmaf(g[q], dc[(size_t)q * J + j], s);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) dl[j] = s;
+  for (int j = threadIdx.x; j < J; j += blockDim.x) {
+    float x = 0.0f;
+    for (int k = 0; k < K; ++k) x += colsum[k * J + j];
+    dl[j] = x;
   }
+}
+
+// Y[k] = (S (I_K x l))[k] (K x n_rows) and its inverse Haar Z[k] (K x N).
+static tsr_status relight_basis_images(const tsr_compressed *c, const float *l, float *Y, float *Z, cudaStream_t s) {
+  TSR_CUDA(cudaMemsetAsync(Y, 0, sizeof(float) * (size_t)c->K * c->n_rows, s));
+  relight_y_kernel<<<(c->n_rows + 7) / 8, 256, 0, s>>>(c->row_ptr, c->col, c->val, c->n_rows, c->J, l, Y);
+  ::tsr::count_launch();
+  TSR_CUDA(cudaGetLastError());
+  return haar_inverse(Y, c->K, c->nu, Z, s);
+}
+
+size_t relight_scratch_floats(const tsr_compressed *c) {
+  const size_t N = 10 * (size_t)c->nu * c->nu + 2;
+  return (size_t)c->K * ((size_t)c->n_rows + N);
+}
+
+tsr_status relight_with_scratch(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,
+                                float *scratch, cudaStream_t s) {
+  const int V = n_edit * 3;
+  if (V == 0) return TSR_OK;
+  const int N = 10 * c->nu * c->nu + 2;
+  float *Y = scratch, *Z = scratch + (size_t)c->K * c->n_rows;
+  tsr_status st = relight_basis_images(c, l, Y, Z, s);
+  if (st != TSR_OK) return st;
+  const dim3 grid((N + 255) / 256, (V + RL_VB - 1) / RL_VB);
+  relight_combine_kernel<<<grid, 256, 0, s>>>(Z, N, c->K, V, g, B); ::tsr::count_launch();
+  TSR_CUDA(cudaGetLastError());
+  return TSR_OK;
 }
 
 tsr_status relight(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B, cudaStream_t s) {
-  const int V = n_edit * 3;
-  const int KJ = c->K * c->J;
-  Scratch bw_s;
-  tsr_status st = bw_s.alloc(sizeof(float) * (size_t)V * c->n_rows, s);
+  Scratch sc;
+  tsr_status st = sc.alloc(sizeof(float) * relight_scratch_floats(c), s);
   if (st != TSR_OK) return st;
-  float *bw = static_cast<float *>(bw_s.p);
-  const dim3 grid((c->n_rows + 255) / 256, (V + RL_VG - 1) / RL_VG);
-  const size_t smem = sizeof(float) * KJ * RL_VG;
-  relight_spmm_kernel<<<grid, 256, smem, s>>>(c->row_ptr, c->col, c->val, c->n_rows, c->K, c->J, V, g, l, bw); ::tsr::count_launch();
-  TSR_CUDA(cudaGetLastError());
-  return haar_inverse(bw, V, c->nu, B, s);
-}
-
-// Same two launches as relight(), with the b^w buffer supplied by the caller
-// (used by the allocation-free entry point).
-tsr_status relight_with_scratch(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,
-                                float *bw, cudaStream_t s) {
-  const int V = n_edit * 3;
-  const int KJ = c->K * c->J;
-  const dim3 grid((c->n_rows + 255) / 256, (V + RL_VG - 1) / RL_VG);
-  const size_t smem = sizeof(float) * KJ * RL_VG;
-  relight_spmm_kernel<<<grid, 256, smem, s>>>(c->row_ptr, c->col, c->val, c->n_rows, c->K, c->J, V, g, l, bw); ::tsr::count_launch();
-  TSR_CUDA(cudaGetLastError());
-  return haar_inverse(bw, V, c->nu, B, s);
+  return relight_with_scratch(c, n_edit, g, l, B, static_cast<float *>(sc.p), s);
 }
 
 tsr_status relight_backward(const tsr_compressed *c, int n_edit, const float *g, const float *l, const float *dLdB,
                             float *dg, float *dl, cudaStream_t s) {
   const int V = n_edit * 3;
-  const int KJ = c->K * c->J;
-  Scratch rw_s, dc_s;
-  tsr_status st = rw_s.alloc(sizeof(float) * (size_t)V * c->n_rows, s);
-  if (st == TSR_OK) st = dc_s.alloc(sizeof(float) * (size_t)V * KJ, s);
+  const int K = c->K, J = c->J, KJ = K * J;
+  const int N = 10 * c->nu * c->nu + 2;
+  const size_t nY = (size_t)K * c->n_rows, nZ = (size_t)K * N;
+  Scratch sc;
+  tsr_status st = sc.alloc(sizeof(float) * (2 * nY + (2 + RL_QS) * nZ + (size_t)RL_OSPLIT * V * K + KJ), s);
   if (st != TSR_OK) return st;
-  float *rw = static_cast<float *>(rw_s.p);
-  float *dc = static_cast<float *>(dc_s.p);
-  st = haar_forward(dLdB, V, c->nu, rw, s);
+  float *Y = static_cast<float *>(sc.p), *Z = Y + nY, *Q = Z + nZ, *R = Q + nZ, *part = R + nY;
+  float *colsum = part + (size_t)RL_OSPLIT * V * K, *Qp = colsum + KJ;
+  st = relight_basis_images(c, l, Y, Z, s);
   if (st != TSR_OK) return st;
-  const dim3 grid(KJ, (V + RL_VG - 1) / RL_VG);
-  relight_colgather_kernel<<<grid, 256, 0, s>>>(c->cidx, c->cval, c->n_keep + 2, c->n_rows, KJ, V, rw, dc); ::tsr::count_launch();
-  relight_grad_finish_kernel<<<1, 1024, 0, s>>>(dc, c->K, c->J, V, g, l, dg, dl); ::tsr::count_launch();
+  relight_dg_kernel<<<dim3((V + RL_GV - 1) / RL_GV, RL_OSPLIT), 256, 0, s>>>(dLdB, Z, N, K, V, part);
+  ::tsr::count_launch();
+  relight_q_kernel<<<dim3((N + 255) / 256, RL_QS), 256, 0, s>>>(dLdB, N, K, V, g, Qp); ::tsr::count_launch();
+  relight_qsum_kernel<<<4 * num_sms(), 256, 0, s>>>(Qp, nZ, Q); ::tsr::count_launch();
+  TSR_CUDA(cudaGetLastError());
+  st = haar_forward(Q, K, c->nu, R, s);
+  if (st != TSR_OK) return st;
+  relight_colsum_kernel<<<KJ, 256, 0, s>>>(c->cidx, c->cval, c->n_keep + 2, c->n_rows, J, R, colsum);
+  ::tsr::count_launch();
+  relight_grad_finish_kernel<<<1, 1024, 0, s>>>(part, V, K, J, colsum, dg, dl); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }

@@ -5,18 +5,20 @@
 // and forbids allocations after start-up (for example a render loop that owns a
 // fixed memory budget, or a plugin inside such a host), and code that must not
 // pay for, or may not issue, an allocation call in the middle of a frame.
-// tsr_relight takes its intermediate buffer (the wavelet-domain result b^w,
-// n_edit * 3 * (10 P^2 + 2) floats) from cudaMallocAsync; this variant takes it
-// from a fixed array in device memory that the library reserves when it is
-// loaded, so the call itself allocates nothing.
+// tsr_relight takes its intermediate buffers (the light-contracted transfer Y and
+// its inverse Haar Z, K (10 P^2 + 2 + N) floats, whatever the number of edits)
+// from cudaMallocAsync; this variant takes them from a fixed array in device
+// memory that the library reserves when it is loaded, so the call itself
+// allocates nothing.
 #include <mutex>
 
 #include "handles.cuh"
 
 namespace {
 
-// Scratch for b^w: 8 Mi floats = 32 MiB.  Every GPU that loads the library holds
-// this array until the process exits.
+// Scratch for Y and Z: 8 Mi floats = 32 MiB (the largest case, K = 16 on a
+// 163,842-vertex mesh, needs 5.2 Mi).  Every GPU that loads the library holds this
+// array until the process exits.
 constexpr size_t kNoallocScratchFloats = size_t(8) << 20;
 static __device__ __align__(256) float g_relight_scratch[kNoallocScratchFloats];
 
@@ -52,17 +54,16 @@ extern "C" tsr_status tsr_relight_noalloc(const tsr_compressed *c, int n_edit, c
   TSR_CHECK_ARG(c && g && l && B, "tsr_relight_noalloc: NULL argument");
   TSR_CHECK_ARG(n_edit >= 0 && n_edit <= (1 << 20), "tsr_relight_noalloc: n_edit=%d out of range", n_edit);
   TSR_CHECK_ARG(tsr::aligned(g, 4) && tsr::aligned(l, 4) && tsr::aligned(B, 4), "tsr_relight_noalloc: misaligned pointer");
-  const size_t need = (size_t)n_edit * 3 * (size_t)c->n_rows;
+  const size_t need = tsr::relight_scratch_floats(c);
   TSR_CHECK_ARG(need <= kNoallocScratchFloats,
-                "tsr_relight_noalloc: n_edit*3*(10 P^2 + 2) = %zu floats exceeds the fixed scratch of %zu floats "
-                "(use fewer edits per call, or tsr_relight)",
-                need, kNoallocScratchFloats);
+                "tsr_relight_noalloc: K*(10 P^2 + 2 + N) = %zu floats exceeds the fixed scratch of %zu floats", need,
+                kNoallocScratchFloats);
   tsr_status st = tsr::require_device();
   if (st != TSR_OK || n_edit == 0) return st;
-  float *bw = nullptr;
-  st = scratch_for_current_device(&bw);
+  float *scratch = nullptr;
+  st = scratch_for_current_device(&scratch);
   if (st != TSR_OK) return st;
-  // Every b^w entry is written by the sparse product before the inverse Haar reads it,
-  // so the array needs no clearing between calls.
-  return tsr::relight_with_scratch(c, n_edit, g, l, B, bw, reinterpret_cast<cudaStream_t>(stream));
+  // Every Y and Z entry is written before it is read, so the array needs no
+  // clearing between calls.
+  return tsr::relight_with_scratch(c, n_edit, g, l, B, scratch, reinterpret_cast<cudaStream_t>(stream));
 }

@@ -69,15 +69,34 @@ def test_noalloc_matches_relight_on_two_calls(env, nu, K, J, E, p):
         assert _rel(B, want) <= 2e-6, (call, _rel(B, want))
 
 
-def test_noalloc_rejects_sizes_beyond_the_fixed_scratch(env):
+def test_noalloc_scratch_does_not_grow_with_edits(env):
+    """The scratch holds K (10 P^2 + 2 + N) floats whatever the number of edits: 1,200 edits of a
+    2,562-vertex transfer (whose per-edit wavelet images alone would take 9.2 Mi floats) run in it."""
     torch, tsr = env
-    comp = _case(torch, tsr, 16, 4, 4, 0.1, seed=3)         # 2,562 wavelet rows
+    comp = _case(torch, tsr, 16, 12, 16, 0.1, seed=3)
+    rng = np.random.default_rng(11)
+    E = 1200
+    g = torch.tensor(rng.standard_normal((E, 3, 12)).astype(np.float32), device="cuda")
+    light = torch.tensor(rng.standard_normal(16).astype(np.float32), device="cuda")
+    want = tsr.relight(comp, g, light)
+    B = torch.full((E, 3, comp.n), float("nan"), device="cuda")
+    assert _noalloc(tsr, comp, g, light, B) == 0, tsr.lib().tsr_last_error()
+    torch.cuda.synchronize()
+    tsr.stream_status()
+    assert _rel(B, want) <= 2e-6
+
+
+def test_noalloc_rejects_invalid_arguments(env):
+    torch, tsr = env
+    comp = _case(torch, tsr, 16, 4, 4, 0.1, seed=3)
     g = torch.zeros((1, 3, 4), device="cuda")
     light = torch.zeros(4, device="cuda")
     B = torch.zeros((1, 3, comp.n), device="cuda")
-    too_many = (8 * 1024 * 1024) // (3 * comp.n_rows) + 1  # one edit past 8 Mi floats
-    st = tsr.lib().tsr_relight_noalloc(comp.handle, too_many, ctypes.c_void_p(g.data_ptr()),
+    st = tsr.lib().tsr_relight_noalloc(comp.handle, (1 << 20) + 1, ctypes.c_void_p(g.data_ptr()),
                                        ctypes.c_void_p(light.data_ptr()), ctypes.c_void_p(B.data_ptr()),
                                        ctypes.c_void_p(torch_stream(g)))
     assert st == -1
-    assert b"exceeds the fixed scratch" in tsr.lib().tsr_last_error()
+    assert b"out of range" in tsr.lib().tsr_last_error()
+    st = tsr.lib().tsr_relight_noalloc(comp.handle, 1, None, ctypes.c_void_p(light.data_ptr()),
+                                       ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(torch_stream(g)))
+    assert st == -1
