@@ -240,10 +240,12 @@ void tsr_compressed_destroy(tsr_compressed *c);
  *   B[e][c][.]   = W^-1 b^w[e][c][.]         (inverse Haar per chart)
  *   g : device [n_edit][3][K] FP32;  l: device [J] FP32 (one light for all edits);
  *   B : device [n_edit][3][N] FP32 out.
- * Evaluated with the light contracted first (the same B by linearity):
+ * For n_edit > 2 it is evaluated with the light contracted first (the same B
+ * by linearity):
  *   Y[k][w] = sum_j S[w][kj] l[j],  Z[k] = W^-1 Y[k],  B[e][c] = sum_k g[e][c][k] Z[k],
- * so the kept coefficients are read once per call, whatever n_edit.
- * Scratch: Y and Z, K*(10 P^2 + 2 + N) FP32.
+ * so the kept coefficients are read once per call, whatever n_edit; for one or
+ * two edits as written (one pass over S for their 3 or 6 vectors).
+ * Scratch: max(K*(10 P^2 + 2 + N), 6*(10 P^2 + 2)) FP32.
  *
  * tsr_relight_backward: reverse mode for an upstream gradient dLdB
  * [n_edit][3][N] (r^w = W dLdB, dc = S^T r^w, dg = sum_j l_j dc, dl = sum g dc),
@@ -266,7 +268,7 @@ tsr_status tsr_relight_backward(const tsr_compressed *c, int n_edit, const float
  * comes from a fixed 32 MiB array of device memory that the library reserves on
  * every GPU where it is loaded (held until the process exits), so the call
  * itself allocates nothing.
- *   - Limit: K * (10 P^2 + 2 + N) <= 8,388,608 floats, else TSR_ERR_INVALID_ARG
+ *   - Limit: the scratch above <= 8,388,608 floats, else TSR_ERR_INVALID_ARG
  *     (the largest case the library accepts, K = 16 on nu = 128, needs 5.2 Mi;
  *     the number of edits does not enter).
  *   - The first call on each device looks up the array's device address

@@ -228,16 +228,21 @@ template <bool GRAD>
 __global__ void __launch_bounds__(256) project_kernel(const double *__restrict__ f, int K, int n_r, double dr,
                                                       const double *__restrict__ sa, const double *__restrict__ ss,
                                                       const double *__restrict__ eta, double *__restrict__ g,
-                                                      float *__restrict__ g32, double *__restrict__ dg) {
+                                                      float *__restrict__ g32, double *__restrict__ dg,
+                                                      double *__restrict__ part) {
+  // block (edit e, channel c) x (sample range blockIdx.y of gridDim.y): with one range
+  // the block writes g (and dg); with several it writes part[range][e c][NV] for
+  // project_finish_kernel to add in range order.
   constexpr int NV = GRAD ? 64 : 16;
   __shared__ double red[NV * 32];
   const int e = blockIdx.x / 3;
   const int ch = blockIdx.x % 3;
+  const int m0 = (int)((long long)n_r * blockIdx.y / gridDim.y), m1 = (int)((long long)n_r * (blockIdx.y + 1) / gridDim.y);
   const DipoleMaterial mat = dipole_material(sa[e * 3 + ch], ss[e * 3 + ch], eta[e]);
   double acc[NV];
 #pragma unroll
   for (int q = 0; q < NV; ++q) acc[q] = 0.0;
-  for (int m = threadIdx.x; m < n_r; m += blockDim.x) {
+  for (int m = m0 + threadIdx.x; m < m1; m += blockDim.x) {
     const double r = dr * m;
     double R, dRa = 0.0, dRs = 0.0, dRe = 0.0;
     if (GRAD)
@@ -258,18 +263,42 @@ __global__ void __launch_bounds__(256) project_kernel(const double *__restrict__
     }
   }
   block_sum<NV>(acc, red);
-  if (threadIdx.x == 0) {
-    const size_t base = (size_t)(e * 3 + ch) * K;
-    for (int k = 0; k < K; ++k) {
-      g[base + k] = acc[k];
-      if (g32) g32[base + k] = (float)acc[k];
-      if (GRAD) {
-        dg[(base + k) * 3 + 0] = acc[16 + 3 * k + 0];
-        dg[(base + k) * 3 + 1] = acc[16 + 3 * k + 1];
-        dg[(base + k) * 3 + 2] = acc[16 + 3 * k + 2];
-      }
+  if (threadIdx.x != 0) return;
+  if (gridDim.y > 1) {
+    double *pp = part + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * NV;
+    for (int q = 0; q < NV; ++q) pp[q] = acc[q];
+    return;
+  }
+  const size_t base = (size_t)(e * 3 + ch) * K;
+  for (int k = 0; k < K; ++k) {
+    g[base + k] = acc[k];
+    if (g32) g32[base + k] = (float)acc[k];
+    if (GRAD) {
+      dg[(base + k) * 3 + 0] = acc[16 + 3 * k + 0];
+      dg[(base + k) * 3 + 1] = acc[16 + 3 * k + 1];
+      dg[(base + k) * 3 + 2] = acc[16 + 3 * k + 2];
     }
   }
+}
+
+template <bool GRAD>
+__global__ void project_finish_kernel(const double *__restrict__ part, int n3, int n_split, int K,
+                                      double *__restrict__ g, float *__restrict__ g32, double *__restrict__ dg) {
+  constexpr int NV = GRAD ? 64 : 16;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;   // (e c, k)
+  if (idx >= n3 * K) return;
+  const int ec = idx / K, k = idx % K;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int sp = 0; sp < n_split; ++sp) {
+    const double *pp = part + ((size_t)sp * n3 + ec) * NV;
+    v[0] += pp[k];
+    if (GRAD)
+      for (int a = 0; a < 3; ++a) v[1 + a] += pp[16 + 3 * k + a];
+  }
+  g[idx] = v[0];
+  if (g32) g32[idx] = (float)v[0];
+  if (GRAD)
+    for (int a = 0; a < 3; ++a) dg[(size_t)idx * 3 + a] = v[1 + a];
 }
 
 // One block per (edit, channel): dL/dtheta = sum_k dL/dg_k dg_k/dtheta.  The
@@ -472,13 +501,32 @@ extern "C" tsr_status tsr_project_material(const tsr_basis *basis, int n, const 
   if (n == 0) return TSR_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const double dr = basis->r_max / (basis->n_r - 1);
+  // few edits: cut the samples of each (edit, channel) into ranges so that the grid fills the GPU
+  const int n3 = n * 3;
+  const int n_split = std::max(1, std::min(8, (2 * num_sms() + n3 - 1) / n3));
+  Scratch ps;
+  double *part = nullptr;
+  if (n_split > 1) {
+    st = ps.alloc(sizeof(double) * (size_t)n_split * n3 * (dg ? 64 : 16), s);
+    if (st != TSR_OK) return st;
+    part = static_cast<double *>(ps.p);
+  }
+  const dim3 grid(n3, n_split);
   if (dg)
-    project_kernel<true><<<n * 3, 256, 0, s>>>(basis->f64, basis->K, basis->n_r, dr, sigma_a, sigma_s, eta, g,
-                                               g32, dg);
+    project_kernel<true><<<grid, 256, 0, s>>>(basis->f64, basis->K, basis->n_r, dr, sigma_a, sigma_s, eta, g, g32,
+                                              dg, part);
   else
-    project_kernel<false><<<n * 3, 256, 0, s>>>(basis->f64, basis->K, basis->n_r, dr, sigma_a, sigma_s, eta,
-                                                g, g32, nullptr);
+    project_kernel<false><<<grid, 256, 0, s>>>(basis->f64, basis->K, basis->n_r, dr, sigma_a, sigma_s, eta, g,
+                                               g32, nullptr, part);
   ::tsr::count_launch();
+  if (n_split > 1) {
+    const int nt = n3 * basis->K;
+    if (dg)
+      project_finish_kernel<true><<<(nt + 255) / 256, 256, 0, s>>>(part, n3, n_split, basis->K, g, g32, dg);
+    else
+      project_finish_kernel<false><<<(nt + 255) / 256, 256, 0, s>>>(part, n3, n_split, basis->K, g, g32, nullptr);
+    ::tsr::count_launch();
+  }
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }

@@ -9,7 +9,9 @@
 //   Z[k]    = w_1^{-1} Y[k]                K inverse Haar transforms
 //   B_v     = sum_k g_v[k] Z[k]            a K-term combination per output value
 // The compressed transfer is read once per call whatever the number of edits,
-// and the per-edit work is K multiply-adds per vertex.
+// and the per-edit work is K multiply-adds per vertex.  Calls with at most
+// RL_DV vectors (one or two edits) take Steps 4-5 as written instead, which
+// moves less data for so few outputs.
 //
 // Reverse, for an upstream gradient dL/dB (w_1 is orthonormal, so the adjoint of
 // w_1^{-1} is w_1):
@@ -54,6 +56,59 @@ __global__ void __launch_bounds__(256) relight_y_kernel(const int64_t *__restric
     const int k_next = __shfl_down_sync(0xffffffffu, k, 1);
     if (in && (lane == 31 || k_next != k)) Y[(size_t)k * n_rows + w] += x;
   }
+}
+
+// Few vectors (V = 3 n_edit <= RL_DV: one or two RGB edits): Steps 4-5 as written, since the
+// factorised form would move K (10 P^2 + 2 + N) intermediates for 3 outputs.
+// b^w[v][w] = sum over row w's entries of val * g[v][k] l[j]: RL_LPR lanes per row
+// (rows average n_keep K J / (10 P^2) entries, ~20 at 5 % of K J = 400), four rows
+// per warp, a full complement of blocks looping over rows (many rows in flight per
+// SM; the c table in shared memory is built once per block); the V partial sums
+// are reduced over the row's lanes.
+constexpr int RL_DV = 6;
+constexpr int RL_LPR = 8;
+template <int VV>
+__global__ void __launch_bounds__(256) relight_direct_kernel(const int64_t *__restrict__ row_ptr,
+                                                            const uint16_t *__restrict__ col,
+                                                            const float *__restrict__ val, int n_rows, int K, int J,
+                                                            const float *__restrict__ g, const float *__restrict__ l,
+                                                            float *__restrict__ bw) {
+  extern __shared__ float cs[];   // [K J][VV]
+  const int KJ = K * J;
+  for (int q = threadIdx.x; q < KJ * VV; q += blockDim.x) {
+    const int kj = q / VV, v = q % VV;
+    cs[q] = g[(size_t)v * K + kj / J] * l[kj % J];
+  }
+  __syncthreads();
+  const int sub = threadIdx.x % RL_LPR;
+  const int groups = gridDim.x * (blockDim.x / RL_LPR);
+  for (int w = blockIdx.x * (blockDim.x / RL_LPR) + threadIdx.x / RL_LPR; w < n_rows; w += groups) {
+    float acc[VV];
+#pragma unroll
+    for (int v = 0; v < VV; ++v) acc[v] = 0.0f;
+    const int64_t pe = row_ptr[w + 1];
+    for (int64_t p = row_ptr[w] + sub; p < pe; p += RL_LPR) {
+      const float a = val[p];
+      const float *c = cs + (int)col[p] * VV;
+#pragma unroll
+      for (int v = 0; v < VV; ++v) acc[v] = fmaf(a, c[v], acc[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < VV; ++v)
+#pragma unroll
+      for (int o = RL_LPR / 2; o > 0; o >>= 1) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+    if (sub == 0)
+#pragma unroll
+      for (int v = 0; v < VV; ++v) bw[(size_t)v * n_rows + w] = acc[v];
+  }
+}
+
+template <int VV>
+static void launch_direct(const tsr_compressed *c, const float *g, const float *l, float *bw, cudaStream_t s) {
+  const size_t smem = sizeof(float) * (size_t)c->K * c->J * VV;
+  const int blocks = std::min((c->n_rows + 255 / RL_LPR) / (256 / RL_LPR), 8 * num_sms());
+  relight_direct_kernel<VV><<<blocks, 256, smem, s>>>(c->row_ptr, c->col, c->val, c->n_rows, c->K, c->J, g, l, bw);
+  ::tsr::count_launch();
 }
 
 // B[v][o] = sum_k g[v][k] Z[k][o]: a thread per output vertex o and a chunk of RL_VB vectors.
@@ -229,7 +284,7 @@ static tsr_status relight_basis_images(const tsr_compressed *c, const float *l, 
 
 size_t relight_scratch_floats(const tsr_compressed *c) {
   const size_t N = 10 * (size_t)c->nu * c->nu + 2;
-  return (size_t)c->K * ((size_t)c->n_rows + N);
+  return std::max((size_t)c->K * ((size_t)c->n_rows + N), (size_t)RL_DV * c->n_rows);
 }
 
 tsr_status relight_with_scratch(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,
@@ -237,6 +292,14 @@ tsr_status relight_with_scratch(const tsr_compressed *c, int n_edit, const float
   const int V = n_edit * 3;
   if (V == 0) return TSR_OK;
   const int N = 10 * c->nu * c->nu + 2;
+  if (V <= RL_DV) {
+    if (V == 3)
+      launch_direct<3>(c, g, l, scratch, s);
+    else
+      launch_direct<6>(c, g, l, scratch, s);   // V = 3 n_edit <= RL_DV: 3 or 6
+    TSR_CUDA(cudaGetLastError());
+    return haar_inverse(scratch, V, c->nu, B, s);
+  }
   float *Y = scratch, *Z = scratch + (size_t)c->K * c->n_rows;
   tsr_status st = relight_basis_images(c, l, Y, Z, s);
   if (st != TSR_OK) return st;

@@ -6,7 +6,8 @@
 // fixed memory budget, or a plugin inside such a host), and code that must not
 // pay for, or may not issue, an allocation call in the middle of a frame.
 // tsr_relight takes its intermediate buffers (the light-contracted transfer Y and
-// its inverse Haar Z, K (10 P^2 + 2 + N) floats, whatever the number of edits)
+// its inverse Haar Z, K (10 P^2 + 2 + N) floats, whatever the number of edits;
+// for one or two edits the wavelet images b^w, at most 6 (10 P^2 + 2) floats)
 // from cudaMallocAsync; this variant takes them from a fixed array in device
 // memory that the library reserves when it is loaded, so the call itself
 // allocates nothing.
@@ -56,14 +57,14 @@ extern "C" tsr_status tsr_relight_noalloc(const tsr_compressed *c, int n_edit, c
   TSR_CHECK_ARG(tsr::aligned(g, 4) && tsr::aligned(l, 4) && tsr::aligned(B, 4), "tsr_relight_noalloc: misaligned pointer");
   const size_t need = tsr::relight_scratch_floats(c);
   TSR_CHECK_ARG(need <= kNoallocScratchFloats,
-                "tsr_relight_noalloc: K*(10 P^2 + 2 + N) = %zu floats exceeds the fixed scratch of %zu floats", need,
+                "tsr_relight_noalloc: the relight needs %zu floats of scratch, beyond the fixed %zu floats", need,
                 kNoallocScratchFloats);
   tsr_status st = tsr::require_device();
   if (st != TSR_OK || n_edit == 0) return st;
   float *scratch = nullptr;
   st = scratch_for_current_device(&scratch);
   if (st != TSR_OK) return st;
-  // Every Y and Z entry is written before it is read, so the array needs no
-  // clearing between calls.
+  // Every intermediate the relight reads from the array is written earlier in the
+  // same call, so the array needs no clearing between calls.
   return tsr::relight_with_scratch(c, n_edit, g, l, B, scratch, reinterpret_cast<cudaStream_t>(stream));
 }

@@ -14,39 +14,53 @@
 
 namespace tsr {
 
-__device__ __forceinline__ int morton2(int r, int c, int bits) {
-  int m = 0;
-  for (int b = 0; b < bits; ++b) {
-    m |= ((c >> b) & 1) << (2 * b);
-    m |= ((r >> b) & 1) << (2 * b + 1);
-  }
-  return m;
+// Morton position m of (r, c) in a P x P chart: c's bits at even positions of m,
+// r's at odd ones; compact_bits recovers c from m and r from m >> 1.
+__device__ __forceinline__ unsigned compact_bits(unsigned x) {
+  x &= 0x55555555u;
+  x = (x | (x >> 1)) & 0x33333333u;
+  x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+  x = (x | (x >> 4)) & 0x00FF00FFu;
+  x = (x | (x >> 8)) & 0x0000FFFFu;
+  return x;
 }
 
+// Charts of more than HAAR_SEG Morton positions are transformed in two kernels:
+// the first log2(HAAR_SEG) levels act on independent runs of HAAR_SEG positions
+// (one block per run), the remaining levels on the runs' approximations (one
+// block per chart).  Smaller charts take one block per chart.
+constexpr int HAAR_SEG = 1024;
+constexpr int HAAR_SEG_THREADS = 256;
+
 // ---------------------------------------------------------------- Haar forward
-// One block per (row, chart).  Approximations ping-pong in shared memory; the
-// details of each level are final and are written straight to global memory.
-__global__ void __launch_bounds__(1024) haar_forward_kernel(const float *__restrict__ X, int nu, int P, int bits,
-                                                           int N, int NW, float *__restrict__ Xw) {
+// Levels on positions [seg S, (seg+1) S) of chart d of `row` (S = seg_len): the
+// approximations ping-pong in shared memory, the details of each level are final
+// and go straight to their global positions; the run's approximation goes to
+// A[row][d][seg] (or, for a whole chart, to Xw position 0 with the poles).
+__global__ void __launch_bounds__(1024) haar_forward_kernel(const float *__restrict__ X, int nu, int P, int N, int NW,
+                                                           int seg_len, float *__restrict__ Xw,
+                                                           float *__restrict__ A) {
   extern __shared__ float sh[];
-  const int P2 = P * P;
-  float *b0 = sh, *b1 = sh + P2;
-  const int row = blockIdx.x / 10, d = blockIdx.x % 10;
+  float *b0 = sh, *b1 = sh + seg_len;
+  const int P2 = P * P, nseg = P2 / seg_len;
+  const int seg = blockIdx.x % nseg, d = (blockIdx.x / nseg) % 10, row = blockIdx.x / (nseg * 10);
   const float *x = X + (size_t)row * N + (size_t)d * nu * nu;
   float *out = Xw + (size_t)row * NW + (size_t)d * P2;
-  if (nu != P)
-    for (int q = threadIdx.x; q < P2; q += blockDim.x) b0[q] = 0.0f;
-  __syncthreads();
-  for (int q = threadIdx.x; q < nu * nu; q += blockDim.x) b0[morton2(q / nu, q % nu, bits)] = x[q];
+  for (int q = threadIdx.x; q < seg_len; q += blockDim.x) {
+    const unsigned m = (unsigned)(seg * seg_len + q);
+    const int r = (int)compact_bits(m >> 1), c = (int)compact_bits(m);
+    b0[q] = (r < nu && c < nu) ? x[r * nu + c] : 0.0f;
+  }
   __syncthreads();
   const float rs2 = 0.70710678118654752440f;
   float *src = b0, *dst = b1;
-  for (int n = P2; n > 1; n >>= 1) {
+  int ng = P2;   // current length of the whole chart's approximation
+  for (int n = seg_len; n > 1; n >>= 1, ng >>= 1) {
     const int h = n >> 1;
     for (int t = threadIdx.x; t < h; t += blockDim.x) {
       const float a = src[2 * t], b = src[2 * t + 1];
       dst[t] = (a + b) * rs2;
-      out[h + t] = (a - b) * rs2;
+      out[(ng >> 1) + seg * h + t] = (a - b) * rs2;
     }
     __syncthreads();
     float *tmp = src;
@@ -54,7 +68,41 @@ __global__ void __launch_bounds__(1024) haar_forward_kernel(const float *__restr
     dst = tmp;
   }
   if (threadIdx.x == 0) {
-    out[0] = src[0];
+    if (nseg == 1) {
+      out[0] = src[0];
+      if (d == 0) {
+        Xw[(size_t)row * NW + 10 * (size_t)P2] = X[(size_t)row * N + 10 * (size_t)nu * nu];
+        Xw[(size_t)row * NW + 10 * (size_t)P2 + 1] = X[(size_t)row * N + 10 * (size_t)nu * nu + 1];
+      }
+    } else {
+      A[((size_t)row * 10 + d) * nseg + seg] = src[0];
+    }
+  }
+}
+
+// The levels above the runs: block per (row, chart) over its nseg approximations.
+__global__ void haar_forward_top_kernel(const float *__restrict__ X, const float *__restrict__ A, int nu, int P,
+                                        int N, int NW, int nseg, float *__restrict__ Xw) {
+  __shared__ float b[2][HAAR_SEG];
+  const int d = blockIdx.x % 10, row = blockIdx.x / 10;
+  const int P2 = P * P;
+  float *out = Xw + (size_t)row * NW + (size_t)d * P2;
+  for (int q = threadIdx.x; q < nseg; q += blockDim.x) b[0][q] = A[((size_t)row * 10 + d) * nseg + q];
+  __syncthreads();
+  const float rs2 = 0.70710678118654752440f;
+  int cur = 0;
+  for (int n = nseg; n > 1; n >>= 1) {
+    const int h = n >> 1;
+    for (int t = threadIdx.x; t < h; t += blockDim.x) {
+      const float a = b[cur][2 * t], bb = b[cur][2 * t + 1];
+      b[cur ^ 1][t] = (a + bb) * rs2;
+      out[h + t] = (a - bb) * rs2;
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  if (threadIdx.x == 0) {
+    out[0] = b[cur][0];
     if (d == 0) {
       Xw[(size_t)row * NW + 10 * (size_t)P2] = X[(size_t)row * N + 10 * (size_t)nu * nu];
       Xw[(size_t)row * NW + 10 * (size_t)P2 + 1] = X[(size_t)row * N + 10 * (size_t)nu * nu + 1];
@@ -63,21 +111,47 @@ __global__ void __launch_bounds__(1024) haar_forward_kernel(const float *__restr
 }
 
 // ---------------------------------------------------------------- Haar inverse
-__global__ void __launch_bounds__(1024) haar_inverse_kernel(const float *__restrict__ Xw, int nu, int P, int bits,
-                                                           int N, int NW, float *__restrict__ X) {
+// The levels above the runs: the nseg approximations of each (row, chart) into A.
+__global__ void haar_inverse_top_kernel(const float *__restrict__ Xw, int P, int NW, int nseg,
+                                        float *__restrict__ A) {
+  __shared__ float b[2][HAAR_SEG];
+  const int d = blockIdx.x % 10, row = blockIdx.x / 10;
+  const float *cw = Xw + (size_t)row * NW + (size_t)d * P * P;
+  if (threadIdx.x == 0) b[0][0] = cw[0];
+  __syncthreads();
+  const float rs2 = 0.70710678118654752440f;
+  int cur = 0;
+  for (int n = 1; n < nseg; n <<= 1) {
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const float a = b[cur][t], dd = cw[n + t];
+      b[cur ^ 1][2 * t] = (a + dd) * rs2;
+      b[cur ^ 1][2 * t + 1] = (a - dd) * rs2;
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  for (int q = threadIdx.x; q < nseg; q += blockDim.x) A[((size_t)row * 10 + d) * nseg + q] = b[cur][q];
+}
+
+// Levels inside run seg of chart d (its approximation from A, or cw[0] for a whole
+// chart), then the values scattered from Morton positions to vertex ids.
+__global__ void __launch_bounds__(1024) haar_inverse_kernel(const float *__restrict__ Xw, const float *__restrict__ A,
+                                                           int nu, int P, int N, int NW, int seg_len,
+                                                           float *__restrict__ X) {
   extern __shared__ float sh[];
-  const int P2 = P * P;
-  float *b0 = sh, *b1 = sh + P2;
-  const int row = blockIdx.x / 10, d = blockIdx.x % 10;
+  float *b0 = sh, *b1 = sh + seg_len;
+  const int P2 = P * P, nseg = P2 / seg_len;
+  const int seg = blockIdx.x % nseg, d = (blockIdx.x / nseg) % 10, row = blockIdx.x / (nseg * 10);
   const float *cw = Xw + (size_t)row * NW + (size_t)d * P2;
   float *x = X + (size_t)row * N + (size_t)d * nu * nu;
-  if (threadIdx.x == 0) b0[0] = cw[0];
+  if (threadIdx.x == 0) b0[0] = (nseg == 1) ? cw[0] : A[((size_t)row * 10 + d) * nseg + seg];
   __syncthreads();
   const float rs2 = 0.70710678118654752440f;
   float *src = b0, *dst = b1;
-  for (int n = 1; n < P2; n <<= 1) {   // src holds n approximations, details at [n, 2n)
+  for (int n = 1; n < seg_len; n <<= 1) {   // src: n approximations of the run; details at [ng, 2 ng) globally
+    const int ng = nseg * n;
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
-      const float a = src[t], dd = cw[n + t];
+      const float a = src[t], dd = cw[ng + seg * n + t];
       dst[2 * t] = (a + dd) * rs2;
       dst[2 * t + 1] = (a - dd) * rs2;
     }
@@ -86,31 +160,61 @@ __global__ void __launch_bounds__(1024) haar_inverse_kernel(const float *__restr
     src = dst;
     dst = tmp;
   }
-  for (int q = threadIdx.x; q < nu * nu; q += blockDim.x) x[q] = src[morton2(q / nu, q % nu, bits)];
-  if (threadIdx.x == 0 && d == 0) {
+  for (int q = threadIdx.x; q < seg_len; q += blockDim.x) {
+    const unsigned m = (unsigned)(seg * seg_len + q);
+    const int r = (int)compact_bits(m >> 1), c = (int)compact_bits(m);
+    if (r < nu && c < nu) x[r * nu + c] = src[q];
+  }
+  if (threadIdx.x == 0 && d == 0 && seg == 0) {
     X[(size_t)row * N + 10 * (size_t)nu * nu] = Xw[(size_t)row * NW + 10 * (size_t)P2];
     X[(size_t)row * N + 10 * (size_t)nu * nu + 1] = Xw[(size_t)row * NW + 10 * (size_t)P2 + 1];
   }
 }
 
-static int haar_threads(int P2) { return std::min(1024, std::max(32, P2 / 2)); }
+static int haar_threads(int len) { return std::min(1024, std::max(32, len / 2)); }
 
 tsr_status haar_forward(const float *X, int rows, int nu, float *Xw, cudaStream_t s) {
-  const int P = chart_side(nu), bits = ilog2(P);
-  const int N = 10 * nu * nu + 2, NW = 10 * P * P + 2;
-  const size_t smem = sizeof(float) * (size_t)P * P * 2;
-  TSR_CUDA(cudaFuncSetAttribute(haar_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  haar_forward_kernel<<<rows * 10, haar_threads(P * P), smem, s>>>(X, nu, P, bits, N, NW, Xw); ::tsr::count_launch();
+  const int P = chart_side(nu), P2 = P * P;
+  const int N = 10 * nu * nu + 2, NW = 10 * P2 + 2;
+  if (P2 <= HAAR_SEG) {
+    const size_t smem = sizeof(float) * (size_t)P2 * 2;
+    haar_forward_kernel<<<rows * 10, haar_threads(P2), smem, s>>>(X, nu, P, N, NW, P2, Xw, nullptr);
+    ::tsr::count_launch();
+    TSR_CUDA(cudaGetLastError());
+    return TSR_OK;
+  }
+  const int nseg = P2 / HAAR_SEG;
+  Scratch as;
+  tsr_status st = as.alloc(sizeof(float) * (size_t)rows * 10 * nseg, s);
+  if (st != TSR_OK) return st;
+  float *A = static_cast<float *>(as.p);
+  const size_t smem = sizeof(float) * HAAR_SEG * 2;
+  haar_forward_kernel<<<rows * 10 * nseg, HAAR_SEG_THREADS, smem, s>>>(X, nu, P, N, NW, HAAR_SEG, Xw, A);
+  ::tsr::count_launch();
+  haar_forward_top_kernel<<<rows * 10, 256, 0, s>>>(X, A, nu, P, N, NW, nseg, Xw); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }
 
 tsr_status haar_inverse(const float *Xw, int rows, int nu, float *X, cudaStream_t s) {
-  const int P = chart_side(nu), bits = ilog2(P);
-  const int N = 10 * nu * nu + 2, NW = 10 * P * P + 2;
-  const size_t smem = sizeof(float) * (size_t)P * P * 2;
-  TSR_CUDA(cudaFuncSetAttribute(haar_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  haar_inverse_kernel<<<rows * 10, haar_threads(P * P), smem, s>>>(Xw, nu, P, bits, N, NW, X); ::tsr::count_launch();
+  const int P = chart_side(nu), P2 = P * P;
+  const int N = 10 * nu * nu + 2, NW = 10 * P2 + 2;
+  if (P2 <= HAAR_SEG) {
+    const size_t smem = sizeof(float) * (size_t)P2 * 2;
+    haar_inverse_kernel<<<rows * 10, haar_threads(P2), smem, s>>>(Xw, nullptr, nu, P, N, NW, P2, X);
+    ::tsr::count_launch();
+    TSR_CUDA(cudaGetLastError());
+    return TSR_OK;
+  }
+  const int nseg = P2 / HAAR_SEG;
+  Scratch as;
+  tsr_status st = as.alloc(sizeof(float) * (size_t)rows * 10 * nseg, s);
+  if (st != TSR_OK) return st;
+  float *A = static_cast<float *>(as.p);
+  haar_inverse_top_kernel<<<rows * 10, 256, 0, s>>>(Xw, P, NW, nseg, A); ::tsr::count_launch();
+  const size_t smem = sizeof(float) * HAAR_SEG * 2;
+  haar_inverse_kernel<<<rows * 10 * nseg, HAAR_SEG_THREADS, smem, s>>>(Xw, A, nu, P, N, NW, HAAR_SEG, X);
+  ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }

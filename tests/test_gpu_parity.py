@@ -211,7 +211,7 @@ def test_transfer_largest_sampled_rows(torch_cuda, tsr, oracle_basis16, precisio
 
 
 # ------------------------------------------------------------------ Eq. 9-10 Haar
-@pytest.mark.parametrize("nu", [1, 3, 4, 5, 16, 64])
+@pytest.mark.parametrize("nu", [1, 3, 4, 5, 16, 33, 64, 100, 128])
 def test_haar_forward_inverse(torch_cuda, tsr, nu):
     torch = torch_cuda
     rng = np.random.default_rng(nu)
