@@ -1,6 +1,8 @@
-"""A single transfer precompute on a seeded displaced icosphere, sized for a profiler capture.
+"""Single cases of the library's kernels on seeded displaced icospheres, sized for a profiler capture.
 
     python -m paper_2203_12339_gb300.profile_case --nu 48 --K 12 --J 16 --precision bf16
+    python -m paper_2203_12339_gb300.profile_case --case relight_frame --nu 128 --K 16 --J 25 --amp 0.15 \
+        --octaves 5 --seed 2 --keep 0.05 --copies 13
 
 The basis is fitted on the device from the seeded PCA materials (n_r = 1024, r_max = 40 mm,
 eta = 1.3, Section 3.2), the scene is the icosphere of the benchmark recipe with 10 nu^2 + 2
@@ -24,6 +26,9 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--precision", default="bf16", help="comma-separated list of bf16, bf16x3, fp32")
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--case", default="transfer", choices=["transfer", "relight_frame"])
+    ap.add_argument("--keep", type=float, default=0.05, help="relight_frame: kept fraction of the Haar coefficients")
+    ap.add_argument("--copies", type=int, default=13, help="relight_frame: compressed copies, one RGB edit each")
     a = ap.parse_args(argv)
     sa, ss = scene.pca_materials(256, seed=0)
     basis, _ = tsr.fit_pca_basis(torch.tensor(sa, device="cuda"), torch.tensor(ss, device="cuda"), 1.3, 1024, 40.0,
@@ -32,12 +37,25 @@ def main(argv=None):
     pos = torch.tensor(np.ascontiguousarray(sc.mesh.pos.astype(np.float32).T), device="cuda")
     area = torch.tensor(sc.mesh.area.astype(np.float32), device="cuda")
     T = torch.tensor(sc.T.astype(np.float32), device="cuda")
-    for prec in a.precision.split(","):
+    if a.case == "transfer":
+        for prec in a.precision.split(","):
+            for _ in range(a.repeat):
+                tsr.precompute_transfer(basis, pos, area, T, prec)
+    else:
+        # the relight frame: `copies` compressed transfers (distinct buffers), one RGB edit each
+        M = tsr.precompute_transfer(basis, pos, area, T, "bf16")
+        copies = [tsr.haar_compress(M, a.nu, a.keep) for _ in range(a.copies)]
+        del M
+        esa, ess, eeta = scene.edit_materials(a.copies, seed=8)
+        _, g32, _ = tsr.project_material(basis, torch.tensor(esa, device="cuda"), torch.tensor(ess, device="cuda"),
+                                         torch.tensor(eeta, device="cuda"))
+        light = torch.tensor(sc.light.astype(np.float32), device="cuda")
         for _ in range(a.repeat):
-            tsr.precompute_transfer(basis, pos, area, T, prec)
+            for i, c in enumerate(copies):
+                tsr.relight(c, g32[i:i + 1], light)
     torch.cuda.synchronize()
     tsr.stream_status()
-    print(f"ok: N={sc.n} K={a.K} J={a.J} precision={a.precision}")
+    print(f"ok: case={a.case} N={sc.n} K={a.K} J={a.J} precision={a.precision}")
 
 
 if __name__ == "__main__":
