@@ -194,6 +194,29 @@ def relight_frame_1080p(tsr, dev, peaks) -> dict:
                              "frac": round(achieved / peak, 4), "bytes_per_frame": int(frame_bytes)}}
 
 
+def energy_keep_curve(tsr, M, nu, g32, light) -> list:
+    """The energy keep rule on the benchmark transfer: per retained-energy fraction, the kept share
+    of the chart coefficients, the compression time (one host synchronisation inside) and the
+    relative error of the relit B against keeping every coefficient (Section 5's trade-off)."""
+    import torch
+    full = tsr.relight(tsr.haar_compress(M, nu, 1.0), g32, light)
+    K, J, _ = M.shape
+    P = 1 << (nu - 1).bit_length()
+    n_coef = 10 * P * P
+    out = []
+    for e in (0.90, 0.95, 0.98, 0.99, 0.999):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        comp = tsr.haar_compress_energy(M, nu, e)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t) * 1e3
+        B = tsr.relight(comp, g32, light)
+        err = float(((B - full).norm() / full.norm()).item())
+        out.append({"energy": e, "kept_fraction": round((comp.nnz - 2 * K * J) / (K * J * n_coef), 5),
+                    "compress_ms": round(ms, 3), "relight_rel_error": round(err, 6)})
+    return out
+
+
 def _smem_roofline(gather_bytes: float, ms: float, peaks: dict) -> dict:
     """Shared-memory gather roofline of the transfer kernel (algorithmic table bytes per launch / time)."""
     import torch
@@ -430,6 +453,8 @@ def run_gpu(args):
         "setup_ms": round(setup_ms, 1),
         "clocks": clk,
     }
+    _, g32_curve, _ = tsr.project_material(basis, d["sa"], d["ss"], d["eta"])
+    line["energy_keep_curve"] = energy_keep_curve(tsr, M, nu, g32_curve, d["light"])
     if not args.no_frame_1080p:
         line["relight_frame_1080p"] = relight_frame_1080p(tsr, dev, peaks)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -225,6 +225,16 @@ tsr_status tsr_wavelet_compress(const float *Mw, int K, int J, int nu, double p,
 tsr_status tsr_haar_compress(const float *M, int K, int J, int nu, double p, tsr_compressed **out,
                              tsr_stream stream);
 tsr_status tsr_haar_recompress(const float *M, tsr_compressed *c, tsr_stream stream);
+/* Step 2 with the paper's energy threshold (Section 3, precompute Step 2: "the
+ * reserved energy exceeds the threshold"; 95-98 % in its results): per (k, j)
+ * the smallest n >= 1 such that the n largest |c| of the chart coefficients
+ * (ties: lower index) hold at least `energy` of the row's energy sum c^2 (FP64);
+ * both poles always kept and not counted.  energy in (0, 1].  The number kept
+ * varies per (k, j); the call reads those counts back (one synchronisation of
+ * `stream`) to size the handle.  tsr_haar_recompress does not apply to such a
+ * handle (TSR_ERR_UNSUPPORTED). */
+tsr_status tsr_haar_compress_energy(const float *M, int K, int J, int nu, double energy, tsr_compressed **out,
+                                    tsr_stream stream);
 /* Sizes of a compressed transfer (host out-pointers, any may be NULL). */
 tsr_status tsr_compressed_info(const tsr_compressed *c, int *K, int *J, int *nu, int64_t *nnz,
                                int *n_rows);

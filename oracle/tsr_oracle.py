@@ -40,6 +40,10 @@ design notes):
   R22 the spatial wavelet is the orthonormal Haar.
   R23 keep rule: per (k, j), the round(p * 10 P^2) largest |coefficients| of the
       charts (ties: lower index); the two pole values are always kept.
+  R32 energy keep rule: per (k, j), the fewest largest |coefficients| of the charts
+      (ties: lower index) whose squares sum to at least the fraction e of the
+      row's energy ("exceeds" read as >=; energies in FP64); at least one; the
+      poles always kept and not counted.
 """
 from __future__ import annotations
 
@@ -336,6 +340,39 @@ def wavelet_to_chart(C, nu):
 def keep_count(p: float, n_coef: int) -> int:
     """Reading R23: n_keep = floor(p * n_coef + 0.5), clamped to [1, n_coef]."""
     return int(min(n_coef, max(1, math.floor(p * n_coef + 0.5))))
+
+
+def energy_keep_count(coef, e: float) -> int:
+    """Precompute Step 2 (Section 3, "a threshold energy is pre-determined ... so that the
+    reserved energy exceeds the threshold") under reading R32: the smallest n >= 1 such that
+    the n largest |c| (ties: lower index) hold at least the fraction e of the row's energy
+    sum c^2.  Energies in FP64, accumulated in that order (the total is the full sum)."""
+    c = np.asarray(coef, dtype=np.float64).reshape(-1)
+    order = np.lexsort((np.arange(c.size), -np.abs(c)))
+    cum = np.cumsum(c[order] ** 2)
+    total = cum[-1]
+    if total == 0.0:
+        return 1
+    n = int(np.searchsorted(cum, e * total, side="left")) + 1   # first n with cum[n-1] >= e * total
+    return min(max(n, 1), c.size)
+
+
+def select_energy(Cw, nu, e):
+    """Keep mask of the energy rule (reading R32) for wavelet coefficients Cw (K, J, 10 P^2 + 2):
+    per (k, j) the energy_keep_count largest chart magnitudes (ties: lower index) plus the poles."""
+    P = chart_side(nu)
+    n_coef = 10 * P * P
+    K, J, _ = Cw.shape
+    mask = np.zeros(Cw.shape, dtype=bool)
+    idx = np.arange(n_coef)
+    for k in range(K):
+        for j in range(J):
+            row = Cw[k, j, :n_coef]
+            nk = energy_keep_count(row, e)
+            order = np.lexsort((idx, -np.abs(row).astype(np.float64)))
+            mask[k, j, order[:nk]] = True
+    mask[:, :, n_coef:] = True
+    return mask
 
 
 def select_top(Cw, nu, p):

@@ -122,6 +122,26 @@ extern "C" tsr_status tsr_haar_compress(const float *M, int K, int J, int nu, do
   return wavelet_compress(static_cast<float *>(mw.p), K, J, nu, p, out, s);
 }
 
+extern "C" tsr_status tsr_haar_compress_energy(const float *M, int K, int J, int nu, double energy,
+                                               tsr_compressed **out, tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(M && out, "tsr_haar_compress_energy: NULL argument");
+  TSR_CHECK_ARG(K >= 1 && K <= 16 && J >= 1 && J <= 32, "tsr_haar_compress_energy: K=%d J=%d out of range", K, J);
+  TSR_CHECK_ARG(nu >= 1 && nu <= 128, "tsr_haar_compress_energy: nu=%d outside [1, 128]", nu);
+  TSR_CHECK_ARG(energy > 0.0 && energy <= 1.0, "tsr_haar_compress_energy: energy=%g outside (0, 1]", energy);
+  *out = nullptr;
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  const int P = chart_side(nu);
+  Scratch mw;
+  st = mw.alloc(sizeof(float) * (size_t)K * J * (10 * P * P + 2), s);
+  if (st != TSR_OK) return st;
+  st = haar_forward(M, K * J, nu, static_cast<float *>(mw.p), s);
+  if (st != TSR_OK) return st;
+  return wavelet_compress_energy(static_cast<float *>(mw.p), K, J, nu, energy, out, s);
+}
+
 extern "C" tsr_status tsr_haar_recompress(const float *M, tsr_compressed *c, tsr_stream stream) {
   clear_error();
   TSR_CHECK_ARG(M && c, "tsr_haar_recompress: NULL argument");

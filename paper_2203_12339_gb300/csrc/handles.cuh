@@ -26,15 +26,18 @@ struct tsr_basis {
 // Compressed wavelet transfer: CSR over wavelet rows w in [0, 10 P^2 + 2).
 struct tsr_compressed {
   int device = -1;
-  int K = 0, J = 0, nu = 0, P = 0, n_rows = 0, n_keep = 0;
+  int K = 0, J = 0, nu = 0, P = 0, n_rows = 0;
+  int n_keep = 0;               // per (k, j) under the top-p rule; -1 under the energy rule
+  int keep_rule = 0;            // 0: top-p fraction, 1: energy threshold
   int64_t nnz = 0;
   int64_t *row_ptr = nullptr;   // [n_rows + 1]
   uint16_t *col = nullptr;      // [nnz]  k*J + j
   float *val = nullptr;         // [nnz]
-  // The same entries by column: column kj holds exactly n_keep + 2 entries
-  // (ascending wavelet row), used by the reverse mode.
-  int32_t *cidx = nullptr;      // [K*J][n_keep + 2] wavelet rows
-  float *cval = nullptr;        // [K*J][n_keep + 2]
+  // The same entries by column, used by the reverse mode: column kj holds its
+  // n_keep + 2 entries (ascending wavelet row) at [col_ptr[kj], col_ptr[kj+1]).
+  int32_t *cidx = nullptr;      // [nnz] wavelet rows
+  float *cval = nullptr;        // [nnz]
+  int64_t *col_ptr = nullptr;   // [K*J + 1]
 };
 
 // Batched-transfer plan: unit and mesh tables on the device (built once, outside
@@ -74,6 +77,8 @@ tsr_status haar_inverse(const float *Xw, int rows, int nu, float *X, cudaStream_
 tsr_status wavelet_compress(const float *Mw, int K, int J, int nu, double p, tsr_compressed **out,
                             cudaStream_t s);
 tsr_status wavelet_compress_into(const float *Mw, tsr_compressed *c, cudaStream_t s);
+tsr_status wavelet_compress_energy(const float *Mw, int K, int J, int nu, double energy, tsr_compressed **out,
+                                   cudaStream_t s);
 tsr_status relight(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,
                    cudaStream_t s);
 tsr_status relight_backward(const tsr_compressed *c, int n_edit, const float *g, const float *l,

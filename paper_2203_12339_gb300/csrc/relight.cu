@@ -235,15 +235,16 @@ __global__ void relight_qsum_kernel(const float *__restrict__ Qp, size_t n, floa
   }
 }
 
-// colsum[kj] = sum over the n_keep + 2 entries (w, val) of column kj of val * R[k][w]: a block per kj.
+// colsum[kj] = sum over the entries (w, val) of column kj of val * R[k][w]: a block per kj.
 __global__ void __launch_bounds__(256) relight_colsum_kernel(const int32_t *__restrict__ cidx,
-                                                            const float *__restrict__ cval, int ncol, int n_rows,
-                                                            int J, const float *__restrict__ R,
-                                                            float *__restrict__ colsum) {
+                                                            const float *__restrict__ cval,
+                                                            const int64_t *__restrict__ col_ptr, int n_rows, int J,
+                                                            const float *__restrict__ R, float *__restrict__ colsum) {
   __shared__ float red[8];
   const int kj = blockIdx.x, k = kj / J;
-  const int32_t *ci = cidx + (size_t)kj * ncol;
-  const float *cv = cval + (size_t)kj * ncol;
+  const int32_t *ci = cidx + col_ptr[kj];
+  const float *cv = cval + col_ptr[kj];
+  const int ncol = (int)(col_ptr[kj + 1] - col_ptr[kj]);
   const float *Rk = R + (size_t)k * n_rows;
   float acc = 0.0f;
   for (int q = threadIdx.x; q < ncol; q += blockDim.x) acc = fmaf(cv[q], Rk[ci[q]], acc);
@@ -336,7 +337,7 @@ tsr_status relight_backward(const tsr_compressed *c, int n_edit, const float *g,
   TSR_CUDA(cudaGetLastError());
   st = haar_forward(Q, K, c->nu, R, s);
   if (st != TSR_OK) return st;
-  relight_colsum_kernel<<<KJ, 256, 0, s>>>(c->cidx, c->cval, c->n_keep + 2, c->n_rows, J, R, colsum);
+  relight_colsum_kernel<<<KJ, 256, 0, s>>>(c->cidx, c->cval, c->col_ptr, c->n_rows, J, R, colsum);
   ::tsr::count_launch();
   relight_grad_finish_kernel<<<1, 1024, 0, s>>>(part, V, K, J, colsum, dg, dl); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());

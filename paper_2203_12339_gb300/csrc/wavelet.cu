@@ -249,6 +249,70 @@ __device__ __forceinline__ unsigned block_excl_scan(unsigned x, unsigned *wsum, 
   return excl;
 }
 
+// Keep flags of one (k, j) row and its column list, in index order: every key above
+// tau, and the first `remaining` keys equal to it (all of them when all_eq).  Chunks of
+// SEL_NT x 8 consecutive coefficients, 8 per thread; a block scan of the per-thread
+// counts places each kept value.  Both poles are kept and end the column list, which
+// holds n_keep + 2 entries.
+__device__ void keep_pass(const float *__restrict__ c, int n_coef, unsigned tau, unsigned remaining, bool all_eq,
+                          int n_keep, uint8_t *__restrict__ kp, int32_t *__restrict__ ci, float *__restrict__ cv,
+                          unsigned *wsum) {
+  unsigned written = 0, eq_seen = 0;
+  for (int base = 0; base < n_coef; base += 8 * SEL_NT) {
+    const int w0 = base + 8 * threadIdx.x;
+    float v[8];
+    unsigned u[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      v[q] = (w0 + q < n_coef) ? c[w0 + q] : 0.f;
+      u[q] = __float_as_uint(v[q]) & 0x7FFFFFFFu;
+    }
+    unsigned er = 0, eq_tot = 0;
+    if (!all_eq) {
+      unsigned neq = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) neq += (w0 + q < n_coef && u[q] == tau) ? 1u : 0u;
+      er = eq_seen + block_excl_scan(neq, wsum, eq_tot);
+    }
+    unsigned kmask = 0, nk = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      bool k = false;
+      if (w0 + q < n_coef) {
+        if (u[q] > tau) {
+          k = true;
+        } else if (u[q] == tau) {
+          k = all_eq || er < remaining;
+          ++er;
+        }
+      }
+      kmask |= (k ? 1u : 0u) << q;
+      nk += k ? 1u : 0u;
+    }
+    unsigned k_tot;
+    unsigned pos = written + block_excl_scan(nk, wsum, k_tot);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (w0 + q < n_coef) kp[w0 + q] = (uint8_t)((kmask >> q) & 1u);
+      if (((kmask >> q) & 1u) && pos < (unsigned)n_keep) {
+        ci[pos] = w0 + q;
+        cv[pos] = v[q];
+        ++pos;
+      }
+    }
+    written += k_tot;
+    eq_seen += eq_tot;
+  }
+  if (threadIdx.x == 0) {
+    kp[n_coef] = 1;
+    kp[n_coef + 1] = 1;
+    ci[n_keep] = n_coef;
+    cv[n_keep] = c[n_coef];
+    ci[n_keep + 1] = n_coef + 1;
+    cv[n_keep + 1] = c[n_coef + 1];
+  }
+}
+
 // One block per (k, j) row.  Radix select (4 x 8 bits) of the n_keep-th largest
 // |c| over the chart coefficients (histograms with warp-aggregated shared atomics:
 // lanes holding the same digit add once; four independent loads per thread in
@@ -322,65 +386,184 @@ __global__ void __launch_bounds__(SEL_NT) select_kernel(const float *__restrict_
     __syncthreads();
   }
   // prefix = key of the n_keep-th largest; keep `remaining` of its n_eq equal keys (lowest index first)
-  const unsigned tau = prefix;
-  const bool all_eq = remaining >= n_eq;
-  const int ncol = n_keep + 2;
-  int32_t *ci = cidx + (size_t)rowi * ncol;
-  float *cv = cval + (size_t)rowi * ncol;
-  unsigned written = 0, eq_seen = 0;
-  for (int base = 0; base < n_coef; base += 8 * SEL_NT) {
-    const int w0 = base + 8 * threadIdx.x;
-    float v[8];
-    unsigned u[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      v[q] = (w0 + q < n_coef) ? c[w0 + q] : 0.f;
-      u[q] = __float_as_uint(v[q]) & 0x7FFFFFFFu;
+  keep_pass(c, n_coef, prefix, remaining, remaining >= n_eq, n_keep, kp, cidx + (size_t)rowi * (n_keep + 2),
+            cval + (size_t)rowi * (n_keep + 2), wsum);
+}
+
+// Energy rule: per (k, j) row the smallest n >= 1 whose n largest |c| (ties: lower
+// index) hold at least a fraction e of the row's energy, the FP64 sum of c^2 over the
+// chart coefficients.  The same radix descent as the count rule on per-digit energies:
+// each warp histograms a contiguous part of the row (lanes holding the same digit are
+// added in lane order by their leader) and the warps' histograms are added in warp
+// order, so the choice is deterministic.  Out: n_keep, the key tau of the n_keep-th
+// largest, how many of the keys equal to tau are kept and how many there are.
+constexpr int EN_NT = 512;
+constexpr int EN_W = EN_NT / 32;
+__global__ void __launch_bounds__(EN_NT) select_energy_kernel(const float *__restrict__ Mw, int n_coef, int NW,
+                                                             double e, int *__restrict__ nk_out,
+                                                             unsigned *__restrict__ tau_out,
+                                                             unsigned *__restrict__ rem_out,
+                                                             unsigned *__restrict__ neq_out) {
+  extern __shared__ double en_smem[];
+  double *he = en_smem;                                        // [EN_W][256]
+  unsigned *hc = reinterpret_cast<unsigned *>(he + EN_W * 256);   // [EN_W][256]
+  __shared__ double Es[256];
+  __shared__ unsigned Cs[256];
+  __shared__ double red[EN_W];
+  __shared__ double s_total, s_eabove;
+  __shared__ unsigned s_sel, s_cabove;
+  const int rowi = blockIdx.x;
+  const float *c = Mw + (size_t)rowi * NW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double acc = 0.0;
+  for (int w = threadIdx.x; w < n_coef; w += EN_NT) {
+    const double x = c[w];
+    acc = fma(x, x, acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < EN_W; ++q) t += red[q];
+    s_total = t;
+  }
+  __syncthreads();
+  const double total = s_total;
+  if (total == 0.0) {   // every coefficient is 0: keep the first
+    if (threadIdx.x == 0) {
+      nk_out[rowi] = 1;
+      tau_out[rowi] = 0u;
+      rem_out[rowi] = 1u;
+      neq_out[rowi] = (unsigned)n_coef;
     }
-    unsigned er = 0, eq_tot = 0;
-    if (!all_eq) {
-      unsigned neq = 0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) neq += (w0 + q < n_coef && u[q] == tau) ? 1u : 0u;
-      er = eq_seen + block_excl_scan(neq, wsum, eq_tot);
+    return;
+  }
+  double rem_e = e * total;
+  unsigned prefix = 0, mask = 0, cnt_above = 0, n_eq = 0;
+  const int chunk = (n_coef + EN_W - 1) / EN_W;
+  const int w0 = warp * chunk, w1 = min(n_coef, w0 + chunk);
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int d = lane; d < 256; d += 32) {
+      he[warp * 256 + d] = 0.0;
+      hc[warp * 256 + d] = 0u;
     }
-    unsigned kmask = 0, nk = 0;
+    __syncwarp();
+    for (int base = w0; base < w1; base += 32) {
+      const int w = base + lane;
+      const float v = (w < w1) ? c[w] : 0.0f;
+      const unsigned u = __float_as_uint(v) & 0x7FFFFFFFu;
+      const bool in = (w < w1) && ((u & mask) == prefix);
+      if (__ballot_sync(0xffffffffu, in) == 0u) continue;
+      const unsigned digit = in ? ((u >> shift) & 255u) : 256u;
+      const double x = in ? (double)v * (double)v : 0.0;
+      const unsigned peers = __match_any_sync(0xffffffffu, digit);
+      double sum = 0.0;
+      for (int src = 0; src < 32; ++src) {
+        const double y = __shfl_sync(0xffffffffu, x, src);
+        if ((peers >> src) & 1u) sum += y;
+      }
+      if (in && lane == __ffs(peers) - 1) {
+        he[warp * 256 + digit] += sum;
+        hc[warp * 256 + digit] += (unsigned)__popc(peers);
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += EN_NT) {
+      double E = 0.0;
+      unsigned C = 0u;
+      for (int q = 0; q < EN_W; ++q) {
+        E += he[q * 256 + d];
+        C += hc[q * 256 + d];
+      }
+      Es[d] = E;
+      Cs[d] = C;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      // lane l holds digits 255 - 8 l down to 248 - 8 l; the first digit (from the top) where
+      // the running energy reaches rem_e is selected (if rounding leaves it short, the lowest
+      // non-empty digit: everything in the set is kept)
+      double he8[8], se = 0.0;
+      unsigned hc8[8], sc = 0u;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      bool k = false;
-      if (w0 + q < n_coef) {
-        if (u[q] > tau) {
-          k = true;
-        } else if (u[q] == tau) {
-          k = all_eq || er < remaining;
-          ++er;
+      for (int q = 0; q < 8; ++q) {
+        he8[q] = Es[255 - 8 * lane - q];
+        hc8[q] = Cs[255 - 8 * lane - q];
+        se += he8[q];
+        sc += hc8[q];
+      }
+      double ie = se;
+      unsigned ic = sc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double ye = __shfl_up_sync(0xffffffffu, ie, o);
+        const unsigned yc = __shfl_up_sync(0xffffffffu, ic, o);
+        if (lane >= o) {
+          ie += ye;
+          ic += yc;
         }
       }
-      kmask |= (k ? 1u : 0u) << q;
-      nk += k ? 1u : 0u;
-    }
-    unsigned k_tot;
-    unsigned pos = written + block_excl_scan(nk, wsum, k_tot);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      if (w0 + q < n_coef) kp[w0 + q] = (uint8_t)((kmask >> q) & 1u);
-      if (((kmask >> q) & 1u) && pos < (unsigned)n_keep) {
-        ci[pos] = w0 + q;
-        cv[pos] = v[q];
-        ++pos;
+      const unsigned hit = __ballot_sync(0xffffffffu, ie >= rem_e);
+      const unsigned nonempty = __ballot_sync(0xffffffffu, sc > 0u);
+      const int L = hit ? __ffs(hit) - 1 : 31 - __clz(nonempty);
+      if (lane == L) {
+        double cum = ie - se;
+        unsigned ccum = ic - sc;
+        int q = 0;
+        if (hit) {
+          for (; q < 7; ++q) {
+            if (cum + he8[q] >= rem_e) break;
+            cum += he8[q];
+            ccum += hc8[q];
+          }
+        } else {
+          int last = 0;
+          for (int t = 0; t < 8; ++t)
+            if (hc8[t] > 0u) last = t;
+          for (; q < last; ++q) {
+            cum += he8[q];
+            ccum += hc8[q];
+          }
+        }
+        s_sel = (unsigned)(255 - 8 * lane - q);
+        s_eabove = cum;
+        s_cabove = ccum;
       }
     }
-    written += k_tot;
-    eq_seen += eq_tot;
+    __syncthreads();
+    rem_e -= s_eabove;
+    cnt_above += s_cabove;
+    prefix |= s_sel << shift;
+    mask |= 255u << shift;
+    n_eq = Cs[s_sel];
+    __syncthreads();
   }
   if (threadIdx.x == 0) {
-    kp[n_coef] = 1;
-    kp[n_coef + 1] = 1;
-    ci[n_keep] = n_coef;
-    cv[n_keep] = c[n_coef];
-    ci[n_keep + 1] = n_coef + 1;
-    cv[n_keep + 1] = c[n_coef + 1];
+    const double tv = (double)__uint_as_float(prefix);
+    const double t2 = tv * tv;
+    double m = (t2 > 0.0) ? ceil(rem_e / t2) : 1.0;
+    m = fmin(fmax(m, 1.0), (double)n_eq);
+    nk_out[rowi] = (int)(cnt_above + (unsigned)m);
+    tau_out[rowi] = prefix;
+    rem_out[rowi] = (unsigned)m;
+    neq_out[rowi] = n_eq;
   }
+}
+
+// Keep flags and column lists of the energy rule: column kj's n_keep + 2 entries at col_ptr[kj].
+__global__ void __launch_bounds__(SEL_NT) keep_energy_kernel(const float *__restrict__ Mw, int n_coef, int NW,
+                                                            const int *__restrict__ nk, const unsigned *__restrict__ tau,
+                                                            const unsigned *__restrict__ rem,
+                                                            const unsigned *__restrict__ neq,
+                                                            const int64_t *__restrict__ col_ptr,
+                                                            uint8_t *__restrict__ keep, int32_t *__restrict__ cidx,
+                                                            float *__restrict__ cval) {
+  __shared__ unsigned wsum[SEL_NT / 32];
+  const int rowi = blockIdx.x;
+  keep_pass(Mw + (size_t)rowi * NW, n_coef, tau[rowi], rem[rowi], rem[rowi] >= neq[rowi], nk[rowi],
+            keep + (size_t)rowi * NW, cidx + col_ptr[rowi], cval + col_ptr[rowi], wsum);
 }
 
 // CSR by wavelet row, in three launches over tiles of 32 rows:
@@ -493,17 +676,14 @@ static int keep_count(double p, int n_coef) {
   return (int)v;
 }
 
-// Selection + packing into an existing handle (its K, J, nu and n_keep).
-tsr_status wavelet_compress_into(const float *Mw, tsr_compressed *c, cudaStream_t s) {
-  const int NW = c->n_rows, n_coef = NW - 2, KJ = c->K * c->J;
-  Scratch keep_s, cnt_s;
-  tsr_status st = keep_s.alloc((size_t)KJ * NW, s);
-  if (st == TSR_OK) st = cnt_s.alloc(sizeof(int64_t) * ((NW + ROW_TILE - 1) / ROW_TILE + 1), s);
-  if (st != TSR_OK) return st;
-  uint8_t *keep = static_cast<uint8_t *>(keep_s.p);
-  int64_t *cnt = static_cast<int64_t *>(cnt_s.p);
+// CSR by wavelet row from the keep flags [K J][n_rows].
+static tsr_status csr_from_keep(const float *Mw, const uint8_t *keep, tsr_compressed *c, cudaStream_t s) {
+  const int NW = c->n_rows, KJ = c->K * c->J;
   const int row_tiles = (NW + ROW_TILE - 1) / ROW_TILE;
-  select_kernel<<<KJ, SEL_NT, 0, s>>>(Mw, n_coef, NW, c->n_keep, keep, c->cidx, c->cval); ::tsr::count_launch();
+  Scratch cnt_s;
+  tsr_status st = cnt_s.alloc(sizeof(int64_t) * (row_tiles + 1), s);
+  if (st != TSR_OK) return st;
+  int64_t *cnt = static_cast<int64_t *>(cnt_s.p);
   count_kernel<<<row_tiles, 256, 0, s>>>(keep, KJ, NW, cnt); ::tsr::count_launch();
   scan_kernel<<<1, 1024, 0, s>>>(cnt, row_tiles); ::tsr::count_launch();
   fill_kernel<<<row_tiles, 256, 0, s>>>(Mw, keep, KJ, NW, cnt, c->row_ptr, c->col, c->val); ::tsr::count_launch();
@@ -511,29 +691,103 @@ tsr_status wavelet_compress_into(const float *Mw, tsr_compressed *c, cudaStream_
   return TSR_OK;
 }
 
-tsr_status wavelet_compress(const float *Mw, int K, int J, int nu, double p, tsr_compressed **out, cudaStream_t s) {
+// Selection + packing into an existing top-p handle (its K, J, nu and n_keep).
+tsr_status wavelet_compress_into(const float *Mw, tsr_compressed *c, cudaStream_t s) {
+  if (c->keep_rule != 0) {
+    set_error("haar_recompress: the energy rule's sizes depend on the data; compress anew");
+    return TSR_ERR_UNSUPPORTED;
+  }
+  const int NW = c->n_rows, n_coef = NW - 2, KJ = c->K * c->J;
+  Scratch keep_s;
+  tsr_status st = keep_s.alloc((size_t)KJ * NW, s);
+  if (st != TSR_OK) return st;
+  uint8_t *keep = static_cast<uint8_t *>(keep_s.p);
+  select_kernel<<<KJ, SEL_NT, 0, s>>>(Mw, n_coef, NW, c->n_keep, keep, c->cidx, c->cval); ::tsr::count_launch();
+  TSR_CUDA(cudaGetLastError());
+  return csr_from_keep(Mw, keep, c, s);
+}
+
+// A handle with its arrays for the given column lengths (n_keep of each (k, j) + 2 poles).
+static tsr_status compressed_alloc(int K, int J, int nu, const std::vector<int> &n_keep_col, tsr_compressed **out) {
   const int P = chart_side(nu);
-  const int n_coef = 10 * P * P, NW = n_coef + 2, KJ = K * J;
+  const int KJ = K * J;
   tsr_compressed *c = new tsr_compressed();
   cudaGetDevice(&c->device);
   c->K = K;
   c->J = J;
   c->nu = nu;
   c->P = P;
-  c->n_rows = NW;
-  c->n_keep = keep_count(p, n_coef);
-  c->nnz = (int64_t)KJ * (c->n_keep + 2);
-  cudaError_t e = cudaMalloc(&c->row_ptr, sizeof(int64_t) * (NW + 1));
+  c->n_rows = 10 * P * P + 2;
+  std::vector<int64_t> cp(KJ + 1, 0);
+  for (int q = 0; q < KJ; ++q) cp[q + 1] = cp[q] + n_keep_col[q] + 2;
+  c->nnz = cp[KJ];
+  cudaError_t e = cudaMalloc(&c->row_ptr, sizeof(int64_t) * (c->n_rows + 1));
   if (e == cudaSuccess) e = cudaMalloc(&c->col, sizeof(uint16_t) * c->nnz);
   if (e == cudaSuccess) e = cudaMalloc(&c->val, sizeof(float) * c->nnz);
   if (e == cudaSuccess) e = cudaMalloc(&c->cidx, sizeof(int32_t) * c->nnz);
   if (e == cudaSuccess) e = cudaMalloc(&c->cval, sizeof(float) * c->nnz);
+  if (e == cudaSuccess) e = cudaMalloc(&c->col_ptr, sizeof(int64_t) * (KJ + 1));
+  if (e == cudaSuccess) e = cudaMemcpy(c->col_ptr, cp.data(), sizeof(int64_t) * (KJ + 1), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
-    set_error("wavelet_compress: %s", cudaGetErrorString(e));
+    set_error("compressed transfer: %s", cudaGetErrorString(e));
     tsr_compressed_destroy(c);
     return e == cudaErrorMemoryAllocation ? TSR_ERR_OOM : TSR_ERR_CUDA;
   }
-  tsr_status st = wavelet_compress_into(Mw, c, s);
+  *out = c;
+  return TSR_OK;
+}
+
+tsr_status wavelet_compress(const float *Mw, int K, int J, int nu, double p, tsr_compressed **out, cudaStream_t s) {
+  const int P = chart_side(nu);
+  const int n_coef = 10 * P * P;
+  const int n_keep = keep_count(p, n_coef);
+  tsr_compressed *c = nullptr;
+  tsr_status st = compressed_alloc(K, J, nu, std::vector<int>(K * J, n_keep), &c);
+  if (st != TSR_OK) return st;
+  c->n_keep = n_keep;
+  c->keep_rule = 0;
+  st = wavelet_compress_into(Mw, c, s);
+  if (st != TSR_OK) {
+    tsr_compressed_destroy(c);
+    return st;
+  }
+  *out = c;
+  return TSR_OK;
+}
+
+// Energy rule: the column lengths depend on the data, so the call reads them back
+// (one stream synchronisation) to size the handle before packing.
+tsr_status wavelet_compress_energy(const float *Mw, int K, int J, int nu, double energy, tsr_compressed **out,
+                                   cudaStream_t s) {
+  const int P = chart_side(nu);
+  const int n_coef = 10 * P * P, NW = n_coef + 2, KJ = K * J;
+  Scratch meta_s, keep_s;
+  tsr_status st = meta_s.alloc(sizeof(int) * 4 * (size_t)KJ, s);
+  if (st == TSR_OK) st = keep_s.alloc((size_t)KJ * NW, s);
+  if (st != TSR_OK) return st;
+  int *nk = static_cast<int *>(meta_s.p);
+  unsigned *tau = reinterpret_cast<unsigned *>(nk + KJ), *rem = tau + KJ, *neq = rem + KJ;
+  const size_t smem = (sizeof(double) + sizeof(unsigned)) * EN_W * 256;
+  TSR_CUDA(cudaFuncSetAttribute(select_energy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  select_energy_kernel<<<KJ, EN_NT, smem, s>>>(Mw, n_coef, NW, energy, nk, tau, rem, neq); ::tsr::count_launch();
+  TSR_CUDA(cudaGetLastError());
+  std::vector<int> nk_h(KJ);
+  TSR_CUDA(cudaMemcpyAsync(nk_h.data(), nk, sizeof(int) * KJ, cudaMemcpyDeviceToHost, s));
+  TSR_CUDA(cudaStreamSynchronize(s));
+  tsr_compressed *c = nullptr;
+  st = compressed_alloc(K, J, nu, nk_h, &c);
+  if (st != TSR_OK) return st;
+  c->n_keep = -1;
+  c->keep_rule = 1;
+  uint8_t *keep = static_cast<uint8_t *>(keep_s.p);
+  keep_energy_kernel<<<KJ, SEL_NT, 0, s>>>(Mw, n_coef, NW, nk, tau, rem, neq, c->col_ptr, keep, c->cidx, c->cval);
+  ::tsr::count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) st = csr_from_keep(Mw, keep, c, s);
+  else {
+    set_error("keep_energy_kernel: %s", cudaGetErrorString(e));
+    st = TSR_ERR_CUDA;
+  }
   if (st != TSR_OK) {
     tsr_compressed_destroy(c);
     return st;
@@ -551,5 +805,6 @@ extern "C" void tsr_compressed_destroy(tsr_compressed *c) {
   cudaFree(c->val);
   cudaFree(c->cidx);
   cudaFree(c->cval);
+  cudaFree(c->col_ptr);
   delete c;
 }

@@ -53,6 +53,7 @@ _SIGNATURES = {
     "tsr_haar_inverse": (_I, [_P, _I, _I, _P, _P]),
     "tsr_wavelet_compress": (_I, [_P, _I, _I, _I, _D, ctypes.POINTER(_P), _P]),
     "tsr_haar_compress": (_I, [_P, _I, _I, _I, _D, ctypes.POINTER(_P), _P]),
+    "tsr_haar_compress_energy": (_I, [_P, _I, _I, _I, _D, ctypes.POINTER(_P), _P]),
     "tsr_haar_recompress": (_I, [_P, _P, _P]),
     "tsr_compressed_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                                  ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_I)]),
@@ -381,6 +382,16 @@ def haar_compress(M: torch.Tensor, nu: int, p: float, out: Compressed | None = N
         return out
     h = _P()
     _check(lib().tsr_haar_compress(_ptr(m), K, J, nu, float(p), ctypes.byref(h), _stream()))
+    return Compressed(h)
+
+
+def haar_compress_energy(M: torch.Tensor, nu: int, energy: float) -> Compressed:
+    """tsr_haar_compress_energy: forward Haar of M [K][J][N], then per (k, j) the fewest largest
+    coefficients holding at least `energy` of the row's energy (the poles always kept)."""
+    K, J, N = M.shape
+    m = _dev(M, torch.float32, (K, J, 10 * nu * nu + 2), "M")
+    h = _P()
+    _check(lib().tsr_haar_compress_energy(_ptr(m), K, J, nu, float(energy), ctypes.byref(h), _stream()))
     return Compressed(h)
 
 

@@ -255,6 +255,80 @@ def test_select_and_pack_exact(torch_cuda, tsr, nu, p):
             assert val[q] == Mw.reshape(K * J, n_rows)[col[q], w]
 
 
+def _energy_boundary_ok(row, e, n_gpu):
+    """True if n_gpu reaches the energy threshold and n_gpu - 1 does not, both within FP64
+    rounding of the summation order (the two sides add the same exact squares in different orders)."""
+    c = np.asarray(row, dtype=np.float64)
+    order = np.lexsort((np.arange(c.size), -np.abs(c)))
+    cum = np.cumsum(c[order] ** 2)
+    total, tol = cum[-1], 1e-12 * cum[-1]
+    return cum[n_gpu - 1] >= e * total - tol and (n_gpu == 1 or cum[n_gpu - 2] < e * total + tol)
+
+
+@pytest.mark.parametrize("nu,e", [(4, 0.95), (8, 0.9), (16, 0.98), (33, 0.95), (64, 0.99)])
+def test_energy_select_and_pack(torch_cuda, tsr, nu, e):
+    """Energy rule (Section 3, precompute Step 2): per (k, j) the kept set equals the oracle's on the
+    same FP32 wavelet coefficients (the GPU's own Haar output), columns of varying length."""
+    torch = torch_cuda
+    K, J = 3, 4
+    P = O.chart_side(nu)
+    n_coef = 10 * P * P
+    rng = np.random.default_rng(100 + nu)
+    N = 10 * nu * nu + 2
+    decay = np.exp(-np.arange(N) % max(1, nu * nu) / max(1.0, nu * nu / 6.0))
+    M = (rng.standard_normal((K, J, N)) * decay).astype(np.float32)
+    Md = _dev(torch, M)
+    Mw = tsr.haar_forward(Md.reshape(K * J, N), nu).reshape(K, J, -1).cpu().numpy()
+    comp = tsr.haar_compress_energy(Md, nu, e)
+    row_ptr, col, val = (t.cpu().numpy() for t in comp.export())
+    n_rows = n_coef + 2
+    got = _mask_from_csr(row_ptr, col, n_rows, K * J).reshape(K, J, n_rows)
+    want = O.select_energy(Mw, nu, e)
+    assert got[:, :, n_coef:].all()
+    for k in range(K):
+        for j in range(J):
+            if np.array_equal(got[k, j], want[k, j]):
+                continue
+            n_gpu = int(got[k, j, :n_coef].sum())   # boundary decided within FP64 rounding: the set
+            assert _energy_boundary_ok(Mw[k, j, :n_coef], e, n_gpu)   # must still be a prefix of the ranking
+            order = np.lexsort((np.arange(n_coef), -np.abs(Mw[k, j, :n_coef]).astype(np.float64)))
+            assert set(np.nonzero(got[k, j, :n_coef])[0].tolist()) == set(order[:n_gpu].tolist())
+    assert comp.nnz == int(got.sum())
+    for w in range(0, n_rows, 5):
+        for q in range(row_ptr[w], row_ptr[w + 1]):
+            assert val[q] == Mw.reshape(K * J, n_rows)[col[q], w]
+    with pytest.raises(tsr.TsrError):
+        tsr.haar_compress(Md, nu, 0.1, out=comp)   # data-dependent sizes: no recompression in place
+
+
+def test_energy_rule_relight_and_adjoint(torch_cuda, tsr):
+    """Relight and its adjoint through a handle with columns of different lengths (the adjoint
+    walks the per-column lists by their offsets)."""
+    torch = torch_cuda
+    nu, K, J, E, e = 8, 6, 9, 4, 0.95
+    N = 10 * nu * nu + 2
+    rng = np.random.default_rng(21)
+    M = (rng.standard_normal((K, J, N)) * np.exp(-np.arange(N) % 64 / 12.0)).astype(np.float32)
+    Md = _dev(torch, M)
+    Mw = tsr.haar_forward(Md.reshape(K * J, N), nu).reshape(K, J, -1).cpu().numpy()
+    comp = tsr.haar_compress_energy(Md, nu, e)
+    row_ptr, col, _ = (t.cpu().numpy() for t in comp.export())
+    mask = _mask_from_csr(row_ptr, col, Mw.shape[-1], K * J).reshape(Mw.shape)
+    counts = mask.sum(axis=-1)
+    assert counts.min() < counts.max()            # the columns really differ in length
+    kept = np.where(mask, Mw.astype(np.float64), 0.0)
+    g = rng.standard_normal((E, 3, K)).astype(np.float32)
+    light = rng.standard_normal(J).astype(np.float32)
+    B = tsr.relight(comp, _dev(torch, g), _dev(torch, light)).cpu().numpy()
+    B_ref = O.relight(kept, nu, g.astype(np.float64), light.astype(np.float64))
+    assert np.max(np.abs(B - B_ref)) <= 1e-5 * np.max(np.abs(B_ref))
+    dB = rng.standard_normal((E, 3, N)).astype(np.float32)
+    dg, dl = tsr.relight_backward(comp, _dev(torch, g), _dev(torch, light), _dev(torch, dB))
+    dg_ref, dl_ref = O.relight_vjp(kept, nu, g.astype(np.float64), light.astype(np.float64), dB.astype(np.float64))
+    assert np.max(np.abs(dg.cpu().numpy() - dg_ref)) <= 1e-5 * np.max(np.abs(dg_ref))
+    assert np.max(np.abs(dl.cpu().numpy() - dl_ref)) <= 1e-5 * np.max(np.abs(dl_ref))
+
+
 # ------------------------------------------------------------------ Steps 3-5 relight
 def _compressed_case(torch, tsr, nu, K, J, p, seed):
     rng = np.random.default_rng(seed)

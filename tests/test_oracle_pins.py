@@ -411,6 +411,57 @@ def test_select_top_brute_force_with_ties():
             assert mask[k, j, n_coef:].all()
 
 
+def _min_subset_size_reaching(vals, target):
+    """Brute force: the size of the smallest subset of vals whose squares sum to >= target
+    (exact rational arithmetic on the integer-valued inputs)."""
+    from itertools import combinations
+    sq = [int(v) * int(v) for v in vals]
+    for n in range(1, len(vals) + 1):
+        if any(sum(c) >= target for c in combinations(sq, n)):
+            return n
+    return len(vals)
+
+
+def test_energy_keep_count_is_the_smallest_subset_by_brute_force():
+    """Greedy-by-magnitude is optimal: for integer coefficients (exact squares and sums) the
+    count equals the smallest subset of any kind that reaches the energy fraction."""
+    from fractions import Fraction
+    rng = np.random.default_rng(3)
+    for trial in range(40):
+        n = int(rng.integers(3, 11))
+        vals = rng.integers(-6, 7, size=n)
+        if not vals.any():
+            continue
+        e = [0.5, 0.8, 0.9, 0.95, 0.98, 1.0][trial % 6]
+        total = sum(int(v) * int(v) for v in vals)
+        target = Fraction(e).limit_denominator(1000) * total
+        want = _min_subset_size_reaching(vals, target)
+        assert O.energy_keep_count(vals.astype(np.float32), e) == want, (vals, e)
+
+
+def test_energy_keep_count_properties():
+    rng = np.random.default_rng(4)
+    c = rng.standard_normal(5000) * np.exp(rng.uniform(-6, 0, 5000))
+    en = np.sort(c ** 2)[::-1]
+    prev = 0
+    for e in (0.5, 0.9, 0.95, 0.98, 0.999):
+        n = O.energy_keep_count(c, e)
+        assert n >= prev                                             # monotone in e
+        assert en[:n].sum() >= e * en.sum() * (1 - 1e-14)            # reaches the threshold ...
+        assert n == 1 or en[:n - 1].sum() < e * en.sum() * (1 + 1e-14)   # ... and no fewer would
+        prev = n
+    z = np.zeros(9)
+    assert O.energy_keep_count(z, 0.95) == 1                         # all zero: keep one
+    z[[2, 5, 7]] = [1.0, -2.0, 0.5]
+    assert O.energy_keep_count(z, 1.0) == 3                          # e = 1: every nonzero value
+    nu = 1   # P = 1: 10 chart coefficients + 2 poles
+    row = np.array([3.0, -3.0, 1.0, 0.0, 3.0, 2.0, 0.0, 1.0, -1.0, 0.0, 5.0, 6.0])
+    mask = O.select_energy(row[None, None, :], nu, 0.6)
+    # energies 9, 9, 9, 4, 1, 1, 1 (total 34): 0.6 * 34 = 20.4 needs three 9s; ties by index: 0, 1, 4
+    assert np.nonzero(mask[0, 0, :10])[0].tolist() == [0, 1, 4]
+    assert mask[0, 0, 10:].all()
+
+
 # ---------------------------------------------------------------- Steps 3-5 relight
 def test_relight_uncompressed_equals_direct_eq6(pca_basis_k16):
     f, _ = pca_basis_k16
