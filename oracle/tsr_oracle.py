@@ -40,6 +40,9 @@ design notes):
   R22 the spatial wavelet is the orthonormal Haar.
   R23 keep rule: per (k, j), the round(p * 10 P^2) largest |coefficients| of the
       charts (ties: lower index); the two pole values are always kept.
+  R33 the paper's Step-2 wavelet "Daubechies 9/7": the biorthogonal CDF 9/7 pair
+      by lifting (symmetric extension, low band DC gain sqrt 2), separable 2D
+      Mallat pyramid of each chart's P x P image down to 1 x 1.
   R32 energy keep rule: per (k, j), the fewest largest |coefficients| of the charts
       (ties: lower index) whose squares sum to at least the fraction e of the
       row's energy ("exceeds" read as >=; energies in FP64); at least one; the
@@ -337,6 +340,113 @@ def wavelet_to_chart(C, nu):
     return out
 
 
+# ---------------------------------------------------------------- CDF 9/7 spatial wavelet
+# The paper's Step-2 wavelet ("Daubechies 9/7", Section 5), reading R33: the
+# biorthogonal Cohen-Daubechies-Feauveau 9/7 pair in the lifting factorisation of
+# Daubechies and Sweldens (the one JPEG 2000 uses), whole-sample symmetric
+# extension at the ends, scaled so that the low band has DC gain sqrt(2) (the
+# normalisation of the orthonormal Haar); on each chart the separable 2D Mallat
+# pyramid of the P x P image (row-major, chart pixel (r, c) = vertex d nu^2 + r nu + c,
+# zero padding), every level transforming rows then columns of the low-low band,
+# down to 1 x 1.
+CDF97_ALPHA = -1.586134342059924
+CDF97_BETA = -0.052980118572961
+CDF97_GAMMA = 0.882911075530934
+CDF97_DELTA = 0.443506852043971
+CDF97_ZETA = 1.149604398860241
+
+
+def _lift_1d(x):
+    """One analysis level on the last axis (even length n): returns [low (n/2) | high (n/2)]."""
+    x = np.asarray(x, dtype=np.float64)
+    s = x[..., 0::2].copy()
+    d = x[..., 1::2].copy()
+    for c, target in ((CDF97_ALPHA, "d"), (CDF97_BETA, "s"), (CDF97_GAMMA, "d"), (CDF97_DELTA, "s")):
+        if target == "d":    # d_i += c (s_i + s_{i+1}), s beyond the end mirrored: s_m = s_{m-1}
+            s_next = np.concatenate([s[..., 1:], s[..., -1:]], axis=-1)
+            d = d + c * (s + s_next)
+        else:                # s_i += c (d_{i-1} + d_i), d_{-1} = d_0
+            d_prev = np.concatenate([d[..., :1], d[..., :-1]], axis=-1)
+            s = s + c * (d_prev + d)
+    return np.concatenate([s * CDF97_ZETA, d / CDF97_ZETA], axis=-1)
+
+
+def _unlift_1d(y):
+    """Inverse of _lift_1d on the last axis."""
+    y = np.asarray(y, dtype=np.float64)
+    m = y.shape[-1] // 2
+    s = y[..., :m] / CDF97_ZETA
+    d = y[..., m:] * CDF97_ZETA
+    for c, target in ((CDF97_DELTA, "s"), (CDF97_GAMMA, "d"), (CDF97_BETA, "s"), (CDF97_ALPHA, "d")):
+        if target == "d":
+            s_next = np.concatenate([s[..., 1:], s[..., -1:]], axis=-1)
+            d = d - c * (s + s_next)
+        else:
+            d_prev = np.concatenate([d[..., :1], d[..., :-1]], axis=-1)
+            s = s - c * (d_prev + d)
+    x = np.empty(y.shape)
+    x[..., 0::2] = s
+    x[..., 1::2] = d
+    return x
+
+
+def cdf97_forward_2d(img):
+    """Mallat pyramid of (..., P, P) images: per level rows then columns of the low-low band."""
+    a = np.array(img, dtype=np.float64)
+    n = a.shape[-1]
+    while n >= 2:
+        a[..., :n, :n] = _lift_1d(a[..., :n, :n])
+        a[..., :n, :n] = np.swapaxes(_lift_1d(np.swapaxes(a[..., :n, :n], -1, -2)), -1, -2)
+        n //= 2
+    return a
+
+
+def cdf97_inverse_2d(coef):
+    a = np.array(coef, dtype=np.float64)
+    P = a.shape[-1]
+    n = 2
+    while n <= P:
+        a[..., :n, :n] = np.swapaxes(_unlift_1d(np.swapaxes(a[..., :n, :n], -1, -2)), -1, -2)
+        a[..., :n, :n] = _unlift_1d(a[..., :n, :n])
+        n *= 2
+    return a
+
+
+def chart_to_cdf97(X, nu):
+    """Spatial CDF 9/7 transform of per-vertex data X[..., N] (reading R33): chart d's image
+    at [d P^2, (d+1) P^2) of the result (row-major pyramid), the two poles last."""
+    X = np.asarray(X, dtype=np.float64)
+    P = chart_side(nu)
+    lead = X.shape[:-1]
+    out = np.zeros(lead + (10 * P * P + 2,))
+    for d in range(10):
+        img = np.zeros(lead + (P, P))
+        img[..., :nu, :nu] = X[..., d * nu * nu:(d + 1) * nu * nu].reshape(lead + (nu, nu))
+        out[..., d * P * P:(d + 1) * P * P] = cdf97_forward_2d(img).reshape(lead + (P * P,))
+    out[..., 10 * P * P:] = X[..., 10 * nu * nu:]
+    return out
+
+
+def cdf97_to_chart(C, nu):
+    """Inverse of chart_to_cdf97 (synthesis; drops the padding)."""
+    C = np.asarray(C, dtype=np.float64)
+    P = chart_side(nu)
+    lead = C.shape[:-1]
+    out = np.zeros(lead + (10 * nu * nu + 2,))
+    for d in range(10):
+        img = cdf97_inverse_2d(C[..., d * P * P:(d + 1) * P * P].reshape(lead + (P, P)))
+        out[..., d * nu * nu:(d + 1) * nu * nu] = img[..., :nu, :nu].reshape(lead + (nu * nu,))
+    out[..., 10 * nu * nu:] = C[..., 10 * P * P:]
+    return out
+
+
+def cdf97_synthesis_matrix(nu):
+    """The explicit matrix S (N x (10 P^2 + 2)) of cdf97_to_chart, column by column (small nu only)."""
+    P = chart_side(nu)
+    NW = 10 * P * P + 2
+    return cdf97_to_chart(np.eye(NW), nu).T
+
+
 def keep_count(p: float, n_coef: int) -> int:
     """Reading R23: n_keep = floor(p * n_coef + 0.5), clamped to [1, n_coef]."""
     return int(min(n_coef, max(1, math.floor(p * n_coef + 0.5))))
@@ -403,15 +513,16 @@ def select_top(Cw, nu, p):
 # ----------------------------------------------------------------------------
 
 
-def relight(Cw_kept, nu, g, light):
-    """Rendering Steps 3-5: B[e, ch, o] = w_1^{-1}( sum_{k,j} g[e,ch,k] l_j Cw[k, j, :] ).
+def relight(Cw_kept, nu, g, light, wavelet="haar"):
+    """Rendering Steps 3-5: B[e, ch, o] = w^{-1}( sum_{k,j} g[e,ch,k] l_j Cw[k, j, :] ).
 
     Cw_kept: (K, J, 10 P^2 + 2) kept wavelet coefficients (zeros where
-    discarded); g: (E, 3, K); light: (J,).  Returns (E, 3, N).
+    discarded); g: (E, 3, K); light: (J,).  Returns (E, 3, N).  wavelet: "haar"
+    (R22) or "cdf97" (R33), the transform the coefficients are in.
     """
     c = np.asarray(g, dtype=np.float64)[..., :, None] * np.asarray(light, dtype=np.float64)[None, None, None, :]
     bw = np.einsum("eckj,kjw->ecw", c, np.asarray(Cw_kept, dtype=np.float64))
-    return wavelet_to_chart(bw, nu)
+    return wavelet_to_chart(bw, nu) if wavelet == "haar" else cdf97_to_chart(bw, nu)
 
 
 def relight_direct(f, pos, area, T, g, light, r_max=40.0, rows=None):
@@ -431,14 +542,18 @@ def relight_direct(f, pos, area, T, g, light, r_max=40.0, rows=None):
     return out
 
 
-def relight_vjp(Cw_kept, nu, g, light, dB):
+def relight_vjp(Cw_kept, nu, g, light, dB, wavelet="haar"):
     """Reverse mode of ``relight``: given dL/dB (E,3,N) return (dL/dg (E,3,K), dL/dl (J,)).
 
-    dL/db^w = w_1 dL/dB (w_1 is orthonormal, so the adjoint of its inverse is
-    itself), dL/dc[e,ch,k,j] = sum_w Cw[k,j,w] dL/db^w[e,ch,w],
+    dL/db^w = S^T dL/dB with S the synthesis (for the orthonormal Haar S^T is the
+    analysis w_1; for CDF 9/7 the explicit transpose of the synthesis matrix),
+    dL/dc[e,ch,k,j] = sum_w Cw[k,j,w] dL/db^w[e,ch,w],
     dL/dg_k = sum_j l_j dL/dc_kj, dL/dl_j = sum_{e,ch,k} g_k dL/dc_kj.
     """
-    rw = chart_to_wavelet(dB, nu)
+    if wavelet == "haar":
+        rw = chart_to_wavelet(dB, nu)
+    else:
+        rw = np.asarray(dB, dtype=np.float64) @ cdf97_synthesis_matrix(nu)
     dc = np.einsum("kjw,ecw->eckj", np.asarray(Cw_kept, dtype=np.float64), rw)
     light = np.asarray(light, dtype=np.float64)
     g = np.asarray(g, dtype=np.float64)

@@ -462,6 +462,70 @@ def test_energy_keep_count_properties():
     assert mask[0, 0, 10:].all()
 
 
+# ---------------------------------------------------------------- CDF 9/7 (reading R33)
+# Analysis filters of the CDF 9/7 pair as published (the JPEG 2000 irreversible
+# filter bank): lowpass normalised to sum 1, highpass to centre value 1.115...
+CDF97_LOW_PUBLISHED = [0.026748757411, -0.016864118443, -0.078223266529, 0.266864118443, 0.602949018236,
+                       0.266864118443, -0.078223266529, -0.016864118443, 0.026748757411]
+CDF97_HIGH_PUBLISHED = [0.091271763114, -0.057543526229, -0.591271763114, 1.115087052457,
+                        -0.591271763114, -0.057543526229, 0.091271763114]
+
+
+def test_cdf97_lifting_reproduces_the_published_filters():
+    """The lifting steps (alpha..delta, zeta) compose to the published 9-tap / 7-tap analysis
+    filters, scaled by sqrt2 and 1/sqrt2 (DC gain sqrt2 of the low band, as for the Haar)."""
+    n = 32
+    low = np.array([O._lift_1d(np.eye(n)[p])[8] for p in range(n)])          # s_8: taps at x[12..20]
+    high = np.array([O._lift_1d(np.eye(n)[p])[16 + 8] for p in range(n)])    # d_8: taps at x[14..20]
+    assert np.allclose(low[12:21], np.sqrt(2) * np.array(CDF97_LOW_PUBLISHED), atol=1e-11)
+    assert np.abs(np.delete(low, range(12, 21))).max() < 1e-15
+    assert np.allclose(high[14:21], np.array(CDF97_HIGH_PUBLISHED) / np.sqrt(2), atol=1e-11)
+    assert np.abs(np.delete(high, range(14, 21))).max() < 1e-15
+
+
+def test_cdf97_moments_boundaries_and_reconstruction():
+    rng = np.random.default_rng(9)
+    i = np.arange(64, dtype=np.float64)
+    cubic = 0.3 - 0.02 * i + 1e-3 * i ** 2 - 2e-5 * i ** 3
+    y = O._lift_1d(cubic)
+    assert np.abs(y[32 + 3:64 - 3]).max() < 1e-12 * np.abs(cubic).max()   # 4 vanishing moments (interior)
+    const = O._lift_1d(np.full(16, 2.5))                                     # symmetric ends: exact at the borders
+    assert np.allclose(const[:8], 2.5 * np.sqrt(2), atol=1e-14) and np.abs(const[8:]).max() < 1e-14
+    x = rng.standard_normal((4, 16))
+    assert np.abs(O._unlift_1d(O._lift_1d(x)) - x).max() < 1e-14
+    img = rng.standard_normal((2, 32, 32))
+    assert np.abs(O.cdf97_inverse_2d(O.cdf97_forward_2d(img)) - img).max() < 1e-13
+    for nu in (1, 3, 4, 6):
+        X = rng.standard_normal((2, 10 * nu * nu + 2))
+        C = O.chart_to_cdf97(X, nu)
+        assert np.abs(O.cdf97_to_chart(C, nu) - X).max() < 1e-13
+        S = O.cdf97_synthesis_matrix(nu)
+        assert np.abs(C @ S.T - X).max() < 1e-13                            # B = S b^w as a matrix
+
+
+def test_cdf97_pyramid_matches_separable_filtering():
+    """One 2D level equals filtering rows then columns with the 1D analysis (an independent restatement
+    through the published taps with mirrored ends)."""
+    rng = np.random.default_rng(10)
+    img = rng.standard_normal((8, 8))
+    lo = np.sqrt(2) * np.array(CDF97_LOW_PUBLISHED)
+    hi = np.array(CDF97_HIGH_PUBLISHED) / np.sqrt(2)
+
+    def analyse(v):
+        n = v.size
+        ext = lambda q: v[abs(q) if q < n else 2 * (n - 1) - q]
+        low = [sum(lo[t] * ext(2 * i + t - 4) for t in range(9)) for i in range(n // 2)]
+        high = [sum(hi[t] * ext(2 * i + 1 + t - 3) for t in range(7)) for i in range(n // 2)]
+        return np.array(low + high)
+
+    rows = np.array([analyse(r) for r in img])
+    both = np.array([analyse(c) for c in rows.T]).T
+    level = O.cdf97_forward_2d(img)
+    # the first level touches everything; the pyramid then continues on the 4 x 4 low-low band
+    assert np.allclose(level[4:, :], both[4:, :], atol=1e-10) and np.allclose(level[:4, 4:], both[:4, 4:], atol=1e-10)
+    assert np.allclose(level[:4, :4], O.cdf97_forward_2d(both[:4, :4]), atol=1e-10)
+
+
 # ---------------------------------------------------------------- Steps 3-5 relight
 def test_relight_uncompressed_equals_direct_eq6(pca_basis_k16):
     f, _ = pca_basis_k16
