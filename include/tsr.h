@@ -225,6 +225,31 @@ tsr_status tsr_wavelet_compress(const float *Mw, int K, int J, int nu, double p,
 tsr_status tsr_haar_compress(const float *M, int K, int J, int nu, double p, tsr_compressed **out,
                              tsr_stream stream);
 tsr_status tsr_haar_recompress(const float *M, tsr_compressed *c, tsr_stream stream);
+/* The paper's Step-2 wavelet (Section 5, "Daubechies 9/7"): the CDF 9/7
+ * biorthogonal pair by lifting (whole-sample symmetric extension, low band DC
+ * gain sqrt 2), as the separable 2D Mallat pyramid of each chart's P x P image
+ * (row-major, pixel (r, c) = vertex d nu^2 + r nu + c, zero padding), every level
+ * transforming the rows, then the columns, of the low-low band down to 1 x 1;
+ * chart d's coefficients at [d P^2, (d+1) P^2), the poles last.  Same shapes as
+ * tsr_haar_forward / tsr_haar_inverse.  tsr_cdf97_inverse_transpose applies the
+ * transpose of the synthesis (the reverse mode of the relight; for this
+ * biorthogonal pair it differs from the analysis). */
+tsr_status tsr_cdf97_forward(const float *X, int rows, int nu, float *Xw, tsr_stream stream);
+tsr_status tsr_cdf97_inverse(const float *Xw, int rows, int nu, float *X, tsr_stream stream);
+tsr_status tsr_cdf97_inverse_transpose(const float *X, int rows, int nu, float *Xw, tsr_stream stream);
+
+#define TSR_WAVELET_HAAR 0
+#define TSR_WAVELET_CDF97 1
+#define TSR_KEEP_TOP_FRACTION 0
+#define TSR_KEEP_ENERGY 1
+/* Step 2 with either spatial wavelet and either keep rule: tsr_haar_compress is
+ * (TSR_WAVELET_HAAR, TSR_KEEP_TOP_FRACTION, p), tsr_haar_compress_energy is
+ * (TSR_WAVELET_HAAR, TSR_KEEP_ENERGY, energy).  The handle remembers its wavelet:
+ * tsr_relight and tsr_relight_backward invert (and transpose) the right one, and
+ * tsr_haar_recompress re-applies it (top-fraction handles only). */
+tsr_status tsr_compress(const float *M, int K, int J, int nu, int wavelet, int rule, double param,
+                        tsr_compressed **out, tsr_stream stream);
+
 /* Step 2 with the paper's energy threshold (Section 3, precompute Step 2: "the
  * reserved energy exceeds the threshold"; 95-98 % in its results): per (k, j)
  * the smallest n >= 1 such that the n largest |c| of the chart coefficients

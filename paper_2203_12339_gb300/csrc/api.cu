@@ -142,6 +142,62 @@ extern "C" tsr_status tsr_haar_compress_energy(const float *M, int K, int J, int
   return wavelet_compress_energy(static_cast<float *>(mw.p), K, J, nu, energy, out, s);
 }
 
+extern "C" tsr_status tsr_compress(const float *M, int K, int J, int nu, int wavelet, int rule, double param,
+                                   tsr_compressed **out, tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(M && out, "tsr_compress: NULL argument");
+  TSR_CHECK_ARG(K >= 1 && K <= 16 && J >= 1 && J <= 32, "tsr_compress: K=%d J=%d out of range", K, J);
+  TSR_CHECK_ARG(nu >= 1 && nu <= 128, "tsr_compress: nu=%d outside [1, 128]", nu);
+  TSR_CHECK_ARG(wavelet == TSR_WAVELET_HAAR || wavelet == TSR_WAVELET_CDF97, "tsr_compress: wavelet=%d unknown",
+                wavelet);
+  TSR_CHECK_ARG(rule == TSR_KEEP_TOP_FRACTION || rule == TSR_KEEP_ENERGY, "tsr_compress: rule=%d unknown", rule);
+  TSR_CHECK_ARG(rule == TSR_KEEP_TOP_FRACTION ? (param >= 0.0 && param <= 1.0) : (param > 0.0 && param <= 1.0),
+                "tsr_compress: param=%g out of range for the rule", param);
+  *out = nullptr;
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  const int P = chart_side(nu);
+  Scratch mw;
+  st = mw.alloc(sizeof(float) * (size_t)K * J * (10 * P * P + 2), s);
+  if (st != TSR_OK) return st;
+  float *Mw = static_cast<float *>(mw.p);
+  st = spatial_forward(wavelet, M, K * J, nu, Mw, s);
+  if (st != TSR_OK) return st;
+  st = (rule == TSR_KEEP_ENERGY) ? wavelet_compress_energy(Mw, K, J, nu, param, out, s)
+                                 : wavelet_compress(Mw, K, J, nu, param, out, s);
+  if (st == TSR_OK) (*out)->wavelet = wavelet;
+  return st;
+}
+
+extern "C" tsr_status tsr_cdf97_forward(const float *X, int rows, int nu, float *Xw, tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(X && Xw, "tsr_cdf97_forward: NULL argument");
+  TSR_CHECK_ARG(rows >= 1 && nu >= 1 && nu <= 128, "tsr_cdf97_forward: rows=%d nu=%d out of range", rows, nu);
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  return cdf97_forward(X, rows, nu, Xw, as_stream(stream));
+}
+
+extern "C" tsr_status tsr_cdf97_inverse(const float *Xw, int rows, int nu, float *X, tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(X && Xw, "tsr_cdf97_inverse: NULL argument");
+  TSR_CHECK_ARG(rows >= 1 && nu >= 1 && nu <= 128, "tsr_cdf97_inverse: rows=%d nu=%d out of range", rows, nu);
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  return cdf97_inverse(Xw, rows, nu, X, as_stream(stream));
+}
+
+extern "C" tsr_status tsr_cdf97_inverse_transpose(const float *X, int rows, int nu, float *Xw, tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(X && Xw, "tsr_cdf97_inverse_transpose: NULL argument");
+  TSR_CHECK_ARG(rows >= 1 && nu >= 1 && nu <= 128, "tsr_cdf97_inverse_transpose: rows=%d nu=%d out of range", rows,
+                nu);
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  return cdf97_inverse_transpose(X, rows, nu, Xw, as_stream(stream));
+}
+
 extern "C" tsr_status tsr_haar_recompress(const float *M, tsr_compressed *c, tsr_stream stream) {
   clear_error();
   TSR_CHECK_ARG(M && c, "tsr_haar_recompress: NULL argument");
@@ -151,7 +207,7 @@ extern "C" tsr_status tsr_haar_recompress(const float *M, tsr_compressed *c, tsr
   Scratch mw;
   st = mw.alloc(sizeof(float) * (size_t)c->K * c->J * c->n_rows, s);
   if (st != TSR_OK) return st;
-  st = haar_forward(M, c->K * c->J, c->nu, static_cast<float *>(mw.p), s);
+  st = spatial_forward(c->wavelet, M, c->K * c->J, c->nu, static_cast<float *>(mw.p), s);
   if (st != TSR_OK) return st;
   return wavelet_compress_into(static_cast<float *>(mw.p), c, s);
 }

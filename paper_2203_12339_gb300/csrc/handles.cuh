@@ -29,6 +29,7 @@ struct tsr_compressed {
   int K = 0, J = 0, nu = 0, P = 0, n_rows = 0;
   int n_keep = 0;               // per (k, j) under the top-p rule; -1 under the energy rule
   int keep_rule = 0;            // 0: top-p fraction, 1: energy threshold
+  int wavelet = 0;              // 0: orthonormal Haar over the Morton order, 1: CDF 9/7 2D pyramid
   int64_t nnz = 0;
   int64_t *row_ptr = nullptr;   // [n_rows + 1]
   uint16_t *col = nullptr;      // [nnz]  k*J + j
@@ -74,6 +75,14 @@ tsr_status transfer_fp32_batched(const tsr_basis *b, int n_mesh, const int64_t *
                                  const float *area, const float *T, int J, float *M, cudaStream_t s);
 tsr_status haar_forward(const float *X, int rows, int nu, float *Xw, cudaStream_t s);
 tsr_status haar_inverse(const float *Xw, int rows, int nu, float *X, cudaStream_t s);
+tsr_status cdf97_forward(const float *X, int rows, int nu, float *Xw, cudaStream_t s);
+tsr_status cdf97_inverse(const float *Xw, int rows, int nu, float *X, cudaStream_t s);
+tsr_status cdf97_inverse_transpose(const float *X, int rows, int nu, float *Xw, cudaStream_t s);
+// The spatial transform of wavelet 0 (Haar) or 1 (CDF 9/7): analysis, synthesis, and the
+// transpose of the synthesis (for the orthonormal Haar, the analysis).
+tsr_status spatial_forward(int wavelet, const float *X, int rows, int nu, float *Xw, cudaStream_t s);
+tsr_status spatial_inverse(int wavelet, const float *Xw, int rows, int nu, float *X, cudaStream_t s);
+tsr_status spatial_inverse_transpose(int wavelet, const float *X, int rows, int nu, float *Xw, cudaStream_t s);
 tsr_status wavelet_compress(const float *Mw, int K, int J, int nu, double p, tsr_compressed **out,
                             cudaStream_t s);
 tsr_status wavelet_compress_into(const float *Mw, tsr_compressed *c, cudaStream_t s);

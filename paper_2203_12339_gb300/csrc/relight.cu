@@ -13,10 +13,11 @@
 // RL_DV vectors (one or two edits) take Steps 4-5 as written instead, which
 // moves less data for so few outputs.
 //
-// Reverse, for an upstream gradient dL/dB (w_1 is orthonormal, so the adjoint of
-// w_1^{-1} is w_1):
+// Reverse, for an upstream gradient dL/dB (with w_1^{-T} the transpose of the
+// synthesis: the analysis w_1 itself for the orthonormal Haar, the transposed
+// lifting steps for CDF 9/7):
 //   dg_v[k] = <dL/dB_v, Z[k]>
-//   Q[k]    = sum_v g_v[k] dL/dB_v,   R[k] = w_1 Q[k]
+//   Q[k]    = sum_v g_v[k] dL/dB_v,   R[k] = w_1^{-T} Q[k]
 //   dl[j]   = sum_k sum_w S[w][kj] R[k][w]
 #include <algorithm>
 
@@ -280,7 +281,7 @@ static tsr_status relight_basis_images(const tsr_compressed *c, const float *l, 
   relight_y_kernel<<<(c->n_rows + 7) / 8, 256, 0, s>>>(c->row_ptr, c->col, c->val, c->n_rows, c->J, l, Y);
   ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
-  return haar_inverse(Y, c->K, c->nu, Z, s);
+  return spatial_inverse(c->wavelet, Y, c->K, c->nu, Z, s);
 }
 
 size_t relight_scratch_floats(const tsr_compressed *c) {
@@ -299,7 +300,7 @@ tsr_status relight_with_scratch(const tsr_compressed *c, int n_edit, const float
     else
       launch_direct<6>(c, g, l, scratch, s);   // V = 3 n_edit <= RL_DV: 3 or 6
     TSR_CUDA(cudaGetLastError());
-    return haar_inverse(scratch, V, c->nu, B, s);
+    return spatial_inverse(c->wavelet, scratch, V, c->nu, B, s);
   }
   float *Y = scratch, *Z = scratch + (size_t)c->K * c->n_rows;
   tsr_status st = relight_basis_images(c, l, Y, Z, s);
@@ -335,7 +336,7 @@ tsr_status relight_backward(const tsr_compressed *c, int n_edit, const float *g,
   relight_q_kernel<<<dim3((N + 255) / 256, RL_QS), 256, 0, s>>>(dLdB, N, K, V, g, Qp); ::tsr::count_launch();
   relight_qsum_kernel<<<4 * num_sms(), 256, 0, s>>>(Qp, nZ, Q); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
-  st = haar_forward(Q, K, c->nu, R, s);
+  st = spatial_inverse_transpose(c->wavelet, Q, K, c->nu, R, s);
   if (st != TSR_OK) return st;
   relight_colsum_kernel<<<KJ, 256, 0, s>>>(c->cidx, c->cval, c->col_ptr, c->n_rows, J, R, colsum);
   ::tsr::count_launch();

@@ -54,6 +54,10 @@ _SIGNATURES = {
     "tsr_wavelet_compress": (_I, [_P, _I, _I, _I, _D, ctypes.POINTER(_P), _P]),
     "tsr_haar_compress": (_I, [_P, _I, _I, _I, _D, ctypes.POINTER(_P), _P]),
     "tsr_haar_compress_energy": (_I, [_P, _I, _I, _I, _D, ctypes.POINTER(_P), _P]),
+    "tsr_compress": (_I, [_P, _I, _I, _I, _I, _I, _D, ctypes.POINTER(_P), _P]),
+    "tsr_cdf97_forward": (_I, [_P, _I, _I, _P, _P]),
+    "tsr_cdf97_inverse": (_I, [_P, _I, _I, _P, _P]),
+    "tsr_cdf97_inverse_transpose": (_I, [_P, _I, _I, _P, _P]),
     "tsr_haar_recompress": (_I, [_P, _P, _P]),
     "tsr_compressed_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
                                  ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_I)]),
@@ -319,6 +323,31 @@ def haar_inverse(Xw: torch.Tensor, nu: int) -> torch.Tensor:
     return X.reshape(Xw.shape[:-1] + (10 * nu * nu + 2,))
 
 
+def _chart_op(fn, x_in: torch.Tensor, n_in: int, n_out: int, nu: int) -> torch.Tensor:
+    x = _dev(x_in, torch.float32, name="input").reshape(-1, n_in)
+    y = torch.empty((x.shape[0], n_out), dtype=torch.float32, device=x.device)
+    _check(fn(_ptr(x), x.shape[0], nu, _ptr(y), _stream()))
+    return y.reshape(x_in.shape[:-1] + (n_out,))
+
+
+def cdf97_forward(X: torch.Tensor, nu: int) -> torch.Tensor:
+    """tsr_cdf97_forward: X [rows][10 nu^2 + 2] -> Xw [rows][10 P^2 + 2] (CDF 9/7 pyramid per chart)."""
+    P = chart_side(nu)
+    return _chart_op(lib().tsr_cdf97_forward, X, 10 * nu * nu + 2, 10 * P * P + 2, nu)
+
+
+def cdf97_inverse(Xw: torch.Tensor, nu: int) -> torch.Tensor:
+    """tsr_cdf97_inverse: the synthesis, Xw [rows][10 P^2 + 2] -> X [rows][10 nu^2 + 2]."""
+    P = chart_side(nu)
+    return _chart_op(lib().tsr_cdf97_inverse, Xw, 10 * P * P + 2, 10 * nu * nu + 2, nu)
+
+
+def cdf97_inverse_transpose(X: torch.Tensor, nu: int) -> torch.Tensor:
+    """tsr_cdf97_inverse_transpose: the transpose of the synthesis, X [rows][N] -> [rows][10 P^2 + 2]."""
+    P = chart_side(nu)
+    return _chart_op(lib().tsr_cdf97_inverse_transpose, X, 10 * nu * nu + 2, 10 * P * P + 2, nu)
+
+
 class Compressed:
     """Compressed wavelet transfer (CSR over wavelet rows; owned by the library)."""
 
@@ -392,6 +421,20 @@ def haar_compress_energy(M: torch.Tensor, nu: int, energy: float) -> Compressed:
     m = _dev(M, torch.float32, (K, J, 10 * nu * nu + 2), "M")
     h = _P()
     _check(lib().tsr_haar_compress_energy(_ptr(m), K, J, nu, float(energy), ctypes.byref(h), _stream()))
+    return Compressed(h)
+
+
+WAVELETS = {"haar": 0, "cdf97": 1}
+KEEP_RULES = {"top": 0, "energy": 1}
+
+
+def compress(M: torch.Tensor, nu: int, wavelet: str = "haar", rule: str = "top", param: float = 0.1) -> Compressed:
+    """tsr_compress: Step 2 with the Haar or CDF 9/7 spatial wavelet and the top-fraction or energy keep rule."""
+    K, J, N = M.shape
+    m = _dev(M, torch.float32, (K, J, 10 * nu * nu + 2), "M")
+    h = _P()
+    _check(lib().tsr_compress(_ptr(m), K, J, nu, WAVELETS[wavelet], KEEP_RULES[rule], float(param), ctypes.byref(h),
+                              _stream()))
     return Compressed(h)
 
 

@@ -223,6 +223,78 @@ def test_haar_forward_inverse(torch_cuda, tsr, nu):
     assert np.max(np.abs(back - X)) <= 2e-6 * np.max(np.abs(X))
 
 
+@pytest.mark.parametrize("nu", [1, 2, 3, 5, 8, 16, 33, 64, 128])
+def test_cdf97_forward_inverse(torch_cuda, tsr, nu):
+    """The paper's Step-2 wavelet (CDF 9/7): analysis and synthesis against the oracle's lifting."""
+    torch = torch_cuda
+    rng = np.random.default_rng(200 + nu)
+    X = rng.standard_normal((5, 10 * nu * nu + 2)).astype(np.float32)
+    Xw = tsr.cdf97_forward(_dev(torch, X), nu).cpu().numpy()
+    ref = O.chart_to_cdf97(X, nu)
+    assert np.max(np.abs(Xw - ref)) <= 2e-6 * np.max(np.abs(ref))
+    back = tsr.cdf97_inverse(_dev(torch, ref.astype(np.float32)), nu).cpu().numpy()
+    assert np.max(np.abs(back - X)) <= 2e-6 * np.max(np.abs(X))
+
+
+@pytest.mark.parametrize("nu", [1, 2, 3, 4, 6, 8])
+def test_cdf97_inverse_transpose_matches_the_matrix(torch_cuda, tsr, nu):
+    """S^T (the reverse mode of the relight) against the transpose of the oracle's explicit synthesis matrix."""
+    torch = torch_cuda
+    rng = np.random.default_rng(300 + nu)
+    dB = rng.standard_normal((4, 10 * nu * nu + 2)).astype(np.float32)
+    got = tsr.cdf97_inverse_transpose(_dev(torch, dB), nu).cpu().numpy()
+    want = dB.astype(np.float64) @ O.cdf97_synthesis_matrix(nu)
+    assert np.max(np.abs(got - want)) <= 2e-6 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("nu", [16, 64, 128])
+def test_cdf97_adjoint_identity(torch_cuda, tsr, nu):
+    """<S c, y> = <c, S^T y> between the GPU synthesis and its transpose (sizes the explicit matrix cannot reach)."""
+    torch = torch_cuda
+    rng = np.random.default_rng(400 + nu)
+    P = O.chart_side(nu)
+    c = rng.standard_normal((3, 10 * P * P + 2)).astype(np.float32)
+    y = rng.standard_normal((3, 10 * nu * nu + 2)).astype(np.float32)
+    Sc = tsr.cdf97_inverse(_dev(torch, c), nu).cpu().numpy().astype(np.float64)
+    STy = tsr.cdf97_inverse_transpose(_dev(torch, y), nu).cpu().numpy().astype(np.float64)
+    lhs = np.sum(Sc * y, axis=1)
+    rhs = np.sum(c * STy, axis=1)
+    scale = np.sqrt(np.sum(Sc ** 2, axis=1) * np.sum(y ** 2, axis=1))
+    assert np.max(np.abs(lhs - rhs) / scale) <= 1e-6
+
+
+def test_cdf97_compress_relight_and_adjoint(torch_cuda, tsr):
+    """Step 2 with CDF 9/7 (top fraction and energy rules): kept sets equal the oracle's on the GPU's
+    own coefficients; relight and its adjoint against the oracle in the same wavelet."""
+    torch = torch_cuda
+    nu, K, J, E = 8, 5, 9, 3
+    N = 10 * nu * nu + 2
+    rng = np.random.default_rng(31)
+    M = (rng.standard_normal((K, J, N)) * np.exp(-np.arange(N) % 64 / 16.0)).astype(np.float32)
+    Md = _dev(torch, M)
+    Mw = tsr.cdf97_forward(Md.reshape(K * J, N), nu).reshape(K, J, -1).cpu().numpy()
+    n_rows = Mw.shape[-1]
+    g = rng.standard_normal((E, 3, K)).astype(np.float32)
+    light = rng.standard_normal(J).astype(np.float32)
+    dB = rng.standard_normal((E, 3, N)).astype(np.float32)
+    for rule, param, want in (("top", 0.1, O.select_top(Mw, nu, 0.1)), ("energy", 0.97, O.select_energy(Mw, nu, 0.97))):
+        comp = tsr.compress(Md, nu, "cdf97", rule, param)
+        row_ptr, col, _ = (t.cpu().numpy() for t in comp.export())
+        got = _mask_from_csr(row_ptr, col, n_rows, K * J).reshape(K, J, n_rows)
+        assert np.array_equal(got, want), rule
+        kept = np.where(got, Mw.astype(np.float64), 0.0)
+        B = tsr.relight(comp, _dev(torch, g), _dev(torch, light)).cpu().numpy()
+        B_ref = O.relight(kept, nu, g.astype(np.float64), light.astype(np.float64), wavelet="cdf97")
+        assert np.max(np.abs(B - B_ref)) <= 1e-5 * np.max(np.abs(B_ref))
+        B1 = tsr.relight(comp, _dev(torch, g[:1]), _dev(torch, light)).cpu().numpy()   # direct path (3 vectors)
+        assert np.max(np.abs(B1 - B_ref[:1])) <= 1e-5 * np.max(np.abs(B_ref[:1]))
+        dg, dl = tsr.relight_backward(comp, _dev(torch, g), _dev(torch, light), _dev(torch, dB))
+        dg_ref, dl_ref = O.relight_vjp(kept, nu, g.astype(np.float64), light.astype(np.float64),
+                                       dB.astype(np.float64), wavelet="cdf97")
+        assert np.max(np.abs(dg.cpu().numpy() - dg_ref)) <= 1e-5 * np.max(np.abs(dg_ref))
+        assert np.max(np.abs(dl.cpu().numpy() - dl_ref)) <= 1e-5 * np.max(np.abs(dl_ref))
+
+
 # ------------------------------------------------------------------ Step 2 selection (bit-exact)
 def _mask_from_csr(row_ptr, col, n_rows, KJ):
     mask = np.zeros((KJ, n_rows), dtype=bool)
