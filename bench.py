@@ -217,6 +217,20 @@ def energy_keep_curve(tsr, M, nu, g32, light) -> list:
     return out
 
 
+def wavelet_comparison(tsr, M, nu, g32, light) -> list:
+    """Relight error against keeping every coefficient, Haar vs the paper's CDF 9/7, at equal
+    numbers of kept coefficients (top fraction per (k, j))."""
+    full = tsr.relight(tsr.compress(M, nu, "haar", "top", 1.0), g32, light)
+    out = []
+    for p in (0.01, 0.05, 0.10):
+        row = {"kept": p}
+        for wname in ("haar", "cdf97"):
+            B = tsr.relight(tsr.compress(M, nu, wname, "top", p), g32, light)
+            row[wname + "_rel_error"] = round(float(((B - full).norm() / full.norm()).item()), 6)
+        out.append(row)
+    return out
+
+
 def _smem_roofline(gather_bytes: float, ms: float, peaks: dict) -> dict:
     """Shared-memory gather roofline of the transfer kernel (algorithmic table bytes per launch / time)."""
     import torch
@@ -455,6 +469,7 @@ def run_gpu(args):
     }
     _, g32_curve, _ = tsr.project_material(basis, d["sa"], d["ss"], d["eta"])
     line["energy_keep_curve"] = energy_keep_curve(tsr, M, nu, g32_curve, d["light"])
+    line["wavelet_comparison"] = wavelet_comparison(tsr, M, nu, g32_curve, d["light"])
     if not args.no_frame_1080p:
         line["relight_frame_1080p"] = relight_frame_1080p(tsr, dev, peaks)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
