@@ -40,6 +40,11 @@ design notes):
   R22 the spatial wavelet is the orthonormal Haar.
   R23 keep rule: per (k, j), the round(p * 10 P^2) largest |coefficients| of the
       charts (ties: lower index); the two pole values are always kept.
+  R34 F_t(eta, omega) = 1 - exact unpolarised Fresnel reflectance (relative index
+      eta, outside cosine mu), 0 for mu <= 0; the output factor (1/pi) F_t(eta, omega_o)
+      of Eq. 6 uses the caller's per-vertex cosine n_o . omega_o.
+  R35 the incident F_t(eta, omega_i) is folded into the SH transfer T through the
+      zonal coefficients A_l(eta) (Funk-Hecke) at the precompute's eta.
   R33 the paper's Step-2 wavelet "Daubechies 9/7": the biorthogonal CDF 9/7 pair
       by lifting (symmetric extension, low band DC gain sqrt 2), separable 2D
       Mallat pyramid of each chart's P x P image down to 1 x 1.
@@ -338,6 +343,84 @@ def wavelet_to_chart(C, nu):
         out[..., d * nu * nu:(d + 1) * nu * nu] = dom[..., mort]
     out[..., 10 * nu * nu:] = C[..., 10 * P * P:]
     return out
+
+
+# ---------------------------------------------------------------- Fresnel transmittance
+def fresnel_transmittance(eta, mu):
+    """F_t(eta, omega) of Eq. 3 and Eq. 6 under reading R34: one minus the exact unpolarised
+    Fresnel reflectance of a dielectric boundary of relative index eta, for a direction outside at
+    cosine mu to the normal (by reciprocity the same for light leaving towards omega); 0 for mu <= 0."""
+    mu = np.asarray(mu)
+    eta = np.asarray(eta)
+    mpos = np.where(np.real(mu) > 0, mu, 1.0)
+    ct = np.sqrt(1.0 - (1.0 - mpos * mpos) / (eta * eta))          # cosine of the refracted ray
+    rs = (mpos - eta * ct) / (mpos + eta * ct)
+    rp = (eta * mpos - ct) / (eta * mpos + ct)
+    Ft = 1.0 - 0.5 * (rs * rs + rp * rp)
+    return np.where(np.real(mu) > 0, Ft, 0.0)
+
+
+def fresnel_transmittance_deta(eta, mu):
+    """Hand derivative dF_t/deta of fresnel_transmittance (0 for mu <= 0)."""
+    mu = np.asarray(mu, dtype=np.float64)
+    eta = np.asarray(eta, dtype=np.float64)
+    mpos = np.where(mu > 0, mu, 1.0)
+    q = 1.0 - mpos * mpos
+    ct = np.sqrt(1.0 - q / (eta * eta))
+    dct = q / (eta ** 3 * ct)
+    a, da = eta * ct, ct + eta * dct
+    rs = (mpos - a) / (mpos + a)
+    drs = -2.0 * mpos * da / (mpos + a) ** 2
+    u, w = eta * mpos - ct, eta * mpos + ct
+    rp = u / w
+    drp = ((mpos - dct) * w - u * (mpos + dct)) / (w * w)
+    return np.where(mu > 0, -(rs * drs + rp * drp), 0.0)
+
+
+def fresnel_output(B, eta, cos_o):
+    """Eq. 6's view-dependent factor (1/pi) F_t(eta, omega_o) applied to B (E, 3, N), per edit eta (E,)
+    and per output vertex cos_o (N,) = n_o . omega_o."""
+    fac = fresnel_transmittance(np.asarray(eta, dtype=np.float64)[:, None], np.asarray(cos_o, dtype=np.float64)[None, :])
+    return np.asarray(B, dtype=np.float64) * (fac / math.pi)[:, None, :]
+
+
+def fresnel_output_vjp(B, eta, cos_o, dBout):
+    """Reverse mode of fresnel_output: (dL/dB (E,3,N), dL/deta (E,))."""
+    eta = np.asarray(eta, dtype=np.float64)[:, None]
+    cos_o = np.asarray(cos_o, dtype=np.float64)[None, :]
+    fac = fresnel_transmittance(eta, cos_o) / math.pi
+    dfac = fresnel_transmittance_deta(eta, cos_o) / math.pi
+    dBout = np.asarray(dBout, dtype=np.float64)
+    dB = dBout * fac[:, None, :]
+    deta = np.einsum("eco,eco,eo->e", dBout, np.asarray(B, dtype=np.float64), dfac)
+    return dB, deta
+
+
+def sh_zonal_fresnel(eta, order):
+    """Zonal coefficients of h(mu) = F_t(eta, mu) max(mu, 0) (reading R35):
+    A_l = 2 pi int_0^1 F_t(eta, mu) mu P_l(mu) dmu, l < order, so that by the Funk-Hecke theorem
+    int Y_lm(w) h(n . w) dw = A_l Y_lm(n).  eta = 1 gives the clamped cosine."""
+    from scipy.integrate import quad
+    from numpy.polynomial import legendre
+    out = np.empty(order)
+    for l in range(order):
+        Pl = legendre.Legendre.basis(l)
+        val, _ = quad(lambda m: float(fresnel_transmittance(eta, m)) * m * Pl(m), 0.0, 1.0,
+                      limit=400, epsabs=1e-13, epsrel=1e-13)
+        out[l] = 2.0 * math.pi * val
+    return out
+
+
+def sh_transfer_fresnel(normals, J, eta):
+    """T[j, i] = A_l(eta) Y_lm(n_i): the unshadowed irradiance transfer with the incident Fresnel
+    transmittance folded in (Eq. 6 with F_t(eta, omega_i) inside E; readings R18, R19, R35)."""
+    from paper_2203_12339_gb300.scene import sh_real
+    order = int(round(math.sqrt(J)))
+    Y = sh_real(order, np.asarray(normals, dtype=np.float64))
+    A = sh_zonal_fresnel(eta, order)
+    for l in range(order):
+        Y[l * l:(l + 1) * (l + 1)] *= A[l]
+    return Y
 
 
 # ---------------------------------------------------------------- CDF 9/7 spatial wavelet

@@ -462,6 +462,78 @@ def test_energy_keep_count_properties():
     assert mask[0, 0, 10:].all()
 
 
+# ---------------------------------------------------------------- Fresnel factors (readings R34, R35)
+@pytest.mark.parametrize("eta", [1.2, 1.3, 1.5])
+def test_fresnel_transmittance_limits(eta):
+    mu = np.linspace(1e-6, 1.0, 2001)
+    Ft = O.fresnel_transmittance(eta, mu)
+    assert np.all(np.diff(Ft) > 0)                                                    # rises towards the normal
+    assert Ft[-1] == pytest.approx(1 - ((eta - 1) / (eta + 1)) ** 2, rel=1e-14)      # normal incidence
+    assert O.fresnel_transmittance(eta, 1e-9) < 1e-7                                 # grazing: everything reflected
+    assert O.fresnel_transmittance(eta, -0.3) == 0.0 and O.fresnel_transmittance(eta, 0.0) == 0.0
+    assert np.allclose(O.fresnel_transmittance(1.0, mu), 1.0, atol=1e-15)            # matched index
+
+
+def test_fresnel_transmittance_derivative_by_complex_step():
+    mu = np.array([0.05, 0.3, 0.7, 1.0])
+    for eta in (1.15, 1.3, 1.6):
+        h = 1e-30
+        cs = np.imag(O.fresnel_transmittance(eta + 1j * h, mu.astype(complex))) / h
+        assert np.allclose(O.fresnel_transmittance_deta(eta, mu), cs, rtol=1e-11, atol=1e-14)
+
+
+def test_fresnel_output_vjp_matches_finite_differences():
+    rng = np.random.default_rng(12)
+    E, N = 2, 7
+    B = rng.standard_normal((E, 3, N))
+    eta = np.array([1.25, 1.45])
+    cos_o = np.array([0.9, 0.4, -0.2, 0.05, 1.0, 0.7, 0.0])
+    W = rng.standard_normal((E, 3, N))
+    L = lambda B_, e_: float(np.sum(W * O.fresnel_output(B_, e_, cos_o)))
+    dB, deta = O.fresnel_output_vjp(B, eta, cos_o, W)
+    h = 1e-6
+    for e in range(E):
+        ep, em = eta.copy(), eta.copy()
+        ep[e] += h
+        em[e] -= h
+        assert deta[e] == pytest.approx((L(B, ep) - L(B, em)) / (2 * h), rel=1e-7)
+    Bp = B.copy()
+    Bp[1, 2, 3] += 1.0
+    assert dB[1, 2, 3] == pytest.approx(L(Bp, eta) - L(B, eta), rel=1e-12)
+
+
+def test_sh_zonal_fresnel_reduces_to_the_clamped_cosine():
+    A = O.sh_zonal_fresnel(1.0, 5)
+    assert np.allclose(A, [math.pi, 2 * math.pi / 3, math.pi / 4, 0.0, -math.pi / 24], atol=1e-12)
+    normals = scene.icosphere(2, 0.0, 3, 0).normal
+    assert np.allclose(O.sh_transfer_fresnel(normals, 16, 1.0), scene.sh_transfer(normals, 16), atol=1e-12)
+
+
+def test_sh_transfer_fresnel_by_direct_integration():
+    """T_j(n) = int Y_j(w) F_t(eta, n.w) max(n.w, 0) dw integrated over the hemisphere around n
+    (Gauss-Legendre in n.w, uniform in azimuth), against A_l(eta) Y_j(n) (Funk-Hecke)."""
+    eta, order = 1.4, 5
+    x, wq = np.polynomial.legendre.leggauss(96)
+    mu = 0.5 * (x + 1.0)
+    wmu = 0.5 * wq
+    phi = np.arange(128) * (2 * math.pi / 128)
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        n = rng.standard_normal(3)
+        n /= np.linalg.norm(n)
+        t1 = np.cross(n, [0.3, 0.5, 0.8])
+        t1 /= np.linalg.norm(t1)
+        t2 = np.cross(n, t1)
+        M, F = np.meshgrid(mu, phi, indexing="ij")
+        st = np.sqrt(1 - M ** 2)
+        dirs = (M[..., None] * n + (st * np.cos(F))[..., None] * t1 + (st * np.sin(F))[..., None] * t2).reshape(-1, 3)
+        Y = scene.sh_real(order, dirs)                                        # (25, n_dirs)
+        weight = (np.outer(wmu, np.full(phi.size, 2 * math.pi / phi.size)) * O.fresnel_transmittance(eta, M) * M).reshape(-1)
+        direct = Y @ weight
+        want = O.sh_transfer_fresnel(n[None, :], order * order, eta)[:, 0]
+        assert np.allclose(direct, want, atol=1e-9)
+
+
 # ---------------------------------------------------------------- CDF 9/7 (reading R33)
 # Analysis filters of the CDF 9/7 pair as published (the JPEG 2000 irreversible
 # filter bank): lowpass normalised to sum 1, highpass to centre value 1.115...
