@@ -270,6 +270,29 @@ tsr_status tsr_compressed_export(const tsr_compressed *c, int64_t *row_ptr, uint
 void tsr_compressed_destroy(tsr_compressed *c);
 
 /* ------------------------------------------------------------------------
+ * Fresnel transmittance factors of Eq. 3 and Eq. 6,
+ *   S = (1/pi) F_t(eta, w_i) R_d F_t(eta, w_o),
+ * F_t(eta, mu) = 1 - (r_s^2 + r_p^2)/2, the exact unpolarised dielectric Fresnel
+ * reflectance for a direction at cosine mu > 0 outside (0 for mu <= 0).
+ * tsr_fresnel_output: Bout[e][c][o] = (1/pi) F_t(eta[e], cos_o[o]) B[e][c][o]
+ *   (eta: device [n_edit] FP64; cos_o: device [N] FP32, the caller's n_o . w_o per
+ *   output vertex; B, Bout: device [n_edit][3][N] FP32, may alias).
+ * tsr_fresnel_output_backward: dB = (1/pi) F_t dBout and
+ *   deta[e] = sum_{c,o} dBout B (1/pi) dF_t/deta (device [n_edit] FP32, overwritten).
+ * tsr_sh_transfer: the unshadowed SH irradiance transfer with the incident F_t
+ *   folded in, T[j][i] = A_l(eta) Y_lm(n_i) (real orthonormal SH, j = l^2 + l + m,
+ *   no Condon-Shortley phase), A_l(eta) = 2 pi int_0^1 F_t(eta, mu) mu P_l(mu) dmu
+ *   (Funk-Hecke; eta = 1 gives the clamped cosine pi, 2pi/3, pi/4, 0, -pi/24).
+ *   normals: device [3][N] FP32 unit vectors; J in {1, 4, 9, 16, 25}; eta in
+ *   [1, 2]; T: device [J][N] FP32 out.
+ * ---------------------------------------------------------------------- */
+tsr_status tsr_fresnel_output(int n_edit, const double *eta, int N, const float *cos_o, const float *B, float *Bout,
+                              tsr_stream stream);
+tsr_status tsr_fresnel_output_backward(int n_edit, const double *eta, int N, const float *cos_o, const float *B,
+                                       const float *dBout, float *dB, float *deta, tsr_stream stream);
+tsr_status tsr_sh_transfer(int N, const float *normals, int J, double eta, float *T, tsr_stream stream);
+
+/* ------------------------------------------------------------------------
  * Relight / material edit (Section 4, rendering Steps 3-5):
  *   b^w[e][c][w] = sum_{(kj,v) in row w} v * g[e][c][k] * l[j]
  *   B[e][c][.]   = W^-1 b^w[e][c][.]         (inverse Haar per chart)

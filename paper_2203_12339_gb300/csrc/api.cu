@@ -198,6 +198,42 @@ extern "C" tsr_status tsr_cdf97_inverse_transpose(const float *X, int rows, int 
   return cdf97_inverse_transpose(X, rows, nu, Xw, as_stream(stream));
 }
 
+extern "C" tsr_status tsr_fresnel_output(int n_edit, const double *eta, int N, const float *cos_o, const float *B,
+                                         float *Bout, tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(eta && cos_o && B && Bout, "tsr_fresnel_output: NULL argument");
+  TSR_CHECK_ARG(n_edit >= 0 && n_edit <= (1 << 20) && N >= 1, "tsr_fresnel_output: n_edit=%d N=%d out of range",
+                n_edit, N);
+  TSR_CHECK_ARG(aligned(cos_o, 4) && aligned(B, 4) && aligned(Bout, 4) && aligned(eta, 8),
+                "tsr_fresnel_output: misaligned pointer");
+  tsr_status st = require_device();
+  if (st != TSR_OK || n_edit == 0) return st;
+  return fresnel_output(n_edit, eta, N, cos_o, B, Bout, as_stream(stream));
+}
+
+extern "C" tsr_status tsr_fresnel_output_backward(int n_edit, const double *eta, int N, const float *cos_o,
+                                                  const float *B, const float *dBout, float *dB, float *deta,
+                                                  tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(eta && cos_o && B && dBout && dB && deta, "tsr_fresnel_output_backward: NULL argument");
+  TSR_CHECK_ARG(n_edit >= 1 && n_edit <= (1 << 20) && N >= 1,
+                "tsr_fresnel_output_backward: n_edit=%d N=%d out of range", n_edit, N);
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  return fresnel_output_backward(n_edit, eta, N, cos_o, B, dBout, dB, deta, as_stream(stream));
+}
+
+extern "C" tsr_status tsr_sh_transfer(int N, const float *normals, int J, double eta, float *T, tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(normals && T, "tsr_sh_transfer: NULL argument");
+  TSR_CHECK_ARG(N >= 1, "tsr_sh_transfer: N=%d", N);
+  TSR_CHECK_ARG(J == 1 || J == 4 || J == 9 || J == 16 || J == 25, "tsr_sh_transfer: J=%d is not a square <= 25", J);
+  TSR_CHECK_ARG(eta >= 1.0 && eta <= 2.0, "tsr_sh_transfer: eta=%g outside [1, 2]", eta);
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  return sh_transfer(N, normals, J, eta, T, as_stream(stream));
+}
+
 extern "C" tsr_status tsr_haar_recompress(const float *M, tsr_compressed *c, tsr_stream stream) {
   clear_error();
   TSR_CHECK_ARG(M && c, "tsr_haar_recompress: NULL argument");

@@ -80,6 +80,11 @@ tsr_status cdf97_inverse(const float *Xw, int rows, int nu, float *X, cudaStream
 tsr_status cdf97_inverse_transpose(const float *X, int rows, int nu, float *Xw, cudaStream_t s);
 // The spatial transform of wavelet 0 (Haar) or 1 (CDF 9/7): analysis, synthesis, and the
 // transpose of the synthesis (for the orthonormal Haar, the analysis).
+tsr_status fresnel_output(int E, const double *eta, int N, const float *cos_o, const float *B, float *Bout,
+                          cudaStream_t s);
+tsr_status fresnel_output_backward(int E, const double *eta, int N, const float *cos_o, const float *B,
+                                   const float *dBout, float *dB, float *deta, cudaStream_t s);
+tsr_status sh_transfer(int N, const float *normals, int J, double eta, float *T, cudaStream_t s);
 tsr_status spatial_forward(int wavelet, const float *X, int rows, int nu, float *Xw, cudaStream_t s);
 tsr_status spatial_inverse(int wavelet, const float *Xw, int rows, int nu, float *X, cudaStream_t s);
 tsr_status spatial_inverse_transpose(int wavelet, const float *X, int rows, int nu, float *Xw, cudaStream_t s);

@@ -55,6 +55,9 @@ _SIGNATURES = {
     "tsr_haar_compress": (_I, [_P, _I, _I, _I, _D, ctypes.POINTER(_P), _P]),
     "tsr_haar_compress_energy": (_I, [_P, _I, _I, _I, _D, ctypes.POINTER(_P), _P]),
     "tsr_compress": (_I, [_P, _I, _I, _I, _I, _I, _D, ctypes.POINTER(_P), _P]),
+    "tsr_fresnel_output": (_I, [_I, _P, _I, _P, _P, _P, _P]),
+    "tsr_fresnel_output_backward": (_I, [_I, _P, _I, _P, _P, _P, _P, _P, _P]),
+    "tsr_sh_transfer": (_I, [_I, _P, _I, _D, _P, _P]),
     "tsr_cdf97_forward": (_I, [_P, _I, _I, _P, _P]),
     "tsr_cdf97_inverse": (_I, [_P, _I, _I, _P, _P]),
     "tsr_cdf97_inverse_transpose": (_I, [_P, _I, _I, _P, _P]),
@@ -436,6 +439,41 @@ def compress(M: torch.Tensor, nu: int, wavelet: str = "haar", rule: str = "top",
     _check(lib().tsr_compress(_ptr(m), K, J, nu, WAVELETS[wavelet], KEEP_RULES[rule], float(param), ctypes.byref(h),
                               _stream()))
     return Compressed(h)
+
+
+# ---------------------------------------------------------------- Fresnel factors
+def fresnel_output(B: torch.Tensor, eta: torch.Tensor, cos_o: torch.Tensor, out: torch.Tensor | None = None):
+    """tsr_fresnel_output: (1/pi) F_t(eta_e, cos_o) B for B [E][3][N], eta [E] FP64, cos_o [N] FP32."""
+    E, _, N = B.shape
+    b = _dev(B, torch.float32, (E, 3, N), "B")
+    e = _dev(eta, torch.float64, (E,), "eta")
+    c = _dev(cos_o, torch.float32, (N,), "cos_o")
+    o = out if out is not None else torch.empty_like(b)
+    _check(lib().tsr_fresnel_output(E, _ptr(e), N, _ptr(c), _ptr(b), _ptr(o), _stream()))
+    return o
+
+
+def fresnel_output_backward(B: torch.Tensor, eta: torch.Tensor, cos_o: torch.Tensor, dBout: torch.Tensor):
+    """tsr_fresnel_output_backward: returns (dL/dB [E][3][N] FP32, dL/deta [E] FP32)."""
+    E, _, N = B.shape
+    b = _dev(B, torch.float32, (E, 3, N), "B")
+    e = _dev(eta, torch.float64, (E,), "eta")
+    c = _dev(cos_o, torch.float32, (N,), "cos_o")
+    g = _dev(dBout, torch.float32, (E, 3, N), "dBout")
+    dB = torch.empty_like(b)
+    deta = torch.empty(E, dtype=torch.float32, device=b.device)
+    _check(lib().tsr_fresnel_output_backward(E, _ptr(e), N, _ptr(c), _ptr(b), _ptr(g), _ptr(dB), _ptr(deta),
+                                             _stream()))
+    return dB, deta
+
+
+def sh_transfer(normals: torch.Tensor, J: int, eta: float = 1.0) -> torch.Tensor:
+    """tsr_sh_transfer: T [J][N] for unit normals [3][N] with the incident Fresnel factor at eta folded in."""
+    N = normals.shape[1]
+    n = _dev(normals, torch.float32, (3, N), "normals")
+    T = torch.empty((J, N), dtype=torch.float32, device=n.device)
+    _check(lib().tsr_sh_transfer(N, _ptr(n), J, float(eta), _ptr(T), _stream()))
+    return T
 
 
 # ---------------------------------------------------------------- relight

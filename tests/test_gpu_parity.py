@@ -493,3 +493,62 @@ def test_transfer_nearfar_path(torch_cuda, tsr, oracle_basis16, precision, monke
         rows = scene.sample_rows(sc.n, 256, seed=5)
         M_ref = O.transfer_rows(f_ref[:K], pos, area, T, rows)
         assert _normwise_k(M.cpu().numpy()[:, :, rows], M_ref) <= TOL[precision]
+
+
+# ------------------------------------------------------------------ Fresnel factors (Eq. 3, Eq. 6)
+def test_fresnel_output_and_reverse_mode(torch_cuda, tsr):
+    torch = torch_cuda
+    rng = np.random.default_rng(41)
+    E, N = 5, 1037
+    B = rng.standard_normal((E, 3, N)).astype(np.float32)
+    eta = rng.uniform(1.0, 1.8, E)
+    cos_o = np.concatenate([rng.uniform(-1, 1, N - 3), [0.0, 1.0, 1e-7]]).astype(np.float32)
+    Bo = tsr.fresnel_output(_dev(torch, B), torch.tensor(eta, device="cuda"), _dev(torch, cos_o)).cpu().numpy()
+    ref = O.fresnel_output(B, eta, cos_o)
+    assert np.max(np.abs(Bo - ref)) <= 2e-6 * np.max(np.abs(ref))
+    dBout = rng.standard_normal((E, 3, N)).astype(np.float32)
+    dB, deta = tsr.fresnel_output_backward(_dev(torch, B), torch.tensor(eta, device="cuda"), _dev(torch, cos_o),
+                                           _dev(torch, dBout))
+    dB_ref, deta_ref = O.fresnel_output_vjp(B, eta, cos_o, dBout)
+    assert np.max(np.abs(dB.cpu().numpy() - dB_ref)) <= 2e-6 * np.max(np.abs(dB_ref))
+    assert np.max(np.abs(deta.cpu().numpy() - deta_ref)) <= 1e-4 * np.max(np.abs(deta_ref))
+
+
+@pytest.mark.parametrize("J,eta", [(9, 1.3), (16, 1.5), (25, 1.0), (1, 1.2)])
+def test_sh_transfer_with_incident_fresnel(torch_cuda, tsr, J, eta):
+    """T[j, i] = A_l(eta) Y_lm(n_i) (Funk-Hecke) on a displaced mesh's normals, against the oracle."""
+    torch = torch_cuda
+    mesh = scene.icosphere(8, 0.12, 3, 4)
+    normals = mesh.normal.astype(np.float32)
+    T = tsr.sh_transfer(_dev(torch, normals.T), J, eta).cpu().numpy()
+    ref = O.sh_transfer_fresnel(normals.astype(np.float64), J, eta)
+    assert np.max(np.abs(T - ref)) <= 2e-6 * np.max(np.abs(ref))
+    if eta == 1.0:
+        assert np.max(np.abs(T - scene.sh_transfer(normals.astype(np.float64), J))) <= 2e-6
+
+
+def test_view_dependent_render_end_to_end(torch_cuda, tsr, oracle_basis16):
+    """Eq. 6 with both Fresnel factors on 252 vertices: T with the incident F_t at the precompute's eta,
+    FP32 transfer, keep-all Haar compression, relight of two edits, output factor for a view direction."""
+    torch = torch_cuda
+    f_ref, _ = oracle_basis16
+    K, J, nu = 6, 9, 5
+    mesh = scene.icosphere(nu, 0.1, 3, 5)
+    pos, area, normals = (a.astype(np.float32) for a in (mesh.pos, mesh.area, mesh.normal))
+    T_ref = O.sh_transfer_fresnel(normals.astype(np.float64), J, 1.3)
+    T = tsr.sh_transfer(_dev(torch, normals.T), J, 1.3)
+    basis = tsr.basis_create(f_ref[:K])
+    M = tsr.precompute_transfer(basis, _dev(torch, pos.T), _dev(torch, area), T, "fp32")
+    comp = tsr.haar_compress(M, nu, 1.0)
+    sa, ss, eta = scene.edit_materials(2, seed=12)
+    g = O.project_material(f_ref[:K], sa, ss, eta)
+    light = scene.sh_light(J, 3)
+    view = np.array([0.3, -0.4, 0.866])
+    cos_o = (normals @ (view / np.linalg.norm(view))).astype(np.float32)
+    B = tsr.relight(comp, _dev(torch, g.astype(np.float32)), _dev(torch, light.astype(np.float32)))
+    Bo = tsr.fresnel_output(B, torch.tensor(eta, device="cuda"), _dev(torch, cos_o)).cpu().numpy()
+    M_ref = O.transfer_full(f_ref[:K], pos, area, T_ref.astype(np.float32))
+    B_ref = O.relight(O.chart_to_wavelet(M_ref, nu), nu, g, light)
+    ref = O.fresnel_output(B_ref, eta, cos_o)
+    err = np.linalg.norm((Bo - ref).reshape(-1, Bo.shape[-1]), axis=1) / np.linalg.norm(ref.reshape(-1, ref.shape[-1]), axis=1)
+    assert err.max() <= 1e-5, err
