@@ -3,9 +3,11 @@ hand-written adjoints running in libtsr (Section 2.2 projection, Section 4
 rendering Steps 3-5).
 
     B = relight(S, project(sigma_a, sigma_s', eta), l)
+    B_view = (1/pi) F_t(eta, n_o . w_o) B          (optional, Eq. 6)
 
 Gradients flow to sigma_a, sigma_s', eta (through the FP64 analytic
-derivative of the dipole R_d) and to the light coefficients l.
+derivative of the dipole R_d, and through dF_t/deta of the view factor) and
+to the light coefficients l.
 """
 from __future__ import annotations
 
@@ -44,8 +46,25 @@ class RelightFn(torch.autograd.Function):
         return dg, dl, None
 
 
+class FresnelOutputFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, B, eta, cos_o):
+        ctx.save_for_backward(B.detach(), eta.detach(), cos_o.detach())
+        return tsr.fresnel_output(B.detach(), eta.detach(), cos_o.detach())
+
+    @staticmethod
+    def backward(ctx, dBout):
+        B, eta, cos_o = ctx.saved_tensors
+        dB, deta = tsr.fresnel_output_backward(B, eta, cos_o, dBout.contiguous())
+        return dB, deta.to(eta.dtype), None
+
+
 def render(comp: "tsr.Compressed", basis: "tsr.Basis", sigma_a: torch.Tensor, sigma_s: torch.Tensor,
-           eta: torch.Tensor, light: torch.Tensor) -> torch.Tensor:
-    """Differentiable relight B [E][3][N] of materials (sigma_a, sigma_s' [E][3] FP64, eta [E] FP64) under light [J]."""
+           eta: torch.Tensor, light: torch.Tensor, cos_o: torch.Tensor | None = None) -> torch.Tensor:
+    """Differentiable relight B [E][3][N] of materials (sigma_a, sigma_s' [E][3] FP64, eta [E] FP64) under
+    light [J]; with cos_o [N] (n_o . w_o per vertex) the view-dependent Fresnel factor of Eq. 6 is applied."""
     g = ProjectMaterialFn.apply(sigma_a, sigma_s, eta, basis)
-    return RelightFn.apply(g, light, comp)
+    B = RelightFn.apply(g, light, comp)
+    if cos_o is not None:
+        B = FresnelOutputFn.apply(B, eta, cos_o)
+    return B

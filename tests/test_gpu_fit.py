@@ -150,3 +150,46 @@ def test_adam_material_fit_reduces_loss(setup):
         losses.append(float(loss))
     assert np.all(np.isfinite(losses))
     assert losses[-1] < 1e-2 * losses[0]
+
+
+def test_gpu_adjoint_with_view_fresnel_matches_oracle(setup):
+    """The same loss with the view-dependent Fresnel factor of Eq. 6 on the rendered shading: the eta
+    gradient now also flows through dF_t/deta; GPU adjoint against the oracle's chain rule."""
+    torch, tsr = setup["torch"], setup["tsr"]
+    from paper_2203_12339_gb300.autograd import render
+    N = 10 * NU * NU + 2
+    cos_o = np.cos(np.linspace(0.0, 1.4, N))
+    theta = _theta0()
+
+    def oracle(theta):
+        sa, ss = np.exp(theta[0:3])[None], np.exp(theta[3:6])[None]
+        eta, light = np.array([theta[6]]), theta[7:]
+        g = O.project_material(setup["f"], sa, ss, eta)
+        B = O.relight(setup["Cw"], NU, g, light)
+        Bv = O.fresnel_output(B, eta, cos_o)
+        target = O.fresnel_output(setup["B_star"], np.array([1.35]), cos_o)
+        loss = float(np.sum((Bv - target) ** 2))
+        dBv = 2.0 * (Bv - target)
+        dB, deta_f = O.fresnel_output_vjp(B, eta, cos_o, dBv)
+        dg, dl = O.relight_vjp(setup["Cw"], NU, g, light, dB)
+        d_sa, d_ss, d_eta = O.project_material_vjp(setup["f"], sa, ss, eta, dg)
+        grad = np.concatenate([d_sa[0] * sa[0], d_ss[0] * ss[0], d_eta + deta_f, dl])
+        return loss, grad, target
+
+    loss_ref, grad_ref, target = oracle(theta)
+    th = torch.tensor(theta, dtype=torch.float64, device="cuda", requires_grad=True)
+    B = render(setup["comp"], setup["basis"], torch.exp(th[0:3]).reshape(1, 3), torch.exp(th[3:6]).reshape(1, 3),
+               th[6:7], th[7:].float(), torch.tensor(cos_o, dtype=torch.float32, device="cuda"))
+    loss = ((B - torch.tensor(target, dtype=torch.float32, device="cuda")) ** 2).sum()
+    loss.backward()
+    tsr.stream_status()
+    assert float(loss) == pytest.approx(loss_ref, rel=1e-5)
+    grad = th.grad.cpu().numpy()
+    for a, b in zip(_groups(grad), _groups(grad_ref)):
+        assert _rel(a, b) <= 1e-4
+    h = 1e-4   # and the oracle chain itself against central differences in eta
+    tp, tm = theta.copy(), theta.copy()
+    tp[6] += h
+    tm[6] -= h
+    fd = (oracle(tp)[0] - oracle(tm)[0]) / (2 * h)
+    assert grad_ref[6] == pytest.approx(fd, rel=1e-4)
