@@ -45,6 +45,9 @@ design notes):
       of Eq. 6 uses the caller's per-vertex cosine n_o . omega_o.
   R35 the incident F_t(eta, omega_i) is folded into the SH transfer T through the
       zonal coefficients A_l(eta) (Funk-Hecke) at the precompute's eta.
+  R36 visibility in T (E11-E14): T[j, i] = (pi/S) sum_s Y_j(w_s) V(x_i, w_s), w_s the
+      S cosine-weighted Hammersley directions in the Duff et al. frame of n_i, rays
+      from x_i + eps n_i, V by an FP32 Moller-Trumbore any-hit over the mesh.
   R33 the paper's Step-2 wavelet "Daubechies 9/7": the biorthogonal CDF 9/7 pair
       by lifting (symmetric extension, low band DC gain sqrt 2), separable 2D
       Mallat pyramid of each chart's P x P image down to 1 x 1.
@@ -421,6 +424,91 @@ def sh_transfer_fresnel(normals, J, eta):
     for l in range(order):
         Y[l * l:(l + 1) * (l + 1)] *= A[l]
     return Y
+
+
+# ---------------------------------------------------------------- ray-cast visibility (reading R36)
+def onb_from_normal(n):
+    """Orthonormal tangents (t1, t2) of unit normals n (..., 3) by the branchless construction of
+    Duff et al. (2017, "Building an orthonormal basis, revisited")."""
+    n = np.asarray(n, dtype=np.float64)
+    sign = np.where(n[..., 2] >= 0.0, 1.0, -1.0)
+    a = -1.0 / (sign + n[..., 2])
+    b = n[..., 0] * n[..., 1] * a
+    t1 = np.stack([1.0 + sign * n[..., 0] ** 2 * a, sign * b, -sign * n[..., 0]], axis=-1)
+    t2 = np.stack([b, sign + n[..., 1] ** 2 * a, -n[..., 1]], axis=-1)
+    return t1, t2
+
+
+def hemisphere_samples(S: int):
+    """Cosine-weighted directions in the local frame (z = normal) from the Hammersley set:
+    u1 = (s + 1/2) / S, u2 = bit-reversed s; r = sqrt(u1), phi = 2 pi u2, z = sqrt(1 - u1)."""
+    s = np.arange(S)
+    u1 = (s + 0.5) / S
+    u2 = np.zeros(S)
+    f, v = 0.5, s.copy()
+    while np.any(v):
+        u2 += f * (v & 1)
+        v >>= 1
+        f *= 0.5
+    r = np.sqrt(u1)
+    return np.stack([r * np.cos(2 * math.pi * u2), r * np.sin(2 * math.pi * u2), np.sqrt(1.0 - u1)], axis=-1)
+
+
+def _f32(x):
+    return np.asarray(x, dtype=np.float32)
+
+
+def ray_hits_any(orig, dirs, v0, v1, v2, t_min=1e-4):
+    """Any-hit of rays (R, 3) against triangles (F, 3 each) by the Moller-Trumbore test, in FP32
+    with a fixed operation order (no fused multiply-add) so that the decision is reproducible:
+    dot(a, b) = (a.x b.x + a.y b.y) + a.z b.z, cross by components, inv = 1/det, a hit needs
+    |det| >= 1e-12, u, v >= 0, u + v <= 1 and t > t_min.  Returns a bool (R,) array."""
+    o, d = _f32(orig)[:, None, :], _f32(dirs)[:, None, :]
+    a, b, c = _f32(v0)[None], _f32(v1)[None], _f32(v2)[None]
+
+    def cross(x, y):
+        return np.stack([x[..., 1] * y[..., 2] - x[..., 2] * y[..., 1],
+                         x[..., 2] * y[..., 0] - x[..., 0] * y[..., 2],
+                         x[..., 0] * y[..., 1] - x[..., 1] * y[..., 0]], axis=-1)
+
+    def dot(x, y):
+        return (x[..., 0] * y[..., 0] + x[..., 1] * y[..., 1]) + x[..., 2] * y[..., 2]
+
+    e1, e2 = b - a, c - a
+    p = cross(d, e2)
+    det = dot(e1, p)
+    ok = np.abs(det) >= np.float32(1e-12)
+    inv = np.float32(1.0) / np.where(ok, det, np.float32(1.0))
+    tv = o - a
+    u = dot(tv, p) * inv
+    q = cross(tv, e1)
+    v = dot(d, q) * inv
+    t = dot(e2, q) * inv
+    hit = ok & (u >= 0) & (v >= 0) & (u + v <= np.float32(1.0)) & (t > np.float32(t_min))
+    return hit.any(axis=1)
+
+
+def visibility_transfer(pos, tris, normals, J, S, eps=1e-3, eta=None):
+    """Self-shadowed SH irradiance transfer T[j, i] = (pi / S) sum_s Y_j(w_s) V(x_i, w_s) [F_t(eta, mu_s)]
+    (Eq. 6's E with visibility; reading R36): w_s the cosine-weighted Hammersley directions in the frame
+    of n_i, rays from x_i + eps n_i (FP32), V = 0 when the ray hits any triangle of the mesh."""
+    from paper_2203_12339_gb300.scene import sh_real
+    pos32, n32 = _f32(pos), _f32(normals)
+    t1, t2 = onb_from_normal(n32.astype(np.float64))
+    loc = hemisphere_samples(S)
+    order = int(round(math.sqrt(J)))
+    N = pos32.shape[0]
+    v0, v1, v2 = pos32[tris[:, 0]], pos32[tris[:, 1]], pos32[tris[:, 2]]
+    T = np.zeros((J, N))
+    for i in range(N):
+        dirs = _f32(loc[:, :1] * t1[i] + loc[:, 1:2] * t2[i] + loc[:, 2:3] * n32[i].astype(np.float64))
+        orig = np.repeat((pos32[i] + np.float32(eps) * n32[i])[None, :], S, axis=0)
+        vis = ~ray_hits_any(orig, dirs, v0, v1, v2)
+        w = (math.pi / S) * vis.astype(np.float64)
+        if eta is not None:
+            w = w * fresnel_transmittance(eta, loc[:, 2])
+        T[:, i] = sh_real(order, dirs.astype(np.float64)) @ w
+    return T
 
 
 # ---------------------------------------------------------------- CDF 9/7 spatial wavelet

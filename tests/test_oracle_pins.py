@@ -534,6 +534,68 @@ def test_sh_transfer_fresnel_by_direct_integration():
         assert np.allclose(direct, want, atol=1e-9)
 
 
+# ---------------------------------------------------------------- visibility transfer (reading R36)
+def test_onb_is_orthonormal_and_right_handed():
+    rng = np.random.default_rng(13)
+    n = rng.standard_normal((200, 3))
+    n = np.concatenate([n, [[0, 0, 1.0], [0, 0, -1.0], [1e-9, 0, -1.0], [1.0, 0, 0]]])
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    t1, t2 = O.onb_from_normal(n)
+    for a, b in ((t1, t2), (t1, n), (t2, n)):
+        assert np.abs(np.sum(a * b, axis=1)).max() < 1e-12
+    for a in (t1, t2):
+        assert np.abs(np.linalg.norm(a, axis=1) - 1).max() < 1e-12
+    assert np.abs(np.cross(t1, t2) - n).max() < 1e-12
+
+
+def test_hemisphere_samples_integrate_the_cosine_lobe():
+    """(pi/S) sum_s Y_j(w_s) over cosine-weighted directions estimates A_l Y_j(z): exact for l = 0,
+    within the quasi-Monte Carlo error for the rest."""
+    loc = O.hemisphere_samples(1024)
+    assert np.abs(np.linalg.norm(loc, axis=1) - 1).max() < 1e-12 and loc[:, 2].min() > 0
+    est = (math.pi / 1024) * scene.sh_real(5, loc).sum(axis=1)
+    exact = scene.sh_transfer(np.array([[0.0, 0.0, 1.0]]), 25)[:, 0]
+    assert est[0] == pytest.approx(exact[0], rel=1e-13)
+    assert np.abs(est - exact).max() < 3e-3
+
+
+def test_ray_hits_match_an_independent_solver():
+    """The FP32 Moller-Trumbore decision against solving o + t d = v0 + u e1 + v e2 in FP64, away
+    from the decision boundaries (where FP32 rounding may legitimately differ)."""
+    rng = np.random.default_rng(14)
+    R, F = 300, 40
+    orig = rng.uniform(-1, 1, (R, 3))
+    dirs = rng.standard_normal((R, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    v0, v1, v2 = (rng.uniform(-2, 2, (F, 3)) for _ in range(3))
+    got = O.ray_hits_any(orig, dirs, v0, v1, v2)
+    clear = np.ones(R, dtype=bool)
+    want = np.zeros(R, dtype=bool)
+    for r in range(R):
+        for f in range(F):
+            A = np.stack([-dirs[r], v1[f] - v0[f], v2[f] - v0[f]], axis=1)
+            t, u, v = np.linalg.solve(A, orig[r] - v0[f])
+            margin = min(abs(u), abs(v), abs(1 - u - v), abs(t - 1e-4))
+            if margin < 1e-4:
+                clear[r] = False
+            if u >= 0 and v >= 0 and u + v <= 1 and t > 1e-4:
+                want[r] = True
+    assert clear.sum() > 200
+    assert np.array_equal(got[clear], want[clear])
+
+
+def test_visibility_transfer_convex_and_covered():
+    """On the undisplaced (convex) sphere no ray is blocked, so T is the plain quadrature of the clamped
+    cosine; under a roof that covers the hemisphere every ray is blocked."""
+    m = scene.icosphere(3, 0.0, 3, 0)
+    T = O.visibility_transfer(m.pos, m.tris, m.normal, 16, 1024)
+    assert np.abs(T - scene.sh_transfer(m.normal, 16)).max() < 3e-3
+    roof = np.array([[-1e4, -1e4, 1.0], [1e4, -1e4, 1.0], [0.0, 1e4, 1.0]])   # a point under a huge triangle
+    loc = O.hemisphere_samples(256)
+    hits = O.ray_hits_any(np.repeat([[0.0, 0.0, 1e-3]], 256, axis=0), loc, roof[[0]], roof[[1]], roof[[2]])
+    assert hits.all()
+
+
 # ---------------------------------------------------------------- CDF 9/7 (reading R33)
 # Analysis filters of the CDF 9/7 pair as published (the JPEG 2000 irreversible
 # filter bank): lowpass normalised to sum 1, highpass to centre value 1.115...
