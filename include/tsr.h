@@ -292,6 +292,19 @@ tsr_status tsr_fresnel_output_backward(int n_edit, const double *eta, int N, con
                                        const float *dBout, float *dB, float *deta, tsr_stream stream);
 tsr_status tsr_sh_transfer(int N, const float *normals, int J, double eta, float *T, tsr_stream stream);
 
+/* Self-shadowed SH irradiance transfer (E of Eq. 6 with the visibility of the
+ * transfer, E11-E14) for displaced meshes:
+ *   T[j][i] = (pi / S) sum_s Y_j(w_s) V(x_i, w_s) [F_t(eta, mu_s)],
+ * w_s the S cosine-weighted Hammersley directions (u1 = (s + 1/2)/S, u2 = the
+ * bit-reversed s; r = sqrt u1, phi = 2 pi u2, mu = sqrt(1 - u1)) in the frame of n_i
+ * (Duff et al. 2017), rays from x_i + eps n_i, V = 0 if a ray hits any triangle
+ * (FP32 Moller-Trumbore, t > 1e-4).  A linear BVH is built on the device per call.
+ *   pos, normals: device [3][N] FP32; tris: device [F][3] int32 vertex indices;
+ *   J in {1, 4, 9, 16, 25}; S in [1, 65536]; eta = 0 (no Fresnel factor) or in
+ *   [1, 2]; T: device [J][N] FP32 out. */
+tsr_status tsr_visibility_transfer(int N, const float *pos, const float *normals, int F, const int32_t *tris, int J,
+                                   int S, double eta, float eps, float *T, tsr_stream stream);
+
 /* ------------------------------------------------------------------------
  * Relight / material edit (Section 4, rendering Steps 3-5):
  *   b^w[e][c][w] = sum_{(kj,v) in row w} v * g[e][c][k] * l[j]

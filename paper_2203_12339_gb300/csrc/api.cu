@@ -234,6 +234,21 @@ extern "C" tsr_status tsr_sh_transfer(int N, const float *normals, int J, double
   return sh_transfer(N, normals, J, eta, T, as_stream(stream));
 }
 
+extern "C" tsr_status tsr_visibility_transfer(int N, const float *pos, const float *normals, int F,
+                                              const int32_t *tris, int J, int S, double eta, float eps, float *T,
+                                              tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(pos && normals && tris && T, "tsr_visibility_transfer: NULL argument");
+  TSR_CHECK_ARG(N >= 1 && F >= 1 && F <= (1 << 26), "tsr_visibility_transfer: N=%d F=%d out of range", N, F);
+  TSR_CHECK_ARG(J == 1 || J == 4 || J == 9 || J == 16 || J == 25, "tsr_visibility_transfer: J=%d", J);
+  TSR_CHECK_ARG(S >= 1 && S <= 65536, "tsr_visibility_transfer: S=%d outside [1, 65536]", S);
+  TSR_CHECK_ARG(eta == 0.0 || (eta >= 1.0 && eta <= 2.0), "tsr_visibility_transfer: eta=%g (0, or [1, 2])", eta);
+  TSR_CHECK_ARG(eps >= 0.0f, "tsr_visibility_transfer: eps=%g < 0", (double)eps);
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  return visibility_transfer(N, pos, normals, F, tris, J, S, eta, eps, T, as_stream(stream));
+}
+
 extern "C" tsr_status tsr_haar_recompress(const float *M, tsr_compressed *c, tsr_stream stream) {
   clear_error();
   TSR_CHECK_ARG(M && c, "tsr_haar_recompress: NULL argument");

@@ -85,6 +85,8 @@ tsr_status fresnel_output(int E, const double *eta, int N, const float *cos_o, c
 tsr_status fresnel_output_backward(int E, const double *eta, int N, const float *cos_o, const float *B,
                                    const float *dBout, float *dB, float *deta, cudaStream_t s);
 tsr_status sh_transfer(int N, const float *normals, int J, double eta, float *T, cudaStream_t s);
+tsr_status visibility_transfer(int N, const float *pos, const float *normals, int F, const int *tris, int J, int S,
+                               double eta, float eps, float *T, cudaStream_t s);
 tsr_status spatial_forward(int wavelet, const float *X, int rows, int nu, float *Xw, cudaStream_t s);
 tsr_status spatial_inverse(int wavelet, const float *Xw, int rows, int nu, float *X, cudaStream_t s);
 tsr_status spatial_inverse_transpose(int wavelet, const float *X, int rows, int nu, float *Xw, cudaStream_t s);

@@ -58,6 +58,7 @@ _SIGNATURES = {
     "tsr_fresnel_output": (_I, [_I, _P, _I, _P, _P, _P, _P]),
     "tsr_fresnel_output_backward": (_I, [_I, _P, _I, _P, _P, _P, _P, _P, _P]),
     "tsr_sh_transfer": (_I, [_I, _P, _I, _D, _P, _P]),
+    "tsr_visibility_transfer": (_I, [_I, _P, _P, _I, _P, _I, _I, _D, ctypes.c_float, _P, _P]),
     "tsr_cdf97_forward": (_I, [_P, _I, _I, _P, _P]),
     "tsr_cdf97_inverse": (_I, [_P, _I, _I, _P, _P]),
     "tsr_cdf97_inverse_transpose": (_I, [_P, _I, _I, _P, _P]),
@@ -465,6 +466,19 @@ def fresnel_output_backward(B: torch.Tensor, eta: torch.Tensor, cos_o: torch.Ten
     _check(lib().tsr_fresnel_output_backward(E, _ptr(e), N, _ptr(c), _ptr(b), _ptr(g), _ptr(dB), _ptr(deta),
                                              _stream()))
     return dB, deta
+
+
+def visibility_transfer(pos: torch.Tensor, normals: torch.Tensor, tris: torch.Tensor, J: int, S: int = 256,
+                        eta: float = 0.0, eps: float = 1e-3) -> torch.Tensor:
+    """tsr_visibility_transfer: self-shadowed T [J][N] for positions/normals [3][N] and triangles [F][3] int32."""
+    N = pos.shape[1]
+    p = _dev(pos, torch.float32, (3, N), "pos")
+    n = _dev(normals, torch.float32, (3, N), "normals")
+    t = _dev(tris, torch.int32, (tris.shape[0], 3), "tris")
+    T = torch.empty((J, N), dtype=torch.float32, device=p.device)
+    _check(lib().tsr_visibility_transfer(N, _ptr(p), _ptr(n), t.shape[0], _ptr(t), J, S, float(eta), float(eps),
+                                         _ptr(T), _stream()))
+    return T
 
 
 def sh_transfer(normals: torch.Tensor, J: int, eta: float = 1.0) -> torch.Tensor:

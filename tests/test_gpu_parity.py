@@ -552,3 +552,41 @@ def test_view_dependent_render_end_to_end(torch_cuda, tsr, oracle_basis16):
     ref = O.fresnel_output(B_ref, eta, cos_o)
     err = np.linalg.norm((Bo - ref).reshape(-1, Bo.shape[-1]), axis=1) / np.linalg.norm(ref.reshape(-1, ref.shape[-1]), axis=1)
     assert err.max() <= 1e-5, err
+
+
+# ------------------------------------------------------------------ ray-cast visibility in T
+def _vis_compare(T_gpu, T_ref, S):
+    """Equal up to FP32 accumulation, except at the few vertices where a grazing ray's hit decision sits
+    on a rounding boundary (a sample then moves by pi/S |Y_j| <= pi/S)."""
+    diff = np.abs(T_gpu - T_ref).max(axis=0)
+    tight = diff <= 1e-5 * np.abs(T_ref).max()
+    assert tight.mean() >= 0.99, (tight.mean(), diff.max())
+    assert diff.max() <= 2.0 * math.pi / S * 0.8
+
+
+@pytest.mark.parametrize("nu,amp,seed,J,S,eta", [(6, 0.2, 3, 9, 64, 0.0), (8, 0.15, 5, 16, 128, 1.3)])
+def test_visibility_transfer_matches_oracle(torch_cuda, tsr, nu, amp, seed, J, S, eta):
+    torch = torch_cuda
+    mesh = scene.icosphere(nu, amp, 3, seed)
+    pos, normals = mesh.pos.astype(np.float32), mesh.normal.astype(np.float32)
+    T = tsr.visibility_transfer(_dev(torch, pos.T), _dev(torch, normals.T),
+                                torch.tensor(mesh.tris.astype(np.int32), device="cuda"), J, S, eta).cpu().numpy()
+    T_ref = O.visibility_transfer(pos, mesh.tris, normals, J, S, eta=(eta if eta > 0 else None))
+    _vis_compare(T, T_ref, S)
+    unshadowed = O.sh_transfer_fresnel(normals.astype(np.float64), J, eta) if eta > 0 else scene.sh_transfer(normals, J)
+    assert (T[0] < 0.97 * unshadowed[0]).any()          # the displaced mesh does shadow itself
+
+
+def test_visibility_transfer_convex_sphere_and_single_triangle(torch_cuda, tsr):
+    torch = torch_cuda
+    mesh = scene.icosphere(4, 0.0, 3, 0)
+    pos, normals = mesh.pos.astype(np.float32), mesh.normal.astype(np.float32)
+    T = tsr.visibility_transfer(_dev(torch, pos.T), _dev(torch, normals.T),
+                                torch.tensor(mesh.tris.astype(np.int32), device="cuda"), 9, 512).cpu().numpy()
+    assert np.abs(T - scene.sh_transfer(normals, 9)).max() < 5e-3   # nothing blocked: the cosine quadrature
+    # one triangle above one point: every ray blocked (the single-leaf path)
+    pos1 = np.array([[0.0, 0.0, 0.0], [-1e4, -1e4, 1.0], [1e4, -1e4, 1.0], [0.0, 1e4, 1.0]], dtype=np.float32)
+    nrm1 = np.array([[0.0, 0.0, 1.0]] * 4, dtype=np.float32)
+    T1 = tsr.visibility_transfer(_dev(torch, pos1.T), _dev(torch, nrm1.T),
+                                 torch.tensor([[1, 2, 3]], dtype=torch.int32, device="cuda"), 4, 64).cpu().numpy()
+    assert np.abs(T1[:, 0]).max() == 0.0
