@@ -231,6 +231,32 @@ def wavelet_comparison(tsr, M, nu, g32, light) -> list:
     return out
 
 
+def visibility_timing(tsr, dev) -> dict:
+    """Self-shadowed SH transfer (BVH build + S = 256 rays per vertex) on the benchmark mesh."""
+    import torch
+    from paper_2203_12339_gb300 import scene
+    w = scene.WORKLOADS[WORKLOAD]
+    mesh = scene.icosphere(w["nu"], w["amp"], w["octaves"], w["seed"])
+    pos = torch.tensor(mesh.pos.astype(np.float32).T.copy(), device=dev)
+    nrm = torch.tensor(mesh.normal.astype(np.float32).T.copy(), device=dev)
+    tris = torch.tensor(mesh.tris.astype(np.int32), device=dev)
+    S = 256
+    tsr.visibility_transfer(pos, nrm, tris, w["J"], S)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    T = tsr.visibility_transfer(pos, nrm, tris, w["J"], S)
+    b.record()
+    torch.cuda.synchronize()
+    tsr.stream_status()
+    ms = a.elapsed_time(b)
+    shadowed = float((T[0] < 0.97 * torch.tensor(scene.sh_transfer(mesh.normal, w["J"])[0], device=dev)).float().mean())
+    return {"workload": f"{mesh.pos.shape[0]} vertices, {mesh.tris.shape[0]} triangles, J={w['J']}, S={S}",
+            "ms": round(ms, 3), "g_rays_per_s": round(mesh.pos.shape[0] * S / (ms * 1e-3) / 1e9, 3),
+            "shadowed_vertex_share": round(shadowed, 4)}
+
+
 def _smem_roofline(gather_bytes: float, ms: float, peaks: dict) -> dict:
     """Shared-memory gather roofline of the transfer kernel (algorithmic table bytes per launch / time)."""
     import torch
@@ -470,6 +496,7 @@ def run_gpu(args):
     _, g32_curve, _ = tsr.project_material(basis, d["sa"], d["ss"], d["eta"])
     line["energy_keep_curve"] = energy_keep_curve(tsr, M, nu, g32_curve, d["light"])
     line["wavelet_comparison"] = wavelet_comparison(tsr, M, nu, g32_curve, d["light"])
+    line["visibility_transfer"] = visibility_timing(tsr, dev)
     if not args.no_frame_1080p:
         line["relight_frame_1080p"] = relight_frame_1080p(tsr, dev, peaks)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
