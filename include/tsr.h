@@ -315,7 +315,9 @@ tsr_status tsr_visibility_transfer(int N, const float *pos, const float *normals
  * by linearity):
  *   Y[k][w] = sum_j S[w][kj] l[j],  Z[k] = W^-1 Y[k],  B[e][c] = sum_k g[e][c][k] Z[k],
  * so the kept coefficients are read once per call, whatever n_edit; for one or
- * two edits as written (one pass over S for their 3 or 6 vectors).
+ * two edits as written (one pass over S for their 3 or 6 vectors; under the
+ * Haar with P <= 256 the product and the inverse Haar run fused per chart run
+ * without scratch).
  * Scratch: max(K*(10 P^2 + 2 + N), 6*(10 P^2 + 2)) FP32.
  *
  * tsr_relight_backward: reverse mode for an upstream gradient dLdB
@@ -329,6 +331,27 @@ tsr_status tsr_relight(const tsr_compressed *c, int n_edit, const float *g, cons
                        tsr_stream stream);
 tsr_status tsr_relight_backward(const tsr_compressed *c, int n_edit, const float *g, const float *l,
                                 const float *dLdB, float *dg, float *dl, tsr_stream stream);
+
+/* ------------------------------------------------------------------------
+ * tsr_relight_many: Steps 4-5 (Section 4) for n_copy compressed transfers at
+ * once -- the objects of a scene, or the pieces of a frame too large for one
+ * mesh -- each relit under its own edits and one shared light.
+ *   c      : HOST array [n_copy] of handles (0 <= n_copy <= 65536), all with
+ *            the same K and J, on the current device;
+ *   n_edit : edits per copy (0 <= n_edit <= 2^20);
+ *   g      : device [n_copy][n_edit][3][K] FP32;  l: device [J] FP32;
+ *   B      : device FP32 out, the copies' [n_edit][3][N_i] blocks back to back
+ *            (copy i starts at n_edit * 3 * (N_0 + ... + N_{i-1}), N_i = 10 nu_i^2 + 2).
+ * Result per copy: exactly tsr_relight of that copy.  With one or two edits,
+ * copies under the orthonormal Haar with charts of P <= 256 go through one
+ * fused kernel per 32 copies (b^w = S c and the inverse Haar per chart run in
+ * shared memory; no scratch, no allocation); the other copies, and calls with
+ * more edits, run tsr_relight copy by copy (stream-ordered scratch).
+ * Errors: TSR_ERR_INVALID_ARG for NULL or misaligned pointers, a NULL handle or
+ * handles whose K or J differ from the first one's; nothing is launched then.
+ * ---------------------------------------------------------------------- */
+tsr_status tsr_relight_many(int n_copy, const tsr_compressed *const *c, int n_edit, const float *g, const float *l,
+                            float *B, tsr_stream stream);
 
 /* ------------------------------------------------------------------------
  * tsr_relight_noalloc: tsr_relight for callers that cannot allocate device

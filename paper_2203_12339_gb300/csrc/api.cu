@@ -297,6 +297,43 @@ extern "C" tsr_status tsr_relight(const tsr_compressed *c, int n_edit, const flo
   return relight(c, n_edit, g, l, B, as_stream(stream));
 }
 
+extern "C" tsr_status tsr_relight_many(int n_copy, const tsr_compressed *const *c, int n_edit, const float *g,
+                                       const float *l, float *B, tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(n_copy >= 0 && n_copy <= 65536, "tsr_relight_many: n_copy=%d out of range", n_copy);
+  TSR_CHECK_ARG(n_edit >= 0 && n_edit <= (1 << 20), "tsr_relight_many: n_edit=%d out of range", n_edit);
+  if (n_copy == 0) return TSR_OK;
+  TSR_CHECK_ARG(c && g && l && B, "tsr_relight_many: NULL argument");
+  TSR_CHECK_ARG(aligned(g, 4) && aligned(l, 4) && aligned(B, 4), "tsr_relight_many: misaligned pointer");
+  for (int i = 0; i < n_copy; ++i) {
+    TSR_CHECK_ARG(c[i], "tsr_relight_many: handle %d is NULL", i);
+    TSR_CHECK_ARG(c[i]->K == c[0]->K && c[i]->J == c[0]->J, "tsr_relight_many: handle %d has K=%d J=%d, handle 0 K=%d J=%d",
+                  i, c[i]->K, c[i]->J, c[0]->K, c[0]->J);
+  }
+  tsr_status st = require_device();
+  if (st != TSR_OK || n_edit == 0) return st;
+  cudaStream_t s = as_stream(stream);
+  const size_t V = 3 * (size_t)n_edit, K = (size_t)c[0]->K;
+  std::vector<const tsr_compressed *> fc;
+  std::vector<const float *> fg;
+  std::vector<float *> fb;
+  size_t off = 0;
+  for (int i = 0; i < n_copy; ++i) {
+    const float *gi = g + (size_t)i * V * K;
+    float *Bi = B + off;
+    off += V * (10 * (size_t)c[i]->nu * c[i]->nu + 2);
+    if (relight_fusable(c[i], n_edit)) {
+      fc.push_back(c[i]);
+      fg.push_back(gi);
+      fb.push_back(Bi);
+    } else {
+      st = relight(c[i], n_edit, gi, l, Bi, s);
+      if (st != TSR_OK) return st;
+    }
+  }
+  return relight_fused((int)fc.size(), fc.data(), n_edit, fg.data(), l, fb.data(), s);
+}
+
 extern "C" tsr_status tsr_relight_backward(const tsr_compressed *c, int n_edit, const float *g, const float *l,
                                            const float *dLdB, float *dg, float *dl, tsr_stream stream) {
   clear_error();

@@ -101,6 +101,11 @@ tsr_status relight_backward(const tsr_compressed *c, int n_edit, const float *g,
                             const float *dLdB, float *dg, float *dl, cudaStream_t s);
 // Floats of caller-provided scratch relight_with_scratch needs: K (10 P^2 + 2 + N).
 size_t relight_scratch_floats(const tsr_compressed *c);
+// Steps 4-5 for one or two edits with the product and the inverse Haar fused, over
+// n compressed transfers (Haar, P <= 256, same K and J) in one launch per 32.
+bool relight_fusable(const tsr_compressed *c, int n_edit);
+tsr_status relight_fused(int n, const tsr_compressed *const *c, int n_edit, const float *const *gi, const float *l,
+                         float *const *Bi, cudaStream_t s);
 tsr_status relight_with_scratch(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,
                                 float *scratch, cudaStream_t s);
 }  // namespace tsr

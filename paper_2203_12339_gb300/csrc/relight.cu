@@ -294,6 +294,7 @@ tsr_status relight_with_scratch(const tsr_compressed *c, int n_edit, const float
   const int V = n_edit * 3;
   if (V == 0) return TSR_OK;
   const int N = 10 * c->nu * c->nu + 2;
+  if (relight_fusable(c, n_edit)) return relight_fused(1, &c, n_edit, &g, l, &B, s);
   if (V <= RL_DV) {
     if (V == 3)
       launch_direct<3>(c, g, l, scratch, s);

@@ -722,8 +722,10 @@ static tsr_status compressed_alloc(int K, int J, int nu, const std::vector<int> 
   for (int q = 0; q < KJ; ++q) cp[q + 1] = cp[q] + n_keep_col[q] + 2;
   c->nnz = cp[KJ];
   cudaError_t e = cudaMalloc(&c->row_ptr, sizeof(int64_t) * (c->n_rows + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&c->col, sizeof(uint16_t) * c->nnz);
-  if (e == cudaSuccess) e = cudaMalloc(&c->val, sizeof(float) * c->nnz);
+  // col and val padded to whole groups of 4 entries (the fused relight reads aligned 4-entry groups)
+  const size_t nnz4 = ((size_t)c->nnz + 3) & ~(size_t)3;
+  if (e == cudaSuccess) e = cudaMalloc(&c->col, sizeof(uint16_t) * nnz4);
+  if (e == cudaSuccess) e = cudaMalloc(&c->val, sizeof(float) * nnz4);
   if (e == cudaSuccess) e = cudaMalloc(&c->cidx, sizeof(int32_t) * c->nnz);
   if (e == cudaSuccess) e = cudaMalloc(&c->cval, sizeof(float) * c->nnz);
   if (e == cudaSuccess) e = cudaMalloc(&c->col_ptr, sizeof(int64_t) * (KJ + 1));

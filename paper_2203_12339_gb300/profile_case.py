@@ -42,7 +42,7 @@ def main(argv=None):
             for _ in range(a.repeat):
                 tsr.precompute_transfer(basis, pos, area, T, prec)
     else:
-        # the relight frame: `copies` compressed transfers (distinct buffers), one RGB edit each
+        # the relight frame: `copies` compressed transfers (distinct buffers), one RGB edit each, relit by one call
         M = tsr.precompute_transfer(basis, pos, area, T, "bf16")
         copies = [tsr.haar_compress(M, a.nu, a.keep) for _ in range(a.copies)]
         del M
@@ -50,9 +50,9 @@ def main(argv=None):
         _, g32, _ = tsr.project_material(basis, torch.tensor(esa, device="cuda"), torch.tensor(ess, device="cuda"),
                                          torch.tensor(eeta, device="cuda"))
         light = torch.tensor(sc.light.astype(np.float32), device="cuda")
+        g_frame = g32.reshape(a.copies, 1, 3, a.K).contiguous()
         for _ in range(a.repeat):
-            for i, c in enumerate(copies):
-                tsr.relight(c, g32[i:i + 1], light)
+            tsr.relight_many(copies, g_frame, light)
     torch.cuda.synchronize()
     tsr.stream_status()
     print(f"ok: case={a.case} N={sc.n} K={a.K} J={a.J} precision={a.precision}")

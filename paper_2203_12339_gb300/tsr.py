@@ -70,6 +70,7 @@ _SIGNATURES = {
     "tsr_relight": (_I, [_P, _I, _P, _P, _P, _P]),
     "tsr_relight_backward": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
     "tsr_relight_noalloc": (_I, [_P, _I, _P, _P, _P, _P]),
+    "tsr_relight_many": (_I, [_I, _P, _I, _P, _P, _P, _P]),
 }
 
 
@@ -499,6 +500,32 @@ def relight(comp: Compressed, g: torch.Tensor, light: torch.Tensor, out: torch.T
     B = out if out is not None else torch.empty((E, 3, comp.n), dtype=torch.float32, device=gg.device)
     _check(lib().tsr_relight(comp.handle, E, _ptr(gg), _ptr(ll), _ptr(B), _stream()))
     return B
+
+
+def relight_many(comps, g: torch.Tensor, light: torch.Tensor, out: torch.Tensor | None = None):
+    """tsr_relight_many: g [n_copy][E][3][K] FP32, light [J] -> list of B_i [E][3][N_i], views of one
+    buffer (the copies' blocks back to back, returned as `out` when given)."""
+    comps = list(comps)
+    n = len(comps)
+    if n == 0:
+        return []
+    K, J = comps[0].K, comps[0].J
+    E = g.shape[1] if g.dim() == 4 else 0
+    gg = _dev(g, torch.float32, (n, E, 3, K), "g")
+    ll = _dev(light, torch.float32, (J,), "light")
+    sizes = [E * 3 * c.n for c in comps]
+    total = sum(sizes)
+    if out is None:
+        out = torch.empty(total, device=gg.device, dtype=torch.float32)
+    out = _dev(out, torch.float32, (total,), "out")
+    handles = (ctypes.c_void_p * n)(*[c.handle.value for c in comps])
+    _check(lib().tsr_relight_many(n, ctypes.cast(handles, ctypes.c_void_p), E, _ptr(gg), _ptr(ll), _ptr(out),
+                                  _stream()))
+    views, o = [], 0
+    for c, sz in zip(comps, sizes):
+        views.append(out[o:o + sz].view(E, 3, c.n))
+        o += sz
+    return views
 
 
 def relight_backward(comp: Compressed, g: torch.Tensor, light: torch.Tensor, dLdB: torch.Tensor):

@@ -425,6 +425,81 @@ def test_relight_matches_oracle(torch_cuda, tsr, nu, K, J, E, p):
     assert np.max(num / den) <= 2e-6
 
 
+def _relight_err(B, B_ref):
+    E = B_ref.shape[0]
+    num = np.linalg.norm((B - B_ref).reshape(E * 3, -1), axis=1)
+    den = np.linalg.norm(B_ref.reshape(E * 3, -1), axis=1)
+    return float(np.max(num / den))
+
+
+@pytest.mark.parametrize("nu,K,J,p", [(40, 3, 4, 0.1), (64, 2, 3, 0.05), (100, 2, 2, 0.05), (128, 2, 2, 0.05)])
+def test_relight_one_edit_large_charts(torch_cuda, tsr, nu, K, J, p):
+    """One and two edits on charts of 64^2 and 128^2 Morton positions (4 and 16 runs of 1,024 per chart;
+    ragged nu = 40 and nu = 100 among them, up to the library's nu = 128): the fused product + inverse
+    Haar per run against the oracle."""
+    torch = torch_cuda
+    comp, kept = _compressed_case(torch, tsr, nu, K, J, p, nu + 7)
+    rng = np.random.default_rng(nu)
+    light = rng.standard_normal(J).astype(np.float32)
+    for E in (1, 2):
+        g = rng.standard_normal((E, 3, K)).astype(np.float32)
+        B = tsr.relight(comp, _dev(torch, g), _dev(torch, light)).cpu().numpy()
+        B_ref = O.relight(kept, nu, g.astype(np.float64), light.astype(np.float64))
+        assert _relight_err(B, B_ref) <= 2e-6, (E, _relight_err(B, B_ref))
+
+
+def test_relight_many_uneven_copies(torch_cuda, tsr):
+    """tsr_relight_many over uneven copies (1 to 40 vertices per chart side, Haar and CDF 9/7): every
+    copy against the oracle's relight of its own kept coefficients, for 1, 2 and 3 edits (fused launch,
+    per-copy fallbacks); also more copies than one launch takes (32)."""
+    torch = torch_cuda
+    K, J = 4, 5
+    nus = [1, 3, 5, 8, 16, 40, 17, 2]
+    comps, kepts = [], []
+    for i, nu in enumerate(nus):
+        comp, kept = _compressed_case(torch, tsr, nu, K, J, 0.2, 100 + i)
+        comps.append(comp)
+        kepts.append(kept)
+    # one CDF 9/7 copy (not fused: relit by tsr_relight inside the call)
+    nu_c = 8
+    N_c = 10 * nu_c * nu_c + 2
+    rng = np.random.default_rng(5)
+    Mc = (rng.standard_normal((K, J, N_c)) * np.exp(-np.arange(N_c) % 64 / 16.0)).astype(np.float32)
+    Mcd = _dev(torch, Mc)
+    Mcw = tsr.cdf97_forward(Mcd.reshape(K * J, N_c), nu_c).reshape(K, J, -1).cpu().numpy()
+    comp_c = tsr.compress(Mcd, nu_c, "cdf97", "top", 0.2)
+    comps.append(comp_c)
+    kepts.append(np.where(O.select_top(Mcw, nu_c, 0.2), Mcw.astype(np.float64), 0.0))
+    nus.append(nu_c)
+    light = rng.standard_normal(J).astype(np.float32)
+    for E in (1, 2, 3):
+        g = rng.standard_normal((len(comps), E, 3, K)).astype(np.float32)
+        Bs = tsr.relight_many(comps, _dev(torch, g), _dev(torch, light))
+        torch.cuda.synchronize()
+        for i, (B, kept, nu) in enumerate(zip(Bs, kepts, nus)):
+            wav = "cdf97" if i == len(comps) - 1 else "haar"
+            B_ref = O.relight(kept, nu, g[i].astype(np.float64), light.astype(np.float64), wavelet=wav)
+            err = _relight_err(B.cpu().numpy(), B_ref)
+            assert err <= (1e-5 if wav == "cdf97" else 2e-6), (E, i, nu, err)
+    # 70 copies: three fused launches of at most 32 copies, results equal to relighting each alone
+    many = [comps[i % 6] for i in range(70)]
+    g = rng.standard_normal((70, 1, 3, K)).astype(np.float32)
+    gd = _dev(torch, g)
+    Bs = tsr.relight_many(many, gd, _dev(torch, light))
+    for i in (0, 31, 32, 63, 64, 69):
+        want = tsr.relight(many[i], gd[i], _dev(torch, light))
+        assert torch.equal(Bs[i], want), i
+
+
+def test_relight_many_rejects_mismatched_handles(torch_cuda, tsr):
+    torch = torch_cuda
+    a, _ = _compressed_case(torch, tsr, 4, 4, 5, 0.2, 1)
+    b, _ = _compressed_case(torch, tsr, 4, 3, 5, 0.2, 2)
+    g = torch.zeros((2, 1, 3, 4), device="cuda")
+    with pytest.raises(tsr.TsrError):
+        tsr.relight_many([a, b], g, torch.zeros(5, device="cuda"))
+
+
 @pytest.mark.parametrize("nu,K,J,E,p", [(4, 8, 9, 5, 0.1), (5, 12, 16, 3, 0.2), (8, 16, 25, 11, 0.05)])
 def test_relight_backward_matches_oracle(torch_cuda, tsr, nu, K, J, E, p):
     torch = torch_cuda

@@ -57,6 +57,16 @@ def test_argument_checks_run_before_any_device_work(libtsr):
     g = libtsr.tsr_haar_forward
     g.restype = ctypes.c_int
     assert g(None, 1, 4, None, None) == -1
+    m = libtsr.tsr_relight_many
+    m.restype = ctypes.c_int
+    m.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_void_p]
+    assert m(-1, None, 1, None, None, None, None) == -1
+    assert m(2, None, 1, None, None, None, None) == -1
+    handles = (ctypes.c_void_p * 2)(None, None)
+    buf = ctypes.create_string_buffer(64)
+    assert m(2, ctypes.cast(handles, ctypes.c_void_p), 1, ctypes.addressof(buf), ctypes.addressof(buf),
+             ctypes.addressof(buf), None) == -1
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
