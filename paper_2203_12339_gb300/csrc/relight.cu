@@ -83,12 +83,17 @@ __global__ void __launch_bounds__(256) relight_direct_kernel(const int64_t *__re
   __syncthreads();
   const int sub = threadIdx.x % RL_LPR;
   const int groups = gridDim.x * (blockDim.x / RL_LPR);
-  for (int w = blockIdx.x * (blockDim.x / RL_LPR) + threadIdx.x / RL_LPR; w < n_rows; w += groups) {
+  // the loop runs the same number of times in every lane of a warp (the xor-shuffles
+  // below name all 32 lanes); groups past the last row sum nothing
+  const int w_first = blockIdx.x * (blockDim.x / RL_LPR) + (threadIdx.x & ~31) / RL_LPR;
+  for (int wb = w_first; wb < n_rows; wb += groups) {
+    const int w = wb + (threadIdx.x & 31) / RL_LPR;
     float acc[VV];
 #pragma unroll
     for (int v = 0; v < VV; ++v) acc[v] = 0.0f;
-    const int64_t pe = row_ptr[w + 1];
-    for (int64_t p = row_ptr[w] + sub; p < pe; p += RL_LPR) {
+    const bool row_ok = w < n_rows;
+    const int64_t pe = row_ok ? row_ptr[w + 1] : 0;
+    for (int64_t p = row_ok ? row_ptr[w] + sub : 0; p < pe; p += RL_LPR) {
       const float a = val[p];
       const float *c = cs + (int)col[p] * VV;
 #pragma unroll
@@ -98,7 +103,7 @@ __global__ void __launch_bounds__(256) relight_direct_kernel(const int64_t *__re
     for (int v = 0; v < VV; ++v)
 #pragma unroll
       for (int o = RL_LPR / 2; o > 0; o >>= 1) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
-    if (sub == 0)
+    if (sub == 0 && row_ok)
 #pragma unroll
       for (int v = 0; v < VV; ++v) bw[(size_t)v * n_rows + w] = acc[v];
   }
