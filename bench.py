@@ -183,6 +183,97 @@ def relight_frame_1080p(tsr, dev, peaks) -> dict:
                              "frac": round(achieved / peak, 4), "bytes_per_frame": int(frame_bytes)}}
 
 
+def batched_scene(tsr, dev, peaks, n_mesh: int = 256, n_edit: int = 1024) -> dict:
+    """The uneven batch: n_mesh displaced icospheres (vertex counts log-uniform in 642-40,962, seeds 1000 + b,
+    amplitude 0.1, 3 octaves), K=12, J=16.  One pass = the BF16 transfer of every mesh in one persistent launch
+    (autotuned plan), Step 2 of every mesh read in place from the batched M (top 10 %), and the relight of
+    n_edit material edits (projected once, shared by the meshes) on every mesh: basis images of all meshes in
+    one fused pass, then one combine writing n_edit x 3 x sum(N) outputs.  Timed per stage (CUDA events,
+    eager) and as one CUDA-graph replay of the whole pass."""
+    import torch
+    from paper_2203_12339_gb300 import scene
+    K, J = 12, 16
+    nus = scene.batched_nus(n_mesh, seed=4)
+    meshes = [scene.make_scene(int(nu), K=K, J=J, amp=0.1, octaves=3, seed=1000 + b) for b, nu in enumerate(nus)]
+    offs = np.concatenate([[0], np.cumsum([m.n for m in meshes])]).astype(np.int64)
+    total = int(offs[-1])
+    pos = torch.tensor(np.concatenate([m.mesh.pos for m in meshes]).astype(np.float32).T.copy(), device=dev)
+    area = torch.tensor(np.concatenate([m.mesh.area for m in meshes]).astype(np.float32), device=dev)
+    T = torch.tensor(np.concatenate([m.T for m in meshes], axis=1).astype(np.float32), device=dev)
+    light = torch.tensor(meshes[0].light.astype(np.float32), device=dev)
+    del meshes
+    sa_pca, ss_pca = scene.pca_materials(256, seed=0)
+    basis, _ = tsr.fit_pca_basis(torch.tensor(sa_pca, device=dev), torch.tensor(ss_pca, device=dev), 1.3, 1024,
+                                 40.0, K)
+    esa, ess, eeta = scene.edit_materials(n_edit, seed=6)
+    _, g32, _ = tsr.project_material(basis, torch.tensor(esa, device=dev), torch.tensor(ess, device=dev),
+                                     torch.tensor(eeta, device=dev))
+    g_all = g32.unsqueeze(0).expand(n_mesh, n_edit, 3, K).contiguous()
+    plan = tsr.BatchPlan(basis, offs, J, "bf16")
+    M = torch.empty((K, J, total), device=dev, dtype=torch.float32)
+    plan.autotune(pos, area, T, out=M)
+    plan.run(pos, area, T, out=M)
+    comps = tsr.haar_compress_batched(M, offs, 0.10)
+    B = torch.empty(n_edit * 3 * total, device=dev, dtype=torch.float32)
+    stages = (lambda: plan.run(pos, area, T, out=M),
+              lambda: tsr.haar_recompress_batched(M, offs, comps),
+              lambda: tsr.relight_many(comps, g_all, light, out=B))
+    for f in stages:
+        f()
+    torch.cuda.synchronize()
+    ms = []
+    for f in stages:
+        reps = []
+        for _ in range(3):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            f()
+            b.record()
+            torch.cuda.synchronize()
+            reps.append(a.elapsed_time(b))
+        ms.append(statistics.median(reps))
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side, capture_error_mode="thread_local"):
+            for f in stages:
+                f()
+    torch.cuda.current_stream().wait_stream(side)
+    graph.replay()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(3):
+        graph.replay()
+    b.record()
+    torch.cuda.synchronize()
+    tsr.stream_status()
+    graph_ms = a.elapsed_time(b) / 3
+    n_per = offs[1:] - offs[:-1]
+    pairs = float(np.sum(n_per.astype(np.float64) ** 2))
+    out_bytes = 4.0 * n_edit * 3 * total
+    nnz = sum(c.nnz for c in comps)
+    relight_bytes = out_bytes + 6.0 * nnz
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    info = plan.info()
+    res = {"workload": f"{n_mesh} uneven displaced icospheres ({int(n_per.min())}-{int(n_per.max())} vertices, "
+                       f"{total} in all), K={K}, J={J}, BF16 transfer, top-10 % Haar, {n_edit} edits per mesh",
+           "pairs": pairs, "bases_per_group": info["bases_per_group"],
+           "transfer_ms": round(ms[0], 3), "transfer_g_pair_kj_per_s": round(pairs * K * J / (ms[0] * 1e-3) / 1e9, 1),
+           "compress_ms": round(ms[1], 3), "relight_ms": round(ms[2], 3),
+           "relight_hbm_roofline": {"bound": "hbm", "achieved": round(relight_bytes / (ms[2] * 1e-3) / 1e9, 1),
+                                    "peak": peak, "unit": "GB/s",
+                                    "frac": round(relight_bytes / (ms[2] * 1e-3) / 1e9 / peak, 4),
+                                    "bytes": int(relight_bytes)},
+           "graph_ms": round(graph_ms, 3)}
+    del B, M, comps, g_all
+    torch.cuda.empty_cache()
+    return res
+
+
 def energy_keep_curve(tsr, M, nu, g32, light) -> list:
     """The energy keep rule on the benchmark transfer: per retained-energy fraction, the kept share
     of the chart coefficients, the compression time (one host synchronisation inside) and the
@@ -488,6 +579,8 @@ def run_gpu(args):
     line["visibility_transfer"] = visibility_timing(tsr, dev)
     if not args.no_frame_1080p:
         line["relight_frame_1080p"] = relight_frame_1080p(tsr, dev, peaks)
+    if not args.no_batched and world == 1:   # a one-GPU measurement of the uneven batch
+        line["batched_scene"] = batched_scene(tsr, dev, peaks)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(rows=args.cpu_rows)
     if rank == 0:
@@ -577,6 +670,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-sweep", action="store_true")
     ap.add_argument("--no-frame-1080p", action="store_true", help="skip the 13 x 163,842-vertex relight frame")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-mesh batch (transfer, Step 2, relight)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -225,6 +225,24 @@ tsr_status tsr_wavelet_compress(const float *Mw, int K, int J, int nu, double p,
 tsr_status tsr_haar_compress(const float *M, int K, int J, int nu, double p, tsr_compressed **out,
                              tsr_stream stream);
 tsr_status tsr_haar_recompress(const float *M, tsr_compressed *c, tsr_stream stream);
+/* Step 2 (Section 3, Eq. 9-10) for every mesh of a batched transfer: M is the
+ * device [K][J][total] output of tsr_precompute_transfer_batched (mesh b's
+ * values at columns offsets[b] .. offsets[b+1]-1 of every (k, j) row, read in
+ * place with row stride total); offsets: HOST [n_mesh + 1] int64, each mesh
+ * 10 nu^2 + 2 vertices (nu <= 128).  Per mesh: the Haar analysis of its rows and
+ * the top-fraction selection of tsr_haar_compress, one launch per kernel per mesh.
+ *   tsr_haar_compress_batched   creates the n_mesh handles in out (HOST array;
+ *                               allocates device memory, synchronises); on error
+ *                               none is left (out[b] = NULL).
+ *   tsr_haar_recompress_batched refills them for a new M (Haar top-fraction
+ *                               handles whose nu matches each mesh); stream-ordered
+ *                               scratch only, so it may be captured in a CUDA graph.
+ * TSR_ERR_INVALID_ARG for NULL pointers, a mesh size not of the chart form, or a
+ * handle that does not fit its mesh. */
+tsr_status tsr_haar_compress_batched(int n_mesh, const int64_t *offsets, const float *M, int K, int J, double p,
+                                     tsr_compressed **out, tsr_stream stream);
+tsr_status tsr_haar_recompress_batched(int n_mesh, const int64_t *offsets, const float *M,
+                                       tsr_compressed *const *c, tsr_stream stream);
 /* The paper's Step-2 wavelet (Section 5, "Daubechies 9/7"): the CDF 9/7
  * biorthogonal pair by lifting (whole-sample symmetric extension, low band DC
  * gain sqrt 2), as the separable 2D Mallat pyramid of each chart's P x P image
@@ -342,11 +360,14 @@ tsr_status tsr_relight_backward(const tsr_compressed *c, int n_edit, const float
  *   g      : device [n_copy][n_edit][3][K] FP32;  l: device [J] FP32;
  *   B      : device FP32 out, the copies' [n_edit][3][N_i] blocks back to back
  *            (copy i starts at n_edit * 3 * (N_0 + ... + N_{i-1}), N_i = 10 nu_i^2 + 2).
- * Result per copy: exactly tsr_relight of that copy.  With one or two edits,
- * copies under the orthonormal Haar with charts of P <= 256 go through one
- * fused kernel per 32 copies (b^w = S c and the inverse Haar per chart run in
- * shared memory; no scratch, no allocation); the other copies, and calls with
- * more edits, run tsr_relight copy by copy (stream-ordered scratch).
+ * Result per copy: tsr_relight of that copy (FP32 sums in another order for
+ * more than two edits).  Copies under the orthonormal Haar go through fused
+ * kernels, 32 copies per launch: with one or two edits b^w = S c and the inverse
+ * Haar per chart run in shared memory (no scratch); with more, the
+ * light-contracted basis images Z[k] = W^-1 (S (e_k x l)) of every copy in one
+ * such pass, then B = sum_k g_k Z[k] for all copies and edits in one launch
+ * (stream-ordered scratch K (N_0 + ... ) floats).  CDF 9/7 copies run
+ * tsr_relight copy by copy.
  * Errors: TSR_ERR_INVALID_ARG for NULL or misaligned pointers, a NULL handle or
  * handles whose K or J differ from the first one's; nothing is launched then.
  * ---------------------------------------------------------------------- */

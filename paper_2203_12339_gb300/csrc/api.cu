@@ -263,6 +263,78 @@ extern "C" tsr_status tsr_haar_recompress(const float *M, tsr_compressed *c, tsr
   return wavelet_compress_into(static_cast<float *>(mw.p), c, s);
 }
 
+// nu of a mesh of N vertices in the chart layout (N = 10 nu^2 + 2), or 0.
+static int chart_nu_of(int64_t N) {
+  for (int nu = 1; nu <= 128; ++nu)
+    if (10 * (int64_t)nu * nu + 2 == N) return nu;
+  return 0;
+}
+
+extern "C" tsr_status tsr_haar_compress_batched(int n_mesh, const int64_t *offsets, const float *M, int K, int J,
+                                                double p, tsr_compressed **out, tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(offsets && M && out, "tsr_haar_compress_batched: NULL argument");
+  TSR_CHECK_ARG(n_mesh >= 1 && n_mesh <= 65536, "tsr_haar_compress_batched: n_mesh=%d out of range", n_mesh);
+  TSR_CHECK_ARG(K >= 1 && K <= 16 && J >= 1 && J <= 32, "tsr_haar_compress_batched: K=%d J=%d out of range", K, J);
+  TSR_CHECK_ARG(p >= 0.0 && p <= 1.0, "tsr_haar_compress_batched: p=%g outside [0, 1]", p);
+  TSR_CHECK_ARG(offsets[0] == 0, "tsr_haar_compress_batched: offsets[0] must be 0");
+  for (int b = 0; b < n_mesh; ++b) {
+    out[b] = nullptr;
+    TSR_CHECK_ARG(chart_nu_of(offsets[b + 1] - offsets[b]) > 0,
+                  "tsr_haar_compress_batched: mesh %d has %lld vertices, not 10 nu^2 + 2 with nu <= 128", b,
+                  (long long)(offsets[b + 1] - offsets[b]));
+  }
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  const long long total = offsets[n_mesh];
+  for (int b = 0; b < n_mesh && st == TSR_OK; ++b) {
+    const int nu = chart_nu_of(offsets[b + 1] - offsets[b]), P = chart_side(nu);
+    Scratch mw;
+    st = mw.alloc(sizeof(float) * (size_t)K * J * (10 * P * P + 2), s);
+    if (st == TSR_OK) st = haar_forward_ld(M + offsets[b], total, K * J, nu, static_cast<float *>(mw.p), s);
+    if (st == TSR_OK) st = wavelet_compress(static_cast<float *>(mw.p), K, J, nu, p, &out[b], s);
+  }
+  if (st != TSR_OK)
+    for (int b = 0; b < n_mesh; ++b) {
+      tsr_compressed_destroy(out[b]);
+      out[b] = nullptr;
+    }
+  return st;
+}
+
+extern "C" tsr_status tsr_haar_recompress_batched(int n_mesh, const int64_t *offsets, const float *M,
+                                                  tsr_compressed *const *c, tsr_stream stream) {
+  clear_error();
+  TSR_CHECK_ARG(offsets && M && c, "tsr_haar_recompress_batched: NULL argument");
+  TSR_CHECK_ARG(n_mesh >= 1 && n_mesh <= 65536, "tsr_haar_recompress_batched: n_mesh=%d out of range", n_mesh);
+  TSR_CHECK_ARG(offsets[0] == 0, "tsr_haar_recompress_batched: offsets[0] must be 0");
+  size_t mw_max = 0;
+  for (int b = 0; b < n_mesh; ++b) {
+    TSR_CHECK_ARG(c[b], "tsr_haar_recompress_batched: handle %d is NULL", b);
+    TSR_CHECK_ARG(c[b]->wavelet == 0 && c[b]->keep_rule == 0,
+                  "tsr_haar_recompress_batched: handle %d is not a Haar top-fraction handle", b);
+    TSR_CHECK_ARG(offsets[b + 1] - offsets[b] == 10 * (int64_t)c[b]->nu * c[b]->nu + 2,
+                  "tsr_haar_recompress_batched: mesh %d has %lld vertices, its handle nu=%d", b,
+                  (long long)(offsets[b + 1] - offsets[b]), c[b]->nu);
+    mw_max = std::max(mw_max, (size_t)c[b]->K * c[b]->J * c[b]->n_rows);
+  }
+  tsr_status st = require_device();
+  if (st != TSR_OK) return st;
+  cudaStream_t s = as_stream(stream);
+  const long long total = offsets[n_mesh];
+  Scratch mw;   // one wavelet buffer, reused mesh after mesh (stream order)
+  st = mw.alloc(sizeof(float) * mw_max, s);
+  if (st != TSR_OK) return st;
+  float *Mw = static_cast<float *>(mw.p);
+  for (int b = 0; b < n_mesh; ++b) {
+    st = haar_forward_ld(M + offsets[b], total, c[b]->K * c[b]->J, c[b]->nu, Mw, s);
+    if (st == TSR_OK) st = wavelet_compress_into(Mw, c[b], s);
+    if (st != TSR_OK) return st;
+  }
+  return TSR_OK;
+}
+
 extern "C" tsr_status tsr_compressed_info(const tsr_compressed *c, int *K, int *J, int *nu, int64_t *nnz,
                                           int *n_rows) {
   clear_error();
@@ -314,24 +386,43 @@ extern "C" tsr_status tsr_relight_many(int n_copy, const tsr_compressed *const *
   if (st != TSR_OK || n_edit == 0) return st;
   cudaStream_t s = as_stream(stream);
   const size_t V = 3 * (size_t)n_edit, K = (size_t)c[0]->K;
+  const bool few = n_edit <= 2;
   std::vector<const tsr_compressed *> fc;
   std::vector<const float *> fg;
   std::vector<float *> fb;
-  size_t off = 0;
+  std::vector<int> fn;
+  size_t off = 0, z_total = 0;
   for (int i = 0; i < n_copy; ++i) {
     const float *gi = g + (size_t)i * V * K;
     float *Bi = B + off;
-    off += V * (10 * (size_t)c[i]->nu * c[i]->nu + 2);
-    if (relight_fusable(c[i], n_edit)) {
+    const int Ni = 10 * c[i]->nu * c[i]->nu + 2;
+    off += V * (size_t)Ni;
+    if (few ? relight_fusable(c[i], n_edit) : relight_fusable_basis(c[i])) {
       fc.push_back(c[i]);
       fg.push_back(gi);
       fb.push_back(Bi);
+      fn.push_back(Ni);
+      z_total += K * (size_t)Ni;
     } else {
       st = relight(c[i], n_edit, gi, l, Bi, s);
       if (st != TSR_OK) return st;
     }
   }
-  return relight_fused((int)fc.size(), fc.data(), n_edit, fg.data(), l, fb.data(), s);
+  if (fc.empty()) return TSR_OK;
+  if (few) return relight_fused((int)fc.size(), fc.data(), n_edit, fg.data(), l, fb.data(), s);
+  // more edits: the light-contracted basis images of every copy, then one combine
+  Scratch sc;
+  st = sc.alloc(sizeof(float) * z_total, s);
+  if (st != TSR_OK) return st;
+  std::vector<float *> zi(fc.size());
+  float *zp = static_cast<float *>(sc.p);
+  for (size_t i = 0; i < fc.size(); ++i) {
+    zi[i] = zp;
+    zp += K * (size_t)fn[i];
+  }
+  st = relight_basis_images_many((int)fc.size(), fc.data(), l, zi.data(), s);
+  if (st != TSR_OK) return st;
+  return relight_combine_many((int)fc.size(), zi.data(), fn.data(), (int)K, (int)V, fg.data(), fb.data(), s);
 }
 
 extern "C" tsr_status tsr_relight_backward(const tsr_compressed *c, int n_edit, const float *g, const float *l,

@@ -74,6 +74,8 @@ tsr_status transfer_tc_batched(const tsr_basis *b, int n_mesh, const int64_t *of
 tsr_status transfer_fp32_batched(const tsr_basis *b, int n_mesh, const int64_t *offsets, const float *pos,
                                  const float *area, const float *T, int J, float *M, cudaStream_t s);
 tsr_status haar_forward(const float *X, int rows, int nu, float *Xw, cudaStream_t s);
+// The same with input rows ldx apart (ldx >= 10 nu^2 + 2), e.g. one mesh of a batched M.
+tsr_status haar_forward_ld(const float *X, long long ldx, int rows, int nu, float *Xw, cudaStream_t s);
 tsr_status haar_inverse(const float *Xw, int rows, int nu, float *X, cudaStream_t s);
 tsr_status cdf97_forward(const float *X, int rows, int nu, float *Xw, cudaStream_t s);
 tsr_status cdf97_inverse(const float *Xw, int rows, int nu, float *X, cudaStream_t s);
@@ -102,10 +104,18 @@ tsr_status relight_backward(const tsr_compressed *c, int n_edit, const float *g,
 // Floats of caller-provided scratch relight_with_scratch needs: K (10 P^2 + 2 + N).
 size_t relight_scratch_floats(const tsr_compressed *c);
 // Steps 4-5 for one or two edits with the product and the inverse Haar fused, over
-// n compressed transfers (Haar, P <= 256, same K and J) in one launch per 32.
+// n compressed transfers (Haar, P <= 128, same K and J) in one launch per 32.
 bool relight_fusable(const tsr_compressed *c, int n_edit);
 tsr_status relight_fused(int n, const tsr_compressed *const *c, int n_edit, const float *const *gi, const float *l,
                          float *const *Bi, cudaStream_t s);
+// The factorised relight over n copies (Haar, P <= 128, same K and J; any number of
+// edits): the light-contracted basis images Z_i ([K][N_i]) in one fused pass per 32
+// copies, then B_i[v] = sum_k g_i[v][k] Z_i[k] in one combine launch per 32 copies.
+bool relight_fusable_basis(const tsr_compressed *c);
+tsr_status relight_basis_images_many(int n, const tsr_compressed *const *c, const float *l, float *const *Zi,
+                                     cudaStream_t s);
+tsr_status relight_combine_many(int n, const float *const *Zi, const int *Ni, int K, int V, const float *const *gi,
+                                float *const *Bi, cudaStream_t s);
 tsr_status relight_with_scratch(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,
                                 float *scratch, cudaStream_t s);
 }  // namespace tsr

@@ -117,31 +117,52 @@ static void launch_direct(const tsr_compressed *c, const float *g, const float *
   ::tsr::count_launch();
 }
 
-// B[v][o] = sum_k g[v][k] Z[k][o]: a thread per output vertex o and a chunk of RL_VB vectors.
+// B[v][o] = sum_k g[v][k] Z[k][o]: a thread per output vertex o and a chunk of RL_VB
+// vectors; g staged as float4 rows of KT = K rounded up to 4 (zero padded: no
+// per-basis test in the loop, the padding adds fmaf(0, 0, b) = b).
 constexpr int RL_VB = 32;
+template <int KT>
 __global__ void __launch_bounds__(256) relight_combine_kernel(const float *__restrict__ Z, int N, int K, int V,
                                                              const float *__restrict__ g, float *__restrict__ B) {
-  __shared__ float gs[RL_VB * RL_KMAX];
+  __shared__ float4 gs[RL_VB * KT / 4];
+  float *gsf = reinterpret_cast<float *>(gs);
   const int v0 = blockIdx.y * RL_VB;
-  for (int q = threadIdx.x; q < RL_VB * K; q += blockDim.x) {
-    const int vv = q / K, k = q % K;
-    gs[vv * RL_KMAX + k] = (v0 + vv < V) ? g[(size_t)(v0 + vv) * K + k] : 0.0f;
+  for (int q = threadIdx.x; q < RL_VB * KT; q += blockDim.x) {
+    const int vv = q / KT, k = q % KT;
+    gsf[q] = (v0 + vv < V && k < K) ? g[(size_t)(v0 + vv) * K + k] : 0.0f;
   }
   __syncthreads();
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= N) return;
-  float z[RL_KMAX];
+  float z[KT];
 #pragma unroll
-  for (int k = 0; k < RL_KMAX; ++k) z[k] = (k < K) ? Z[(size_t)k * N + o] : 0.0f;
+  for (int k = 0; k < KT; ++k) z[k] = (k < K) ? Z[(size_t)k * N + o] : 0.0f;
   const int vn = min(RL_VB, V - v0);
   for (int vv = 0; vv < vn; ++vv) {
-    const float *gv = gs + vv * RL_KMAX;
     float b = 0.0f;
 #pragma unroll
-    for (int k = 0; k < RL_KMAX; ++k)
-      if (k < K) b = fmaf(gv[k], z[k], b);
+    for (int h = 0; h < KT / 4; ++h) {
+      const float4 gq = gs[vv * (KT / 4) + h];
+      b = fmaf(gq.x, z[4 * h], b);
+      b = fmaf(gq.y, z[4 * h + 1], b);
+      b = fmaf(gq.z, z[4 * h + 2], b);
+      b = fmaf(gq.w, z[4 * h + 3], b);
+    }
     B[(size_t)(v0 + vv) * N + o] = b;
   }
+}
+
+static void launch_combine(const float *Z, int N, int K, int V, const float *g, float *B, cudaStream_t s) {
+  const dim3 grid((N + 255) / 256, (V + RL_VB - 1) / RL_VB);
+  if (K <= 4)
+    relight_combine_kernel<4><<<grid, 256, 0, s>>>(Z, N, K, V, g, B);
+  else if (K <= 8)
+    relight_combine_kernel<8><<<grid, 256, 0, s>>>(Z, N, K, V, g, B);
+  else if (K <= 12)
+    relight_combine_kernel<12><<<grid, 256, 0, s>>>(Z, N, K, V, g, B);
+  else
+    relight_combine_kernel<16><<<grid, 256, 0, s>>>(Z, N, K, V, g, B);
+  ::tsr::count_launch();
 }
 
 // dg partials: block (vector group of RL_GV, o-split s) forms sum over its o-range of
@@ -311,8 +332,7 @@ tsr_status relight_with_scratch(const tsr_compressed *c, int n_edit, const float
   float *Y = scratch, *Z = scratch + (size_t)c->K * c->n_rows;
   tsr_status st = relight_basis_images(c, l, Y, Z, s);
   if (st != TSR_OK) return st;
-  const dim3 grid((N + 255) / 256, (V + RL_VB - 1) / RL_VB);
-  relight_combine_kernel<<<grid, 256, 0, s>>>(Z, N, c->K, V, g, B); ::tsr::count_launch();
+  launch_combine(Z, N, c->K, V, g, B, s);
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }

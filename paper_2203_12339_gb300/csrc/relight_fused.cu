@@ -46,6 +46,7 @@ struct RelightCopy {
 struct RelightBatch {
   RelightCopy c[RF_MAXC];
   int n;
+  int nv;   // output rows written per copy (the kernel's VV, or K in basis-image mode)
 };
 
 __device__ __forceinline__ unsigned rf_compact(unsigned x) {   // even bits of x, packed
@@ -83,33 +84,37 @@ __device__ __forceinline__ void rf_store(float (*x)[RF_SEG], float (*top)[RF_MAX
 // each aligned block of 32 columns.
 __device__ __forceinline__ int rf_crow(int kj) { return kj ^ ((kj >> 3) & 3); }
 
-// c_v[kj] for one entry, VV of them from the padded row (float4 loads).
+// c_v[kj] for one entry, VV of them from the padded row (float4 loads); one FMA
+// per vector and entry.
 template <int VV>
 __device__ __forceinline__ void rf_fma(const float4 *cs4, int kj, float a, float (&acc)[VV]) {
   constexpr int VQ = (VV + 3) / 4;
   kj = rf_crow(kj);
-  const float4 c0 = cs4[kj * VQ];
-  acc[0] = fmaf(a, c0.x, acc[0]);
-  acc[1] = fmaf(a, c0.y, acc[1]);
-  acc[2] = fmaf(a, c0.z, acc[2]);
-  if (VV > 3) {
-    const float4 c1 = cs4[kj * VQ + (VQ - 1)];
-    acc[3 % VV] = fmaf(a, c0.w, acc[3 % VV]);
-    acc[4 % VV] = fmaf(a, c1.x, acc[4 % VV]);
-    acc[5 % VV] = fmaf(a, c1.y, acc[5 % VV]);
+#pragma unroll
+  for (int h = 0; h < VQ; ++h) {
+    const float4 c = cs4[kj * VQ + h];
+    const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (4 * h + e < VV) acc[4 * h + e] = fmaf(a, cv[e], acc[4 * h + e]);
   }
 }
 
 template <int VV>
-__global__ void __launch_bounds__(RF_THREADS, 5) relight_fused_kernel(const __grid_constant__ RelightBatch bt, int K,
+__global__ void __launch_bounds__(RF_THREADS, VV <= 6 ? 5 : 2) relight_fused_kernel(const __grid_constant__ RelightBatch bt, int K,
                                                                   int J, const float *__restrict__ l) {
   constexpr int VQ = (VV + 3) / 4;   // float4s per c row
+  constexpr bool XDYN = VV > 6;      // x in dynamic shared memory (above 24 KB)
   // Non-empty rows of the block: {first entry - e0, q << 16 | entries}.
   __shared__ int2 lst[RF_MAX_ROWS];
-  __shared__ __align__(16) float x[VV][RF_SEG];
+  __shared__ __align__(16) float xs[XDYN ? 1 : VV][RF_SEG];
   __shared__ float top[VV][RF_MAX_TOP + 2];   // path rows, then the poles
   __shared__ int n_rows_ne;
-  extern __shared__ float4 cs4[];             // [K J rounded up to 32][VQ]: c_v[kj] = g_v[k] l[j] at row rf_crow(kj)
+  // dynamic: [x: VV][RF_SEG] floats when XDYN, then the c table
+  // [K J rounded up to 32][VQ] float4: c_v[kj] = g_v[k] l[j] at row rf_crow(kj)
+  extern __shared__ float4 dyn4[];
+  float (*x)[RF_SEG] = XDYN ? reinterpret_cast<float (*)[RF_SEG]>(dyn4) : xs;
+  float4 *cs4 = dyn4 + (XDYN ? VV * RF_SEG / 4 : 0);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int ci = 0;
@@ -132,7 +137,8 @@ __global__ void __launch_bounds__(RF_THREADS, 5) relight_fused_kernel(const __gr
   const int64_t e0 = row_ptr[wbase];   // entries of the block's rows lie in [e0, e0 + 2^31 - 4)
 
   // Empty rows contribute zeros.
-  for (int q = tid; q < VV * RF_SEG; q += RF_THREADS) (&x[0][0])[q] = 0.0f;
+  for (int q = tid; q < VV * RF_SEG / 4; q += RF_THREADS)
+    reinterpret_cast<float4 *>(&x[0][0])[q] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   if (tid < VV * (RF_MAX_TOP + 2)) (&top[0][0])[tid] = 0.0f;
   if (tid == 0) n_rows_ne = 0;
   const int KJ = K * J;
@@ -141,7 +147,8 @@ __global__ void __launch_bounds__(RF_THREADS, 5) relight_fused_kernel(const __gr
     const float lj = l[q - k * J];
     float c[4 * VQ];
 #pragma unroll
-    for (int v = 0; v < 4 * VQ; ++v) c[v] = v < VV ? cp.g[v * K + k] * lj : 0.0f;
+    for (int v = 0; v < 4 * VQ; ++v)   // basis-image mode (no g): c_v[kj] = l[j] for v = k, else 0
+      c[v] = v < VV ? (cp.g ? cp.g[v * K + k] : (v == k ? 1.0f : 0.0f)) * lj : 0.0f;
 #pragma unroll
     for (int h = 0; h < VQ; ++h)
       cs4[rf_crow(q) * VQ + h] = make_float4(c[4 * h], c[4 * h + 1], c[4 * h + 2], c[4 * h + 3]);
@@ -269,7 +276,8 @@ __global__ void __launch_bounds__(RF_THREADS, 5) relight_fused_kernel(const __gr
   const int r0 = (int)rf_compact(m0 >> 1), c0 = (int)rf_compact(m0);
   const int N = 10 * nu * nu + 2;
   float *__restrict__ B = cp.B;
-  for (int it = tid; it < (VV << lgI); it += RF_THREADS) {
+  const int nv = bt.nv;
+  for (int it = tid; it < (nv << lgI); it += RF_THREADS) {
     const int v = it >> lgI, t = it & ((1 << lgI) - 1);
     float a = top[v][0];
     for (int lv = 0; lv < lgn; ++lv) {
@@ -301,36 +309,49 @@ __global__ void __launch_bounds__(RF_THREADS, 5) relight_fused_kernel(const __gr
       if (r < nu && c < nu) B[(size_t)v * N + (size_t)d * nu * nu + (size_t)r * nu + c] = out[b];
     }
   }
-  if (poles && tid < VV) {
+  if (poles && tid < nv) {
     B[(size_t)tid * N + 10 * (size_t)nu * nu] = top[tid][RF_MAX_TOP];
     B[(size_t)tid * N + 10 * (size_t)nu * nu + 1] = top[tid][RF_MAX_TOP + 1];
   }
 }
 
 bool relight_fusable(const tsr_compressed *c, int n_edit) {
-  return c->wavelet == 0 && n_edit >= 1 && n_edit <= 2 && c->P <= (1 << (RF_MAX_LGN / 2 + 5)) && c->nnz < (1ll << 31);
+  return c->wavelet == 0 && n_edit >= 1 && n_edit <= 2 && relight_fusable_basis(c);
 }
 
-// Copies must all be fusable for n_edit and share K and J; copy i reads g from gi[i]
-// ([n_edit][3][K]) and writes B to Bi[i] ([n_edit][3][N_i]).
-tsr_status relight_fused(int n, const tsr_compressed *const *c, int n_edit, const float *const *gi, const float *l,
-                         float *const *Bi, cudaStream_t s) {
-  if (n <= 0) return TSR_OK;
-  const int K = c[0]->K, J = c[0]->J, VV = 3 * n_edit;
-  const size_t smem = sizeof(float4) * (size_t)((K * J + 31) & ~31) * (VV == 3 ? 1 : 2);
-  if (VV == 6) {   // 33 KB static + up to 16 KB of c: above the default 48 KB (set once per device)
+bool relight_fusable_basis(const tsr_compressed *c) {
+  return c->wavelet == 0 && c->P <= (1 << (RF_MAX_LGN / 2 + 5)) && c->nnz < (1ll << 31);
+}
+
+// Dynamic shared memory of relight_fused_kernel<VV>: x (VV > 6) and the c table.
+template <int VV>
+static size_t fused_smem(int K, int J) {
+  constexpr int VQ = (VV + 3) / 4;
+  return (VV > 6 ? sizeof(float) * VV * RF_SEG : 0) + sizeof(float4) * (size_t)((K * J + 31) & ~31) * VQ;
+}
+
+// Launches relight_fused_kernel<VV> over the copies, RF_MAXC per launch.  g: per-copy
+// [nv][K] pointers, or all null for the basis images (nv = K rows: c_k[kj] = l[j] for
+// the entries of basis k).
+template <int VV>
+static tsr_status launch_fused(int n, const tsr_compressed *const *c, int nv, const float *const *gi, const float *l,
+                               float *const *Bi, cudaStream_t s) {
+  const int K = c[0]->K, J = c[0]->J;
+  const size_t smem = fused_smem<VV>(K, J);
+  {   // dynamic shared memory up to the largest case (K = 16, J = 32), set once per device
     static bool attr_set[64] = {};
     int dev = 0;
     TSR_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-      TSR_CUDA(cudaFuncSetAttribute(relight_fused_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)(sizeof(float4) * 16 * 32 * 2)));
+      TSR_CUDA(cudaFuncSetAttribute(relight_fused_kernel<VV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)fused_smem<VV>(16, 32)));
       if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
   }
   for (int b0 = 0; b0 < n; b0 += RF_MAXC) {
     RelightBatch bt{};
     bt.n = std::min(RF_MAXC, n - b0);
+    bt.nv = nv;
     int items = 0;
     for (int i = 0; i < bt.n; ++i) {
       const tsr_compressed *h = c[b0 + i];
@@ -338,21 +359,125 @@ tsr_status relight_fused(int n, const tsr_compressed *const *c, int n_edit, cons
       cp.row_ptr = h->row_ptr;
       cp.col = h->col;
       cp.val = h->val;
-      cp.g = gi[b0 + i];
+      cp.g = gi ? gi[b0 + i] : nullptr;
       cp.B = Bi[b0 + i];
       cp.nu = h->nu;
       cp.lgP = ilog2(h->P);
       cp.item0 = items;
       items += 10 * std::max(1, (h->P * h->P) / RF_SEG);
     }
-    if (VV == 3)
-      relight_fused_kernel<3><<<items, RF_THREADS, smem, s>>>(bt, K, J, l);
-    else
-      relight_fused_kernel<6><<<items, RF_THREADS, smem, s>>>(bt, K, J, l);
+    relight_fused_kernel<VV><<<items, RF_THREADS, smem, s>>>(bt, K, J, l);
     ::tsr::count_launch();
     TSR_CUDA(cudaGetLastError());
   }
   return TSR_OK;
+}
+
+// Copies must all be fusable for n_edit and share K and J; copy i reads g from gi[i]
+// ([n_edit][3][K]) and writes B to Bi[i] ([n_edit][3][N_i]).
+tsr_status relight_fused(int n, const tsr_compressed *const *c, int n_edit, const float *const *gi, const float *l,
+                         float *const *Bi, cudaStream_t s) {
+  if (n <= 0) return TSR_OK;
+  return n_edit == 1 ? launch_fused<3>(n, c, 3, gi, l, Bi, s) : launch_fused<6>(n, c, 6, gi, l, Bi, s);
+}
+
+// Z_i[k] = w_1^{-1} (S_i (e_k x l)) for every copy (Zi[i]: [K][N_i]), one fused pass
+// per 32 copies: the light-contracted basis images of the factorised relight.
+tsr_status relight_basis_images_many(int n, const tsr_compressed *const *c, const float *l, float *const *Zi,
+                                     cudaStream_t s) {
+  if (n <= 0) return TSR_OK;
+  const int K = c[0]->K;
+  if (K <= 3) return launch_fused<3>(n, c, K, nullptr, l, Zi, s);
+  if (K <= 6) return launch_fused<6>(n, c, K, nullptr, l, Zi, s);
+  if (K <= 12) return launch_fused<12>(n, c, K, nullptr, l, Zi, s);
+  return launch_fused<16>(n, c, K, nullptr, l, Zi, s);
+}
+
+// ---------------------------------------------------------------- combine, many copies
+// B_i[v][o] = sum_k g_i[v][k] Z_i[k][o] for every copy i: a block per (256 vertices of
+// one copy, RC_VB vectors), the K values of Z of its vertex held in registers, the
+// vectors' g in shared memory as float4 rows of KT = K rounded up to 4 (zero padded,
+// so the loop has no per-basis test; the padding adds fmaf(0, 0, b) = b).  Same
+// arithmetic as relight_combine_kernel.
+constexpr int RC_VB = 32;
+struct CombineCopy {
+  const float *Z;   // [K][N]
+  const float *g;   // [V][K]
+  float *B;         // [V][N]
+  int N;
+  int blk0;         // first vertex block of the copy
+};
+struct CombineBatch {
+  CombineCopy c[RF_MAXC];
+  int n, K, V;
+};
+
+template <int KT>
+__global__ void __launch_bounds__(256) relight_combine_many_kernel(const __grid_constant__ CombineBatch cb) {
+  __shared__ float4 gs[RC_VB * KT / 4];
+  int ci = 0;
+  while (ci + 1 < cb.n && cb.c[ci + 1].blk0 <= (int)blockIdx.x) ++ci;
+  const CombineCopy &cp = cb.c[ci];
+  const int K = cb.K, V = cb.V, N = cp.N;
+  const int v0 = blockIdx.y * RC_VB;
+  float *gsf = reinterpret_cast<float *>(gs);
+  for (int q = threadIdx.x; q < RC_VB * KT; q += blockDim.x) {
+    const int vv = q / KT, k = q - vv * KT;
+    gsf[q] = (v0 + vv < V && k < K) ? cp.g[(size_t)(v0 + vv) * K + k] : 0.0f;
+  }
+  __syncthreads();
+  const int o = ((int)blockIdx.x - cp.blk0) * blockDim.x + threadIdx.x;
+  if (o >= N) return;
+  float z[KT];
+#pragma unroll
+  for (int k = 0; k < KT; ++k) z[k] = (k < K) ? __ldg(cp.Z + (size_t)k * N + o) : 0.0f;
+  const int vn = min(RC_VB, V - v0);
+  float *__restrict__ B = cp.B + (size_t)v0 * N + o;
+  for (int vv = 0; vv < vn; ++vv) {
+    float b = 0.0f;
+#pragma unroll
+    for (int h = 0; h < KT / 4; ++h) {
+      const float4 gq = gs[vv * (KT / 4) + h];
+      b = fmaf(gq.x, z[4 * h], b);
+      b = fmaf(gq.y, z[4 * h + 1], b);
+      b = fmaf(gq.z, z[4 * h + 2], b);
+      b = fmaf(gq.w, z[4 * h + 3], b);
+    }
+    B[(size_t)vv * N] = b;
+  }
+}
+
+template <int KT>
+static tsr_status launch_combine_many(int n, const float *const *Zi, const int *Ni, int K, int V,
+                                      const float *const *gi, float *const *Bi, cudaStream_t s) {
+  for (int b0 = 0; b0 < n; b0 += RF_MAXC) {
+    CombineBatch cb{};
+    cb.n = std::min(RF_MAXC, n - b0);
+    cb.K = K;
+    cb.V = V;
+    int blocks = 0;
+    for (int i = 0; i < cb.n; ++i) {
+      CombineCopy &cp = cb.c[i];
+      cp.Z = Zi[b0 + i];
+      cp.g = gi[b0 + i];
+      cp.B = Bi[b0 + i];
+      cp.N = Ni[b0 + i];
+      cp.blk0 = blocks;
+      blocks += (cp.N + 255) / 256;
+    }
+    relight_combine_many_kernel<KT><<<dim3(blocks, (V + RC_VB - 1) / RC_VB), 256, 0, s>>>(cb);
+    ::tsr::count_launch();
+    TSR_CUDA(cudaGetLastError());
+  }
+  return TSR_OK;
+}
+
+tsr_status relight_combine_many(int n, const float *const *Zi, const int *Ni, int K, int V, const float *const *gi,
+                                float *const *Bi, cudaStream_t s) {
+  if (K <= 4) return launch_combine_many<4>(n, Zi, Ni, K, V, gi, Bi, s);
+  if (K <= 8) return launch_combine_many<8>(n, Zi, Ni, K, V, gi, Bi, s);
+  if (K <= 12) return launch_combine_many<12>(n, Zi, Ni, K, V, gi, Bi, s);
+  return launch_combine_many<16>(n, Zi, Ni, K, V, gi, Bi, s);
 }
 
 }  // namespace tsr

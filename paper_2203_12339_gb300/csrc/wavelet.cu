@@ -37,14 +37,14 @@ constexpr int HAAR_SEG_THREADS = 256;
 // approximations ping-pong in shared memory, the details of each level are final
 // and go straight to their global positions; the run's approximation goes to
 // A[row][d][seg] (or, for a whole chart, to Xw position 0 with the poles).
-__global__ void __launch_bounds__(1024) haar_forward_kernel(const float *__restrict__ X, int nu, int P, int N, int NW,
-                                                           int seg_len, float *__restrict__ Xw,
+__global__ void __launch_bounds__(1024) haar_forward_kernel(const float *__restrict__ X, int nu, int P, long long ldx,
+                                                           int NW, int seg_len, float *__restrict__ Xw,
                                                            float *__restrict__ A) {
   extern __shared__ float sh[];
   float *b0 = sh, *b1 = sh + seg_len;
   const int P2 = P * P, nseg = P2 / seg_len;
   const int seg = blockIdx.x % nseg, d = (blockIdx.x / nseg) % 10, row = blockIdx.x / (nseg * 10);
-  const float *x = X + (size_t)row * N + (size_t)d * nu * nu;
+  const float *x = X + (size_t)row * ldx + (size_t)d * nu * nu;
   float *out = Xw + (size_t)row * NW + (size_t)d * P2;
   for (int q = threadIdx.x; q < seg_len; q += blockDim.x) {
     const unsigned m = (unsigned)(seg * seg_len + q);
@@ -71,8 +71,8 @@ __global__ void __launch_bounds__(1024) haar_forward_kernel(const float *__restr
     if (nseg == 1) {
       out[0] = src[0];
       if (d == 0) {
-        Xw[(size_t)row * NW + 10 * (size_t)P2] = X[(size_t)row * N + 10 * (size_t)nu * nu];
-        Xw[(size_t)row * NW + 10 * (size_t)P2 + 1] = X[(size_t)row * N + 10 * (size_t)nu * nu + 1];
+        Xw[(size_t)row * NW + 10 * (size_t)P2] = X[(size_t)row * ldx + 10 * (size_t)nu * nu];
+        Xw[(size_t)row * NW + 10 * (size_t)P2 + 1] = X[(size_t)row * ldx + 10 * (size_t)nu * nu + 1];
       }
     } else {
       A[((size_t)row * 10 + d) * nseg + seg] = src[0];
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(1024) haar_forward_kernel(const float *__restr
 
 // The levels above the runs: block per (row, chart) over its nseg approximations.
 __global__ void haar_forward_top_kernel(const float *__restrict__ X, const float *__restrict__ A, int nu, int P,
-                                        int N, int NW, int nseg, float *__restrict__ Xw) {
+                                        long long ldx, int NW, int nseg, float *__restrict__ Xw) {
   __shared__ float b[2][HAAR_SEG];
   const int d = blockIdx.x % 10, row = blockIdx.x / 10;
   const int P2 = P * P;
@@ -104,8 +104,8 @@ __global__ void haar_forward_top_kernel(const float *__restrict__ X, const float
   if (threadIdx.x == 0) {
     out[0] = b[cur][0];
     if (d == 0) {
-      Xw[(size_t)row * NW + 10 * (size_t)P2] = X[(size_t)row * N + 10 * (size_t)nu * nu];
-      Xw[(size_t)row * NW + 10 * (size_t)P2 + 1] = X[(size_t)row * N + 10 * (size_t)nu * nu + 1];
+      Xw[(size_t)row * NW + 10 * (size_t)P2] = X[(size_t)row * ldx + 10 * (size_t)nu * nu];
+      Xw[(size_t)row * NW + 10 * (size_t)P2 + 1] = X[(size_t)row * ldx + 10 * (size_t)nu * nu + 1];
     }
   }
 }
@@ -174,11 +174,15 @@ __global__ void __launch_bounds__(1024) haar_inverse_kernel(const float *__restr
 static int haar_threads(int len) { return std::min(1024, std::max(32, len / 2)); }
 
 tsr_status haar_forward(const float *X, int rows, int nu, float *Xw, cudaStream_t s) {
+  return haar_forward_ld(X, 10 * (long long)nu * nu + 2, rows, nu, Xw, s);
+}
+
+tsr_status haar_forward_ld(const float *X, long long ldx, int rows, int nu, float *Xw, cudaStream_t s) {
   const int P = chart_side(nu), P2 = P * P;
-  const int N = 10 * nu * nu + 2, NW = 10 * P2 + 2;
+  const int NW = 10 * P2 + 2;
   if (P2 <= HAAR_SEG) {
     const size_t smem = sizeof(float) * (size_t)P2 * 2;
-    haar_forward_kernel<<<rows * 10, haar_threads(P2), smem, s>>>(X, nu, P, N, NW, P2, Xw, nullptr);
+    haar_forward_kernel<<<rows * 10, haar_threads(P2), smem, s>>>(X, nu, P, ldx, NW, P2, Xw, nullptr);
     ::tsr::count_launch();
     TSR_CUDA(cudaGetLastError());
     return TSR_OK;
@@ -189,9 +193,9 @@ tsr_status haar_forward(const float *X, int rows, int nu, float *Xw, cudaStream_
   if (st != TSR_OK) return st;
   float *A = static_cast<float *>(as.p);
   const size_t smem = sizeof(float) * HAAR_SEG * 2;
-  haar_forward_kernel<<<rows * 10 * nseg, HAAR_SEG_THREADS, smem, s>>>(X, nu, P, N, NW, HAAR_SEG, Xw, A);
+  haar_forward_kernel<<<rows * 10 * nseg, HAAR_SEG_THREADS, smem, s>>>(X, nu, P, ldx, NW, HAAR_SEG, Xw, A);
   ::tsr::count_launch();
-  haar_forward_top_kernel<<<rows * 10, 256, 0, s>>>(X, A, nu, P, N, NW, nseg, Xw); ::tsr::count_launch();
+  haar_forward_top_kernel<<<rows * 10, 256, 0, s>>>(X, A, nu, P, ldx, NW, nseg, Xw); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return TSR_OK;
 }

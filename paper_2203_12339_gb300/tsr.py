@@ -71,6 +71,8 @@ _SIGNATURES = {
     "tsr_relight_backward": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
     "tsr_relight_noalloc": (_I, [_P, _I, _P, _P, _P, _P]),
     "tsr_relight_many": (_I, [_I, _P, _I, _P, _P, _P, _P]),
+    "tsr_haar_compress_batched": (_I, [_I, _P, _P, _I, _I, _D, _P, _P]),
+    "tsr_haar_recompress_batched": (_I, [_I, _P, _P, _P, _P]),
 }
 
 
@@ -417,6 +419,37 @@ def haar_compress(M: torch.Tensor, nu: int, p: float, out: Compressed | None = N
     h = _P()
     _check(lib().tsr_haar_compress(_ptr(m), K, J, nu, float(p), ctypes.byref(h), _stream()))
     return Compressed(h)
+
+
+def _offsets_host(offsets):
+    import numpy as np
+    offs = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    return offs, offs.ctypes.data_as(ctypes.c_void_p)
+
+
+def haar_compress_batched(M: torch.Tensor, offsets, p: float) -> list:
+    """tsr_haar_compress_batched: M [K][J][total] (a batched transfer) -> one Compressed per mesh."""
+    K, J, total = M.shape
+    m = _dev(M, torch.float32, name="M")
+    offs, op = _offsets_host(offsets)
+    n = len(offs) - 1
+    if offs[-1] != total:
+        raise ValueError(f"offsets end at {offs[-1]}, M has {total} columns")
+    hs = (ctypes.c_void_p * n)()
+    _check(lib().tsr_haar_compress_batched(n, op, _ptr(m), K, J, float(p), ctypes.cast(hs, ctypes.c_void_p),
+                                           _stream()))
+    return [Compressed(ctypes.c_void_p(h)) for h in hs]
+
+
+def haar_recompress_batched(M: torch.Tensor, offsets, comps) -> None:
+    """tsr_haar_recompress_batched: refill the per-mesh handles from a new batched M [K][J][total]."""
+    m = _dev(M, torch.float32, name="M")
+    offs, op = _offsets_host(offsets)
+    comps = list(comps)
+    if len(comps) != len(offs) - 1:
+        raise ValueError("one handle per mesh")
+    hs = (ctypes.c_void_p * len(comps))(*[c.handle.value for c in comps])
+    _check(lib().tsr_haar_recompress_batched(len(comps), op, _ptr(m), ctypes.cast(hs, ctypes.c_void_p), _stream()))
 
 
 def haar_compress_energy(M: torch.Tensor, nu: int, energy: float) -> Compressed:

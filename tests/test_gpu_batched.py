@@ -1,5 +1,6 @@
 """Batched transfer over meshes of uneven size: one persistent launch (BF16) or per-mesh launches (FP32),
-against the oracle per mesh; the plan API, its autotuner and CUDA-graph capture."""
+against the oracle per mesh; the plan API, its autotuner and CUDA-graph capture; per-mesh compression of
+the batched M in place and the relight of all meshes in one call."""
 import numpy as np
 import pytest
 
@@ -71,3 +72,45 @@ def test_plan_autotune_and_graph_capture(env):
     torch.cuda.synchronize()
     tsr.stream_status()
     _check(M.cpu().numpy(), offs, refs, 2e-3)
+
+
+def test_batched_compress_recompress_and_relight(env):
+    """Step 2 on the batched M read in place equals compressing each mesh's columns alone (bit-exact: same
+    kernels on the same values); recompress refills the handles for a new M inside a CUDA graph; the relight
+    of all meshes in one call (five edits: basis images + combine) equals the per-mesh relight within FP32
+    reordering (2e-6)."""
+    torch, tsr, basis, offs, d, refs = env
+    M = tsr.precompute_transfer_batched(basis, offs, d["pos"], d["area"], d["T"], "fp32")
+    comps = tsr.haar_compress_batched(M, offs, 0.1)
+    for b, c in enumerate(comps):
+        alone = tsr.haar_compress(M[:, :, offs[b]:offs[b + 1]].contiguous(), NUS[b], 0.1)
+        for x, y in zip(c.export(), alone.export()):
+            assert torch.equal(x, y), b
+    M2 = M * 1.5 - 0.25 * M.flip(-1)
+    torch.cuda.synchronize()
+    tsr.haar_recompress_batched(M2, offs, comps)   # warm (scratch pools)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+            tsr.haar_recompress_batched(M2, offs, comps)
+    torch.cuda.current_stream().wait_stream(s)
+    tsr.haar_recompress_batched(M, offs, comps)    # back to M, then the graph refills from M2
+    g.replay()
+    torch.cuda.synchronize()
+    for b, c in enumerate(comps):
+        alone = tsr.haar_compress(M2[:, :, offs[b]:offs[b + 1]].contiguous(), NUS[b], 0.1)
+        for x, y in zip(c.export(), alone.export()):
+            assert torch.equal(x, y), b
+    rng = np.random.default_rng(12)
+    E = 5
+    gg = torch.tensor(rng.standard_normal((len(NUS), E, 3, K)).astype(np.float32), device="cuda")
+    light = torch.tensor(rng.standard_normal(J).astype(np.float32), device="cuda")
+    Bs = tsr.relight_many(comps, gg, light)
+    for b, c in enumerate(comps):
+        want = tsr.relight(c, gg[b], light)
+        err = ((Bs[b] - want).reshape(E * 3, -1).norm(dim=1) / want.reshape(E * 3, -1).norm(dim=1)).max().item()
+        assert err <= 2e-6, (b, err)
+    tsr.stream_status()

@@ -491,6 +491,29 @@ def test_relight_many_uneven_copies(torch_cuda, tsr):
         assert torch.equal(Bs[i], want), i
 
 
+@pytest.mark.parametrize("K,J,E", [(2, 3, 4), (5, 4, 7), (8, 9, 3), (16, 25, 5)])
+def test_relight_many_factorised_batch(torch_cuda, tsr, K, J, E):
+    """More than two edits: the light-contracted basis images of every copy in one fused pass (K of 2 to 16
+    images per copy) and one combine over all copies and edits; copies of 1 to 16 runs per chart, ragged
+    nu among them; every copy against the oracle."""
+    torch = torch_cuda
+    nus = [3, 8, 40, 100, 16]
+    comps, kepts = [], []
+    for i, nu in enumerate(nus):
+        comp, kept = _compressed_case(torch, tsr, nu, K, J, 0.1, 200 + 7 * i + K)
+        comps.append(comp)
+        kepts.append(kept)
+    rng = np.random.default_rng(K * J)
+    light = rng.standard_normal(J).astype(np.float32)
+    g = rng.standard_normal((len(comps), E, 3, K)).astype(np.float32)
+    Bs = tsr.relight_many(comps, _dev(torch, g), _dev(torch, light))
+    torch.cuda.synchronize()
+    for i, (B, kept, nu) in enumerate(zip(Bs, kepts, nus)):
+        B_ref = O.relight(kept, nu, g[i].astype(np.float64), light.astype(np.float64))
+        err = _relight_err(B.cpu().numpy(), B_ref)
+        assert err <= 2e-6, (i, nu, err)
+
+
 def test_relight_many_rejects_mismatched_handles(torch_cuda, tsr):
     torch = torch_cuda
     a, _ = _compressed_case(torch, tsr, 4, 4, 5, 0.2, 1)
