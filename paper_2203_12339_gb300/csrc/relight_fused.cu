@@ -20,6 +20,7 @@
 // 1; each synthesis step is (a + d) / sqrt2 or (a - d) / sqrt2, as in the
 // level-by-level inverse.
 #include <algorithm>
+#include <atomic>
 
 #include "handles.cuh"
 
@@ -339,13 +340,13 @@ static tsr_status launch_fused(int n, const tsr_compressed *const *c, int nv, co
   const int K = c[0]->K, J = c[0]->J;
   const size_t smem = fused_smem<VV>(K, J);
   {   // dynamic shared memory up to the largest case (K = 16, J = 32), set once per device
-    static bool attr_set[64] = {};
+    static std::atomic<bool> attr_set[64];   // the call is idempotent: threads racing here set the same value
     int dev = 0;
     TSR_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    if (dev < 0 || dev >= 64 || !attr_set[dev].load(std::memory_order_acquire)) {
       TSR_CUDA(cudaFuncSetAttribute(relight_fused_kernel<VV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)fused_smem<VV>(16, 32)));
-      if (dev >= 0 && dev < 64) attr_set[dev] = true;
+      if (dev >= 0 && dev < 64) attr_set[dev].store(true, std::memory_order_release);
     }
   }
   for (int b0 = 0; b0 < n; b0 += RF_MAXC) {
