@@ -407,15 +407,17 @@ def run_gpu(args):
     ev_tr = []
     comp_box = [tsr.haar_compress(M, nu, KEEP)]   # handle reused by every step (tsr_haar_recompress)
 
-    def step(inp, on_B=None):
+    def step(inp, on_B=None, timed=True):
         """The per-scene path; returns (B, gradient tensors).  on_B(B) runs as soon as B is issued."""
         _, g32, _ = tsr.project_material(basis, inp["sa"], inp["ss"], inp["eta"])
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
+        if timed:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
         tsr.precompute_transfer(basis, inp["pos"], inp["area"], inp["T"], "bf16", out=M)
-        e1.record()
-        ev_tr.append((e0, e1))
+        if timed:
+            e1.record()
+            ev_tr.append((e0, e1))
         comp = tsr.haar_compress(M, nu, KEEP, out=comp_box[0])
         B = tsr.relight(comp, g32, inp["light"])
         if on_B is not None:
@@ -435,12 +437,13 @@ def run_gpu(args):
             h_B.copy_(B, non_blocking=True)
         B.record_stream(d2h_stream)
 
-    def step_e2e():
+    def step_e2e(timed=True):
         inp = {k: v.to(dev, non_blocking=True) for k, v in dict(pos=h_pos, area=h_area, T=h_T, sa=h_sa, ss=h_ss,
                                                                  eta=h_eta, light=h_light).items()}
-        B, grads, comp = step(inp, on_B=copy_B_out)
+        B, grads, comp = step(inp, on_B=copy_B_out, timed=timed)
         flat = torch.cat([g.reshape(-1).float() for g in grads])
         h_grads.copy_(flat, non_blocking=True)
+        torch.cuda.current_stream().wait_stream(d2h_stream)   # B's copy joins the step
         return comp
 
     for _ in range(args.warmup):
@@ -473,7 +476,9 @@ def run_gpu(args):
     ms_transfer = [a.elapsed_time(b) for a, b in ev_tr]
     ms_per_step = sum(ms_steps) / len(ms_steps)
 
-    # end-to-end through host buffers
+    # end-to-end through host buffers, wall clock per step: H2D of the inputs from pinned memory, every
+    # library call, D2H of B and the gradients.  Eagerly from Python (e2e_eager), and as a CUDA graph of
+    # the same calls captured once and replayed per step (e2e: a render or fitting loop's launch path).
     e2e_ms = []
     for _ in range(max(1, args.steps)):
         flush.zero_()
@@ -482,7 +487,30 @@ def run_gpu(args):
         step_e2e()
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t) * 1e3)
-    e2e_step = sum(e2e_ms) / len(e2e_ms)
+    e2e_eager = sum(e2e_ms) / len(e2e_ms)
+    e2e_mode = "CUDA graph of the whole step (H2D, library calls, D2H), replayed per step"
+    try:
+        g_e2e = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream()
+        cap.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cap):
+            with torch.cuda.graph(g_e2e, stream=cap, capture_error_mode="thread_local"):
+                step_e2e(timed=False)
+        torch.cuda.current_stream().wait_stream(cap)
+        g_e2e.replay()
+        torch.cuda.synchronize()
+        tsr.stream_status()
+        e2e_ms = []
+        for _ in range(max(1, args.steps)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            g_e2e.replay()
+            torch.cuda.synchronize()
+            e2e_ms.append((time.perf_counter() - t) * 1e3)
+        e2e_step = sum(e2e_ms) / len(e2e_ms)
+    except RuntimeError as exc:   # capture refused: report the eager loop
+        e2e_step, e2e_mode = e2e_eager, f"eager (graph capture failed: {exc})"[:200]
     h2d = sum(t.numel() * t.element_size() for t in (h_pos, h_area, h_T, h_sa, h_ss, h_eta, h_light))
     d2h = h_B.numel() * h_B.element_size() + h_grads.numel() * h_grads.element_size()
 
@@ -539,7 +567,8 @@ def run_gpu(args):
             by_prec[prec] = round(a.elapsed_time(b), 3)
         tsr.stream_status()
 
-    ms_per_step, e2e_step, tr_mean = reduce_max([ms_per_step, e2e_step, statistics.mean(ms_transfer)], world, dev)
+    ms_per_step, e2e_step, tr_mean, e2e_eager_max = reduce_max([ms_per_step, e2e_step, statistics.mean(ms_transfer),
+                                                                e2e_eager], world, dev)
     units = float(N) * N * K * J
     value = weak_scaling_value(units, world, ms_per_step)
     e2e_value = weak_scaling_value(units, world, e2e_step)
@@ -556,7 +585,9 @@ def run_gpu(args):
                    "l2": "flushed between timed steps (256 MB write)",
                    "per_step": "project -> transfer(bf16) -> haar+select -> relight -> adjoint"},
         "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": round(e2e_step, 3)},
+                "ms_per_step": round(e2e_step, 3), "mode": e2e_mode,
+                "eager": {"value": round(weak_scaling_value(units, world, e2e_eager_max), 1),
+                          "ms_per_step": round(e2e_eager_max, 3)}},
         "gpu_launches": launches,
         "roofline": {"bound": "tensor", "achieved": round(achieved_tflops, 2), "peak": peak_tf,
                      "unit": "TFLOP/s", "frac": round(achieved_tflops / peak_tf, 4), "traffic": traffic,
