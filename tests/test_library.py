@@ -67,6 +67,25 @@ def test_argument_checks_run_before_any_device_work(libtsr):
     buf = ctypes.create_string_buffer(64)
     assert m(2, ctypes.cast(handles, ctypes.c_void_p), 1, ctypes.addressof(buf), ctypes.addressof(buf),
              ctypes.addressof(buf), None) == -1
+    # batched Step 2: mesh sizes must be 10 nu^2 + 2; NULL handles rejected; nothing reaches the device
+    libtsr.tsr_last_error.restype = ctypes.c_char_p
+    cb = libtsr.tsr_haar_compress_batched
+    cb.restype = ctypes.c_int
+    cb.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                   ctypes.c_void_p, ctypes.c_void_p]
+    offs = (ctypes.c_int64 * 3)(0, 642, 642 + 100)          # 100 is not of the chart form
+    outs = (ctypes.c_void_p * 2)()
+    assert cb(2, ctypes.addressof(offs), ctypes.addressof(buf), 4, 4, 0.1, ctypes.addressof(outs), None) == -1
+    assert b"not 10 nu^2 + 2" in libtsr.tsr_last_error()
+    offs_ok = (ctypes.c_int64 * 3)(0, 642, 642 + 2562)
+    assert cb(2, ctypes.addressof(offs_ok), None, 4, 4, 0.1, ctypes.addressof(outs), None) == -1
+    assert cb(2, ctypes.addressof(offs_ok), ctypes.addressof(buf), 17, 4, 0.1, ctypes.addressof(outs), None) == -1
+    rb = libtsr.tsr_haar_recompress_batched
+    rb.restype = ctypes.c_int
+    rb.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    nulls = (ctypes.c_void_p * 2)(None, None)
+    assert rb(2, ctypes.addressof(offs_ok), ctypes.addressof(buf), ctypes.addressof(nulls), None) == -1
+    assert b"is NULL" in libtsr.tsr_last_error()
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
