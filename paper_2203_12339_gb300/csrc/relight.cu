@@ -117,11 +117,10 @@ static void launch_direct(const tsr_compressed *c, const float *g, const float *
   ::tsr::count_launch();
 }
 
-// B[v][o] = sum_k g[v][k] Z[k][o]: a thread per RL_CV output vertices (o, o + 256, ...) and
-// a chunk of RL_VB vectors; g staged as float4 rows of KT = K rounded up to 4 (zero padded: no
+// B[v][o] = sum_k g[v][k] Z[k][o]: a thread per two output vertices (o, o + 256) and a
+// chunk of RL_VB vectors; g staged as float4 rows of KT = K rounded up to 4 (zero padded: no
 // per-basis test in the loop, the padding adds fmaf(0, 0, b) = b).
 constexpr int RL_VB = 32;
-constexpr int RL_CV = 2;   // vertices per thread (4 measured slower: registers)
 template <int KT>
 __global__ void __launch_bounds__(256) relight_combine_kernel(const float *__restrict__ Z, int N, int K, int V,
                                                              const float *__restrict__ g, float *__restrict__ B) {
@@ -133,38 +132,38 @@ __global__ void __launch_bounds__(256) relight_combine_kernel(const float *__res
     gsf[q] = (v0 + vv < V && k < K) ? g[(size_t)(v0 + vv) * K + k] : 0.0f;
   }
   __syncthreads();
-  // RL_CV vertices per thread (o, o + 256, ...): each g row read from shared memory serves all of them
-  const int o = blockIdx.x * 256 * RL_CV + threadIdx.x;
+  // two vertices per thread (o and o + 256): each g row read from shared memory serves both
+  const int o = blockIdx.x * 512 + threadIdx.x;
   if (o >= N) return;
-  float z[RL_CV][KT];
+  const bool two = o + 256 < N;
+  float z[2][KT];
 #pragma unroll
-  for (int a = 0; a < RL_CV; ++a)
-#pragma unroll
-    for (int k = 0; k < KT; ++k) z[a][k] = (k < K && o + 256 * a < N) ? Z[(size_t)k * N + o + 256 * a] : 0.0f;
+  for (int k = 0; k < KT; ++k) {
+    z[0][k] = (k < K) ? Z[(size_t)k * N + o] : 0.0f;
+    z[1][k] = (k < K && two) ? Z[(size_t)k * N + o + 256] : 0.0f;
+  }
   const int vn = min(RL_VB, V - v0);
   for (int vv = 0; vv < vn; ++vv) {
-    float b[RL_CV];
-#pragma unroll
-    for (int a = 0; a < RL_CV; ++a) b[a] = 0.0f;
+    float b0 = 0.0f, b1 = 0.0f;
 #pragma unroll
     for (int h = 0; h < KT / 4; ++h) {
       const float4 gq = gs[vv * (KT / 4) + h];
-#pragma unroll
-      for (int a = 0; a < RL_CV; ++a) {
-        b[a] = fmaf(gq.x, z[a][4 * h], b[a]);
-        b[a] = fmaf(gq.y, z[a][4 * h + 1], b[a]);
-        b[a] = fmaf(gq.z, z[a][4 * h + 2], b[a]);
-        b[a] = fmaf(gq.w, z[a][4 * h + 3], b[a]);
-      }
+      b0 = fmaf(gq.x, z[0][4 * h], b0);
+      b1 = fmaf(gq.x, z[1][4 * h], b1);
+      b0 = fmaf(gq.y, z[0][4 * h + 1], b0);
+      b1 = fmaf(gq.y, z[1][4 * h + 1], b1);
+      b0 = fmaf(gq.z, z[0][4 * h + 2], b0);
+      b1 = fmaf(gq.z, z[1][4 * h + 2], b1);
+      b0 = fmaf(gq.w, z[0][4 * h + 3], b0);
+      b1 = fmaf(gq.w, z[1][4 * h + 3], b1);
     }
-#pragma unroll
-    for (int a = 0; a < RL_CV; ++a)
-      if (o + 256 * a < N) B[(size_t)(v0 + vv) * N + o + 256 * a] = b[a];
+    B[(size_t)(v0 + vv) * N + o] = b0;
+    if (two) B[(size_t)(v0 + vv) * N + o + 256] = b1;
   }
 }
 
 static void launch_combine(const float *Z, int N, int K, int V, const float *g, float *B, cudaStream_t s) {
-  const dim3 grid((N + 256 * RL_CV - 1) / (256 * RL_CV), (V + RL_VB - 1) / RL_VB);
+  const dim3 grid((N + 511) / 512, (V + RL_VB - 1) / RL_VB);
   if (K <= 4)
     relight_combine_kernel<4><<<grid, 256, 0, s>>>(Z, N, K, V, g, B);
   else if (K <= 8)

@@ -395,14 +395,13 @@ tsr_status relight_basis_images_many(int n, const tsr_compressed *const *c, cons
 }
 
 // ---------------------------------------------------------------- combine, many copies
-// B_i[v][o] = sum_k g_i[v][k] Z_i[k][o] for every copy i: a block per (256 RC_CV vertices of
+// B_i[v][o] = sum_k g_i[v][k] Z_i[k][o] for every copy i: a block per (512 vertices of
 // one copy, RC_VB vectors), the K values of Z of its vertex held in registers, the
 // vectors' g in shared memory as float4 rows of KT = K rounded up to 4 (zero padded,
 // so the loop has no per-basis test; the padding adds fmaf(0, 0, b) = b).  Same
 // arithmetic as relight_combine_kernel.
 constexpr int RC_VB = 32;
-constexpr int RC_CV = 2;                // vertices per thread (4 measured slower: registers)
-constexpr int RC_VERTS = 256 * RC_CV;   // vertices per block
+constexpr int RC_VERTS = 512;   // vertices per block (two per thread; four measured slower: registers)
 struct CombineCopy {
   const float *Z;   // [K][N]
   const float *g;   // [V][K]
@@ -429,35 +428,34 @@ __global__ void __launch_bounds__(256) relight_combine_many_kernel(const __grid_
     gsf[q] = (v0 + vv < V && k < K) ? cp.g[(size_t)(v0 + vv) * K + k] : 0.0f;
   }
   __syncthreads();
-  // CV vertices per thread (o, o + 256, ...): each g row read from shared memory serves all of them
+  // two vertices per thread (o and o + 256): each g row read from shared memory serves both
   const int o = ((int)blockIdx.x - cp.blk0) * RC_VERTS + threadIdx.x;
   if (o >= N) return;
-  float z[RC_CV][KT];
+  const bool two = o + 256 < N;
+  float z[2][KT];
 #pragma unroll
-  for (int a = 0; a < RC_CV; ++a)
-#pragma unroll
-    for (int k = 0; k < KT; ++k)
-      z[a][k] = (k < K && o + 256 * a < N) ? __ldg(cp.Z + (size_t)k * N + o + 256 * a) : 0.0f;
+  for (int k = 0; k < KT; ++k) {
+    z[0][k] = (k < K) ? __ldg(cp.Z + (size_t)k * N + o) : 0.0f;
+    z[1][k] = (k < K && two) ? __ldg(cp.Z + (size_t)k * N + o + 256) : 0.0f;
+  }
   const int vn = min(RC_VB, V - v0);
   float *__restrict__ B = cp.B + (size_t)v0 * N + o;
   for (int vv = 0; vv < vn; ++vv) {
-    float b[RC_CV];
-#pragma unroll
-    for (int a = 0; a < RC_CV; ++a) b[a] = 0.0f;
+    float b0 = 0.0f, b1 = 0.0f;
 #pragma unroll
     for (int h = 0; h < KT / 4; ++h) {
       const float4 gq = gs[vv * (KT / 4) + h];
-#pragma unroll
-      for (int a = 0; a < RC_CV; ++a) {
-        b[a] = fmaf(gq.x, z[a][4 * h], b[a]);
-        b[a] = fmaf(gq.y, z[a][4 * h + 1], b[a]);
-        b[a] = fmaf(gq.z, z[a][4 * h + 2], b[a]);
-        b[a] = fmaf(gq.w, z[a][4 * h + 3], b[a]);
-      }
+      b0 = fmaf(gq.x, z[0][4 * h], b0);
+      b1 = fmaf(gq.x, z[1][4 * h], b1);
+      b0 = fmaf(gq.y, z[0][4 * h + 1], b0);
+      b1 = fmaf(gq.y, z[1][4 * h + 1], b1);
+      b0 = fmaf(gq.z, z[0][4 * h + 2], b0);
+      b1 = fmaf(gq.z, z[1][4 * h + 2], b1);
+      b0 = fmaf(gq.w, z[0][4 * h + 3], b0);
+      b1 = fmaf(gq.w, z[1][4 * h + 3], b1);
     }
-#pragma unroll
-    for (int a = 0; a < RC_CV; ++a)
-      if (o + 256 * a < N) B[(size_t)vv * N + 256 * a] = b[a];
+    B[(size_t)vv * N] = b0;
+    if (two) B[(size_t)vv * N + 256] = b1;
   }
 }
 
