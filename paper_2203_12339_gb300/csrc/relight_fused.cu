@@ -19,6 +19,10 @@
 // (sub, sub + 8, ...) in order, the 8 partial sums meeting in xor-shuffles 4, 2,
 // 1; each synthesis step is (a + d) / sqrt2 or (a - d) / sqrt2, as in the
 // level-by-level inverse.
+//
+// With g = identity the same kernel yields the light-contracted basis images
+// Z[k] = w_1^{-1} (S (e_k x l)) (K "vectors"); the relight of many edits on many
+// copies is then those images plus relight_combine_many_kernel, B = sum_k g_k Z[k].
 #include <algorithm>
 #include <atomic>
 
