@@ -287,6 +287,18 @@ tsr_status tsr_compressed_export(const tsr_compressed *c, int64_t *row_ptr, uint
                                  tsr_stream stream);
 void tsr_compressed_destroy(tsr_compressed *c);
 
+/* Checkpoint and resume of the precompute's result (the paper has no
+ * counterpart): tsr_compressed_save writes the handle to a file (synchronous
+ * device-to-host copies; little-endian binary: an 8-byte magic "TSRCMP01", the
+ * int32 fields K, J, nu, P, n_rows, n_keep, keep rule, wavelet, the int64 nnz,
+ * then row_ptr, col, val, the column lists and col_ptr); tsr_compressed_load
+ * reads one back into a new handle on the current device, equal to the saved one
+ * for every call.  TSR_ERR_INVALID_ARG, with nothing allocated, for a file that
+ * cannot be opened, is not such a file, is truncated, or whose header, pointers
+ * or indices are out of range (all checked on the host before any device work). */
+tsr_status tsr_compressed_save(const tsr_compressed *c, const char *path);
+tsr_status tsr_compressed_load(const char *path, tsr_compressed **out);
+
 /* ------------------------------------------------------------------------
  * Fresnel transmittance factors of Eq. 3 and Eq. 6,
  *   S = (1/pi) F_t(eta, w_i) R_d F_t(eta, w_o),

@@ -72,6 +72,8 @@ _SIGNATURES = {
     "tsr_relight_noalloc": (_I, [_P, _I, _P, _P, _P, _P]),
     "tsr_relight_many": (_I, [_I, _P, _I, _P, _P, _P, _P]),
     "tsr_haar_compress_batched": (_I, [_I, _P, _P, _I, _I, _D, _P, _P]),
+    "tsr_compressed_save": (_I, [_P, ctypes.c_char_p]),
+    "tsr_compressed_load": (_I, [ctypes.c_char_p, ctypes.POINTER(_P)]),
     "tsr_haar_recompress_batched": (_I, [_I, _P, _P, _P, _P]),
 }
 
@@ -382,6 +384,17 @@ class Compressed:
         _check(lib().tsr_compressed_export(self._h, _ptr(row_ptr), _ptr(col16), _ptr(val), _stream()))
         col = col16.to(torch.int32) & 0xFFFF
         return row_ptr, col, val
+
+    def save(self, path: str) -> None:
+        """tsr_compressed_save: write the handle to `path`."""
+        _check(lib().tsr_compressed_save(self._h, os.fsencode(path)))
+
+    @staticmethod
+    def load(path: str) -> "Compressed":
+        """tsr_compressed_load: a new handle on the current device from a file written by save()."""
+        h = _P()
+        _check(lib().tsr_compressed_load(os.fsencode(path), ctypes.byref(h)))
+        return Compressed(h)
 
     def close(self):
         if self._h:

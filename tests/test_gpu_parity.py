@@ -514,6 +514,31 @@ def test_relight_many_factorised_batch(torch_cuda, tsr, K, J, E):
         assert err <= 2e-6, (i, nu, err)
 
 
+def test_compressed_save_and_load_round_trip(torch_cuda, tsr, tmp_path):
+    """Checkpoint/resume of a compressed transfer (top-fraction Haar, and energy-rule CDF 9/7): the loaded
+    handle exports the same arrays and relights and back-propagates bit-identically."""
+    torch = torch_cuda
+    comp, _ = _compressed_case(torch, tsr, 20, 6, 9, 0.1, 77)
+    nu_c, K, J = 8, 5, 9
+    rng = np.random.default_rng(78)
+    M = (rng.standard_normal((K, J, 10 * nu_c * nu_c + 2)) * np.exp(-np.arange(10 * nu_c * nu_c + 2) % 64 / 16.0))
+    comp_c = tsr.compress(_dev(torch, M.astype(np.float32)), nu_c, "cdf97", "energy", 0.97)
+    for i, c in enumerate((comp, comp_c)):
+        path = str(tmp_path / f"c{i}.tsr")
+        c.save(path)
+        d = tsr.Compressed.load(path)
+        assert (d.K, d.J, d.nu, d.nnz, d.n_rows) == (c.K, c.J, c.nu, c.nnz, c.n_rows)
+        for x, y in zip(c.export(), d.export()):
+            assert torch.equal(x, y)
+        g = torch.tensor(rng.standard_normal((3, 3, c.K)).astype(np.float32), device="cuda")
+        light = torch.tensor(rng.standard_normal(c.J).astype(np.float32), device="cuda")
+        for E in (1, 3):
+            assert torch.equal(tsr.relight(c, g[:E], light), tsr.relight(d, g[:E], light))
+        dB = torch.randn((3, 3, c.n), device="cuda")
+        for x, y in zip(tsr.relight_backward(c, g, light, dB), tsr.relight_backward(d, g, light, dB)):
+            assert torch.equal(x, y)
+
+
 def test_relight_many_rejects_mismatched_handles(torch_cuda, tsr):
     torch = torch_cuda
     a, _ = _compressed_case(torch, tsr, 4, 4, 5, 0.2, 1)

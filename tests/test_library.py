@@ -94,3 +94,34 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(tsr, "_lib", None)
     with pytest.raises(RuntimeError):
         tsr.lib()
+
+
+def test_compressed_load_rejects_bad_files_on_the_host(libtsr, tmp_path):
+    """Checkpoint files are validated before any device work: missing, foreign, truncated and
+    out-of-range files give TSR_ERR_INVALID_ARG and no handle."""
+    import struct
+    load = libtsr.tsr_compressed_load
+    load.restype = ctypes.c_int
+    load.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]
+    libtsr.tsr_last_error.restype = ctypes.c_char_p
+    out = ctypes.c_void_p(1)
+    assert load(str(tmp_path / "missing.tsr").encode(), ctypes.byref(out)) == -1 and not out.value
+    foreign = tmp_path / "foreign.tsr"
+    foreign.write_bytes(b"NOTATSRC" + b"\0" * 64)
+    assert load(str(foreign).encode(), ctypes.byref(out)) == -1
+    assert b"not a compressed transfer file" in libtsr.tsr_last_error()
+    short = tmp_path / "short.tsr"
+    short.write_bytes(b"TSRCMP01" + b"\0" * 10)
+    assert load(str(short).encode(), ctypes.byref(out)) == -1
+    assert b"truncated header" in libtsr.tsr_last_error()
+    # K = 99: out of range
+    bad = tmp_path / "bad.tsr"
+    bad.write_bytes(b"TSRCMP01" + struct.pack("<8iq", 99, 4, 4, 4, 162, 1, 0, 0, 0))
+    assert load(str(bad).encode(), ctypes.byref(out)) == -1
+    assert b"header out of range" in libtsr.tsr_last_error()
+    # a valid header (K = J = 1, nu = 1, P = 1, n_rows = 12, nnz = 2) but the arrays cut short
+    cut = tmp_path / "cut.tsr"
+    cut.write_bytes(b"TSRCMP01" + struct.pack("<8iq", 1, 1, 1, 1, 12, 0, 0, 0, 2) + b"\0" * 8)
+    assert load(str(cut).encode(), ctypes.byref(out)) == -1
+    assert b"truncated arrays" in libtsr.tsr_last_error()
+    assert not out.value
