@@ -16,7 +16,7 @@ extern "C" const char *tsr_last_error(void) { return error_string(); }
 extern "C" int tsr_version(void) { return 100; }
 
 extern "C" tsr_status tsr_stream_status(tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   tsr_status st = require_device();
   if (st != TSR_OK) return st;
   TSR_CUDA(cudaStreamSynchronize(as_stream(stream)));
@@ -26,7 +26,7 @@ extern "C" tsr_status tsr_stream_status(tsr_stream stream) {
 extern "C" tsr_status tsr_precompute_transfer(const tsr_basis *basis, int N, const float *pos, const float *area,
                                               const float *T, int J, tsr_precision prec, float *M,
                                               tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(basis && pos && area && T && M, "tsr_precompute_transfer: NULL argument");
   TSR_CHECK_ARG(N >= 12 && N <= (1 << 24), "tsr_precompute_transfer: N=%d outside [12, 2^24]", N);
   TSR_CHECK_ARG(J >= 1 && J <= 32, "tsr_precompute_transfer: J=%d outside [1, 32]", J);
@@ -51,7 +51,7 @@ extern "C" tsr_status tsr_precompute_transfer(const tsr_basis *basis, int N, con
 extern "C" tsr_status tsr_precompute_transfer_batched(const tsr_basis *basis, int n_mesh, const int64_t *offsets,
                                                       const float *pos, const float *area, const float *T, int J,
                                                       tsr_precision prec, float *M, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(basis && offsets && pos && area && T && M, "tsr_precompute_transfer_batched: NULL argument");
   TSR_CHECK_ARG(n_mesh >= 1 && n_mesh <= 65536, "tsr_precompute_transfer_batched: n_mesh=%d out of range", n_mesh);
   TSR_CHECK_ARG(J >= 1 && J <= 32, "tsr_precompute_transfer_batched: J=%d outside [1, 32]", J);
@@ -70,7 +70,7 @@ extern "C" tsr_status tsr_precompute_transfer_batched(const tsr_basis *basis, in
 }
 
 extern "C" tsr_status tsr_haar_forward(const float *X, int rows, int nu, float *Xw, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(X && Xw, "tsr_haar_forward: NULL argument");
   TSR_CHECK_ARG(rows >= 0 && rows <= (1 << 20), "tsr_haar_forward: rows=%d out of range", rows);
   TSR_CHECK_ARG(nu >= 1 && nu <= 128, "tsr_haar_forward: nu=%d outside [1, 128]", nu);
@@ -80,7 +80,7 @@ extern "C" tsr_status tsr_haar_forward(const float *X, int rows, int nu, float *
 }
 
 extern "C" tsr_status tsr_haar_inverse(const float *Xw, int rows, int nu, float *X, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(X && Xw, "tsr_haar_inverse: NULL argument");
   TSR_CHECK_ARG(rows >= 0 && rows <= (1 << 20), "tsr_haar_inverse: rows=%d out of range", rows);
   TSR_CHECK_ARG(nu >= 1 && nu <= 128, "tsr_haar_inverse: nu=%d outside [1, 128]", nu);
@@ -91,7 +91,7 @@ extern "C" tsr_status tsr_haar_inverse(const float *Xw, int rows, int nu, float 
 
 extern "C" tsr_status tsr_wavelet_compress(const float *Mw, int K, int J, int nu, double p, tsr_compressed **out,
                                            tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(Mw && out, "tsr_wavelet_compress: NULL argument");
   TSR_CHECK_ARG(K >= 1 && K <= 16 && J >= 1 && J <= 32, "tsr_wavelet_compress: K=%d J=%d out of range", K, J);
   TSR_CHECK_ARG(nu >= 1 && nu <= 128, "tsr_wavelet_compress: nu=%d outside [1, 128]", nu);
@@ -104,7 +104,7 @@ extern "C" tsr_status tsr_wavelet_compress(const float *Mw, int K, int J, int nu
 
 extern "C" tsr_status tsr_haar_compress(const float *M, int K, int J, int nu, double p, tsr_compressed **out,
                                         tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(M && out, "tsr_haar_compress: NULL argument");
   TSR_CHECK_ARG(K >= 1 && K <= 16 && J >= 1 && J <= 32, "tsr_haar_compress: K=%d J=%d out of range", K, J);
   TSR_CHECK_ARG(nu >= 1 && nu <= 128, "tsr_haar_compress: nu=%d outside [1, 128]", nu);
@@ -124,7 +124,7 @@ extern "C" tsr_status tsr_haar_compress(const float *M, int K, int J, int nu, do
 
 extern "C" tsr_status tsr_haar_compress_energy(const float *M, int K, int J, int nu, double energy,
                                                tsr_compressed **out, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(M && out, "tsr_haar_compress_energy: NULL argument");
   TSR_CHECK_ARG(K >= 1 && K <= 16 && J >= 1 && J <= 32, "tsr_haar_compress_energy: K=%d J=%d out of range", K, J);
   TSR_CHECK_ARG(nu >= 1 && nu <= 128, "tsr_haar_compress_energy: nu=%d outside [1, 128]", nu);
@@ -144,7 +144,7 @@ extern "C" tsr_status tsr_haar_compress_energy(const float *M, int K, int J, int
 
 extern "C" tsr_status tsr_compress(const float *M, int K, int J, int nu, int wavelet, int rule, double param,
                                    tsr_compressed **out, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(M && out, "tsr_compress: NULL argument");
   TSR_CHECK_ARG(K >= 1 && K <= 16 && J >= 1 && J <= 32, "tsr_compress: K=%d J=%d out of range", K, J);
   TSR_CHECK_ARG(nu >= 1 && nu <= 128, "tsr_compress: nu=%d outside [1, 128]", nu);
@@ -171,7 +171,7 @@ extern "C" tsr_status tsr_compress(const float *M, int K, int J, int nu, int wav
 }
 
 extern "C" tsr_status tsr_cdf97_forward(const float *X, int rows, int nu, float *Xw, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(X && Xw, "tsr_cdf97_forward: NULL argument");
   TSR_CHECK_ARG(rows >= 1 && nu >= 1 && nu <= 128, "tsr_cdf97_forward: rows=%d nu=%d out of range", rows, nu);
   tsr_status st = require_device();
@@ -180,7 +180,7 @@ extern "C" tsr_status tsr_cdf97_forward(const float *X, int rows, int nu, float 
 }
 
 extern "C" tsr_status tsr_cdf97_inverse(const float *Xw, int rows, int nu, float *X, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(X && Xw, "tsr_cdf97_inverse: NULL argument");
   TSR_CHECK_ARG(rows >= 1 && nu >= 1 && nu <= 128, "tsr_cdf97_inverse: rows=%d nu=%d out of range", rows, nu);
   tsr_status st = require_device();
@@ -189,7 +189,7 @@ extern "C" tsr_status tsr_cdf97_inverse(const float *Xw, int rows, int nu, float
 }
 
 extern "C" tsr_status tsr_cdf97_inverse_transpose(const float *X, int rows, int nu, float *Xw, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(X && Xw, "tsr_cdf97_inverse_transpose: NULL argument");
   TSR_CHECK_ARG(rows >= 1 && nu >= 1 && nu <= 128, "tsr_cdf97_inverse_transpose: rows=%d nu=%d out of range", rows,
                 nu);
@@ -200,7 +200,7 @@ extern "C" tsr_status tsr_cdf97_inverse_transpose(const float *X, int rows, int 
 
 extern "C" tsr_status tsr_fresnel_output(int n_edit, const double *eta, int N, const float *cos_o, const float *B,
                                          float *Bout, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(eta && cos_o && B && Bout, "tsr_fresnel_output: NULL argument");
   TSR_CHECK_ARG(n_edit >= 0 && n_edit <= (1 << 20) && N >= 1, "tsr_fresnel_output: n_edit=%d N=%d out of range",
                 n_edit, N);
@@ -214,7 +214,7 @@ extern "C" tsr_status tsr_fresnel_output(int n_edit, const double *eta, int N, c
 extern "C" tsr_status tsr_fresnel_output_backward(int n_edit, const double *eta, int N, const float *cos_o,
                                                   const float *B, const float *dBout, float *dB, float *deta,
                                                   tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(eta && cos_o && B && dBout && dB && deta, "tsr_fresnel_output_backward: NULL argument");
   TSR_CHECK_ARG(n_edit >= 1 && n_edit <= (1 << 20) && N >= 1,
                 "tsr_fresnel_output_backward: n_edit=%d N=%d out of range", n_edit, N);
@@ -224,7 +224,7 @@ extern "C" tsr_status tsr_fresnel_output_backward(int n_edit, const double *eta,
 }
 
 extern "C" tsr_status tsr_sh_transfer(int N, const float *normals, int J, double eta, float *T, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(normals && T, "tsr_sh_transfer: NULL argument");
   TSR_CHECK_ARG(N >= 1, "tsr_sh_transfer: N=%d", N);
   TSR_CHECK_ARG(J == 1 || J == 4 || J == 9 || J == 16 || J == 25, "tsr_sh_transfer: J=%d is not a square <= 25", J);
@@ -237,7 +237,7 @@ extern "C" tsr_status tsr_sh_transfer(int N, const float *normals, int J, double
 extern "C" tsr_status tsr_visibility_transfer(int N, const float *pos, const float *normals, int F,
                                               const int32_t *tris, int J, int S, double eta, float eps, float *T,
                                               tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(pos && normals && tris && T, "tsr_visibility_transfer: NULL argument");
   TSR_CHECK_ARG(N >= 1 && F >= 1 && F <= (1 << 26), "tsr_visibility_transfer: N=%d F=%d out of range", N, F);
   TSR_CHECK_ARG(J == 1 || J == 4 || J == 9 || J == 16 || J == 25, "tsr_visibility_transfer: J=%d", J);
@@ -250,7 +250,7 @@ extern "C" tsr_status tsr_visibility_transfer(int N, const float *pos, const flo
 }
 
 extern "C" tsr_status tsr_haar_recompress(const float *M, tsr_compressed *c, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(M && c, "tsr_haar_recompress: NULL argument");
   tsr_status st = require_device();
   if (st != TSR_OK) return st;
@@ -272,7 +272,7 @@ static int chart_nu_of(int64_t N) {
 
 extern "C" tsr_status tsr_haar_compress_batched(int n_mesh, const int64_t *offsets, const float *M, int K, int J,
                                                 double p, tsr_compressed **out, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(offsets && M && out, "tsr_haar_compress_batched: NULL argument");
   TSR_CHECK_ARG(n_mesh >= 1 && n_mesh <= 65536, "tsr_haar_compress_batched: n_mesh=%d out of range", n_mesh);
   TSR_CHECK_ARG(K >= 1 && K <= 16 && J >= 1 && J <= 32, "tsr_haar_compress_batched: K=%d J=%d out of range", K, J);
@@ -305,7 +305,7 @@ extern "C" tsr_status tsr_haar_compress_batched(int n_mesh, const int64_t *offse
 
 extern "C" tsr_status tsr_haar_recompress_batched(int n_mesh, const int64_t *offsets, const float *M,
                                                   tsr_compressed *const *c, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(offsets && M && c, "tsr_haar_recompress_batched: NULL argument");
   TSR_CHECK_ARG(n_mesh >= 1 && n_mesh <= 65536, "tsr_haar_recompress_batched: n_mesh=%d out of range", n_mesh);
   TSR_CHECK_ARG(offsets[0] == 0, "tsr_haar_recompress_batched: offsets[0] must be 0");
@@ -337,7 +337,7 @@ extern "C" tsr_status tsr_haar_recompress_batched(int n_mesh, const int64_t *off
 
 extern "C" tsr_status tsr_compressed_info(const tsr_compressed *c, int *K, int *J, int *nu, int64_t *nnz,
                                           int *n_rows) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(c, "tsr_compressed_info: NULL handle");
   if (K) *K = c->K;
   if (J) *J = c->J;
@@ -349,7 +349,7 @@ extern "C" tsr_status tsr_compressed_info(const tsr_compressed *c, int *K, int *
 
 extern "C" tsr_status tsr_compressed_export(const tsr_compressed *c, int64_t *row_ptr, uint16_t *col, float *val,
                                             tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(c && row_ptr && col && val, "tsr_compressed_export: NULL argument");
   cudaStream_t s = as_stream(stream);
   TSR_CUDA(cudaMemcpyAsync(row_ptr, c->row_ptr, sizeof(int64_t) * (c->n_rows + 1), cudaMemcpyDeviceToDevice, s));
@@ -360,7 +360,7 @@ extern "C" tsr_status tsr_compressed_export(const tsr_compressed *c, int64_t *ro
 
 extern "C" tsr_status tsr_relight(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,
                                   tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(c && g && l && B, "tsr_relight: NULL argument");
   TSR_CHECK_ARG(n_edit >= 0 && n_edit <= (1 << 20), "tsr_relight: n_edit=%d out of range", n_edit);
   TSR_CHECK_ARG(aligned(g, 4) && aligned(l, 4) && aligned(B, 4), "tsr_relight: misaligned pointer");
@@ -371,7 +371,7 @@ extern "C" tsr_status tsr_relight(const tsr_compressed *c, int n_edit, const flo
 
 extern "C" tsr_status tsr_relight_many(int n_copy, const tsr_compressed *const *c, int n_edit, const float *g,
                                        const float *l, float *B, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(n_copy >= 0 && n_copy <= 65536, "tsr_relight_many: n_copy=%d out of range", n_copy);
   TSR_CHECK_ARG(n_edit >= 0 && n_edit <= (1 << 20), "tsr_relight_many: n_edit=%d out of range", n_edit);
   if (n_copy == 0) return TSR_OK;
@@ -427,7 +427,7 @@ extern "C" tsr_status tsr_relight_many(int n_copy, const tsr_compressed *const *
 
 extern "C" tsr_status tsr_relight_backward(const tsr_compressed *c, int n_edit, const float *g, const float *l,
                                            const float *dLdB, float *dg, float *dl, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(c && g && l && dLdB && dg && dl, "tsr_relight_backward: NULL argument");
   TSR_CHECK_ARG(n_edit >= 1 && n_edit <= (1 << 20), "tsr_relight_backward: n_edit=%d out of range", n_edit);
   tsr_status st = require_device();
@@ -437,7 +437,7 @@ extern "C" tsr_status tsr_relight_backward(const tsr_compressed *c, int n_edit, 
 
 extern "C" tsr_status tsr_batch_plan_create(const tsr_basis *basis, int n_mesh, const int64_t *offsets, int J,
                                             tsr_precision prec, tsr_batch_plan **out) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(basis && offsets && out, "tsr_batch_plan_create: NULL argument");
   TSR_CHECK_ARG(n_mesh >= 1 && n_mesh <= 65536, "tsr_batch_plan_create: n_mesh=%d out of range", n_mesh);
   TSR_CHECK_ARG(J >= 1 && J <= 32, "tsr_batch_plan_create: J=%d outside [1, 32]", J);
@@ -454,7 +454,7 @@ extern "C" tsr_status tsr_batch_plan_create(const tsr_basis *basis, int n_mesh, 
 
 extern "C" tsr_status tsr_precompute_transfer_plan(const tsr_batch_plan *plan, const float *pos, const float *area,
                                                    const float *T, float *M, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(plan && pos && area && T && M, "tsr_precompute_transfer_plan: NULL argument");
   TSR_CHECK_ARG(aligned(pos, 16), "tsr_precompute_transfer_plan: misaligned pos");
   tsr_status st = require_device();
@@ -464,7 +464,7 @@ extern "C" tsr_status tsr_precompute_transfer_plan(const tsr_batch_plan *plan, c
 
 extern "C" tsr_status tsr_batch_plan_autotune(tsr_batch_plan *plan, const float *pos, const float *area,
                                               const float *T, float *M, tsr_stream stream, float *best_ms) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(plan && pos && area && T && M, "tsr_batch_plan_autotune: NULL argument");
   tsr_status st = require_device();
   if (st != TSR_OK) return st;
@@ -472,7 +472,7 @@ extern "C" tsr_status tsr_batch_plan_autotune(tsr_batch_plan *plan, const float 
 }
 
 extern "C" tsr_status tsr_batch_plan_info(const tsr_batch_plan *plan, int *n_units, int *kb) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(plan, "tsr_batch_plan_info: NULL plan");
   if (n_units) *n_units = plan->n_units;
   if (kb) *kb = plan->kb;

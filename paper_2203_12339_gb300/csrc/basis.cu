@@ -342,7 +342,7 @@ using namespace tsr;
 extern "C" tsr_status tsr_fit_pca_basis(int n_mat, const double *sigma_a, const double *sigma_s, double eta,
                                         int n_r, double r_max, int K, double *sing_vals, tsr_basis **out,
                                         tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(out && sigma_a && sigma_s, "tsr_fit_pca_basis: NULL argument");
   TSR_CHECK_ARG(n_mat >= 2 && n_mat <= 1024, "tsr_fit_pca_basis: n_mat=%d outside [2, 1024]", n_mat);
   TSR_CHECK_ARG(n_r >= 16 && n_r <= 4096, "tsr_fit_pca_basis: n_r=%d outside [16, 4096]", n_r);
@@ -428,7 +428,7 @@ extern "C" tsr_status tsr_fit_pca_basis(int n_mat, const double *sigma_a, const 
 }
 
 extern "C" tsr_status tsr_basis_create(int K, int n_r, double r_max, const double *f_host, tsr_basis **out) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(out && f_host, "tsr_basis_create: NULL argument");
   TSR_CHECK_ARG(K >= 1 && K <= 16, "tsr_basis_create: K=%d outside [1, 16]", K);
   TSR_CHECK_ARG(n_r >= 16 && n_r <= 4096, "tsr_basis_create: n_r=%d outside [16, 4096]", n_r);
@@ -465,7 +465,7 @@ extern "C" tsr_status tsr_basis_create(int K, int n_r, double r_max, const doubl
 }
 
 extern "C" tsr_status tsr_basis_table(const tsr_basis *basis, double *f, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(basis && f, "tsr_basis_table: NULL argument");
   TSR_CUDA(cudaMemcpyAsync(f, basis->f64, sizeof(double) * basis->K * basis->n_r, cudaMemcpyDeviceToDevice,
                            reinterpret_cast<cudaStream_t>(stream)));
@@ -473,7 +473,7 @@ extern "C" tsr_status tsr_basis_table(const tsr_basis *basis, double *f, tsr_str
 }
 
 extern "C" tsr_status tsr_basis_info(const tsr_basis *basis, int *K, int *n_r, double *r_max) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(basis, "tsr_basis_info: NULL basis");
   if (K) *K = basis->K;
   if (n_r) *n_r = basis->n_r;
@@ -493,7 +493,7 @@ extern "C" void tsr_basis_destroy(tsr_basis *b) {
 extern "C" tsr_status tsr_project_material(const tsr_basis *basis, int n, const double *sigma_a,
                                            const double *sigma_s, const double *eta, double *g, float *g32,
                                            double *dg, tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(basis && sigma_a && sigma_s && eta && g, "tsr_project_material: NULL argument");
   TSR_CHECK_ARG(n >= 0 && n <= (1 << 22), "tsr_project_material: n=%d out of range", n);
   tsr_status st = require_device();
@@ -535,7 +535,7 @@ extern "C" tsr_status tsr_project_material_backward(const tsr_basis *basis, int 
                                                     const double *sigma_s, const double *eta, const float *dLdg,
                                                     float *dsigma_a, float *dsigma_s, float *deta,
                                                     tsr_stream stream) {
-  clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(basis && sigma_a && sigma_s && eta && dLdg && dsigma_a && dsigma_s && deta,
                 "tsr_project_material_backward: NULL argument");
   TSR_CHECK_ARG(n >= 0 && n <= (1 << 22), "tsr_project_material_backward: n=%d out of range", n);

@@ -63,7 +63,7 @@ tsr_status upload(T **d, const std::vector<T> &h, size_t n_alloc) {
 }  // namespace
 
 extern "C" tsr_status tsr_compressed_save(const tsr_compressed *c, const char *path) {
-  tsr::clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(c && path, "tsr_compressed_save: NULL argument");
   const size_t KJ = (size_t)c->K * c->J, nnz = (size_t)c->nnz;
   std::vector<int64_t> row_ptr, col_ptr;
@@ -90,7 +90,7 @@ extern "C" tsr_status tsr_compressed_save(const tsr_compressed *c, const char *p
 }
 
 extern "C" tsr_status tsr_compressed_load(const char *path, tsr_compressed **out) {
-  tsr::clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(path && out, "tsr_compressed_load: NULL argument");
   *out = nullptr;
   File in;

@@ -51,7 +51,7 @@ tsr_status scratch_for_current_device(float **out) {
 
 extern "C" tsr_status tsr_relight_noalloc(const tsr_compressed *c, int n_edit, const float *g, const float *l,
                                           float *B, tsr_stream stream) {
-  tsr::clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(c && g && l && B, "tsr_relight_noalloc: NULL argument");
   TSR_CHECK_ARG(n_edit >= 0 && n_edit <= (1 << 20), "tsr_relight_noalloc: n_edit=%d out of range", n_edit);
   TSR_CHECK_ARG(tsr::aligned(g, 4) && tsr::aligned(l, 4) && tsr::aligned(B, 4), "tsr_relight_noalloc: misaligned pointer");

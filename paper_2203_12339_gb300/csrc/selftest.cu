@@ -20,7 +20,7 @@ __global__ void bounded_wait_selftest_kernel(unsigned limit, unsigned *status) {
 }  // namespace
 
 extern "C" tsr_status tsr_selftest_bounded_wait(unsigned limit, tsr_stream stream) {
-  tsr::clear_error();
+  TSR_API_ENTRY();
   TSR_CHECK_ARG(limit >= 1 && limit <= 1000000u, "tsr_selftest_bounded_wait: limit=%u outside [1, 1e6]", limit);
   tsr_status st = tsr::require_device();
   if (st != TSR_OK) return st;

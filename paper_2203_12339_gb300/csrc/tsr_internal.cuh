@@ -33,6 +33,36 @@ const char *error_string();
     }                                                                               \
   } while (0)
 
+// NVTX range named after each C-ABI call, for profilers that show them (the NVTX v3
+// headers are header-only; without a tool attached a range costs a test of a null
+// pointer).  Absent headers leave the ranges out.
+#if defined(__has_include)
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define TSR_HAVE_NVTX 1
+#endif
+#endif
+struct NvtxRange {
+  explicit NvtxRange(const char *name) {
+#ifdef TSR_HAVE_NVTX
+    nvtxRangePushA(name);
+#else
+    (void)name;
+#endif
+  }
+  ~NvtxRange() {
+#ifdef TSR_HAVE_NVTX
+    nvtxRangePop();
+#endif
+  }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+// First statement of every C-ABI call: clears the thread's error string and opens the call's range.
+#define TSR_API_ENTRY()  \
+  ::tsr::clear_error(); \
+  ::tsr::NvtxRange tsr_api_range_(__func__)
+
 // Device-side status word written by kernels whose bounded waits ran out.
 // One word per device; kernels OR in a code, the host reads and clears it.
 enum : unsigned { DEV_ERR_TIMEOUT = 1u, DEV_ERR_BOUNDS = 2u };
