@@ -346,7 +346,7 @@ tsr_status tsr_visibility_transfer(int N, const float *pos, const float *normals
  *   Y[k][w] = sum_j S[w][kj] l[j],  Z[k] = W^-1 Y[k],  B[e][c] = sum_k g[e][c][k] Z[k],
  * so the kept coefficients are read once per call, whatever n_edit; for one or
  * two edits as written (one pass over S for their 3 or 6 vectors; under the
- * Haar with P <= 256 the product and the inverse Haar run fused per chart run
+ * Haar (every chart the library accepts) the product and the inverse Haar run fused per chart run
  * without scratch).
  * Scratch: max(K*(10 P^2 + 2 + N), 6*(10 P^2 + 2)) FP32.
  *
