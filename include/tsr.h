@@ -90,6 +90,21 @@ tsr_status tsr_selftest_bounded_wait(unsigned limit, tsr_stream stream);
  * error, if any.  The device status word is cleared. */
 tsr_status tsr_stream_status(tsr_stream stream);
 
+/* Host-side fault injection, for testing a caller's error handling without
+ * faulting a GPU (the paper has no counterpart).  The next n occurrences of a
+ * kind fail as if the underlying call had failed (n = 0 clears; process-wide):
+ *   TSR_FAULT_ALLOC   (1): stream-ordered scratch allocations -> TSR_ERR_OOM;
+ *   TSR_FAULT_CUDA    (2): checked CUDA runtime calls (launch checks, copies,
+ *                          allocations) -> TSR_ERR_CUDA; the call itself ran;
+ *   TSR_FAULT_TIMEOUT (3): tsr_stream_status -> TSR_ERR_TIMEOUT, as if a kernel's
+ *                          bounded wait had run out.
+ * An injected failure leaves the call's outputs undefined, as a real one would.
+ * TSR_ERR_INVALID_ARG for an unknown kind or n outside [0, 2^20]. */
+#define TSR_FAULT_ALLOC 1
+#define TSR_FAULT_CUDA 2
+#define TSR_FAULT_TIMEOUT 3
+tsr_status tsr_fault_inject(int kind, int n);
+
 /* ------------------------------------------------------------------------
  * Basis (Section 2.2, Eq. 5).
  *

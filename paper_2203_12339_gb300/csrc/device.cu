@@ -25,6 +25,16 @@ static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 unsigned long long launches() { return g_launches.load(std::memory_order_relaxed); }
 
+// Host-side fault injection (tsr_fault_inject): per kind, how many more occurrences fail.
+static std::atomic<int> g_fault[4];
+bool fault_hit(int kind) {
+  if (kind < 1 || kind > 3) return false;
+  int n = g_fault[kind].load(std::memory_order_relaxed);
+  while (n > 0)
+    if (g_fault[kind].compare_exchange_weak(n, n - 1, std::memory_order_relaxed)) return true;
+  return false;
+}
+
 static std::mutex g_mu;
 static std::map<int, unsigned *> g_status;   // device -> status word
 static std::map<int, int> g_sms;
@@ -76,6 +86,11 @@ unsigned *device_status_ptr() {
 }
 
 tsr_status check_device_status(cudaStream_t s) {
+  if (fault_hit(FAULT_TIMEOUT)) {
+    TSR_CUDA(cudaStreamSynchronize(s));
+    set_error("injected fault: a bounded wait ran out (tsr_fault_inject); outputs are undefined");
+    return TSR_ERR_TIMEOUT;
+  }
   unsigned *p = device_status_ptr();
   if (!p) {
     set_error("device status word unavailable");
@@ -100,3 +115,11 @@ tsr_status check_device_status(cudaStream_t s) {
 }  // namespace tsr
 
 extern "C" uint64_t tsr_kernel_launches(void) { return (uint64_t)tsr::launches(); }
+
+extern "C" tsr_status tsr_fault_inject(int kind, int n) {
+  TSR_API_ENTRY();
+  TSR_CHECK_ARG(kind >= TSR_FAULT_ALLOC && kind <= TSR_FAULT_TIMEOUT, "tsr_fault_inject: kind=%d unknown", kind);
+  TSR_CHECK_ARG(n >= 0 && n <= (1 << 20), "tsr_fault_inject: n=%d out of range", n);
+  tsr::g_fault[kind].store(n, std::memory_order_relaxed);
+  return TSR_OK;
+}

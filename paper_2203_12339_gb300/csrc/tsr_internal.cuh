@@ -24,13 +24,24 @@ const char *error_string();
     }                                         \
   } while (0)
 
-#define TSR_CUDA(call)                                                              \
-  do {                                                                              \
-    cudaError_t e_ = (call);                                                        \
-    if (e_ != cudaSuccess) {                                                        \
-      ::tsr::set_error("%s:%d: %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
-      return e_ == cudaErrorMemoryAllocation ? TSR_ERR_OOM : TSR_ERR_CUDA;          \
-    }                                                                               \
+// Host-side fault injection (tsr_fault_inject): true while injected failures of
+// `kind` remain (each call consumes one).
+enum { FAULT_ALLOC = 1, FAULT_CUDA = 2, FAULT_TIMEOUT = 3 };
+bool fault_hit(int kind);
+
+#define TSR_CUDA(call)                                                                            \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    bool injected_ = false;                                                                       \
+    if (e_ == cudaSuccess && ::tsr::fault_hit(::tsr::FAULT_CUDA)) {                               \
+      e_ = cudaErrorLaunchFailure; /* the call itself succeeded */                                \
+      injected_ = true;                                                                           \
+    }                                                                                             \
+    if (e_ != cudaSuccess) {                                                                      \
+      ::tsr::set_error("%s:%d: %s: %s%s", __FILE__, __LINE__, #call, cudaGetErrorString(e_),       \
+                       injected_ ? " (injected fault, tsr_fault_inject)" : "");                   \
+      return e_ == cudaErrorMemoryAllocation ? TSR_ERR_OOM : TSR_ERR_CUDA;                        \
+    }                                                                                             \
   } while (0)
 
 // NVTX range named after each C-ABI call, for profilers that show them (the NVTX v3
@@ -85,6 +96,10 @@ struct Scratch {
   }
   tsr_status alloc(size_t bytes, cudaStream_t stream) {
     s = stream;
+    if (fault_hit(FAULT_ALLOC)) {
+      set_error("injected fault: cudaMallocAsync(%zu) failed (tsr_fault_inject)", bytes);
+      return TSR_ERR_OOM;
+    }
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMallocAsync(&p, bytes, stream);
     if (e != cudaSuccess) {

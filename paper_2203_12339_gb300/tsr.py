@@ -73,6 +73,7 @@ _SIGNATURES = {
     "tsr_relight_many": (_I, [_I, _P, _I, _P, _P, _P, _P]),
     "tsr_haar_compress_batched": (_I, [_I, _P, _P, _I, _I, _D, _P, _P]),
     "tsr_compressed_save": (_I, [_P, ctypes.c_char_p]),
+    "tsr_fault_inject": (_I, [_I, _I]),
     "tsr_compressed_load": (_I, [ctypes.c_char_p, ctypes.POINTER(_P)]),
     "tsr_haar_recompress_batched": (_I, [_I, _P, _P, _P, _P]),
 }
@@ -132,6 +133,14 @@ def stream_status() -> None:
 def kernel_launches() -> int:
     """Kernel launches made by the library so far in this process."""
     return int(lib().tsr_kernel_launches())
+
+
+FAULT_KINDS = {"alloc": 1, "cuda": 2, "timeout": 3}
+
+
+def fault_inject(kind: str, n: int = 1) -> None:
+    """tsr_fault_inject: the next n occurrences of `kind` ("alloc", "cuda", "timeout") fail on the host."""
+    _check(lib().tsr_fault_inject(FAULT_KINDS[kind], n))
 
 
 def selftest_bounded_wait(limit: int = 1000) -> None:

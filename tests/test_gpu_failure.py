@@ -38,3 +38,37 @@ def test_invalid_selftest_limit_rejected_on_host(env):
     with pytest.raises(tsr.TsrError) as e:
         tsr.selftest_bounded_wait(0)
     assert e.value.status == -1
+
+
+def test_injected_faults_are_reported_and_recoverable(env):
+    """Host-side fault injection: an allocation that fails (TSR_ERR_OOM), a CUDA call that fails
+    (TSR_ERR_CUDA) and a bounded wait that runs out (TSR_ERR_TIMEOUT) are reported by the call that meets
+    them; the next calls succeed and give the same result as before the faults."""
+    torch, tsr = env
+    rng = np.random.default_rng(4)
+    nu, K, J, E = 8, 4, 9, 5                      # five edits: the factorised path, which needs scratch
+    P = 8
+    Mw = torch.tensor(rng.standard_normal((K, J, 10 * P * P + 2)).astype(np.float32), device="cuda")
+    comp = tsr.wavelet_compress(Mw, nu, 0.2)
+    g = torch.tensor(rng.standard_normal((E, 3, K)).astype(np.float32), device="cuda")
+    light = torch.tensor(rng.standard_normal(J).astype(np.float32), device="cuda")
+    want = tsr.relight(comp, g, light)
+    tsr.stream_status()
+    try:
+        for kind, status in (("alloc", -3), ("cuda", -2)):
+            tsr.fault_inject(kind, 1)
+            with pytest.raises(tsr.TsrError) as e:
+                tsr.relight(comp, g, light)
+            assert e.value.status == status, kind
+            assert "injected" in str(e.value)
+            torch.cuda.synchronize()
+            assert torch.equal(tsr.relight(comp, g, light), want), kind
+        tsr.fault_inject("timeout", 1)
+        with pytest.raises(tsr.TsrError) as e:
+            tsr.stream_status()
+        assert e.value.status == -4
+        tsr.stream_status()                       # consumed: the next query is clean
+        assert torch.equal(tsr.relight(comp, g, light), want)
+    finally:
+        for kind in ("alloc", "cuda", "timeout"):
+            tsr.fault_inject(kind, 0)

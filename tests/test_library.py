@@ -125,3 +125,12 @@ def test_compressed_load_rejects_bad_files_on_the_host(libtsr, tmp_path):
     assert load(str(cut).encode(), ctypes.byref(out)) == -1
     assert b"truncated arrays" in libtsr.tsr_last_error()
     assert not out.value
+
+
+def test_fault_injection_arguments_checked_on_the_host(libtsr):
+    f = libtsr.tsr_fault_inject
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int, ctypes.c_int]
+    assert f(0, 1) == -1 and f(4, 1) == -1 and f(1, -1) == -1
+    for kind in (1, 2, 3):
+        assert f(kind, 0) == 0
