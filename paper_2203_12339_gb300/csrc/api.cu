@@ -34,6 +34,7 @@ extern "C" tsr_status tsr_precompute_transfer(const tsr_basis *basis, int N, con
                 "tsr_precompute_transfer: misaligned pointer");
   TSR_CHECK_ARG((size_t)basis->K * J * (size_t)N < ((size_t)1 << 40), "tsr_precompute_transfer: output too large");
   tsr_status st = require_device();
+  if (st == TSR_OK) st = require_same_device(basis->device, "tsr_precompute_transfer");
   if (st != TSR_OK) return st;
   switch (prec) {
     case TSR_FP32:
@@ -64,6 +65,7 @@ extern "C" tsr_status tsr_precompute_transfer_batched(const tsr_basis *basis, in
   TSR_CHECK_ARG(prec == TSR_BF16 || prec == TSR_FP32, "tsr_precompute_transfer_batched: precision %d unsupported",
                 (int)prec);
   tsr_status st = require_device();
+  if (st == TSR_OK) st = require_same_device(basis->device, "tsr_precompute_transfer_batched");
   if (st != TSR_OK) return st;
   if (prec == TSR_BF16) return transfer_tc_batched(basis, n_mesh, offsets, pos, area, T, J, M, as_stream(stream));
   return transfer_fp32_batched(basis, n_mesh, offsets, pos, area, T, J, M, as_stream(stream));
@@ -253,6 +255,7 @@ extern "C" tsr_status tsr_haar_recompress(const float *M, tsr_compressed *c, tsr
   TSR_API_ENTRY();
   TSR_CHECK_ARG(M && c, "tsr_haar_recompress: NULL argument");
   tsr_status st = require_device();
+  if (st == TSR_OK) st = require_same_device(c->device, "tsr_haar_recompress");
   if (st != TSR_OK) return st;
   cudaStream_t s = as_stream(stream);
   Scratch mw;
@@ -320,6 +323,7 @@ extern "C" tsr_status tsr_haar_recompress_batched(int n_mesh, const int64_t *off
     mw_max = std::max(mw_max, (size_t)c[b]->K * c[b]->J * c[b]->n_rows);
   }
   tsr_status st = require_device();
+  for (int b = 0; b < n_mesh && st == TSR_OK; ++b) st = require_same_device(c[b]->device, "tsr_haar_recompress_batched");
   if (st != TSR_OK) return st;
   cudaStream_t s = as_stream(stream);
   const long long total = offsets[n_mesh];
@@ -365,6 +369,7 @@ extern "C" tsr_status tsr_relight(const tsr_compressed *c, int n_edit, const flo
   TSR_CHECK_ARG(n_edit >= 0 && n_edit <= (1 << 20), "tsr_relight: n_edit=%d out of range", n_edit);
   TSR_CHECK_ARG(aligned(g, 4) && aligned(l, 4) && aligned(B, 4), "tsr_relight: misaligned pointer");
   tsr_status st = require_device();
+  if (st == TSR_OK) st = require_same_device(c->device, "tsr_relight");
   if (st != TSR_OK || n_edit == 0) return st;
   return relight(c, n_edit, g, l, B, as_stream(stream));
 }
@@ -383,6 +388,7 @@ extern "C" tsr_status tsr_relight_many(int n_copy, const tsr_compressed *const *
                   i, c[i]->K, c[i]->J, c[0]->K, c[0]->J);
   }
   tsr_status st = require_device();
+  for (int i = 0; i < n_copy && st == TSR_OK; ++i) st = require_same_device(c[i]->device, "tsr_relight_many");
   if (st != TSR_OK || n_edit == 0) return st;
   cudaStream_t s = as_stream(stream);
   const size_t V = 3 * (size_t)n_edit, K = (size_t)c[0]->K;
@@ -431,6 +437,7 @@ extern "C" tsr_status tsr_relight_backward(const tsr_compressed *c, int n_edit, 
   TSR_CHECK_ARG(c && g && l && dLdB && dg && dl, "tsr_relight_backward: NULL argument");
   TSR_CHECK_ARG(n_edit >= 1 && n_edit <= (1 << 20), "tsr_relight_backward: n_edit=%d out of range", n_edit);
   tsr_status st = require_device();
+  if (st == TSR_OK) st = require_same_device(c->device, "tsr_relight_backward");
   if (st != TSR_OK) return st;
   return relight_backward(c, n_edit, g, l, dLdB, dg, dl, as_stream(stream));
 }
@@ -448,6 +455,7 @@ extern "C" tsr_status tsr_batch_plan_create(const tsr_basis *basis, int n_mesh, 
   TSR_CHECK_ARG(prec == TSR_BF16 || prec == TSR_FP32, "tsr_batch_plan_create: precision %d unsupported", (int)prec);
   *out = nullptr;
   tsr_status st = require_device();
+  if (st == TSR_OK) st = require_same_device(basis->device, "tsr_batch_plan_create");
   if (st != TSR_OK) return st;
   return batch_plan_create(basis, n_mesh, offsets, J, (int)prec, out);
 }
@@ -458,6 +466,7 @@ extern "C" tsr_status tsr_precompute_transfer_plan(const tsr_batch_plan *plan, c
   TSR_CHECK_ARG(plan && pos && area && T && M, "tsr_precompute_transfer_plan: NULL argument");
   TSR_CHECK_ARG(aligned(pos, 16), "tsr_precompute_transfer_plan: misaligned pos");
   tsr_status st = require_device();
+  if (st == TSR_OK) st = require_same_device(plan->device, "tsr_precompute_transfer_plan");
   if (st != TSR_OK) return st;
   return batch_plan_run(plan, pos, area, T, M, as_stream(stream));
 }
@@ -467,6 +476,7 @@ extern "C" tsr_status tsr_batch_plan_autotune(tsr_batch_plan *plan, const float 
   TSR_API_ENTRY();
   TSR_CHECK_ARG(plan && pos && area && T && M, "tsr_batch_plan_autotune: NULL argument");
   tsr_status st = require_device();
+  if (st == TSR_OK) st = require_same_device(plan->device, "tsr_batch_plan_autotune");
   if (st != TSR_OK) return st;
   return batch_plan_autotune(plan, pos, area, T, M, as_stream(stream), best_ms);
 }

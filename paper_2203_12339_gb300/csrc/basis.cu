@@ -497,6 +497,7 @@ extern "C" tsr_status tsr_project_material(const tsr_basis *basis, int n, const 
   TSR_CHECK_ARG(basis && sigma_a && sigma_s && eta && g, "tsr_project_material: NULL argument");
   TSR_CHECK_ARG(n >= 0 && n <= (1 << 22), "tsr_project_material: n=%d out of range", n);
   tsr_status st = require_device();
+  if (st == TSR_OK) st = require_same_device(basis->device, "tsr_project_material");
   if (st != TSR_OK) return st;
   if (n == 0) return TSR_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -540,6 +541,7 @@ extern "C" tsr_status tsr_project_material_backward(const tsr_basis *basis, int 
                 "tsr_project_material_backward: NULL argument");
   TSR_CHECK_ARG(n >= 0 && n <= (1 << 22), "tsr_project_material_backward: n=%d out of range", n);
   tsr_status st = require_device();
+  if (st == TSR_OK) st = require_same_device(basis->device, "tsr_project_material_backward");
   if (st != TSR_OK) return st;
   if (n == 0) return TSR_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -63,6 +63,16 @@ tsr_status require_device() {
   return TSR_OK;
 }
 
+tsr_status require_same_device(int device, const char *who) {
+  int dev = -1;
+  TSR_CUDA(cudaGetDevice(&dev));
+  if (dev != device) {
+    set_error("%s: the handle lives on device %d, the current device is %d", who, device, dev);
+    return TSR_ERR_INVALID_ARG;
+  }
+  return TSR_OK;
+}
+
 int num_sms() {
   int dev = 0;
   cudaGetDevice(&dev);

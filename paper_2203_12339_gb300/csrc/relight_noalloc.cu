@@ -60,6 +60,7 @@ extern "C" tsr_status tsr_relight_noalloc(const tsr_compressed *c, int n_edit, c
                 "tsr_relight_noalloc: the relight needs %zu floats of scratch, beyond the fixed %zu floats", need,
                 kNoallocScratchFloats);
   tsr_status st = tsr::require_device();
+  if (st == TSR_OK) st = tsr::require_same_device(c->device, "tsr_relight_noalloc");
   if (st != TSR_OK || n_edit == 0) return st;
   float *scratch = nullptr;
   st = scratch_for_current_device(&scratch);

@@ -85,6 +85,8 @@ void count_launch();
 
 // Verifies that the current device is an sm_103 part (the only compiled target).
 tsr_status require_device();
+// TSR_ERR_INVALID_ARG unless `device` (where a handle was made) is the current device.
+tsr_status require_same_device(int device, const char *who);
 int num_sms();
 
 // Stream-ordered scratch owned by one call.
