@@ -261,7 +261,7 @@ def batched_scene(tsr, dev, peaks, n_mesh: int = 256, n_edit: int = 1024) -> dic
     info = plan.info()
     res = {"workload": f"{n_mesh} uneven displaced icospheres ({int(n_per.min())}-{int(n_per.max())} vertices, "
                        f"{total} in all), K={K}, J={J}, BF16 transfer, top-10 % Haar, {n_edit} edits per mesh",
-           "pairs": pairs, "bases_per_group": info["bases_per_group"],
+           "pairs": pairs, "generator": info["generator"], "generator_param": info["param"],
            "transfer_ms": round(ms[0], 3), "transfer_g_pair_kj_per_s": round(pairs * K * J / (ms[0] * 1e-3) / 1e9, 1),
            "compress_ms": round(ms[1], 3), "relight_ms": round(ms[2], 3),
            "relight_hbm_roofline": {"bound": "hbm", "achieved": round(relight_bytes / (ms[2] * 1e-3) / 1e9, 1),

@@ -76,6 +76,14 @@ int tsr_version(void);
  * threads and devices); a diagnostic for counting launches in a region. */
 uint64_t tsr_kernel_launches(void);
 
+/* Device timing of the transfer's tensor-core kernel, for measurement: while
+ * enabled (enable = 1), every launch of that kernel is bracketed by two CUDA
+ * events on its stream.  tsr_kernel_timing_read synchronises on the recorded
+ * events, returns the sum of their elapsed times (ms) and their number, and
+ * releases them.  Enable it only outside stream capture. */
+tsr_status tsr_kernel_timing(int enable);
+tsr_status tsr_kernel_timing_read(double *total_ms, int *launches);
+
 /* Diagnostic of the failure path: launches one block that waits, with at most
  * `limit` (1..1e6) polls, on an mbarrier phase that nothing completes.  The
  * wait gives up, the kernel records a timeout in the device status word and
@@ -125,6 +133,12 @@ tsr_status tsr_fault_inject(int kind, int n);
  *
  * tsr_basis_table: copies f[K][n_r] (FP64) to a device buffer.
  * tsr_basis_info: K, n_r and r_max of a handle (host out-pointers, any may be NULL).
+ * tsr_basis_far_series: the far-field series the BF16 transfer evaluates
+ *   instead of the table (Section 3, Eq. 6-7; see tsr_precompute_transfer):
+ *   *rel_err = max_k max over r in [3/40 r_max, r_max] of
+ *   |sum_{p<12} c_kp T_p(x(r)) - r^2 f_k(r)| / max_r |r^2 f_k(r)|, computed on the
+ *   device when the handle was made; *used = 1 when rel_err <= 2e-3 (the BF16
+ *   transfer then uses the series, else the table).  Out-pointers may be NULL.
  * ---------------------------------------------------------------------- */
 tsr_status tsr_fit_pca_basis(int n_mat, const double *sigma_a, const double *sigma_s, double eta,
                              int n_r, double r_max, int K, double *sing_vals, tsr_basis **out,
@@ -132,6 +146,7 @@ tsr_status tsr_fit_pca_basis(int n_mat, const double *sigma_a, const double *sig
 tsr_status tsr_basis_create(int K, int n_r, double r_max, const double *f_host, tsr_basis **out);
 tsr_status tsr_basis_table(const tsr_basis *basis, double *f, tsr_stream stream);
 tsr_status tsr_basis_info(const tsr_basis *basis, int *K, int *n_r, double *r_max);
+tsr_status tsr_basis_far_series(const tsr_basis *basis, double *rel_err, int *used);
 void tsr_basis_destroy(tsr_basis *basis);
 
 /* ------------------------------------------------------------------------
@@ -168,7 +183,22 @@ tsr_status tsr_project_material_backward(const tsr_basis *basis, int n, const do
  *   T    : device [J][N] FP32.
  *   M    : device [K][J][N] FP32 out (overwritten).
  *   prec : TSR_FP32, TSR_BF16 or TSR_BF16X3.
- * Scratch: a pre-tiled copy of (x_i, A_i T[.,i]), about N*(2*J_pad*2+12) bytes.
+ * Precisions:
+ *   TSR_FP32   CUDA cores, FP32 table of f_k, Kahan-compensated sums.
+ *   TSR_BF16   tensor cores (BF16 x BF16 -> FP32) for the far pairs, those with
+ *              r^2 >= r_e^2, r_e = max(3/40 r_max, 2 h), h^2 = sum(A)/N; the near
+ *              pairs r^2 < r_e^2 (the self pair among them) are summed exactly in
+ *              FP32 and added.  The far kernel values come from the 12-term
+ *              series f_k(r) = sum_p c_kp T_p(x) / r^2 (x linear in log r on
+ *              [3/40 r_max, r_max]) when tsr_basis_far_series reports it accurate,
+ *              else from the BF16 table.
+ *   TSR_BF16X3 split BF16 (hi + lo of both operands, three products) for every
+ *              pair from the table, the self pair replaced in FP32.
+ * Scratch: a pre-tiled copy of (x_i, A_i T[.,i]), about N*(2*J_pad*2+12) bytes,
+ * and for TSR_BF16 the Morton-sorted copy of the inputs the near field reads,
+ * about N*(4*J_pad+40) bytes (stream-ordered, freed by the call).
+ * Errors: TSR_ERR_INVALID_ARG for NULL or misaligned pointers or N, J out of
+ * range; TSR_ERR_OOM when scratch cannot be allocated; nothing is launched then.
  * ---------------------------------------------------------------------- */
 tsr_status tsr_precompute_transfer(const tsr_basis *basis, int N, const float *pos, const float *area,
                                    const float *T, int J, tsr_precision prec, float *M,
@@ -185,13 +215,18 @@ tsr_status tsr_precompute_transfer(const tsr_basis *basis, int N, const float *p
  * tsr_precompute_transfer_batched synchronises the stream (it builds and frees
  * a plan).  For repeated or graph-captured use, build a plan once:
  *   tsr_batch_plan_create   uploads the unit and mesh tables (synchronous);
- *   tsr_batch_plan_autotune times each tile configuration (bases per CTA group)
- *                           on the caller's data, keeps the fastest, returns its
- *                           time in *best_ms (synchronises; outside any capture);
+ *   tsr_batch_plan_autotune times each generator configuration of the BF16
+ *                           transfer (the far-field series with one or two 16-i
+ *                           steps in flight; the table with 4, 8, 12 or 16 bases
+ *                           per CTA group) on the caller's data, keeps the
+ *                           fastest, returns its time in *best_ms (synchronises;
+ *                           outside any capture);
  *   tsr_precompute_transfer_plan enqueues the transfer only (kernels and
  *                           stream-ordered scratch), so it may be captured in a
  *                           CUDA graph;
- *   tsr_batch_plan_info     units and chosen bases per group (0 = default);
+ *   tsr_batch_plan_info     units, the chosen generator (0: far-field series,
+ *                           1: table) and its parameter (steps in flight, or
+ *                           bases per group; 0 = default);
  *   tsr_batch_plan_destroy. */
 tsr_status tsr_precompute_transfer_batched(const tsr_basis *basis, int n_mesh, const int64_t *offsets,
                                            const float *pos, const float *area, const float *T, int J,
@@ -203,7 +238,7 @@ tsr_status tsr_batch_plan_autotune(tsr_batch_plan *plan, const float *pos, const
                                    float *M, tsr_stream stream, float *best_ms);
 tsr_status tsr_precompute_transfer_plan(const tsr_batch_plan *plan, const float *pos, const float *area,
                                         const float *T, float *M, tsr_stream stream);
-tsr_status tsr_batch_plan_info(const tsr_batch_plan *plan, int *n_units, int *kb);
+tsr_status tsr_batch_plan_info(const tsr_batch_plan *plan, int *n_units, int *generator, int *param);
 void tsr_batch_plan_destroy(tsr_batch_plan *plan);
 
 /* ------------------------------------------------------------------------
@@ -409,7 +444,8 @@ tsr_status tsr_relight_many(int n_copy, const tsr_compressed *const *c, int n_ed
  * Same arguments, layouts and result as tsr_relight.  Its intermediate buffer
  * comes from a fixed 32 MiB array of device memory that the library reserves on
  * every GPU where it is loaded (held until the process exits), so the call
- * itself allocates nothing.
+ * itself allocates nothing (the array also holds the run approximations that
+ * the inverse Haar of charts larger than 32 x 32 needs).
  *   - Limit: the scratch above <= 8,388,608 floats, else TSR_ERR_INVALID_ARG
  *     (the largest case the library accepts, K = 16 on nu = 128, needs 5.2 Mi;
  *     the number of edits does not enter).

@@ -399,6 +399,28 @@ def fresnel_output_vjp(B, eta, cos_o, dBout):
     return dB, deta
 
 
+def sh_real_oracle(order: int, dirs) -> np.ndarray:
+    """Real orthonormal spherical harmonics Y_j(w), j = l^2 + l + m, l < order (reading R19):
+    Y_l0 = N_l0 P_l(z), Y_lm = sqrt(2) N_lm P_l^m(z) cos(m phi), Y_l,-m = sqrt(2) N_lm P_l^m(z) sin(m phi),
+    N_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!), with P_l^m the associated Legendre function WITHOUT the
+    Condon-Shortley phase (scipy's lpmv carries (-1)^m, which is removed here).  Returns (order^2, R)."""
+    from scipy.special import lpmv
+    d = np.asarray(dirs, dtype=np.float64)
+    z = np.clip(d[:, 2], -1.0, 1.0)
+    phi = np.arctan2(d[:, 1], d[:, 0])
+    out = np.empty((order * order, d.shape[0]))
+    for l in range(order):
+        for m in range(0, l + 1):
+            Nlm = math.sqrt((2 * l + 1) / (4.0 * math.pi) * math.factorial(l - m) / math.factorial(l + m))
+            Plm = (-1.0) ** m * lpmv(m, l, z)
+            if m == 0:
+                out[l * l + l] = Nlm * Plm
+            else:
+                out[l * l + l + m] = math.sqrt(2.0) * Nlm * Plm * np.cos(m * phi)
+                out[l * l + l - m] = math.sqrt(2.0) * Nlm * Plm * np.sin(m * phi)
+    return out
+
+
 def sh_zonal_fresnel(eta, order):
     """Zonal coefficients of h(mu) = F_t(eta, mu) max(mu, 0) (reading R35):
     A_l = 2 pi int_0^1 F_t(eta, mu) mu P_l(mu) dmu, l < order, so that by the Funk-Hecke theorem
@@ -417,9 +439,8 @@ def sh_zonal_fresnel(eta, order):
 def sh_transfer_fresnel(normals, J, eta):
     """T[j, i] = A_l(eta) Y_lm(n_i): the unshadowed irradiance transfer with the incident Fresnel
     transmittance folded in (Eq. 6 with F_t(eta, omega_i) inside E; readings R18, R19, R35)."""
-    from paper_2203_12339_gb300.scene import sh_real
     order = int(round(math.sqrt(J)))
-    Y = sh_real(order, np.asarray(normals, dtype=np.float64))
+    Y = sh_real_oracle(order, np.asarray(normals, dtype=np.float64))
     A = sh_zonal_fresnel(eta, order)
     for l in range(order):
         Y[l * l:(l + 1) * (l + 1)] *= A[l]
@@ -492,7 +513,6 @@ def visibility_transfer(pos, tris, normals, J, S, eps=1e-3, eta=None):
     """Self-shadowed SH irradiance transfer T[j, i] = (pi / S) sum_s Y_j(w_s) V(x_i, w_s) [F_t(eta, mu_s)]
     (Eq. 6's E with visibility; reading R36): w_s the cosine-weighted Hammersley directions in the frame
     of n_i, rays from x_i + eps n_i (FP32), V = 0 when the ray hits any triangle of the mesh."""
-    from paper_2203_12339_gb300.scene import sh_real
     pos32, n32 = _f32(pos), _f32(normals)
     t1, t2 = onb_from_normal(n32.astype(np.float64))
     loc = hemisphere_samples(S)
@@ -507,7 +527,7 @@ def visibility_transfer(pos, tris, normals, J, S, eps=1e-3, eta=None):
         w = (math.pi / S) * vis.astype(np.float64)
         if eta is not None:
             w = w * fresnel_transmittance(eta, loc[:, 2])
-        T[:, i] = sh_real(order, dirs.astype(np.float64)) @ w
+        T[:, i] = sh_real_oracle(order, dirs.astype(np.float64)) @ w
     return T
 
 

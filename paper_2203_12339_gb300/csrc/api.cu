@@ -481,11 +481,13 @@ extern "C" tsr_status tsr_batch_plan_autotune(tsr_batch_plan *plan, const float 
   return batch_plan_autotune(plan, pos, area, T, M, as_stream(stream), best_ms);
 }
 
-extern "C" tsr_status tsr_batch_plan_info(const tsr_batch_plan *plan, int *n_units, int *kb) {
+extern "C" tsr_status tsr_batch_plan_info(const tsr_batch_plan *plan, int *n_units, int *generator, int *param) {
   TSR_API_ENTRY();
   TSR_CHECK_ARG(plan, "tsr_batch_plan_info: NULL plan");
+  const int gen = (plan->gen == 0 && plan->basis->cheb_ok) ? 0 : 1;
   if (n_units) *n_units = plan->n_units;
-  if (kb) *kb = plan->kb;
+  if (generator) *generator = gen;
+  if (param) *param = gen == 0 ? plan->conc : plan->kb;
   return TSR_OK;
 }
 

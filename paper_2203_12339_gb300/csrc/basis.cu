@@ -173,10 +173,16 @@ __global__ void build_tables_kernel(const double *__restrict__ f, int K, int KP,
   tab16[idx] = (uint32_t)__bfloat16_as_ushort(bv) | ((uint32_t)__bfloat16_as_ushort(bs) << 16);
 }
 
-// Chebyshev projection of the piecewise-linear f_k on [r_near, r_max] in the
-// variable x = 2 (ln r - ln r_near)/(ln r_max - ln r_near) - 1, at the nodes
+// Far-field series of the BF16 transfer.  On [r_near, r_max] the weighted basis
+// g_k(r) = r^2 f_k(r) (R_d falls off like 1/r^2 away from the source, so g_k has
+// little dynamic range) is projected on Chebyshev polynomials in the variable
+// x = 2 (ln r - ln r_near)/(ln r_max - ln r_near) - 1, at the nodes
 // x_n = cos(theta_n), theta_n = pi (n + 1/2)/N:
-//   c_p = (2 - [p = 0]) / N * sum_n f_k(r(x_n)) cos(p theta_n).
+//   c_p = (2 - [p = 0]) / N * sum_n g_k(r(x_n)) cos(p theta_n).
+// Then f_k(r) ~= sum_p c_p T_p(x) / r^2.  The transfer kernel generates
+// W_p = sigma_p T_p(x) / r^2 with sigma_p = (-1)^(p(p-1)/2), for which the
+// Chebyshev recurrence needs only additions: W_{p+1} = (-1)^p 2x W_p + W_{p-1};
+// the stored coefficients carry the sign, cheb[k][p] = sigma_p c_p.
 // One block per basis function, FP64.
 __global__ void __launch_bounds__(256) cheb_fit_kernel(const double *__restrict__ f, int n_r, double r_max,
                                                        double r_near, float *__restrict__ cheb) {
@@ -195,14 +201,68 @@ __global__ void __launch_bounds__(256) cheb_fit_kernel(const double *__restrict_
     if (m > n_r - 2) m = n_r - 2;
     if (m < 0) m = 0;
     const double t = xm - m;
-    const double fv = f[(size_t)k * n_r + m] * (1.0 - t) + f[(size_t)k * n_r + m + 1] * t;
+    const double gv = r * r * (f[(size_t)k * n_r + m] * (1.0 - t) + f[(size_t)k * n_r + m + 1] * t);
 #pragma unroll
-    for (int p = 0; p < TSR_CHEB_P; ++p) acc[p] += fv * cos(p * th);
+    for (int p = 0; p < TSR_CHEB_P; ++p) acc[p] += gv * cos(p * th);
   }
   block_sum<TSR_CHEB_P>(acc, red);
   if (threadIdx.x < TSR_CHEB_P) {
     const int p = threadIdx.x;
-    cheb[k * TSR_CHEB_P + p] = (float)((p == 0 ? 1.0 : 2.0) / TSR_CHEB_NODES * acc[p]);
+    const double sigma = ((p * (p - 1) / 2) & 1) ? -1.0 : 1.0;
+    cheb[k * TSR_CHEB_P + p] = (float)(sigma * (p == 0 ? 1.0 : 2.0) / TSR_CHEB_NODES * acc[p]);
+  }
+}
+
+// Quality of the truncated series (TSR_CHEB_BF16 terms) per basis: max over a
+// log-spaced grid of [r_near, r_max] of |sum_p c_p T_p(x) - g_k(r)| / max |g_k|.
+// err[k] is written; the BF16 transfer uses the series only when every err[k]
+// is small (the PCA bases of R_d are smooth there; an arbitrary basis may not be).
+__global__ void __launch_bounds__(256) cheb_check_kernel(const double *__restrict__ f, int n_r, double r_max,
+                                                         double r_near, const float *__restrict__ cheb,
+                                                         double *__restrict__ err) {
+  __shared__ double red[2 * 32];
+  const int k = blockIdx.x;
+  const double lo = log(r_near), hi = log(r_max), dr = r_max / (n_r - 1);
+  constexpr int NPT = 4096;
+  double e = 0.0, gmax = 0.0;
+  for (int n = threadIdx.x; n < NPT; n += blockDim.x) {
+    const double x = -1.0 + 2.0 * n / (NPT - 1);
+    const double r = exp(lo + 0.5 * (x + 1.0) * (hi - lo));
+    const double xm = r / dr;
+    int m = (int)floor(xm);
+    if (m > n_r - 2) m = n_r - 2;
+    if (m < 0) m = 0;
+    const double t = xm - m;
+    const double gv = r * r * (f[(size_t)k * n_r + m] * (1.0 - t) + f[(size_t)k * n_r + m + 1] * t);
+    double t0 = 1.0, t1 = x, approx = 0.0;
+    for (int p = 0; p < TSR_CHEB_BF16; ++p) {
+      const double sigma = ((p * (p - 1) / 2) & 1) ? -1.0 : 1.0;
+      approx += sigma * (double)cheb[k * TSR_CHEB_P + p] * t0;
+      const double t2 = 2.0 * x * t1 - t0;
+      t0 = t1;
+      t1 = t2;
+    }
+    e = fmax(e, fabs(approx - gv));
+    gmax = fmax(gmax, fabs(gv));
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    e = fmax(e, __shfl_xor_sync(0xffffffffu, e, o));
+    gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  }
+  if (lane == 0) {
+    red[warp] = e;
+    red[32 + warp] = gmax;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double em = 0.0, gm = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      em = fmax(em, red[w]);
+      gm = fmax(gm, red[32 + w]);
+    }
+    err[k] = gm > 0.0 ? em / gm : 0.0;
   }
 }
 
@@ -215,9 +275,18 @@ tsr_status basis_build_tables(tsr_basis *b, cudaStream_t s) {
   const double lo = std::log(b->r_near), hi = std::log(b->r_max);
   b->x_alpha = (float)(std::log(2.0) / (hi - lo));
   b->x_beta = (float)(-1.0 - 2.0 * lo / (hi - lo));
-  if (!b->cheb) TSR_CUDA(cudaMalloc(&b->cheb, sizeof(float) * b->K * TSR_CHEB_P));
+  if (!b->cheb) TSR_CUDA(cudaMalloc(&b->cheb, sizeof(float) * b->K * TSR_CHEB_P + sizeof(double) * 16));
   cheb_fit_kernel<<<b->K, 256, 0, s>>>(b->f64, b->n_r, b->r_max, b->r_near, b->cheb); ::tsr::count_launch();
+  double *d_err = reinterpret_cast<double *>(b->cheb + (((size_t)b->K * TSR_CHEB_P + 1) & ~(size_t)1));
+  cheb_check_kernel<<<b->K, 256, 0, s>>>(b->f64, b->n_r, b->r_max, b->r_near, b->cheb, d_err); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
+  double h_err[16] = {0.0};
+  TSR_CUDA(cudaMemcpyAsync(h_err, d_err, sizeof(double) * b->K, cudaMemcpyDeviceToHost, s));
+  TSR_CUDA(cudaStreamSynchronize(s));   // basis creation is a one-time, synchronous step
+  double worst = 0.0;
+  for (int k = 0; k < b->K; ++k) worst = std::max(worst, h_err[k]);
+  b->cheb_err = worst;
+  b->cheb_ok = worst <= TSR_CHEB_MAX_ERR;
   return TSR_OK;
 }
 
@@ -478,6 +547,14 @@ extern "C" tsr_status tsr_basis_info(const tsr_basis *basis, int *K, int *n_r, d
   if (K) *K = basis->K;
   if (n_r) *n_r = basis->n_r;
   if (r_max) *r_max = basis->r_max;
+  return TSR_OK;
+}
+
+extern "C" tsr_status tsr_basis_far_series(const tsr_basis *basis, double *rel_err, int *used) {
+  TSR_API_ENTRY();
+  TSR_CHECK_ARG(basis, "tsr_basis_far_series: NULL basis");
+  if (rel_err) *rel_err = basis->cheb_err;
+  if (used) *used = basis->cheb_ok ? 1 : 0;
   return TSR_OK;
 }
 

@@ -225,8 +225,8 @@ tsr_status cdf97_inverse_transpose(const float *X, int rows, int nu, float *Xw, 
 tsr_status spatial_forward(int wavelet, const float *X, int rows, int nu, float *Xw, cudaStream_t s) {
   return wavelet == 1 ? cdf97_forward(X, rows, nu, Xw, s) : haar_forward(X, rows, nu, Xw, s);
 }
-tsr_status spatial_inverse(int wavelet, const float *Xw, int rows, int nu, float *X, cudaStream_t s) {
-  return wavelet == 1 ? cdf97_inverse(Xw, rows, nu, X, s) : haar_inverse(Xw, rows, nu, X, s);
+tsr_status spatial_inverse(int wavelet, const float *Xw, int rows, int nu, float *X, cudaStream_t s, float *seg) {
+  return wavelet == 1 ? cdf97_inverse(Xw, rows, nu, X, s) : haar_inverse(Xw, rows, nu, X, s, seg);
 }
 tsr_status spatial_inverse_transpose(int wavelet, const float *X, int rows, int nu, float *Xw, cudaStream_t s) {
   return wavelet == 1 ? cdf97_inverse_transpose(X, rows, nu, Xw, s) : haar_forward(X, rows, nu, Xw, s);

@@ -3,6 +3,8 @@
 #include <cstdarg>
 #include <mutex>
 #include <map>
+#include <utility>
+#include <vector>
 
 #include "tsr_internal.cuh"
 
@@ -24,6 +26,33 @@ const char *error_string() { return g_err; }
 static std::atomic<unsigned long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 unsigned long long launches() { return g_launches.load(std::memory_order_relaxed); }
+
+// Optional device timing of the transfer's tensor-core kernel (tsr_kernel_timing): a
+// pair of CUDA events around each launch, read and released by tsr_kernel_timing_read.
+static std::atomic<int> g_timing{0};
+static std::mutex g_timing_mu;
+static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_timing_ev;
+
+KernelTimer::KernelTimer(cudaStream_t stream) : s(stream) {
+  if (!g_timing.load(std::memory_order_relaxed)) return;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess || cudaEventRecord(a, s) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    a = b = nullptr;
+  }
+}
+
+void KernelTimer::stop() {
+  if (!a) return;
+  if (cudaEventRecord(b, s) == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    g_timing_ev.emplace_back(a, b);
+  } else {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+  a = b = nullptr;
+}
 
 // Host-side fault injection (tsr_fault_inject): per kind, how many more occurrences fail.
 static std::atomic<int> g_fault[4];
@@ -125,6 +154,39 @@ tsr_status check_device_status(cudaStream_t s) {
 }  // namespace tsr
 
 extern "C" uint64_t tsr_kernel_launches(void) { return (uint64_t)tsr::launches(); }
+
+extern "C" tsr_status tsr_kernel_timing(int enable) {
+  TSR_API_ENTRY();
+  tsr::g_timing.store(enable ? 1 : 0, std::memory_order_relaxed);
+  return TSR_OK;
+}
+
+extern "C" tsr_status tsr_kernel_timing_read(double *total_ms, int *launches) {
+  TSR_API_ENTRY();
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  {
+    std::lock_guard<std::mutex> lk(tsr::g_timing_mu);
+    ev.swap(tsr::g_timing_ev);
+  }
+  double sum = 0.0;
+  cudaError_t err = cudaSuccess;
+  for (auto &p : ev) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(p.second);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.first, p.second);
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+    sum += ms;
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  if (total_ms) *total_ms = sum;
+  if (launches) *launches = (int)ev.size();
+  if (err != cudaSuccess) {
+    tsr::set_error("tsr_kernel_timing_read: %s", cudaGetErrorString(err));
+    return TSR_ERR_CUDA;
+  }
+  return TSR_OK;
+}
 
 extern "C" tsr_status tsr_fault_inject(int kind, int n) {
   TSR_API_ENTRY();

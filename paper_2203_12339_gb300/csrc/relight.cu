@@ -311,18 +311,26 @@ __global__ void __launch_bounds__(1024) relight_grad_finish_kernel(const float *
   }
 }
 
-// Y[k] = (S (I_K x l))[k] (K x n_rows) and its inverse Haar Z[k] (K x N).
-static tsr_status relight_basis_images(const tsr_compressed *c, const float *l, float *Y, float *Z, cudaStream_t s) {
+// Y[k] = (S (I_K x l))[k] (K x n_rows) and its inverse Haar Z[k] (K x N).  seg: the
+// inverse Haar's run approximations (NULL: stream-ordered scratch).
+static tsr_status relight_basis_images(const tsr_compressed *c, const float *l, float *Y, float *Z, cudaStream_t s,
+                                       float *seg = nullptr) {
   TSR_CUDA(cudaMemsetAsync(Y, 0, sizeof(float) * (size_t)c->K * c->n_rows, s));
   relight_y_kernel<<<(c->n_rows + 7) / 8, 256, 0, s>>>(c->row_ptr, c->col, c->val, c->n_rows, c->J, l, Y);
   ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
-  return spatial_inverse(c->wavelet, Y, c->K, c->nu, Z, s);
+  return spatial_inverse(c->wavelet, Y, c->K, c->nu, Z, s, seg);
+}
+
+// Layout of the caller's scratch: [intermediates | run approximations of the inverse Haar]
+static size_t relight_main_floats(const tsr_compressed *c) {
+  const size_t N = 10 * (size_t)c->nu * c->nu + 2;
+  return std::max((size_t)c->K * ((size_t)c->n_rows + N), (size_t)RL_DV * c->n_rows);
 }
 
 size_t relight_scratch_floats(const tsr_compressed *c) {
-  const size_t N = 10 * (size_t)c->nu * c->nu + 2;
-  return std::max((size_t)c->K * ((size_t)c->n_rows + N), (size_t)RL_DV * c->n_rows);
+  const size_t seg = c->wavelet == 1 ? 0 : haar_inverse_seg_floats(std::max(c->K, RL_DV), c->nu);
+  return relight_main_floats(c) + seg;
 }
 
 tsr_status relight_with_scratch(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,
@@ -331,16 +339,17 @@ tsr_status relight_with_scratch(const tsr_compressed *c, int n_edit, const float
   if (V == 0) return TSR_OK;
   const int N = 10 * c->nu * c->nu + 2;
   if (relight_fusable(c, n_edit)) return relight_fused(1, &c, n_edit, &g, l, &B, s);
+  float *seg = scratch + relight_main_floats(c);   // never handed to the allocating path
   if (V <= RL_DV) {
     if (V == 3)
       launch_direct<3>(c, g, l, scratch, s);
     else
       launch_direct<6>(c, g, l, scratch, s);   // V = 3 n_edit <= RL_DV: 3 or 6
     TSR_CUDA(cudaGetLastError());
-    return spatial_inverse(c->wavelet, scratch, V, c->nu, B, s);
+    return spatial_inverse(c->wavelet, scratch, V, c->nu, B, s, seg);
   }
   float *Y = scratch, *Z = scratch + (size_t)c->K * c->n_rows;
-  tsr_status st = relight_basis_images(c, l, Y, Z, s);
+  tsr_status st = relight_basis_images(c, l, Y, Z, s, seg);
   if (st != TSR_OK) return st;
   launch_combine(Z, N, c->K, V, g, B, s);
   TSR_CUDA(cudaGetLastError());

@@ -17,8 +17,9 @@
 
 namespace {
 
-// Scratch for Y and Z: 8 Mi floats = 32 MiB (the largest case, K = 16 on a
-// 163,842-vertex mesh, needs 5.2 Mi).  Every GPU that loads the library holds this
+// Scratch for Y and Z (or b^w) and the run approximations of the two-kernel inverse
+// Haar of charts larger than 32 x 32: 8 Mi floats = 32 MiB (the largest case, K = 16
+// on a 163,842-vertex mesh, needs 5.2 Mi).  Every GPU that loads the library holds this
 // array until the process exits.
 constexpr size_t kNoallocScratchFloats = size_t(8) << 20;
 static __device__ __align__(256) float g_relight_scratch[kNoallocScratchFloats];

@@ -8,16 +8,22 @@
 //    accumulates all J products per pair, with the partial sum of each 64-i
 //    tile added into a Kahan-compensated total.
 //  * transfer_tc:   tensor-core path (tcgen05).  A block owns 128 output rows
-//    (the UMMA M = 128) and a group of KB bases.  Per 16-i step, 256 threads
-//    evaluate F_k[o, i] = f_k(r_oi) (BF16, or hi/lo BF16 for the split
-//    variant) into shared memory in the canonical K-major layout, while the
-//    Tensor Memory Accelerator streams the matching tile of
-//    T'[j][i] = A_i T[j][i] (pre-tiled BF16 records that also carry the x_i).
-//    One thread issues tcgen05.mma with FP32 accumulators for all KB bases in
-//    tensor memory (KB x J_pad columns); the epilogue reads TMEM back with
-//    tcgen05.ld and writes M.
+//    (the UMMA M = 128).  Per 16-i step, 512 generator threads write the A
+//    operand (128 rows x 16 i, BF16) into tensor memory or shared memory, while
+//    the Tensor Memory Accelerator streams the matching tile of
+//    T'[j][i] = A_i T[j][i] (pre-tiled BF16 records that also carry the x_i), and
+//    one warp issues tcgen05.mma with FP32 accumulators in tensor memory; the
+//    epilogue reads TMEM back with tcgen05.ld and writes M.  Two generators:
+//      - BF16 (default): the far field r >= r_e from the scaled Chebyshev series
+//        of the basis (f_k(r) = sum_p c_kp W_p(r), W_p = sigma_p T_p(x) / r^2, 12
+//        terms), the W_p evaluated in registers by a packed BF16 recurrence, the
+//        accumulators holding G[p][j] = sum_i W_p T'[j][i] and the epilogue
+//        forming M[k][j] = sum_p c_kp G[p][j]; the near field r < r_e is added
+//        exactly in FP32 by near.cu;
+//      - table (split BF16, and bases whose series is not accurate): F_k from
+//        the shared-memory table of {value, slope} per radius sample.
 //
-// Pair geometry (both paths): dx = fl(x_o - x_i) etc. and
+// Pair geometry (every path): dx = fl(x_o - x_i) etc. and
 // r2 = fl(fl(fl(dx^2) + fl(dy^2)) + fl(dz^2)) without contraction; pairs with
 // r2 > fl(r_max^2) are cut off (f_k = 0).  Otherwise r = sqrt(r2),
 // x = r / dr, m = min(floor(x), n_r - 2), t = x - m and
@@ -28,6 +34,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "handles.cuh"
@@ -271,6 +278,24 @@ __device__ __forceinline__ void umma_bf16_ta_elect(uint32_t d_tmem, uint32_t a_t
       "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
+// Four MMAs of consecutive columns groups (accumulators d0 + c JP, A tiles a0 + 8 c, c < 4)
+// under one elect.sync, all with the same B tile and accumulate flag.
+template <int JP>
+__device__ __forceinline__ void umma4_ta(uint32_t d0, uint32_t a0, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p, e;\n\t.reg .b32 d, a;\n\t"
+      "elect.sync _|e, 0xffffffff;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t"
+      "add.u32 d, %0, %5;\n\tadd.u32 a, %1, 8;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d], [a], %2, %3, p;\n\t"
+      "add.u32 d, %0, %6;\n\tadd.u32 a, %1, 16;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d], [a], %2, %3, p;\n\t"
+      "add.u32 d, %0, %7;\n\tadd.u32 a, %1, 24;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [d], [a], %2, %3, p;\n\t}" ::"r"(d0),
+      "r"(a0), "l"(b), "r"(idesc), "r"(acc), "n"(JP), "n"(2 * JP), "n"(3 * JP)
+      : "memory");
+}
 __device__ __forceinline__ void umma_commit_elect(uint64_t *bar) {
   asm volatile(
       "{\n\t.reg .pred e;\n\t"
@@ -294,6 +319,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -329,26 +359,31 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 }
 
 // ---------------------------------------------------------------- the kernel
-// One pipeline, two generators of the A operand (128 output rows x 16 i per step):
-//  * MODE_NEAR: A[o][i] = f_k(r_oi), k in the CTA's group of CB bases, from the
-//    shared-memory table, for the pairs with r_oi^2 < rn2 (rn2 = +inf: all pairs);
-//    the pass visits only the i-chunks listed for the tile (NULL list: all).
-//  * MODE_FAR:  A[o][i] = phi_p(r_oi) = T_p(x(r_oi)), p in the CTA's group of CB
-//    Chebyshev columns, x = alpha log2(r^2) + beta, for rn2 <= r^2 <= r_max^2,
-//    evaluated in registers by the recurrence T_{p+1} = 2x T_p - T_{p-1}.  The
-//    accumulators hold G[p][j] = sum_i phi_p(r_oi) T'[j][i]; the epilogue forms
-//    M[k][j] = sum_p C[k][p] G[p][j].
-enum { MODE_NEAR = 0, MODE_FAR = 1, MODE_NEAR_TMEM = 2 };
-// MODE_NEAR_TMEM: the MODE_NEAR generator writing the A operand to tensor memory
-// (tcgen05.st) instead of shared memory; the MMA reads A from TMEM.  Warp w then
-// owns TMEM lanes (rows) 32 (w mod 4) .. +31 and i-quarter w / 4 of every step.
+// One pipeline, three generators of the A operand (128 output rows x 16 i per step):
+//  * MODE_NEAR:      A[o][i] = f_k(r_oi), k in the CTA's group of CB bases, from the
+//    shared-memory table, written to shared memory (canonical K-major layout);
+//  * MODE_NEAR_TMEM: the same values written to tensor memory (tcgen05.st); the
+//    MMA reads A from TMEM.  Warp w owns TMEM lanes (rows) 32 (w mod 4) .. +31 and
+//    i-quarter w / 4 of every step;
+//  * MODE_CHEB:      A[o][i] = W_p(r_oi), p < CB = 12, the scaled Chebyshev terms of
+//    the far field, in tensor memory; the accumulators hold
+//    G[p][j] = sum_i W_p(r_oi) T'[j][i] and the epilogue forms M[k][j] = sum_p c_kp G[p][j].
+//    The warps form CONC groups that fill the A slots of alternate steps (group g
+//    takes the steps s with s mod CONC = g), each thread a run of 4 CONC
+//    consecutive i of one row, so that a step's A tile is written while the tensor
+//    core consumes the previous one.
+// Table modes take the pairs with rn2 <= r^2 <= r_max^2 (rn2 = 0 when no separate
+// near field is added: the self pair is then replaced in FP32 by the epilogue);
+// MODE_CHEB takes the same far pairs, whose near complement near.cu adds in FP32.
+enum { MODE_NEAR = 0, MODE_CHEB = 1, MODE_NEAR_TMEM = 2 };
 
 struct TcArgs {
   int N;             // vertices (rows o and columns i)
   int n_steps;       // 16-i records
   int n_r;           // radius samples
-  float inv_dr, r2max, rn2;
-  float r2lim;       // largest r^2 of a table pair: min(r2max, the float below rn2)
+  float inv_dr, r2max;
+  const float *rn2;  // [n_mesh] near radius^2 of each mesh (NULL: 0, every pair in this pass)
+  int self_fix;      // table modes: the epilogue replaces the self pair's BF16 product by FP32
   int K, J, KP;
   int n_otiles, n_groups, n_split;
   const float *pos;  // [3][N] (rows o)
@@ -356,8 +391,6 @@ struct TcArgs {
   const float *T;    // [J][N]   (self pair, FP32 epilogue)
   const uint32_t *tab16;   // [n_r + 1][KP] bf16x2
   const float2 *tab32;     // [n_r + 1][KP]
-  const int *near_off;     // [n_otiles + 1] or NULL
-  const int *near_idx;     // chunk indices of tile t: near_idx[near_off[t] .. near_off[t+1])
   const float *cheb;       // [K][PCH]
   int PCH;
   float x_alpha, x_beta;
@@ -386,6 +419,7 @@ struct TcArgs {
 // Everything a CTA needs to know about one unit of work.
 struct Unit {
   int t, sp, sb, se;   // tile, split, stage range [sb, se)
+  int mesh;            // mesh of the unit (0: one mesh)
   int Nb;              // vertices of the unit's mesh
   long long voff;      // first vertex of the mesh
   int soff;            // first record of the mesh
@@ -394,9 +428,10 @@ struct Unit {
 template <int MODE, int CB, int JP, bool SPLIT, int NS>
 struct TcCfg {
   static constexpr int LOOKAHEAD = 8;                      // records in flight ahead of the generators
+  static constexpr int CONC = (MODE == MODE_CHEB) ? NS : 1;   // generator groups (steps in flight)
   static constexpr int NR = NS + LOOKAHEAD;                // record slots
   static constexpr int REC = rec_bytes(JP, SPLIT);
-  static constexpr bool ATMEM = (MODE == MODE_NEAR_TMEM);
+  static constexpr bool ATMEM = (MODE == MODE_NEAR_TMEM || MODE == MODE_CHEB);
   static constexpr bool TABLE = (MODE == MODE_NEAR || MODE == MODE_NEAR_TMEM);
   static constexpr int A_TILE = 128 * 16 * 2;              // one (column, 16-i step) BF16 tile
   static constexpr int A_STAGE = ATMEM ? 0 : CB * (SPLIT ? 2 : 1) * A_TILE;
@@ -404,7 +439,7 @@ struct TcCfg {
   static constexpr int TAB_ELEM = TABLE ? (SPLIT ? 8 : 4) : 0;
   static constexpr int U = TABLE ? CB * TAB_ELEM / 16 : 1;   // 16-byte units per table row
   static constexpr int NGEN = 512;                         // generator threads (warps 0-15)
-  static constexpr int NTHREADS = NGEN + 32;               // + one control warp (TMA + MMA issue)
+  static constexpr int NTHREADS = NGEN + 64;               // + the MMA-issue warp and the TMA warp
   static constexpr int ACC_COLS = CB * JP;                 // FP32 accumulators
   static constexpr int A_COLS = ATMEM ? CB * 8 : 0;        // A tile of one stage in TMEM (16 BF16 per row = 8 columns)
   static constexpr int USED_COLS = ACC_COLS + NS * A_COLS;
@@ -413,7 +448,7 @@ struct TcCfg {
   static_assert(USED_COLS <= 512, "tensor memory holds 512 columns");
   static size_t smem_bytes(int n_r, int K) {
     return 1024 + (size_t)NS * A_STAGE + (size_t)NR * REC_STAGE + (size_t)(n_r + 1) * CB * TAB_ELEM +
-           (MODE == MODE_FAR ? (size_t)K * CB * sizeof(float) : 0) + 256;
+           (MODE == MODE_CHEB ? (size_t)K * CB * sizeof(float) : 0) + 512;
   }
 };
 
@@ -447,21 +482,41 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return y;
 }
 
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// One run of W consecutive 32-bit TMEM columns of this thread's lane (W = 2 or 4).
+template <int W>
+__device__ __forceinline__ void tmem_st_run(uint32_t taddr, const uint32_t (&v)[W]) {
+  if constexpr (W == 2) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(v[0]), "r"(v[1]) : "memory");
+  } else {
+    static_assert(W == 4, "runs of 2 or 4 columns");
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
+                 "r"(v[2]), "r"(v[3])
+                 : "memory");
+  }
+}
+
 __device__ __forceinline__ float fast_lg2(float x) {
   float y;
-  asm("lg2.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 
 // Decodes unit u.  One mesh: u = tile * S + split, stages over all records (or
 // over the tile's near-chunk list); batched: the unit table.
-__device__ __forceinline__ Unit decode_unit(int u, int S, int SPT, int N, const int *near_off, const int4 *units,
-                                            const int *mesh_N, const long long *mesh_voff, const int *mesh_soff) {
+__device__ __forceinline__ Unit decode_unit(int u, int S, int SPT, int N, const int4 *units, const int *mesh_N,
+                                            const long long *mesh_voff, const int *mesh_soff) {
   Unit r;
   if (units) {
     const int4 d = units[u];
     r.t = d.y;
     r.sp = d.z;
+    r.mesh = d.x;
     r.Nb = mesh_N[d.x];
     r.voff = mesh_voff[d.x];
     r.soff = mesh_soff[d.x];
@@ -472,22 +527,13 @@ __device__ __forceinline__ Unit decode_unit(int u, int S, int SPT, int N, const 
   }
   r.t = u / S;
   r.sp = u % S;
+  r.mesh = 0;
   r.Nb = N;
   r.voff = 0;
   r.soff = 0;
-  if (near_off) {
-    const int n0 = near_off[r.t], n = near_off[r.t + 1] - n0;
-    r.sb = n0 + r.sp * n / S;
-    r.se = n0 + (r.sp + 1) * n / S;
-  } else {
-    r.sb = r.sp * SPT / S;
-    r.se = (r.sp + 1) * SPT / S;
-  }
+  r.sb = r.sp * SPT / S;
+  r.se = (r.sp + 1) * SPT / S;
   return r;
-}
-// record holding stage q of a unit
-__device__ __forceinline__ int chunk_at(const int *near_idx, int q, int soff) {
-  return soff + (near_idx ? near_idx[q] : q);
 }
 
 template <int MODE, int CB, int JP, bool SPLIT, int NS>
@@ -500,16 +546,17 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
   uint8_t *sA = smem;                                   // NS * A_STAGE
   uint8_t *sRec = sA + (size_t)NS * C::A_STAGE;         // NR * REC_STAGE
   uint8_t *sTab = sRec + (size_t)C::NR * C::REC_STAGE;  // (n_r+1) * CB * TAB_ELEM   (MODE_NEAR)
-  float *sC = reinterpret_cast<float *>(sTab + (size_t)(args.n_r + 1) * CB * C::TAB_ELEM);   // [K][CB] (MODE_FAR)
+  float *sC = reinterpret_cast<float *>(sTab + (size_t)(args.n_r + 1) * CB * C::TAB_ELEM);   // [K][CB] (MODE_CHEB)
   uint64_t *bar = reinterpret_cast<uint64_t *>(
-      reinterpret_cast<uint8_t *>(sC) + (MODE == MODE_FAR ? (((size_t)args.K * CB * 4 + 15) / 16) * 16 : 0));
+      reinterpret_cast<uint8_t *>(sC) + (MODE == MODE_CHEB ? (((size_t)args.K * CB * 4 + 15) / 16) * 16 : 0));
   uint64_t *bar_tma = bar;                        // [NR] records landed
-  uint64_t *bar_full = bar + C::NR;               // [NS] A stage written by all generators
+  uint64_t *bar_full = bar + C::NR;               // [NS] A stage written by its generator group
   uint64_t *bar_mma = bar + C::NR + NS;           // [NS] MMAs of a stage completed
   uint64_t *bar_tfree = bar + C::NR + 2 * NS;     // [1]  epilogue finished reading TMEM
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + C::NR + 2 * NS + 1);
+  uint64_t *bar_seg = bar + C::NR + 2 * NS + 1;   // [1]  MMAs of an accumulation segment completed (MODE_CHEB)
+  uint64_t *bar_rfree = bar + C::NR + 2 * NS + 2; // [NR] MMAs that read a record slot completed
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bar + 2 * C::NR + 2 * NS + 2);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_holder + 1);
-  volatile long *tma_done = reinterpret_cast<volatile long *>(tmem_holder + 2);   // stages whose records generators saw
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -517,7 +564,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
   // group b % G and units b / G, b / G + grid / G, ... of that group.
   const int G = args.n_groups;
   const int group = blockIdx.x % G;
-  const int c0 = group * CB;        // first basis (MODE_NEAR) or Chebyshev column (MODE_FAR)
+  const int c0 = group * CB;        // first basis (table modes) or Chebyshev column (MODE_CHEB)
   const int S = args.n_split;
   const int SPT = args.n_steps;     // stages of a whole tile (one 16-i record per stage)
   const int SKP = args.streamk_P;
@@ -538,8 +585,6 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
     unit_step = gridDim.x / G;
     n_units = args.units ? args.n_units_total : args.n_otiles * S;
   }
-  const int *const near_off = args.near_off;
-  const int *const near_idx = args.near_idx;
   const int4 *const units = args.units;
   const int *const mesh_N = args.mesh_N;
   const long long *const mesh_voff = args.mesh_voff;
@@ -553,30 +598,27 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
     r.sb = (int)((sk0 > base ? sk0 : base) - base);
     r.se = (int)((sk1 < base + SPT ? sk1 : base + SPT) - base);
     r.sp = r.sb > 0 ? 1 : 0;
+    r.mesh = 0;
     r.Nb = args.N;
     r.voff = 0;
     r.soff = 0;
     return r;
   };
 #define TSR_UNIT(u) \
-  (SKP > 0 ? streamk_unit(u) : decode_unit((u), S, SPT, args.N, near_off, units, mesh_N, mesh_voff, mesh_soff))
-  long total_stages = 0;
-  for (int u = unit_first; u < n_units; u += unit_step) {
-    const Unit un = TSR_UNIT(u);
-    total_stages += un.se - un.sb;
-  }
+  (SKP > 0 ? streamk_unit(u) : decode_unit((u), S, SPT, args.N, units, mesh_N, mesh_voff, mesh_soff))
   const int seg_stages = args.seg_stages;
   const size_t KJN = (size_t)args.K * args.J * (size_t)stride;
 
   if (tid == 0) {
     for (int q = 0; q < C::NR; ++q) mbar_init(&bar_tma[q], 1);
     for (int q = 0; q < NS; ++q) {
-      mbar_init(&bar_full[q], C::NGEN);
+      mbar_init(&bar_full[q], C::NGEN / C::CONC);
       mbar_init(&bar_mma[q], 1);
     }
     mbar_init(bar_tfree, C::NGEN);
+    mbar_init(bar_seg, 1);
+    for (int q = 0; q < C::NR; ++q) mbar_init(&bar_rfree[q], 1);
     *abort_flag = 0;
-    *tma_done = 0;
     fence_mbar_init();
     fence_proxy_async_smem();
   }
@@ -628,80 +670,64 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
   const uint32_t tmem_base = *tmem_holder;
   const int rows_per_stage = C::REC_STAGE / 128;
 
-  if (warp == C::NGEN / 32) {
-    // ------------------------------------------------------------ control warp
+  if (warp == C::NGEN / 32 + 1) {
+    // ------------------------------------------------------------ TMA warp
+    // Streams the records of this CTA's stages in order into the NR record slots; a slot
+    // is refilled once the MMAs that read its previous record have completed (bar_rfree).
+    long issued = 0;
+    int slot = 0;
+    uint32_t ph = 0u;   // use parity of the slot
+    bool run = true;
+    for (int u = unit_first; u < n_units && run; u += unit_step) {
+      const Unit un = TSR_UNIT(u);
+      for (int q = un.sb; q < un.se; ++q) {
+        if (issued >= C::NR && !__all_sync(0xffffffffu, wait_or_abort(&bar_rfree[slot], ph ^ 1u, abort_flag))) {
+          run = false;
+          break;
+        }
+        if (lane == 0) {
+          mbar_arrive_expect_tx(&bar_tma[slot], C::REC_STAGE);
+          tma_load_2d(sRec + (size_t)slot * C::REC_STAGE, &tmap, &bar_tma[slot], 0, (un.soff + q) * rows_per_stage);
+        }
+        __syncwarp();
+        ++issued;
+        if (++slot == C::NR) {
+          slot = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && *abort_flag) {   // let the copies still in flight land before the CTA exits
+      for (long q = issued > C::NR ? issued - C::NR : 0; q < issued; ++q) {
+        for (uint32_t it = 0; it < TSR_WAIT_LIMIT; ++it)
+          if (mbar_try_wait(&bar_tma[q % C::NR], (uint32_t)((q / C::NR) & 1))) break;
+      }
+    }
+    __syncwarp();
+  } else if (warp == C::NGEN / 32) {
+    // ------------------------------------------------------------ MMA warp
     // All 32 lanes run the loop on warp-uniform state, so the MMA operands stay in
-    // uniform registers; one elected lane issues each TMA, MMA and commit.  (An
-    // issue loop run by one lane alone costs about twice the tensor core's own
-    // ~47 cycles per M = 128 MMA.)
+    // uniform registers; one elected lane issues each group of MMAs and each commit.
     const uint32_t idesc = umma_idesc_bf16(JP);
     const uint64_t desc_a0 = umma_desc(smem_u32(sA), 128, 256);             // A: K-major, 8x16B core matrices
     const uint64_t desc_b0 = umma_desc(smem_u32(sRec), JP * 16, 128);       // B: T' tile of a record
-    long issued = 0;
-    // TMA cursor: unit tu, stage tq in [tb, te) (runs LOOKAHEAD stages ahead of the MMAs)
-    int tu = unit_first, tq = 0, te = 0, tsoff = 0;
-    auto next_unit = [&]() {
-      while (tu < n_units) {
-        const Unit un = TSR_UNIT(tu);
-        tq = un.sb;
-        te = un.se;
-        tsoff = un.soff;
-        if (tq < te) return;
-        tu += unit_step;
-      }
-    };
-    next_unit();
-    int tslot = 0;   // record slot of the next TMA
-    auto issue_tma = [&]() {
-      if (lane == 0) {
-        mbar_arrive_expect_tx(&bar_tma[tslot], C::REC_STAGE);
-        tma_load_2d(sRec + (size_t)tslot * C::REC_STAGE, &tmap, &bar_tma[tslot], 0,
-                    chunk_at(near_idx, tq, tsoff) * rows_per_stage);
-      }
-      __syncwarp();
-      if (++tslot == C::NR) tslot = 0;
-      if (++tq == te) {
-        tu += unit_step;
-        next_unit();
-      }
-    };
-    // every lane waits (and acquires); the outcome is made warp-uniform
     auto wait_warp = [&](uint64_t *b, uint32_t parity) {
       return __all_sync(0xffffffffu, wait_or_abort(b, parity, abort_flag));
     };
-    for (; issued < C::LOOKAHEAD && issued < total_stages; ++issued) issue_tma();
-    // ring state: A slot sa (phase pa), record slot sr; ps/pp: A slot of stage issued - NR
-    int sa = 0, sr = 0, ps = 0;
-    uint32_t pa = 0u, pp = 0u;
-    long g = 0;
+    int sa = 0, sr = 0;
+    uint32_t pa = 0u;
     int seg_no = 0;   // accumulation segments issued so far
     bool run = true;
     for (int u = unit_first; u < n_units && run; u += unit_step) {
       const Unit un = TSR_UNIT(u);
       const int sb = un.sb, se = un.se;
       int seg_pos = 0;
-      for (int sidx = sb; sidx < se; ++sidx, ++g) {
-        if (__any_sync(0xffffffffu, *abort_flag != 0)) {
-          run = false;
-          break;
-        }
+      for (int sidx = sb; sidx < se; ++sidx) {
         const bool seg_start = seg_pos == 0;
         if (++seg_pos == seg_stages) seg_pos = 0;
-        // TMA of stage g + LOOKAHEAD reuses the slot of stage g - NS: wait for its MMAs
-        if (issued < total_stages && issued <= g + C::LOOKAHEAD) {
-          if (issued >= C::NR) {
-            if (!wait_warp(&bar_mma[ps], pp)) {
-              run = false;
-              break;
-            }
-            if (++ps == NS) {
-              ps = 0;
-              pp ^= 1u;
-            }
-          }
-          issue_tma();
-          ++issued;
-        }
+        const bool seg_end = seg_pos == 0 || sidx + 1 == se;
+        // the A tile of this stage is written (its record landed before that)
         if (!wait_warp(&bar_full[sa], pa)) {
           run = false;
           break;
@@ -718,22 +744,28 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
         const uint64_t dbl = dbh + (uint64_t)((JP * 32) >> 4);
         const uint64_t da = desc_a0 + (uint64_t)((sa * C::A_STAGE) >> 4);
         const uint32_t first = seg_start ? 0u : 1u;
+        if constexpr (C::ATMEM) {
+          const uint32_t a0 = tmem_base + (uint32_t)(C::ACC_COLS + sa * C::A_COLS);
 #pragma unroll
-        for (int cb = 0; cb < CB; ++cb) {
-          const uint32_t d = tmem_base + (uint32_t)(cb * JP);
-          if (C::ATMEM) {
-            umma_bf16_ta_elect(d, tmem_base + (uint32_t)(C::ACC_COLS + sa * C::A_COLS + cb * 8), dbh, idesc, first);
-          } else if (!SPLIT) {
-            umma_bf16_elect(d, da + (uint64_t)((cb * C::A_TILE) >> 4), dbh, idesc, first);
-          } else {
-            const uint64_t dah = da + (uint64_t)(((2 * cb) * C::A_TILE) >> 4);
-            const uint64_t dal = da + (uint64_t)(((2 * cb + 1) * C::A_TILE) >> 4);
-            umma_bf16_elect(d, dah, dbh, idesc, first);
-            umma_bf16_elect(d, dah, dbl, idesc, 1u);
-            umma_bf16_elect(d, dal, dbh, idesc, 1u);
+          for (int cb = 0; cb < CB; cb += 4) umma4_ta<JP>(tmem_base + (uint32_t)(cb * JP), a0 + (uint32_t)(cb * 8), dbh, idesc, first);
+        } else {
+#pragma unroll
+          for (int cb = 0; cb < CB; ++cb) {
+            const uint32_t d = tmem_base + (uint32_t)(cb * JP);
+            if (!SPLIT) {
+              umma_bf16_elect(d, da + (uint64_t)((cb * C::A_TILE) >> 4), dbh, idesc, first);
+            } else {
+              const uint64_t dah = da + (uint64_t)(((2 * cb) * C::A_TILE) >> 4);
+              const uint64_t dal = da + (uint64_t)(((2 * cb + 1) * C::A_TILE) >> 4);
+              umma_bf16_elect(d, dah, dbh, idesc, first);
+              umma_bf16_elect(d, dah, dbl, idesc, 1u);
+              umma_bf16_elect(d, dal, dbh, idesc, 1u);
+            }
           }
         }
-        umma_commit_elect(&bar_mma[sa]);
+        umma_commit_elect(&bar_mma[sa]);     // the A slot may be rewritten
+        umma_commit_elect(&bar_rfree[sr]);   // the record slot may be refilled
+        if (MODE == MODE_CHEB && seg_end) umma_commit_elect(bar_seg);   // the segment's accumulators are final
         if (++sa == NS) {
           sa = 0;
           pa ^= 1u;
@@ -742,15 +774,209 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
       }
     }
     __syncwarp();
-    if (lane == 0 && *abort_flag) {   // let copies already issued land before the CTA exits
-      for (long q = *tma_done; q < issued; ++q) {
-        for (uint32_t it = 0; it < TSR_WAIT_LIMIT; ++it)
-          if (mbar_try_wait(&bar_tma[q % C::NR], (uint32_t)((q / C::NR) & 1))) break;
+  } else if constexpr (MODE == MODE_CHEB) {
+    // ------------------------------------------------------------ generator warps, far-field series
+    // Warp w: TMEM lane quarter w mod 4 (rows 32 (w mod 4) + lane), group w / GW (the
+    // steps s with s mod CONC = group), run (w mod GW) / 4 of IPT consecutive i of the step.
+    constexpr int CONC = C::CONC, GW = 16 / CONC, IPT = 4 * CONC, NWD = IPT / 2;
+    const int quarter = warp & 3, grp = warp / GW, ih = (warp % GW) >> 2;
+    const int orow = quarter * 32 + lane;
+    const uint32_t a_tmem_row =
+        tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(C::ACC_COLS + ih * NWD);
+    const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
+    const float r2max = args.r2max, xa_alpha = args.x_alpha, xa_beta = args.x_beta;
+    // Ring state of this group's steps (steps grp, grp + CONC, ...): A slot sa (phase pa),
+    // record slot sr (phase pr); `own` counts down to this group's next step.
+    int sa = grp % NS, sr = grp % C::NR, own = grp;
+    uint32_t pa = 0u, pr = 0u;
+    bool first_use = true;   // the A slot has not been used yet
+    int seg_done = 0;        // accumulation segments finished by this CTA
+    for (int u = unit_first; u < n_units; u += unit_step) {
+      if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
+      const Unit un = TSR_UNIT(u);
+      const int t = un.t, sp = un.sp, sb = un.sb, se = un.se, Nb = un.Nb;
+      if (sb == se) continue;
+      const int d_idx = sp;
+      const bool to_M = SKP > 0 ? sp == 0 : d_idx == 0;
+      float *dbase;
+      long long dld;
+      if (SKP > 0 && sp != 0) {
+        dbase = args.slots + (size_t)(group * SKP + cta_in_group) * args.K * args.J * 128;
+        dld = 128;
+      } else {
+        dbase = ((d_idx == 0) ? args.M : args.P + (size_t)(d_idx - 1) * KJN) + un.voff + (size_t)t * 128;
+        dld = stride;
       }
+      const bool dst_accumulates = to_M && args.accumulate;
+      const int o = t * 128 + orow;
+      const bool o_ok = o < Nb;
+      const float *pos_m = args.pos + un.voff;
+      const float xo = o_ok ? pos_m[o] : 0.f;
+      const float yo = o_ok ? pos_m[stride + o] : 0.f;
+      const float zo = o_ok ? pos_m[2 * stride + o] : 0.f;
+      const float rlo2 = args.rn2 ? args.rn2[un.mesh] : 0.f;   // below: the exact near field
+      bool ok = true;
+      int seg_pos = 0, seg_count = 0;
+      for (int sidx = sb; sidx < se; ++sidx) {
+        if (own == 0) {
+          own = CONC;
+          if (__any_sync(0xffffffffu, !wait_or_abort(&bar_tma[sr], pr, abort_flag))) {
+            ok = false;
+            break;
+          }
+          const float *rp = reinterpret_cast<const float *>(sRec + (size_t)sr * C::REC_STAGE + JP * 32);
+          // W_0 = s, W_1 = x s, W_p = (-1)^(p-1) 2x W_{p-1} + W_{p-2}, s = 1/r^2 (0 outside the far
+          // field), two consecutive i per packed BF16 word: the word layout of the A operand in TMEM.
+          uint32_t w0[NWD], w1[NWD], mp[NWD], mn[NWD];
+#pragma unroll
+          for (int h = 0; h < NWD; h += 2) {
+            const float4 xs = *reinterpret_cast<const float4 *>(rp + ih * IPT + 2 * h);
+            const float4 ys = *reinterpret_cast<const float4 *>(rp + 16 + ih * IPT + 2 * h);
+            const float4 zs = *reinterpret_cast<const float4 *>(rp + 32 + ih * IPT + 2 * h);
+            const float xa[4] = {xs.x, xs.y, xs.z, xs.w}, ya[4] = {ys.x, ys.y, ys.z, ys.w},
+                        za[4] = {zs.x, zs.y, zs.z, zs.w};
+            float sv[4], xsv[4], x2v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float r2 = pair_r2(xo, yo, zo, xa[q], ya[q], za[q]);
+              const bool far = r2 >= rlo2 && r2 <= r2max;
+              const float rf = far ? r2 : 1.f;   // the special-function calls run unconditionally
+              const float x = far ? fmaf(xa_alpha, fast_lg2(rf), xa_beta) : 0.f;
+              sv[q] = far ? rcp_approx(rf) : 0.f;
+              xsv[q] = x * sv[q];
+              x2v[q] = x + x;
+            }
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              mp[h + e] = pack_bf16x2(x2v[2 * e], x2v[2 * e + 1]);
+              mn[h + e] = mp[h + e] ^ 0x80008000u;
+              w0[h + e] = pack_bf16x2(sv[2 * e], sv[2 * e + 1]);
+              w1[h + e] = pack_bf16x2(xsv[2 * e], xsv[2 * e + 1]);
+            }
+          }
+          const uint32_t a_slot = a_tmem_row + (uint32_t)(sa * C::A_COLS);
+          if constexpr (NS >= 2) {
+            // the slot's previous MMAs (CONC steps back) completed long ago: wait, then stream
+            // the terms to TMEM as the recurrence produces them (few live registers)
+            if (!first_use && __any_sync(0xffffffffu, !wait_or_abort(&bar_mma[sa], pa ^ 1u, abort_flag))) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            tmem_st_run<NWD>(a_slot, w0);
+            tmem_st_run<NWD>(a_slot + 8u, w1);
+#pragma unroll
+            for (int p = 2; p < CB; ++p) {
+              uint32_t w2[NWD];
+#pragma unroll
+              for (int h = 0; h < NWD; ++h) w2[h] = bf16x2_fma((p & 1) ? mp[h] : mn[h], w1[h], w0[h]);
+              tmem_st_run<NWD>(a_slot + (uint32_t)(p * 8), w2);
+#pragma unroll
+              for (int h = 0; h < NWD; ++h) {
+                w0[h] = w1[h];
+                w1[h] = w2[h];
+              }
+            }
+          } else {
+            // one A slot: the previous step's MMAs may still be running, so every term is
+            // formed in registers before the wait
+            uint32_t feat[CB][NWD];
+#pragma unroll
+            for (int h = 0; h < NWD; ++h) {
+              feat[0][h] = w0[h];
+              feat[1][h] = w1[h];
+            }
+#pragma unroll
+            for (int p = 2; p < CB; ++p)
+#pragma unroll
+              for (int h = 0; h < NWD; ++h) feat[p][h] = bf16x2_fma((p & 1) ? mp[h] : mn[h], feat[p - 1][h], feat[p - 2][h]);
+            if (!first_use && __any_sync(0xffffffffu, !wait_or_abort(&bar_mma[sa], pa ^ 1u, abort_flag))) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int p = 0; p < CB; ++p) tmem_st_run<NWD>(a_slot + (uint32_t)(p * 8), feat[p]);
+          }
+          tmem_st_wait();
+          tc_fence_before();
+          mbar_arrive(&bar_full[sa]);
+          // advance this group's ring by CONC steps
+          sa += CONC;
+          if (sa >= NS) {
+            sa -= NS;
+            pa ^= 1u;
+            first_use = false;
+          }
+          sr += CONC;
+          if (sr >= C::NR) {
+            sr -= C::NR;
+            pr ^= 1u;
+          }
+        }
+        --own;
+        if (++seg_pos != seg_stages && sidx + 1 != se) continue;
+        // End of an accumulation segment (every warp): M[k][j] (+)= sum_p c_kp G[p][j] for
+        // 2 k x 8 j per item, G read from TMEM two terms at a time.
+        const bool first_seg = seg_count == 0;
+        seg_pos = 0;
+        ++seg_count;
+        const bool e_ok = wait_or_abort(bar_seg, (uint32_t)(seg_done & 1), abort_flag);
+        ++seg_done;
+        if (__any_sync(0xffffffffu, !e_ok)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int wq = warp >> 2;   // 4 warps share a lane quarter
+        const int oe = t * 128 + quarter * 32 + lane;
+        const bool oe_ok = oe < Nb;
+        const int n_kc = (args.K + 1) / 2;
+        for (int item = wq; item < n_kc * (JP / 8); item += C::NGEN / 128) {
+          const int kc = item / (JP / 8), jc = (item % (JP / 8)) * 8;
+          const int ka = kc * 2, kb = kc * 2 + 1;
+          float acc0[8], acc1[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) acc0[q] = acc1[q] = 0.f;
+#pragma unroll
+          for (int cb0 = 0; cb0 < CB; cb0 += 2) {
+            uint32_t r[2][8];
+#pragma unroll
+            for (int v = 0; v < 2; ++v) tmem_ld8(lane_base + (uint32_t)((cb0 + v) * JP + jc), r[v]);
+            tmem_ld_wait();
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+              const float ca = sC[ka * CB + cb0 + v];
+              const float cbv = (kb < args.K) ? sC[kb * CB + cb0 + v] : 0.f;
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                acc0[q] = fmaf(ca, __uint_as_float(r[v][q]), acc0[q]);
+                acc1[q] = fmaf(cbv, __uint_as_float(r[v][q]), acc1[q]);
+              }
+            }
+          }
+          if (oe_ok) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int j = jc + q;
+              if (j < args.J) {
+                float *da = dbase + ((size_t)ka * args.J + j) * dld + (oe - t * 128);
+                *da = (first_seg && !dst_accumulates) ? acc0[q] : *da + acc0[q];
+                if (kb < args.K) {
+                  float *db = dbase + ((size_t)kb * args.J + j) * dld + (oe - t * 128);
+                  *db = (first_seg && !dst_accumulates) ? acc1[q] : *db + acc1[q];
+                }
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(bar_tfree);
+      }
+      if (!ok) break;
     }
-    __syncwarp();
   } else {
-    // ------------------------------------------------------------ generator warps
+    // ------------------------------------------------------------ generator warps, table
     // Thread (orow, h4): output row orow of the tile, i = 4*h4 .. 4*h4+3 of every 16-i step.
     // A warp covers 16 rows x two neighbouring i-quarters, so its 8-byte stores fill
     // two whole 128-byte core matrices (2 shared-memory wavefronts per store).
@@ -760,8 +986,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
     const uint32_t a_row_off =
         (uint32_t)((orow >> 3) * 256 + (h4 >> 1) * 128 + (orow & 7) * 16 + (h4 & 1) * 8);
     const uint32_t sA_u32 = smem_u32(sA);
-    const float r2max = args.r2max, rn2 = args.rn2, r2lim = args.r2lim, inv_dr2 = args.inv_dr * args.inv_dr;
-    const float xa_alpha = args.x_alpha, xa_beta = args.x_beta;
+    const float r2max = args.r2max, inv_dr2 = args.inv_dr * args.inv_dr;
     const int n_r = args.n_r;
     long g = 0;
     // ring state (advanced once per stage): A slot sa with phase bit pa = (g / NS) & 1,
@@ -773,7 +998,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
       const Unit un = TSR_UNIT(u);
       const int t = un.t, sp = un.sp, sb = un.sb, se = un.se, Nb = un.Nb;
       if (sb == se) continue;
-      const int d_idx = (MODE == MODE_FAR ? group * S : 0) + sp;   // destination (equal splits)
+      const int d_idx = sp;   // destination (equal splits)
       // destination base shifted to the unit's mesh (rows voff .. voff + Nb - 1)
       // destination of this unit: element (k, j, row r of the tile) at dbase + (k J + j) dld + r
       const bool to_M = SKP > 0 ? sp == 0 : d_idx == 0;
@@ -793,6 +1018,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
       const float xo = o_ok ? pos_m[o] : 0.f;
       const float yo = o_ok ? pos_m[stride + o] : 0.f;
       const float zo = o_ok ? pos_m[2 * stride + o] : 0.f;
+      const float rlo2 = args.rn2 ? args.rn2[un.mesh] : 0.f;   // pairs below it: the separate near field
       bool ok = true;
       int seg_pos = 0, seg_count = 0;   // position in / index of the accumulation segment
       for (int sidx = sb; sidx < se; ++sidx) {
@@ -803,7 +1029,6 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
           ok = false;
           break;
         }
-        if (tid == 0) *tma_done = g + 1;   // records of stages <= g have landed
         if (C::ATMEM) tc_fence_after();    // the MMAs that read this A slot have completed
         const uint8_t *rec_stage = sRec + (size_t)sr * C::REC_STAGE;
         const float *rp = reinterpret_cast<const float *>(rec_stage + JP * 32 * (SPLIT ? 2 : 1));
@@ -828,7 +1053,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
             const float x = sqrt_approx(r2 * inv_dr2);   // r / dr
             const int m = __float2int_rd(x);
             tq[q] = x - __int2float_rn(m);
-            row[q] = (r2 <= r2lim) ? m : n_r;            // r2lim: r^2 <= r_max^2 and r^2 < r_near^2
+            row[q] = (r2 >= rlo2 && r2 <= r2max) ? m : n_r;   // far pairs of this pass; the rest read the zero row
           }
           if (!SPLIT) {
             // unit cb4 of a table row: {v_4cb4..+1, v_+2..+3, s_4cb4..+1, s_+2..+3} (bf16 pairs)
@@ -876,45 +1101,6 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
               store_split4(a_stage + (uint32_t)((4 * cb2) * C::A_TILE) + a_row_off, C::A_TILE, F0[0], F0[1], F0[2], F0[3]);
               store_split4(a_stage + (uint32_t)((4 * cb2 + 2) * C::A_TILE) + a_row_off, C::A_TILE, F1[0], F1[1], F1[2],
                            F1[3]);
-            }
-          }
-        } else {
-          // Chebyshev columns c0 .. c0+CB-1 of the far pairs (zero for near or cut-off pairs)
-          float tp[4], tc[4], x2[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const bool far = r2v[q] <= r2max && r2v[q] >= rn2;
-            const float x = far ? fmaf(xa_alpha, fast_lg2(r2v[q]), xa_beta) : 0.f;
-            tp[q] = far ? 1.f : 0.f;   // T_0
-            tc[q] = x;                 // T_1
-            x2[q] = x + x;
-          }
-#pragma unroll
-          for (int p = 0; p < TSR_CHEB_P - CB; ++p) {   // advance to T_{c0}, T_{c0+1}
-            if (p >= c0) break;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float nx = fmaf(x2[q], tc[q], -tp[q]);
-              tp[q] = tc[q];
-              tc[q] = nx;
-            }
-          }
-#pragma unroll
-          for (int cb = 0; cb < CB; ++cb) {   // emit T_{c0+cb}
-            if (!SPLIT) {
-              st_shared_v2(a_stage + (uint32_t)(cb * C::A_TILE) + a_row_off, pack_bf16x2(tp[0], tp[1]),
-                           pack_bf16x2(tp[2], tp[3]));
-            } else {
-              store_split4(a_stage + (uint32_t)((2 * cb) * C::A_TILE) + a_row_off, C::A_TILE, tp[0], tp[1], tp[2],
-                           tp[3]);
-            }
-            if (cb + 1 < CB) {
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const float nx = fmaf(x2[q], tc[q], -tp[q]);
-                tp[q] = tc[q];
-                tc[q] = nx;
-              }
             }
           }
         }
@@ -974,7 +1160,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
                   if (j < args.J) {
                     float *dst = dbase + ((size_t)k * args.J + j) * dld + (oe - t * 128);
                     float v = __uint_as_float(r[q]);
-                    if (first_seg && to_M) {
+                    if (first_seg && to_M && args.self_fix) {
                       const float tpv = a_o * args.T[(size_t)j * stride + un.voff + oe];
                       const float th = __bfloat162float(__float2bfloat16_rn(tpv));
                       float tc_self;
@@ -987,43 +1173,6 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
                       v += f0 * tpv - tc_self;
                     }
                     *dst = (first_seg && !dst_accumulates) ? v : *dst + v;
-                  }
-                }
-              }
-            }
-          }
-        } else {
-          // M[k][j] (+)= sum_{cb} C[k][c0 + cb] G[cb][j], in chunks of 2 k x 16 j
-          const int n_kc = (args.K + 1) / 2;
-          for (int item = wq; item < n_kc * (JP / 16); item += C::NGEN / 128) {
-            const int kc = item / (JP / 16), jc = (item % (JP / 16)) * 16;
-            const int ka = kc * 2, kb = kc * 2 + 1;
-            float acc0[16], acc1[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) acc0[q] = acc1[q] = 0.f;
-#pragma unroll 1
-            for (int cb = 0; cb < CB; ++cb) {
-              uint32_t r[16];
-              tmem_ld16(lane_base + (uint32_t)(cb * JP + jc), r);
-              tmem_ld_wait();
-              const float ca = sC[ka * CB + cb];
-              const float cbv = (kb < args.K) ? sC[kb * CB + cb] : 0.f;
-#pragma unroll
-              for (int q = 0; q < 16; ++q) {
-                acc0[q] = fmaf(ca, __uint_as_float(r[q]), acc0[q]);
-                acc1[q] = fmaf(cbv, __uint_as_float(r[q]), acc1[q]);
-              }
-            }
-            if (oe_ok) {
-#pragma unroll
-              for (int q = 0; q < 16; ++q) {
-                const int j = jc + q;
-                if (j < args.J) {
-                  float *da = dbase + ((size_t)ka * args.J + j) * dld + (oe - t * 128);
-                  *da = (first_seg && !dst_accumulates) ? acc0[q] : *da + acc0[q];
-                  if (kb < args.K) {
-                    float *db = dbase + ((size_t)kb * args.J + j) * dld + (oe - t * 128);
-                    *db = (first_seg && !dst_accumulates) ? acc1[q] : *db + acc1[q];
                   }
                 }
               }
@@ -1043,15 +1192,6 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"((uint32_t)C::TMEM_COLS)
                  : "memory");
-  }
-}
-
-// M += sum of the partial sums of destinations 1 .. n_part (fixed order: deterministic)
-__global__ void add_partials_kernel(float *__restrict__ M, const float *__restrict__ P, int n_part, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    float acc = M[i];
-    for (int q = 0; q < n_part; ++q) acc += P[(size_t)q * n + i];
-    M[i] = acc;
   }
 }
 
@@ -1099,111 +1239,6 @@ __global__ void streamk_fixup_kernel(float *__restrict__ M, const float *__restr
   }
 }
 
-// ---------------------------------------------------------------- near-chunk lists
-// Bounding boxes of 128-row tiles and 16-row chunks (valid vertices only).
-__global__ void bbox_kernel(const float *__restrict__ pos, int N, int rows_per_box, int n_box,
-                            float *__restrict__ box /* [n_box][6] */) {
-  const int bidx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (bidx >= n_box) return;
-  float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
-  const int v0 = bidx * rows_per_box, v1 = min(N, v0 + rows_per_box);
-  for (int v = v0; v < v1; ++v) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float x = pos[(size_t)a * N + v];
-      lo[a] = fminf(lo[a], x);
-      hi[a] = fmaxf(hi[a], x);
-    }
-  }
-  if (v1 <= v0) {   // padding chunk: an empty box far away
-#pragma unroll
-    for (int a = 0; a < 3; ++a) lo[a] = hi[a] = 1e30f;
-  }
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    box[bidx * 6 + a] = lo[a];
-    box[bidx * 6 + 3 + a] = hi[a];
-  }
-}
-
-// A chunk is near a tile if the boxes are closer than r_near (with a small
-// margin, so that every pair the kernels classify as near is inside a listed chunk).
-__device__ __forceinline__ bool boxes_near(const float *a, const float *b, float rn2m) {
-  float d2 = 0.f;
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const float gap = fmaxf(0.f, fmaxf(a[q] - b[3 + q], b[q] - a[3 + q]));
-    d2 = fmaf(gap, gap, d2);
-  }
-  return d2 < rn2m;
-}
-
-// One block per tile: count (pass 0) or write in ascending chunk order (pass 1) the near chunks.
-__global__ void __launch_bounds__(256) near_list_kernel(const float *__restrict__ tile_box,
-                                                        const float *__restrict__ chunk_box, int n_chunks, float rn2m,
-                                                        int pass, int *__restrict__ counts,
-                                                        const int *__restrict__ offsets, int *__restrict__ idx) {
-  __shared__ int warp_tot[8];
-  __shared__ float tb[6];
-  const int t = blockIdx.x;
-  if (threadIdx.x < 6) tb[threadIdx.x] = tile_box[t * 6 + threadIdx.x];
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int written = 0;
-  for (int base = 0; base < n_chunks; base += blockDim.x) {
-    const int c = base + threadIdx.x;
-    const bool nr = (c < n_chunks) && boxes_near(tb, chunk_box + (size_t)c * 6, rn2m);
-    const unsigned bal = __ballot_sync(0xffffffffu, nr);
-    if (lane == 0) warp_tot[warp] = __popc(bal);
-    __syncthreads();
-    int before = 0, total = 0;
-    for (int w = 0; w < 8; ++w) {
-      before += (w < warp) ? warp_tot[w] : 0;
-      total += warp_tot[w];
-    }
-    if (pass == 1 && nr) idx[offsets[t] + written + before + __popc(bal & ((1u << lane) - 1u))] = c;
-    written += total;
-    __syncthreads();
-  }
-  if (pass == 0 && threadIdx.x == 0) counts[t] = written;
-}
-
-// Exclusive scan of n counts into offsets[0..n] (single block).
-__global__ void __launch_bounds__(1024) scan_counts_kernel(const int *__restrict__ counts, int n,
-                                                          int *__restrict__ offsets) {
-  __shared__ int warp_sum[32];
-  __shared__ int carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int base = 0; base < n; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const int v = i < n ? counts[i] : 0;
-    int x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sum[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      int ws = lane < (int)(blockDim.x >> 5) ? warp_sum[lane] : 0;
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, ws, o);
-        if (lane >= o) ws += y;
-      }
-      warp_sum[lane] = ws;
-    }
-    __syncthreads();
-    const int incl = x + (warp > 0 ? warp_sum[warp - 1] : 0) + carry;
-    if (i < n) offsets[i] = incl - v;
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry = incl;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) offsets[n] = carry;
-}
-
 // ---------------------------------------------------------------- host side
 static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -1238,13 +1273,14 @@ static tsr_status make_record_map(CUtensorMap *tmap, const uint8_t *rec, int n_s
   return TSR_OK;
 }
 
-// Launch one pass.  n_cols: bases (MODE_NEAR) or Chebyshev columns (MODE_FAR) in total.
+// Launch one pass.  n_cols: bases (table modes) or Chebyshev terms (MODE_CHEB) in total.
 template <int MODE, int CB, int JP, bool SPLIT, int NS>
 static tsr_status launch_tc(const TcArgs &a0, int n_cols, const CUtensorMap &tmap, bool allow_split, cudaStream_t s) {
   using C = TcCfg<MODE, CB, JP, SPLIT, NS>;
   TcArgs a = a0;
-  a.r2lim = std::min(a.r2max, std::nextafter(a.rn2, 0.0f));   // r^2 <= r2lim  <=>  r^2 <= r2max and r^2 < rn2
-  a.seg_stages = 4096 / 16;   // flush the tensor-core accumulator every 4,096 i
+  // The tensor-core FP32 accumulation does not round to nearest, so long sums are cut
+  // into segments that the epilogue adds with round-to-nearest FP32 adds.
+  a.seg_stages = (MODE == MODE_CHEB ? 8192 : 4096) / 16;
   a.n_groups = (n_cols + CB - 1) / CB;
   const size_t smem = C::smem_bytes(a.n_r, a.K);
   if (smem > 232448) {
@@ -1253,77 +1289,49 @@ static tsr_status launch_tc(const TcArgs &a0, int n_cols, const CUtensorMap &tma
   }
   auto kern = transfer_tc_kernel<MODE, CB, JP, SPLIT, NS>;
   TSR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  // Every CTA keeps one group: the grid is a multiple of the group count.  Each
-  // tile's i-range may be cut into S units so that the last wave is nearly full.
+  // Every CTA keeps one group: the grid is a multiple of the group count.
   const int G = a.n_groups;
   const int sms = num_sms();
-  int best_S = 1;
-  if (allow_split) {
-    double best_cost = 1e30;
-    for (int S = 1; S <= 4 && S <= a.n_steps; ++S) {
-      const long units = (long)a.n_otiles * S * G;
-      int grid = (int)std::min<long>(units, sms);
-      grid = std::max(G, grid / G * G);
-      const long per_cta = (units / G + grid / G - 1) / (grid / G);      // units on the busiest CTA
-      const double cost = (double)per_cta / S * (1.0 + 0.03 * (S - 1));  // in whole-tile units
-      if (cost < best_cost - 1e-9) {
-        best_cost = cost;
-        best_S = S;
-      }
-    }
-  }
-  a.n_split = best_S;
-  const long units = (a.units ? (long)a.n_units_total : (long)a.n_otiles * best_S) * G;
+  a.n_split = 1;
+  const long units = (a.units ? (long)a.n_units_total : (long)a.n_otiles) * G;
   int grid = (int)std::min<long>(units, sms);
   grid = std::max(G, grid / G * G);
-  // Stream-K for one mesh over all its records (table modes): equal stage ranges per CTA.
-  const bool streamk = allow_split && MODE != MODE_FAR && !a.units && !a.near_off;
+  // Stream-K for one mesh over all its records: equal stage ranges per CTA.
+  const bool streamk = allow_split && !a.units;
   Scratch slots;
   if (streamk) {
     const long long T_st = (long long)a.n_otiles * a.n_steps;
     int P = std::max(1, sms / G);
     P = (int)std::min<long long>(P, std::max<long long>(1, T_st / 64));   // at least 64 stages per CTA
     a.streamk_P = P;
-    a.n_split = 1;
-    best_S = 1;
     grid = G * P;
     tsr_status st = slots.alloc(sizeof(float) * (size_t)G * P * a.K * a.J * 128, s);
     if (st != TSR_OK) return st;
     a.slots = static_cast<float *>(slots.p);
   }
-  const int n_dest = (MODE == MODE_FAR ? G : 1) * best_S;
-  Scratch part;
-  const size_t mn = (size_t)a.K * a.J * (size_t)a.stride;
   a.P = nullptr;
-  if (n_dest > 1) {
-    tsr_status st = part.alloc(sizeof(float) * mn * (n_dest - 1), s);
-    if (st != TSR_OK) return st;
-    a.P = static_cast<float *>(part.p);
-  }
+  KernelTimer timer(s);
   kern<<<grid, C::NTHREADS, smem, s>>>(tmap, a); ::tsr::count_launch();
+  timer.stop();
   TSR_CUDA(cudaGetLastError());
   if (streamk) {
-    streamk_fixup_kernel<<<G * a.streamk_P, 1024, 0, s>>>(a.M, a.slots, a.n_otiles, a.n_steps, a.streamk_P, CB, a.K,
-                                                          a.J, a.N, a.stride);
+    streamk_fixup_kernel<<<G * a.streamk_P, 1024, 0, s>>>(a.M, a.slots, a.n_otiles, a.n_steps, a.streamk_P,
+                                                          MODE == MODE_CHEB ? a.K : CB, a.K, a.J, a.N, a.stride);
     ::tsr::count_launch();
-    TSR_CUDA(cudaGetLastError());
-  }
-  if (n_dest > 1) {
-    add_partials_kernel<<<4 * sms, 256, 0, s>>>(a.M, a.P, n_dest - 1, mn); ::tsr::count_launch();
     TSR_CUDA(cudaGetLastError());
   }
   return TSR_OK;
 }
 
-// Exact-table pass over the near chunks (or over everything without lists).
-// kb: bases per CTA group (4, 8, 12 or 16; 0 = the smallest group holding all K).
+// The table generator.  kb: bases per CTA group (4, 8, 12 or 16; 0 = the smallest
+// group holding all K).
 static bool atmem_enabled() {
   const char *e = std::getenv("TSR_TRANSFER_ATMEM");   // "0": A operand staged in shared memory
   return !(e && e[0] == '0');
 }
 
-static tsr_status dispatch_near(const TcArgs &a, int JP, bool split, const CUtensorMap &tmap, bool allow_split,
-                                cudaStream_t s, int kb = 0, int atmem = -1) {
+static tsr_status dispatch_table(const TcArgs &a, int JP, bool split, const CUtensorMap &tmap, bool allow_split,
+                                 cudaStream_t s, int kb = 0, int atmem = -1) {
   const int K = a.K;
   if (atmem < 0) atmem = atmem_enabled() ? 1 : 0;
   // A in tensor memory when the bases of a group and 2..4 A stages fit in 512 columns
@@ -1361,22 +1369,43 @@ static tsr_status dispatch_near(const TcArgs &a, int JP, bool split, const CUten
   return launch_tc<MODE_NEAR, 8, 32, true, 2>(a, K, tmap, allow_split, s);
 }
 
-// Chebyshev pass over every chunk (all TSR_CHEB_P columns).
-static tsr_status dispatch_far(const TcArgs &a, int JP, bool split, const CUtensorMap &tmap, cudaStream_t s) {
-  if (!split) {
-    if (JP == 16) return launch_tc<MODE_FAR, 16, 16, false, 3>(a, TSR_CHEB_P, tmap, true, s);
-    return launch_tc<MODE_FAR, 16, 32, false, 3>(a, TSR_CHEB_P, tmap, true, s);
+// The far-field series generator (TSR_CHEB_BF16 terms).  conc: generator groups (steps
+// written concurrently); with J_pad = 32 the accumulators take 384 of the 512 TMEM
+// columns, which leaves room for one A slot only.
+static tsr_status dispatch_cheb(const TcArgs &a, int JP, const CUtensorMap &tmap, bool allow_split, cudaStream_t s,
+                                int conc = 0) {
+  if (conc == 0) {
+    const char *e = std::getenv("TSR_CHEB_CONC");   // diagnostic: "1" or "2" steps in flight (J_pad = 16)
+    conc = (e && e[0] == '1') ? 1 : 2;
   }
-  if (JP == 16) return launch_tc<MODE_FAR, 8, 16, true, 3>(a, TSR_CHEB_P, tmap, true, s);
-  return launch_tc<MODE_FAR, 8, 32, true, 2>(a, TSR_CHEB_P, tmap, true, s);
+  if (JP == 16) {
+    if (conc == 1) return launch_tc<MODE_CHEB, TSR_CHEB_BF16, 16, false, 1>(a, TSR_CHEB_BF16, tmap, allow_split, s);
+    return launch_tc<MODE_CHEB, TSR_CHEB_BF16, 16, false, 2>(a, TSR_CHEB_BF16, tmap, allow_split, s);
+  }
+  return launch_tc<MODE_CHEB, TSR_CHEB_BF16, 32, false, 1>(a, TSR_CHEB_BF16, tmap, allow_split, s);
 }
 
-// The near/far split (Chebyshev far field) is opt-in: TSR_TRANSFER_NEARFAR=1.
-// Measured on GB300 it does not beat the exact-table path at K <= 16, and its
-// split-BF16 error is larger, so the exact table is the default.
-static bool nearfar_enabled() {
-  const char *e = std::getenv("TSR_TRANSFER_NEARFAR");
-  return e && e[0] == '1';
+// "table": the BF16 transfer uses the table generator even where the series is accurate
+// (a diagnostic switch for comparing the two generators on the same inputs).
+static bool bf16_table_forced() {
+  const char *e = std::getenv("TSR_BF16_GENERATOR");
+  return e && std::string(e) == "table";
+}
+
+static void fill_common_args(TcArgs &a, const tsr_basis *b, int J) {
+  a.n_r = b->n_r;
+  a.inv_dr = static_cast<float>((b->n_r - 1) / b->r_max);
+  a.r2max = static_cast<float>(b->r_max * b->r_max);
+  a.K = b->K;
+  a.J = J;
+  a.KP = b->KP;
+  a.tab16 = b->tab16;
+  a.tab32 = b->tab32;
+  a.cheb = b->cheb;
+  a.PCH = TSR_CHEB_P;
+  a.x_alpha = b->x_alpha;
+  a.x_beta = b->x_beta;
+  a.status = device_status_ptr();
 }
 
 tsr_status transfer_tc(const tsr_basis *b, int N, const float *pos, const float *area, const float *T, int J,
@@ -1396,60 +1425,30 @@ tsr_status transfer_tc(const tsr_basis *b, int N, const float *pos, const float 
   st = make_record_map(&tmap, rec, n_steps, REC);
   if (st != TSR_OK) return st;
   TcArgs a{};
+  fill_common_args(a, b, J);
   a.N = N;
   a.n_steps = n_steps;
-  a.n_r = b->n_r;
-  a.inv_dr = static_cast<float>((b->n_r - 1) / b->r_max);
-  a.r2max = static_cast<float>(b->r_max * b->r_max);
-  a.K = b->K;
-  a.J = J;
-  a.KP = b->KP;
   a.n_otiles = (N + 127) / 128;
   a.pos = pos;
   a.area = area;
   a.T = T;
-  a.tab16 = b->tab16;
-  a.tab32 = b->tab32;
-  a.cheb = b->cheb;
-  a.PCH = TSR_CHEB_P;
-  a.x_alpha = b->x_alpha;
-  a.x_beta = b->x_beta;
   a.M = M;
-  a.status = device_status_ptr();
   a.stride = N;
-  // The Chebyshev far field pays off (and keeps BF16 accuracy, since the near
-  // field then carries most of M) on meshes with many vertices within r_near.
-  if (!nearfar_enabled() || !b->cheb || N < 16384) {
-    a.rn2 = 3.0e38f;   // every pair through the exact table
-    return dispatch_near(a, JP, split, tmap, true, s);
+  if (split) {
+    // split BF16: every pair through the table, the self pair replaced in FP32
+    a.rn2 = nullptr;
+    a.self_fix = 1;
+    return dispatch_table(a, JP, true, tmap, true, s);
   }
-  // far pass: Chebyshev series for r >= r_near (writes M)
-  a.rn2 = static_cast<float>(b->r_near * b->r_near);
-  st = dispatch_far(a, JP, split, tmap, s);
+  // BF16: the far field on the tensor cores, the near field r < r_e exactly in FP32
+  NearField nf;
+  st = near_setup(nf, b, 1, nullptr, N, pos, N, area, T, J, s);
   if (st != TSR_OK) return st;
-  // near pass: exact table for r < r_near over the chunks whose box is within r_near of the tile (adds to M)
-  const int n_tiles = a.n_otiles;
-  Scratch boxes, lists;
-  st = boxes.alloc(sizeof(float) * 6 * ((size_t)n_tiles + n_steps) + sizeof(int) * (2 * (size_t)n_tiles + 1), s);
+  a.rn2 = nf.rn2;
+  a.self_fix = 0;
+  st = (b->cheb_ok && !bf16_table_forced()) ? dispatch_cheb(a, JP, tmap, true, s) : dispatch_table(a, JP, false, tmap, true, s);
   if (st != TSR_OK) return st;
-  float *tile_box = static_cast<float *>(boxes.p);
-  float *chunk_box = tile_box + 6 * (size_t)n_tiles;
-  int *counts = reinterpret_cast<int *>(chunk_box + 6 * (size_t)n_steps);
-  int *offsets = counts + n_tiles;
-  bbox_kernel<<<(n_tiles + 127) / 128, 128, 0, s>>>(pos, N, 128, n_tiles, tile_box); ::tsr::count_launch();
-  bbox_kernel<<<(n_steps + 127) / 128, 128, 0, s>>>(pos, N, 16, n_steps, chunk_box); ::tsr::count_launch();
-  const float rn2m = a.rn2 * 1.001f + 1e-6f;
-  near_list_kernel<<<n_tiles, 256, 0, s>>>(tile_box, chunk_box, n_steps, rn2m, 0, counts, nullptr, nullptr); ::tsr::count_launch();
-  scan_counts_kernel<<<1, 1024, 0, s>>>(counts, n_tiles, offsets); ::tsr::count_launch();
-  st = lists.alloc(sizeof(int) * (size_t)n_tiles * n_steps, s);
-  if (st != TSR_OK) return st;
-  int *idx = static_cast<int *>(lists.p);
-  near_list_kernel<<<n_tiles, 256, 0, s>>>(tile_box, chunk_box, n_steps, rn2m, 1, counts, offsets, idx); ::tsr::count_launch();
-  TSR_CUDA(cudaGetLastError());
-  a.near_off = offsets;
-  a.near_idx = idx;
-  a.accumulate = 1;
-  return dispatch_near(a, JP, split, tmap, false, s);
+  return near_apply(nf, b, M, N, s);
 }
 
 // Batched transfer over independent meshes of uneven size: one persistent launch
@@ -1459,29 +1458,33 @@ tsr_status transfer_tc(const tsr_basis *b, int N, const float *pos, const float 
 // enqueues kernels and stream-ordered scratch, so it can be captured in a CUDA graph.
 tsr_status batch_plan_create(const tsr_basis *b, int n_mesh, const int64_t *offsets, int J, int prec,
                              tsr_batch_plan **out) {
+  int device = -1;
+  TSR_CUDA(cudaGetDevice(&device));
   tsr_batch_plan *p = new tsr_batch_plan();
-  cudaGetDevice(&p->device);
+  p->device = device;
   p->basis = b;
   p->n_mesh = n_mesh;
   p->J = J;
   p->prec = prec;
+  p->gen = b->cheb_ok ? 0 : 1;
   p->offsets.assign(offsets, offsets + n_mesh + 1);
   p->total = offsets[n_mesh];
   std::vector<int> Nm(n_mesh), soff(n_mesh + 1, 0);
-  std::vector<long long> voff(n_mesh);
+  std::vector<long long> voff(n_mesh + 1);
   for (int m = 0; m < n_mesh; ++m) {
     Nm[m] = (int)(offsets[m + 1] - offsets[m]);
     voff[m] = offsets[m];
     soff[m + 1] = soff[m] + (Nm[m] + 15) / 16;
   }
+  voff[n_mesh] = offsets[n_mesh];
   p->total_steps = soff[n_mesh];
   std::vector<int4> units;
   for (int m = 0; m < n_mesh; ++m)
     for (int t = 0; t < (Nm[m] + 127) / 128; ++t) units.push_back(make_int4(m, t, 0, 1));
   std::stable_sort(units.begin(), units.end(), [&](const int4 &x, const int4 &y) { return Nm[x.x] > Nm[y.x]; });
   p->n_units = (int)units.size();
-  const size_t b_units = sizeof(int4) * units.size(), b_voff = sizeof(long long) * n_mesh, b_N = sizeof(int) * n_mesh,
-               b_soff = sizeof(int) * (n_mesh + 1);
+  const size_t b_units = sizeof(int4) * units.size(), b_voff = sizeof(long long) * (n_mesh + 1),
+               b_N = sizeof(int) * n_mesh, b_soff = sizeof(int) * (n_mesh + 1);
   cudaError_t e = cudaMalloc(&p->tables, b_units + b_voff + b_N + b_soff + 64);
   if (e == cudaSuccess) {
     uint8_t *t = static_cast<uint8_t *>(p->tables);
@@ -1523,49 +1526,59 @@ tsr_status batch_plan_run(const tsr_batch_plan *p, const float *pos, const float
   CUtensorMap tmap;
   st = make_record_map(&tmap, rec, p->total_steps, REC);
   if (st != TSR_OK) return st;
+  // the near field of every mesh (its own r_e), exactly in FP32, after the far field
+  NearField nf;
+  st = near_setup(nf, b, p->n_mesh, p->d_voff, p->total, pos, p->total, area, T, J, s);
+  if (st != TSR_OK) return st;
   TcArgs a{};
+  fill_common_args(a, b, J);
   a.N = 0;
   a.n_steps = 1;
-  a.n_r = b->n_r;
-  a.inv_dr = static_cast<float>((b->n_r - 1) / b->r_max);
-  a.r2max = static_cast<float>(b->r_max * b->r_max);
-  a.rn2 = 3.0e38f;
-  a.K = b->K;
-  a.J = J;
-  a.KP = b->KP;
   a.n_otiles = 0;
   a.pos = pos;
   a.area = area;
   a.T = T;
-  a.tab16 = b->tab16;
-  a.tab32 = b->tab32;
   a.M = M;
-  a.status = device_status_ptr();
+  a.rn2 = nf.rn2;
+  a.self_fix = 0;
   a.units = p->d_units;
   a.n_units_total = p->n_units;
   a.mesh_N = p->d_N;
   a.mesh_voff = p->d_voff;
   a.mesh_soff = p->d_soff;
   a.stride = p->total;
-  return dispatch_near(a, JP, false, tmap, false, s, p->kb);
+  st = (p->gen == 0 && b->cheb_ok) ? dispatch_cheb(a, JP, tmap, false, s, p->conc)
+                                   : dispatch_table(a, JP, false, tmap, false, s, p->kb);
+  if (st != TSR_OK) return st;
+  return near_apply(nf, b, M, p->total, s);
 }
 
-// Times every tile configuration (bases per CTA group) once on the caller's data and
-// keeps the fastest in the plan.  Synchronises the stream; not for use inside a capture.
+// Times every generator configuration once on the caller's data and keeps the fastest
+// in the plan: the far-field series with one or two steps in flight (J_pad = 16), and the
+// table with 4, 8, 12 or 16 bases per CTA group.  Synchronises the stream; not for use
+// inside a capture.
 tsr_status batch_plan_autotune(tsr_batch_plan *p, const float *pos, const float *area, const float *T, float *M,
                                cudaStream_t s, float *best_ms) {
   if (p->prec == TSR_FP32) {
     if (best_ms) *best_ms = 0.f;
     return TSR_OK;
   }
-  const std::vector<int> cands = {4, 8, 12, 16};   // bases per CTA group (groups = K / group, rounded up)
+  struct Cand { int gen, conc, kb; };
+  std::vector<Cand> cands;
+  if (p->basis->cheb_ok) {
+    cands.push_back({0, 2, 0});
+    if (p->J <= 16) cands.push_back({0, 1, 0});
+  }
+  for (int kb : {4, 8, 12, 16}) cands.push_back({1, 0, kb});
   cudaEvent_t e0, e1;
   TSR_CUDA(cudaEventCreate(&e0));
   TSR_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_kb = 0;
-  for (int kb : cands) {
-    p->kb = kb;
+  Cand best_c = cands[0];
+  for (const Cand &c : cands) {
+    p->gen = c.gen;
+    p->conc = c.conc;
+    p->kb = c.kb;
     tsr_status st = batch_plan_run(p, pos, area, T, M, s);   // warm
     if (st == TSR_OK) {
       TSR_CUDA(cudaEventRecord(e0, s));
@@ -1582,12 +1595,14 @@ tsr_status batch_plan_autotune(tsr_batch_plan *p, const float *pos, const float 
     TSR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     if (ms < best) {
       best = ms;
-      best_kb = kb;
+      best_c = c;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  p->kb = best_kb;
+  p->gen = best_c.gen;
+  p->conc = best_c.conc;
+  p->kb = best_c.kb;
   if (best_ms) *best_ms = best;
   return TSR_OK;
 }

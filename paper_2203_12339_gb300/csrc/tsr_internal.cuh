@@ -83,6 +83,15 @@ unsigned *device_status_ptr();                     // device address of the word
 // Count of kernel launches made by the library (all threads, all devices).
 void count_launch();
 
+// Events around one kernel launch on stream s while tsr_kernel_timing is enabled
+// (nothing otherwise): construct before the launch, stop() after it.
+struct KernelTimer {
+  explicit KernelTimer(cudaStream_t stream);
+  void stop();
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+};
+
 // Verifies that the current device is an sm_103 part (the only compiled target).
 tsr_status require_device();
 // TSR_ERR_INVALID_ARG unless `device` (where a handle was made) is the current device.

@@ -1,6 +1,6 @@
-// Self-shadowed SH irradiance transfer (Section 3, E(x_i) of Eq. 6 with the
-// visibility of Section 3.3's transfer, E11-E14): on displaced meshes part of the
-// hemisphere above x_i is hidden by the mesh itself.
+// Self-shadowed SH irradiance transfer (Section 3, E(x_i) of Eq. 6, with the
+// visibility term of Section 4's irradiance, E = V L, E11-E14): on displaced meshes
+// part of the hemisphere above x_i is hidden by the mesh itself.
 //   T[j][i] = (pi / S) sum_s Y_j(w_s) V(x_i, w_s) [F_t(eta, mu_s)]
 // with w_s the S cosine-weighted Hammersley directions (u1 = (s + 1/2)/S, u2 the
 // bit-reversed s; r = sqrt u1, phi = 2 pi u2, mu = sqrt(1 - u1)) in the frame of the

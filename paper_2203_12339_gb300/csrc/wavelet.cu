@@ -200,7 +200,12 @@ tsr_status haar_forward_ld(const float *X, long long ldx, int rows, int nu, floa
   return TSR_OK;
 }
 
-tsr_status haar_inverse(const float *Xw, int rows, int nu, float *X, cudaStream_t s) {
+size_t haar_inverse_seg_floats(int rows, int nu) {
+  const int P = chart_side(nu), P2 = P * P;
+  return P2 <= HAAR_SEG ? 0 : (size_t)rows * 10 * (P2 / HAAR_SEG);
+}
+
+tsr_status haar_inverse(const float *Xw, int rows, int nu, float *X, cudaStream_t s, float *seg) {
   const int P = chart_side(nu), P2 = P * P;
   const int N = 10 * nu * nu + 2, NW = 10 * P2 + 2;
   if (P2 <= HAAR_SEG) {
@@ -212,9 +217,12 @@ tsr_status haar_inverse(const float *Xw, int rows, int nu, float *X, cudaStream_
   }
   const int nseg = P2 / HAAR_SEG;
   Scratch as;
-  tsr_status st = as.alloc(sizeof(float) * (size_t)rows * 10 * nseg, s);
-  if (st != TSR_OK) return st;
-  float *A = static_cast<float *>(as.p);
+  float *A = seg;   // the run approximations: the caller's buffer, else stream-ordered scratch
+  if (!A) {
+    tsr_status st = as.alloc(sizeof(float) * haar_inverse_seg_floats(rows, nu), s);
+    if (st != TSR_OK) return st;
+    A = static_cast<float *>(as.p);
+  }
   haar_inverse_top_kernel<<<rows * 10, 256, 0, s>>>(Xw, P, NW, nseg, A); ::tsr::count_launch();
   const size_t smem = sizeof(float) * HAAR_SEG * 2;
   haar_inverse_kernel<<<rows * 10 * nseg, HAAR_SEG_THREADS, smem, s>>>(Xw, A, nu, P, N, NW, HAAR_SEG, X);

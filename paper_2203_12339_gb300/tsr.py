@@ -39,6 +39,9 @@ _SIGNATURES = {
     "tsr_basis_create": (_I, [_I, _I, _D, _P, ctypes.POINTER(_P)]),
     "tsr_basis_table": (_I, [_P, _P, _P]),
     "tsr_basis_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
+    "tsr_basis_far_series": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+    "tsr_kernel_timing": (_I, [_I]),
+    "tsr_kernel_timing_read": (_I, [ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "tsr_basis_destroy": (None, [_P]),
     "tsr_project_material": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P]),
     "tsr_project_material_backward": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -47,7 +50,7 @@ _SIGNATURES = {
     "tsr_batch_plan_create": (_I, [_P, _I, _P, _I, _I, ctypes.POINTER(_P)]),
     "tsr_batch_plan_autotune": (_I, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_float)]),
     "tsr_precompute_transfer_plan": (_I, [_P, _P, _P, _P, _P, _P]),
-    "tsr_batch_plan_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "tsr_batch_plan_info": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "tsr_batch_plan_destroy": (None, [_P]),
     "tsr_haar_forward": (_I, [_P, _I, _I, _P, _P]),
     "tsr_haar_inverse": (_I, [_P, _I, _I, _P, _P]),
@@ -130,6 +133,18 @@ def stream_status() -> None:
     _check(lib().tsr_stream_status(_stream()))
 
 
+def kernel_timing(enable: bool) -> None:
+    """tsr_kernel_timing: bracket each launch of the transfer's tensor-core kernel with CUDA events."""
+    _check(lib().tsr_kernel_timing(1 if enable else 0))
+
+
+def kernel_timing_read():
+    """tsr_kernel_timing_read: (total ms, launches) of the timed kernel launches since the last read."""
+    ms, n = _D(), _I()
+    _check(lib().tsr_kernel_timing_read(ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
 def kernel_launches() -> int:
     """Kernel launches made by the library so far in this process."""
     return int(lib().tsr_kernel_launches())
@@ -161,6 +176,12 @@ class Basis:
     @property
     def handle(self):
         return self._h
+
+    def far_series(self):
+        """tsr_basis_far_series: (relative error of the 12-term far-field series, used by BF16)."""
+        err, used = _D(), _I()
+        _check(lib().tsr_basis_far_series(self._h, ctypes.byref(err), ctypes.byref(used)))
+        return err.value, bool(used.value)
 
     def table(self) -> torch.Tensor:
         f = torch.empty((self.K, self.n_r), dtype=torch.float64, device="cuda")
@@ -285,7 +306,7 @@ class BatchPlan:
         return p, a, t, M
 
     def autotune(self, pos, area, T, out=None) -> float:
-        """tsr_batch_plan_autotune: returns the best time (ms) and keeps that tile configuration."""
+        """tsr_batch_plan_autotune: returns the best time (ms) and keeps that generator configuration."""
         p, a, t, M = self._args(pos, area, T, out)
         best = ctypes.c_float()
         _check(lib().tsr_batch_plan_autotune(self._h, _ptr(p), _ptr(a), _ptr(t), _ptr(M), _stream(), ctypes.byref(best)))
@@ -298,9 +319,10 @@ class BatchPlan:
         return M
 
     def info(self):
-        n, kb = _I(), _I()
-        _check(lib().tsr_batch_plan_info(self._h, ctypes.byref(n), ctypes.byref(kb)))
-        return {"units": n.value, "bases_per_group": kb.value}
+        n, gen, par = _I(), _I(), _I()
+        _check(lib().tsr_batch_plan_info(self._h, ctypes.byref(n), ctypes.byref(gen), ctypes.byref(par)))
+        return {"units": n.value, "generator": "series" if gen.value == 0 else "table",
+                "param": par.value}
 
     def close(self):
         if getattr(self, "_h", None):

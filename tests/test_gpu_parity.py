@@ -55,6 +55,21 @@ def _normwise_k(got, ref):
     return float(np.max(d / n))
 
 
+def _elementwise_k(got, ref):
+    """max over k of max|dM[k]| / max|M[k]| (reading R31's element-wise figure): a localised
+    error on a few rows, which the normwise figure dilutes over all rows, shows here."""
+    d = np.abs(got - ref).reshape(got.shape[0], -1).max(axis=1)
+    n = np.abs(ref).reshape(ref.shape[0], -1).max(axis=1)
+    return float(np.max(d / n))
+
+
+def _check_M(got, ref, precision):
+    nw, ew = _normwise_k(got, ref), _elementwise_k(got, ref)
+    assert nw <= TOL[precision], ("normwise", nw)
+    assert ew <= TOL[precision], ("elementwise", ew)
+    return nw, ew
+
+
 # ------------------------------------------------------------------ Section 2.2
 def test_fit_pca_basis_matches_oracle(torch_cuda, tsr, oracle_basis16):
     torch = torch_cuda
@@ -132,22 +147,66 @@ def test_transfer_full_small(torch_cuda, tsr, oracle_basis16, precision, nu, K, 
     M = tsr.precompute_transfer(basis, _dev(torch, pos.T), _dev(torch, area), _dev(torch, T), precision)
     tsr.stream_status()
     M_ref = O.transfer_full(f_ref[:K], pos, area, T)
-    err = _normwise_k(M.cpu().numpy(), M_ref)
-    assert err <= TOL[precision], err
+    _check_M(M.cpu().numpy(), M_ref, precision)
+
+
+@pytest.mark.parametrize("nu,K,J,seed", [(1, 8, 9, 0), (2, 8, 9, 3), (4, 8, 9, 1), (4, 16, 25, 2), (6, 12, 16, 3),
+                                         (7, 12, 16, 4), (8, 12, 16, 5)])
+def test_transfer_bf16_coarse_meshes(torch_cuda, tsr, oracle_basis16, nu, K, J, seed):
+    """BF16 on coarse meshes (12 to 642 vertices), where a few close pairs carry much of M: the
+    near pairs (r < max(3 mm, 2h)) are summed exactly in FP32, so the bound holds with margin."""
+    torch = torch_cuda
+    f_ref, _ = oracle_basis16
+    sc, pos, area, T = _scene_arrays(nu, K, J, 0.1 if nu > 1 else 0.0, seed)
+    basis = tsr.basis_create(f_ref[:K])
+    M = tsr.precompute_transfer(basis, _dev(torch, pos.T), _dev(torch, area), _dev(torch, T), "bf16")
+    tsr.stream_status()
+    M_ref = O.transfer_full(f_ref[:K], pos, area, T)
+    nw, ew = _check_M(M.cpu().numpy(), M_ref, "bf16")
+    assert nw <= 1e-3, nw   # the normwise gate (R31) with a 2x margin; element-wise within 2e-3 above
+
+
+def test_transfer_bf16_generators_and_series_fallback(torch_cuda, tsr, oracle_basis16, monkeypatch):
+    """The two BF16 far-field generators (the 12-term series and the table) each meet the bound on
+    the same mesh; a basis the series cannot represent (a step at 10 mm) is rejected by the
+    series check at creation and the transfer takes the table, still within the bound."""
+    torch = torch_cuda
+    f_ref, _ = oracle_basis16
+    sc, pos, area, T = _scene_arrays(20, 12, 16, 0.1, 3)
+    args = (_dev(torch, pos.T), _dev(torch, area), _dev(torch, T))
+    basis = tsr.basis_create(f_ref[:12])
+    err, used = basis.far_series()
+    assert used and err < 1e-3, err
+    M_ref = O.transfer_full(f_ref[:12], pos, area, T)
+    M_series = tsr.precompute_transfer(basis, *args, "bf16").cpu().numpy()
+    monkeypatch.setenv("TSR_BF16_GENERATOR", "table")
+    M_table = tsr.precompute_transfer(basis, *args, "bf16").cpu().numpy()
+    monkeypatch.delenv("TSR_BF16_GENERATOR")
+    tsr.stream_status()
+    _check_M(M_series, M_ref, "bf16")
+    _check_M(M_table, M_ref, "bf16")
+    r = O.radius_grid()
+    f_step = f_ref[:4].copy()
+    f_step[:, r > 10.0] *= 0.5
+    b_step = tsr.basis_create(f_step)
+    err, used = b_step.far_series()
+    assert not used and err > 2e-3, err
+    M = tsr.precompute_transfer(b_step, *args, "bf16")
+    tsr.stream_status()
+    _check_M(M.cpu().numpy(), O.transfer_full(f_step, pos, area, T), "bf16")
 
 
 @pytest.mark.parametrize("K,J", [(12, 16), (16, 25)])
 def test_transfer_streamk_cut_tiles(torch_cuda, tsr, oracle_basis16, K, J):
     """4,002 vertices = 32 tiles x 251 steps over ~125 equal stage ranges: most tiles are cut into
     pieces that the fix-up sums (the last, 34-row tile too).
-    - split BF16 against the oracle (1e-4);
+    - split BF16 and BF16 against the oracle (1e-4, 2e-3 with a 2x margin: on this mesh basis 1
+      has ~10x cancellation in M, which a plain BF16 contraction of every pair, self pair
+      excepted, turned into a 3.7e-3 error);
     - BF16 against the same mesh through the batched path, whose units are whole tiles (same BF16
       products, other accumulation segments; the tensor-core accumulation truncates, ~1e-7 per step
       relative to the running sum): 2e-4, where a lost or doubled piece would be off by >1e-2;
-    - two runs bit-identical (the fix-up adds the pieces in a fixed order).
-    (BF16 against the oracle is not asserted at 2e-3 here: on this mesh basis 1 has ~10x
-    cancellation in M and the BF16 design's error is 3.7e-3, the value an exact emulation of its
-    rounding gives.)"""
+    - two runs bit-identical (the fix-up adds the pieces in a fixed order)."""
     torch = torch_cuda
     f_ref, _ = oracle_basis16
     sc, pos, area, T = _scene_arrays(20, K, J, 0.1, 3)
@@ -156,8 +215,10 @@ def test_transfer_streamk_cut_tiles(torch_cuda, tsr, oracle_basis16, K, J):
     args = (_dev(torch, pos.T), _dev(torch, area), _dev(torch, T))
     M_ref = O.transfer_full(f_ref[:K], pos, area, T)
     Ms = tsr.precompute_transfer(basis, *args, "bf16x3")
-    assert _normwise_k(Ms.cpu().numpy(), M_ref) <= TOL["bf16x3"]
+    _check_M(Ms.cpu().numpy(), M_ref, "bf16x3")
     M1 = tsr.precompute_transfer(basis, *args, "bf16")
+    nw, ew = _check_M(M1.cpu().numpy(), M_ref, "bf16")
+    assert nw <= 1e-3, nw
     M2 = tsr.precompute_transfer(basis, *args, "bf16")
     Mb = tsr.precompute_transfer_batched(basis, [0, sc.n], *args, "bf16")
     tsr.stream_status()
@@ -175,7 +236,7 @@ def test_transfer_tiny_mesh_and_single_basis(torch_cuda, tsr, oracle_basis16):
     for precision in ("fp32", "bf16", "bf16x3"):
         M = tsr.precompute_transfer(basis, _dev(torch, pos.T), _dev(torch, area), _dev(torch, T), precision)
         tsr.stream_status()
-        assert _normwise_k(M.cpu().numpy(), M_ref) <= TOL[precision]
+        _check_M(M.cpu().numpy(), M_ref, precision)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "bf16x3"])
@@ -190,8 +251,7 @@ def test_transfer_full_size_sampled_rows(torch_cuda, tsr, oracle_basis16, precis
     tsr.stream_status()
     rows = scene.sample_rows(sc.n, 1024, seed=7)
     M_ref = O.transfer_rows(f_ref[:12], pos, area, T, rows)
-    err = _normwise_k(M.cpu().numpy()[:, :, rows], M_ref)
-    assert err <= TOL[precision], err
+    _check_M(M.cpu().numpy()[:, :, rows], M_ref, precision)
 
 
 @pytest.mark.slow
@@ -207,7 +267,7 @@ def test_transfer_largest_sampled_rows(torch_cuda, tsr, oracle_basis16, precisio
     tsr.stream_status()
     rows = scene.sample_rows(sc.n, 128, seed=7)
     M_ref = O.transfer_rows(f_ref, pos, area, T, rows)
-    assert _normwise_k(M.cpu().numpy()[:, :, rows], M_ref) <= TOL[precision]
+    _check_M(M.cpu().numpy()[:, :, rows], M_ref, precision)
 
 
 # ------------------------------------------------------------------ Eq. 9-10 Haar
@@ -600,22 +660,6 @@ def test_invalid_arguments_are_rejected(torch_cuda, tsr, oracle_basis16):
     with pytest.raises(tsr.TsrError):
         tsr.precompute_transfer(basis, torch.zeros((3, 42), device="cuda"), torch.zeros(42, device="cuda"),
                                 torch.zeros((33, 42), device="cuda"))
-
-
-@pytest.mark.parametrize("precision", ["bf16", "bf16x3"])
-def test_transfer_nearfar_path(torch_cuda, tsr, oracle_basis16, precision, monkeypatch):
-    """Opt-in near/far split (Chebyshev far field in registers, exact table below r_near); same tolerances."""
-    torch = torch_cuda
-    f_ref, _ = oracle_basis16
-    monkeypatch.setenv("TSR_TRANSFER_NEARFAR", "1")
-    for nu, K, J in ((41, 12, 16), (42, 16, 25)):
-        sc, pos, area, T = _scene_arrays(nu, K, J, 0.12, 3)
-        basis = tsr.basis_create(f_ref[:K])
-        M = tsr.precompute_transfer(basis, _dev(torch, pos.T), _dev(torch, area), _dev(torch, T), precision)
-        tsr.stream_status()
-        rows = scene.sample_rows(sc.n, 256, seed=5)
-        M_ref = O.transfer_rows(f_ref[:K], pos, area, T, rows)
-        assert _normwise_k(M.cpu().numpy()[:, :, rows], M_ref) <= TOL[precision]
 
 
 # ------------------------------------------------------------------ Fresnel factors (Eq. 3, Eq. 6)

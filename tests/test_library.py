@@ -134,3 +134,13 @@ def test_fault_injection_arguments_checked_on_the_host(libtsr):
     assert f(0, 1) == -1 and f(4, 1) == -1 and f(1, -1) == -1
     for kind in (1, 2, 3):
         assert f(kind, 0) == 0
+
+
+def test_kernel_timing_toggle_and_empty_read_without_gpu(libtsr):
+    libtsr.tsr_kernel_timing.restype = ctypes.c_int
+    libtsr.tsr_kernel_timing_read.restype = ctypes.c_int
+    assert libtsr.tsr_kernel_timing(1) == 0
+    ms, n = ctypes.c_double(-1.0), ctypes.c_int(-1)
+    assert libtsr.tsr_kernel_timing_read(ctypes.byref(ms), ctypes.byref(n)) == 0
+    assert ms.value == 0.0 and n.value == 0
+    assert libtsr.tsr_kernel_timing(0) == 0

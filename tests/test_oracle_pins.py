@@ -502,6 +502,39 @@ def test_fresnel_output_vjp_matches_finite_differences():
     assert dB[1, 2, 3] == pytest.approx(L(Bp, eta) - L(B, eta), rel=1e-12)
 
 
+def test_oracle_sh_closed_forms_addition_theorem_and_orthonormality():
+    """The oracle's real SH (reading R19: no Condon-Shortley phase, j = l^2 + l + m) against the
+    textbook Cartesian forms for l <= 2, the addition theorem sum_m Y_lm(a) Y_lm(b) = (2l+1)/(4 pi)
+    P_l(a.b), and orthonormality by a product Gauss quadrature on the sphere."""
+    rng = np.random.default_rng(21)
+    d = rng.standard_normal((50, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    x, y, z = d.T
+    Y = O.sh_real_oracle(3, d)
+    c0, c1 = 0.5 / math.sqrt(math.pi), math.sqrt(3 / (4 * math.pi))
+    want = [np.full(50, c0), c1 * y, c1 * z, c1 * x,
+            0.5 * math.sqrt(15 / math.pi) * x * y, 0.5 * math.sqrt(15 / math.pi) * y * z,
+            0.25 * math.sqrt(5 / math.pi) * (3 * z * z - 1), 0.5 * math.sqrt(15 / math.pi) * x * z,
+            0.25 * math.sqrt(15 / math.pi) * (x * x - y * y)]
+    for j in range(9):
+        assert np.allclose(Y[j], want[j], atol=1e-13), j
+    Ya = O.sh_real_oracle(6, d[:25])
+    Yb = O.sh_real_oracle(6, d[25:])
+    cosg = np.sum(d[:25] * d[25:], axis=1)
+    for l in range(6):
+        lhs = np.sum(Ya[l * l:(l + 1) ** 2] * Yb[l * l:(l + 1) ** 2], axis=0)
+        Pl = np.polynomial.legendre.Legendre.basis(l)(cosg)
+        assert np.allclose(lhs, (2 * l + 1) / (4 * math.pi) * Pl, atol=1e-13), l
+    xg, wg = np.polynomial.legendre.leggauss(16)
+    ph = (np.arange(32) + 0.5) * (2 * math.pi / 32)
+    Z, PH = np.meshgrid(xg, ph, indexing="ij")
+    st = np.sqrt(1 - Z ** 2)
+    dirs = np.stack([st * np.cos(PH), st * np.sin(PH), Z], axis=-1).reshape(-1, 3)
+    w = np.outer(wg, np.full(32, 2 * math.pi / 32)).reshape(-1)
+    Yq = O.sh_real_oracle(5, dirs)
+    assert np.allclose((Yq * w) @ Yq.T, np.eye(25), atol=1e-12)
+
+
 def test_sh_zonal_fresnel_reduces_to_the_clamped_cosine():
     A = O.sh_zonal_fresnel(1.0, 5)
     assert np.allclose(A, [math.pi, 2 * math.pi / 3, math.pi / 4, 0.0, -math.pi / 24], atol=1e-12)

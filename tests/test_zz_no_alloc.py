@@ -52,21 +52,67 @@ def _rel(a, b):
     return float(((a - b).norm(dim=1) / b.norm(dim=1)).max())
 
 
-@pytest.mark.parametrize("nu,K,J,E,p", [(16, 12, 16, 5, 0.1), (5, 8, 9, 3, 0.3)])
-def test_noalloc_matches_relight_on_two_calls(env, nu, K, J, E, p):
+def _cdf97_case(torch, tsr, nu, K, J, p, seed):
+    rng = np.random.default_rng(seed)
+    M = rng.standard_normal((K, J, 10 * nu * nu + 2)).astype(np.float32)
+    return tsr.compress(torch.tensor(M, device="cuda"), nu, wavelet="cdf97", rule="top", param=p)
+
+
+@pytest.mark.parametrize("nu,K,J,E,p,wavelet", [
+    (16, 12, 16, 5, 0.1, "haar"),
+    (5, 8, 9, 3, 0.3, "haar"),
+    # charts of 64 x 64 = 4,096 Morton positions: the inverse Haar runs in two kernels and
+    # needs the run approximations, which must come from the fixed array too
+    (64, 12, 16, 3, 0.1, "haar"),
+    (64, 12, 16, 1, 0.1, "haar"),
+    # one edit of a CDF 9/7 transfer: the per-vector wavelet images b^w live in the array
+    (16, 8, 9, 1, 0.1, "cdf97"),
+])
+def test_noalloc_matches_relight_on_two_calls(env, nu, K, J, E, p, wavelet):
     torch, tsr = env
-    comp = _case(torch, tsr, nu, K, J, p, seed=nu + E)
+    if wavelet == "haar":
+        comp = _case(torch, tsr, nu, K, J, p, seed=nu + E)
+    else:
+        comp = _cdf97_case(torch, tsr, nu, K, J, p, seed=nu + E)
     rng = np.random.default_rng(7)
     for call in range(2):   # second call reuses the array left over by the first
         g = torch.tensor(rng.standard_normal((E, 3, K)).astype(np.float32), device="cuda")
         light = torch.tensor(rng.standard_normal(J).astype(np.float32), device="cuda")
         want = tsr.relight(comp, g, light)
+        torch.cuda.synchronize()
         B = torch.full((E, 3, comp.n), float("nan"), device="cuda")
-        assert _noalloc(tsr, comp, g, light, B) == 0, tsr.lib().tsr_last_error()
+        # Every stream-ordered allocation the library attempts from here on fails: the call
+        # must not make one.
+        tsr.fault_inject("alloc", 1 << 20)
+        try:
+            st = _noalloc(tsr, comp, g, light, B)
+        finally:
+            tsr.fault_inject("alloc", 0)
+        assert st == 0, tsr.lib().tsr_last_error()
         torch.cuda.synchronize()
         tsr.stream_status()
         assert torch.isfinite(B).all()
         assert _rel(B, want) <= 2e-6, (call, _rel(B, want))
+
+
+def test_noalloc_python_binding(env):
+    """The binding checks the caller's output buffer and relights into it."""
+    torch, tsr = env
+    comp = _case(torch, tsr, 8, 6, 9, 0.2, seed=5)
+    rng = np.random.default_rng(3)
+    g = torch.tensor(rng.standard_normal((4, 3, 6)).astype(np.float32), device="cuda")
+    light = torch.tensor(rng.standard_normal(9).astype(np.float32), device="cuda")
+    want = tsr.relight(comp, g, light)
+    out = torch.empty((4, 3, comp.n), device="cuda")
+    got = tsr.relight_noalloc(comp, g, light, out)
+    assert got.data_ptr() == out.data_ptr()
+    torch.cuda.synchronize()
+    assert _rel(out, want) <= 2e-6
+    strided = torch.empty((4, 3, 2 * comp.n), device="cuda")[:, :, ::2]
+    with pytest.raises(ValueError):
+        tsr.relight_noalloc(comp, g, light, strided)
+    with pytest.raises(ValueError):
+        tsr.relight_noalloc(comp, g, light, torch.empty((4, 3, comp.n + 1), device="cuda"))
 
 
 def test_noalloc_scratch_does_not_grow_with_edits(env):
