@@ -43,24 +43,36 @@ __device__ __forceinline__ int mesh_of_vertex(long long v, int n_mesh, const lon
 }
 
 // One block per mesh: r_e^2 = max(r_floor^2, 4 sum(A) / N) and the mesh's bounding box.
-__global__ void __launch_bounds__(256) near_mesh_stats_kernel(int n_mesh, const long long *__restrict__ voff,
+__global__ void __launch_bounds__(1024) near_mesh_stats_kernel(int n_mesh, const long long *__restrict__ voff,
                                                                long long total, const float *__restrict__ pos,
                                                                long long stride, const float *__restrict__ area,
                                                                float r_floor2, float *__restrict__ rn2,
                                                                float *__restrict__ mbox) {
-  __shared__ double s_sum[8];
-  __shared__ float s_box[8][6];
+  __shared__ double s_sum[32];
+  __shared__ float s_box[32][6];
   const int m = blockIdx.x;
   const long long v0 = n_mesh > 1 ? voff[m] : 0, v1 = n_mesh > 1 ? voff[m + 1] : total;
   double a = 0.0;
   float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
-  for (long long v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
-    a += (double)area[v];
+  // four vertices per thread and pass, so that several loads are in flight
+  for (long long vb = v0 + threadIdx.x; vb < v1; vb += 4 * (long long)blockDim.x) {
+    float av[4], xv[3][4];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const float x = pos[(size_t)q * stride + v];
-      lo[q] = fminf(lo[q], x);
-      hi[q] = fmaxf(hi[q], x);
+    for (int e = 0; e < 4; ++e) {
+      const long long v = vb + (long long)e * blockDim.x;
+      const bool ok = v < v1;
+      av[e] = ok ? area[v] : 0.f;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) xv[q][e] = ok ? pos[(size_t)q * stride + v] : NAN;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      a += (double)av[e];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        lo[q] = fminf(lo[q], xv[q][e]);   // fminf / fmaxf ignore the NaN of a missing vertex
+        hi[q] = fmaxf(hi[q], xv[q][e]);
+      }
     }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -194,9 +206,13 @@ __global__ void near_box_kernel(const float *__restrict__ pos_s, long long np, l
 
 constexpr int NEAR_ROWS = 64;     // output rows per block
 constexpr int NEAR_SCAN = 256;    // chunk boxes tested per pass
-constexpr int NEAR_BATCH = 8;     // listed chunks staged per barrier
+constexpr int NEAR_BATCH = 4;     // listed chunks staged per barrier (64 candidates)
 
-// One block per 64 sorted output rows; thread (row, kg) owns bases 2 kg, 2 kg + 1.
+// One block per 64 sorted output rows.  Per batch of up to 64 staged candidates i:
+//  phase A: the block tests every (row, i) pair once (a warp covers 32 consecutive i of
+//           one row) and records the near pairs as bit masks plus x = r / dr;
+//  phase B: thread (row, kg) owns bases 2 kg, 2 kg + 1 and walks its row's set bits in
+//           increasing i, adding A_i f_k(r) T[j][i] for every j (deterministic order).
 template <int JP>
 __global__ void __launch_bounds__(512) near_field_kernel(
     const float *__restrict__ pos_s, const float *__restrict__ tq, const int *__restrict__ mesh_s,
@@ -204,9 +220,14 @@ __global__ void __launch_bounds__(512) near_field_kernel(
     const float *__restrict__ chunk_box, int n_mesh, const long long *__restrict__ voff,
     const float *__restrict__ rn2, const float4 *__restrict__ tab, int KG, int n_r, float inv_dr, float r2max,
     int K, int J, float *__restrict__ M, long long stride) {
-  __shared__ __align__(16) float sT[NEAR_BATCH * 16 * JP];
-  __shared__ float sx[NEAR_BATCH * 16], sy[NEAR_BATCH * 16], sz[NEAR_BATCH * 16];
-  __shared__ int sm[NEAR_BATCH * 16];
+  constexpr int NC = NEAR_BATCH * 16;   // candidates per batch (64)
+  __shared__ __align__(16) float sT[NC * JP];
+  __shared__ float sx[NC], sy[NC], sz[NC];
+  __shared__ int sm[NC];
+  __shared__ float s_xv[NEAR_ROWS][NC + 1];       // r / dr of the near pairs (+1: no bank conflicts)
+  __shared__ unsigned s_mask[NEAR_ROWS][NC / 32];
+  __shared__ float s_row[NEAR_ROWS][4];           // x, y, z, r_e^2 of the block's rows
+  __shared__ int s_rmesh[NEAR_ROWS];
   __shared__ int s_list[NEAR_SCAN];
   __shared__ int s_warp[NEAR_SCAN / 32];
   __shared__ float s_tb[6];
@@ -217,9 +238,16 @@ __global__ void __launch_bounds__(512) near_field_kernel(
   const int ol = threadIdx.x / KG;
   const long long os = (long long)blockIdx.x * NEAR_ROWS + ol;
   const bool o_ok = ol < NEAR_ROWS && os < total;
-  const float xo = o_ok ? pos_s[os] : 0.f, yo = o_ok ? pos_s[np + os] : 0.f, zo = o_ok ? pos_s[2 * np + os] : 0.f;
-  const int mo = o_ok ? mesh_s[os] : -2;
-  const float rn2o = o_ok ? rn2[mo] : 0.f;
+  for (int r = threadIdx.x; r < NEAR_ROWS; r += blockDim.x) {
+    const long long q = (long long)blockIdx.x * NEAR_ROWS + r;
+    const bool ok = q < total;
+    const int m = ok ? mesh_s[q] : -2;
+    s_row[r][0] = ok ? pos_s[q] : 0.f;
+    s_row[r][1] = ok ? pos_s[np + q] : 0.f;
+    s_row[r][2] = ok ? pos_s[2 * np + q] : 0.f;
+    s_row[r][3] = ok ? rn2[m] : 0.f;
+    s_rmesh[r] = m;
+  }
   if (threadIdx.x == 0) {
     // meshes of the tile's first and last rows; the chunks of those meshes (sorted blocks)
     const long long t0 = (long long)tile * 128, t1 = min(total, t0 + 128) - 1;
@@ -238,7 +266,7 @@ __global__ void __launch_bounds__(512) near_field_kernel(
   float acc0[JP], acc1[JP];
 #pragma unroll
   for (int j = 0; j < JP; ++j) acc0[j] = acc1[j] = 0.f;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = (int)(blockDim.x >> 5);
   const int scan = min(NEAR_SCAN, (int)blockDim.x);   // chunk boxes tested per pass (a multiple of 32)
   for (int base = s_range[0]; base < s_range[1]; base += scan) {
     // compact the chunks of this pass whose box is within r_e of the tile box
@@ -264,41 +292,61 @@ __global__ void __launch_bounds__(512) near_field_kernel(
     if (keep) s_list[before + __popc(bal & ((1u << lane) - 1u))] = c;
     __syncthreads();
     for (int lb = 0; lb < n_list; lb += NEAR_BATCH) {
-      // stage up to NEAR_BATCH listed chunks (16 i each) at once: one barrier pair per batch
+      // stage up to NEAR_BATCH listed chunks (16 i each); the rest of the batch is empty
       const int nb = min(NEAR_BATCH, n_list - lb);
       for (int q = threadIdx.x; q < nb * 16 * JP / 4; q += blockDim.x) {
-        const int c = q / (16 * JP / 4), w = q % (16 * JP / 4);
+        const int cc = q / (16 * JP / 4), w = q % (16 * JP / 4);
         reinterpret_cast<float4 *>(sT)[q] =
-            reinterpret_cast<const float4 *>(tq + (size_t)s_list[lb + c] * 16 * JP)[w];
+            reinterpret_cast<const float4 *>(tq + (size_t)s_list[lb + cc] * 16 * JP)[w];
       }
-      for (int q = threadIdx.x; q < nb * 16; q += blockDim.x) {
-        const long long i = (long long)s_list[lb + q / 16] * 16 + (q % 16);
-        sx[q] = pos_s[i];
-        sy[q] = pos_s[np + i];
-        sz[q] = pos_s[2 * np + i];
-        sm[q] = mesh_s[i];
+      for (int q = threadIdx.x; q < NC; q += blockDim.x) {
+        if (q < nb * 16) {
+          const long long i = (long long)s_list[lb + q / 16] * 16 + (q % 16);
+          sx[q] = pos_s[i];
+          sy[q] = pos_s[np + i];
+          sz[q] = pos_s[2 * np + i];
+          sm[q] = mesh_s[i];
+        } else {
+          sm[q] = -1;   // no candidate
+        }
       }
       __syncthreads();
-      for (int ii = 0; ii < nb * 16; ++ii) {
-        const float r2 = near_pair_r2(xo, yo, zo, sx[ii], sy[ii], sz[ii]);
-        if (sm[ii] == mo && r2 < rn2o && r2 <= r2max) {
-          const float x = __fsqrt_rn(r2) * inv_dr;
-          const int m = min(static_cast<int>(x), n_r - 2);
-          const float t = x - static_cast<float>(m);
-          const float4 tb = __ldg(tab + (size_t)m * KG + kg);
-          const float F0 = fmaf(t, tb.y, tb.x), F1 = fmaf(t, tb.w, tb.z);
-          const float4 *tv = reinterpret_cast<const float4 *>(sT + ii * JP);
+      // phase A: warp w takes 32 consecutive candidates of one row per turn
+      for (int item = warp; item < NEAR_ROWS * (NC / 32); item += n_warps) {
+        const int r = item / (NC / 32), wd = item % (NC / 32), ii = wd * 32 + lane;
+        const float r2 = near_pair_r2(s_row[r][0], s_row[r][1], s_row[r][2], sx[ii], sy[ii], sz[ii]);
+        const bool nr = sm[ii] == s_rmesh[r] && r2 < s_row[r][3] && r2 <= r2max;
+        if (nr) s_xv[r][ii] = __fsqrt_rn(r2) * inv_dr;
+        const unsigned bits = __ballot_sync(0xffffffffu, nr);
+        if (lane == 0) s_mask[r][wd] = bits;
+      }
+      __syncthreads();
+      // phase B
+      if (o_ok) {
 #pragma unroll
-          for (int j4 = 0; j4 < JP / 4; ++j4) {
-            const float4 v = tv[j4];
-            acc0[4 * j4] = fmaf(F0, v.x, acc0[4 * j4]);
-            acc0[4 * j4 + 1] = fmaf(F0, v.y, acc0[4 * j4 + 1]);
-            acc0[4 * j4 + 2] = fmaf(F0, v.z, acc0[4 * j4 + 2]);
-            acc0[4 * j4 + 3] = fmaf(F0, v.w, acc0[4 * j4 + 3]);
-            acc1[4 * j4] = fmaf(F1, v.x, acc1[4 * j4]);
-            acc1[4 * j4 + 1] = fmaf(F1, v.y, acc1[4 * j4 + 1]);
-            acc1[4 * j4 + 2] = fmaf(F1, v.z, acc1[4 * j4 + 2]);
-            acc1[4 * j4 + 3] = fmaf(F1, v.w, acc1[4 * j4 + 3]);
+        for (int wd = 0; wd < NC / 32; ++wd) {
+          unsigned bits = s_mask[ol][wd];
+          while (bits) {
+            const int ii = wd * 32 + __ffs(bits) - 1;
+            bits &= bits - 1u;
+            const float x = s_xv[ol][ii];
+            const int m = min(static_cast<int>(x), n_r - 2);
+            const float t = x - static_cast<float>(m);
+            const float4 tb = __ldg(tab + (size_t)m * KG + kg);
+            const float F0 = fmaf(t, tb.y, tb.x), F1 = fmaf(t, tb.w, tb.z);
+            const float4 *tv = reinterpret_cast<const float4 *>(sT + ii * JP);
+#pragma unroll
+            for (int j4 = 0; j4 < JP / 4; ++j4) {
+              const float4 v = tv[j4];
+              acc0[4 * j4] = fmaf(F0, v.x, acc0[4 * j4]);
+              acc0[4 * j4 + 1] = fmaf(F0, v.y, acc0[4 * j4 + 1]);
+              acc0[4 * j4 + 2] = fmaf(F0, v.z, acc0[4 * j4 + 2]);
+              acc0[4 * j4 + 3] = fmaf(F0, v.w, acc0[4 * j4 + 3]);
+              acc1[4 * j4] = fmaf(F1, v.x, acc1[4 * j4]);
+              acc1[4 * j4 + 1] = fmaf(F1, v.y, acc1[4 * j4 + 1]);
+              acc1[4 * j4 + 2] = fmaf(F1, v.z, acc1[4 * j4 + 2]);
+              acc1[4 * j4 + 3] = fmaf(F1, v.w, acc1[4 * j4 + 3]);
+            }
           }
         }
       }
@@ -362,7 +410,7 @@ tsr_status near_setup(NearField &nf, const tsr_basis *b, int n_mesh, const long 
   nf.chunk_box = reinterpret_cast<float *>(take(b_cbox));
   void *sort_tmp = take(b_sort);
   const float r_floor = (float)b->r_near;
-  near_mesh_stats_kernel<<<n_mesh, 256, 0, s>>>(n_mesh, d_voff, total, pos, stride, area, r_floor * r_floor,
+  near_mesh_stats_kernel<<<n_mesh, 1024, 0, s>>>(n_mesh, d_voff, total, pos, stride, area, r_floor * r_floor,
                                                nf.rn2, mbox);
   ::tsr::count_launch();
   near_global_box_kernel<<<1, 32, 0, s>>>(n_mesh, mbox, gq); ::tsr::count_launch();

@@ -840,9 +840,12 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
             for (int q = 0; q < 4; ++q) {
               const float r2 = pair_r2(xo, yo, zo, xa[q], ya[q], za[q]);
               const bool far = r2 >= rlo2 && r2 <= r2max;
-              const float rf = far ? r2 : 1.f;   // the special-function calls run unconditionally
-              const float x = far ? fmaf(xa_alpha, fast_lg2(rf), xa_beta) : 0.f;
-              sv[q] = far ? rcp_approx(rf) : 0.f;
+              // lg2 and rcp run on every pair (no branch); a pair outside the far field
+              // gets s = 0, which zeroes all of its terms whatever x is
+              const float rf = far ? r2 : 1.f;
+              const float lg = fast_lg2(rf), rc = rcp_approx(rf);
+              const float x = fmaf(xa_alpha, lg, xa_beta);
+              sv[q] = far ? rc : 0.f;
               xsv[q] = x * sv[q];
               x2v[q] = x + x;
             }
