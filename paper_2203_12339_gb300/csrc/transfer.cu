@@ -1283,7 +1283,7 @@ static tsr_status launch_tc(const TcArgs &a0, int n_cols, const CUtensorMap &tma
   TcArgs a = a0;
   // The tensor-core FP32 accumulation does not round to nearest, so long sums are cut
   // into segments that the epilogue adds with round-to-nearest FP32 adds.
-  a.seg_stages = (MODE == MODE_CHEB ? 8192 : 4096) / 16;
+  a.seg_stages = (MODE == MODE_CHEB ? 16384 : 4096) / 16;
   a.n_groups = (n_cols + CB - 1) / CB;
   const size_t smem = C::smem_bytes(a.n_r, a.K);
   if (smem > 232448) {
