@@ -280,7 +280,11 @@ tsr_status tsr_haar_recompress(const float *M, tsr_compressed *c, tsr_stream str
  * values at columns offsets[b] .. offsets[b+1]-1 of every (k, j) row, read in
  * place with row stride total); offsets: HOST [n_mesh + 1] int64, each mesh
  * 10 nu^2 + 2 vertices (nu <= 128).  Per mesh: the Haar analysis of its rows and
- * the top-fraction selection of tsr_haar_compress, one launch per kernel per mesh.
+ * the top-fraction selection of tsr_haar_compress (the same kernels' work, so each
+ * handle is bit-identical to compressing its mesh alone), in one launch per stage
+ * (Haar, top levels, selection, row counts, scan, packing) and group of 32 meshes
+ * (stream-ordered scratch of the group: about 5 K J (10 P^2 + 2) bytes per mesh).  All
+ * handles share K and J.
  *   tsr_haar_compress_batched   creates the n_mesh handles in out (HOST array;
  *                               allocates device memory, synchronises); on error
  *                               none is left (out[b] = NULL).

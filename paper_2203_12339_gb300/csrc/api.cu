@@ -289,21 +289,7 @@ extern "C" tsr_status tsr_haar_compress_batched(int n_mesh, const int64_t *offse
   }
   tsr_status st = require_device();
   if (st != TSR_OK) return st;
-  cudaStream_t s = as_stream(stream);
-  const long long total = offsets[n_mesh];
-  for (int b = 0; b < n_mesh && st == TSR_OK; ++b) {
-    const int nu = chart_nu_of(offsets[b + 1] - offsets[b]), P = chart_side(nu);
-    Scratch mw;
-    st = mw.alloc(sizeof(float) * (size_t)K * J * (10 * P * P + 2), s);
-    if (st == TSR_OK) st = haar_forward_ld(M + offsets[b], total, K * J, nu, static_cast<float *>(mw.p), s);
-    if (st == TSR_OK) st = wavelet_compress(static_cast<float *>(mw.p), K, J, nu, p, &out[b], s);
-  }
-  if (st != TSR_OK)
-    for (int b = 0; b < n_mesh; ++b) {
-      tsr_compressed_destroy(out[b]);
-      out[b] = nullptr;
-    }
-  return st;
+  return haar_compress_many(n_mesh, offsets, M, K, J, p, out, as_stream(stream));
 }
 
 extern "C" tsr_status tsr_haar_recompress_batched(int n_mesh, const int64_t *offsets, const float *M,
@@ -312,7 +298,6 @@ extern "C" tsr_status tsr_haar_recompress_batched(int n_mesh, const int64_t *off
   TSR_CHECK_ARG(offsets && M && c, "tsr_haar_recompress_batched: NULL argument");
   TSR_CHECK_ARG(n_mesh >= 1 && n_mesh <= 65536, "tsr_haar_recompress_batched: n_mesh=%d out of range", n_mesh);
   TSR_CHECK_ARG(offsets[0] == 0, "tsr_haar_recompress_batched: offsets[0] must be 0");
-  size_t mw_max = 0;
   for (int b = 0; b < n_mesh; ++b) {
     TSR_CHECK_ARG(c[b], "tsr_haar_recompress_batched: handle %d is NULL", b);
     TSR_CHECK_ARG(c[b]->wavelet == 0 && c[b]->keep_rule == 0,
@@ -320,23 +305,14 @@ extern "C" tsr_status tsr_haar_recompress_batched(int n_mesh, const int64_t *off
     TSR_CHECK_ARG(offsets[b + 1] - offsets[b] == 10 * (int64_t)c[b]->nu * c[b]->nu + 2,
                   "tsr_haar_recompress_batched: mesh %d has %lld vertices, its handle nu=%d", b,
                   (long long)(offsets[b + 1] - offsets[b]), c[b]->nu);
-    mw_max = std::max(mw_max, (size_t)c[b]->K * c[b]->J * c[b]->n_rows);
+    TSR_CHECK_ARG(c[b]->K == c[0]->K && c[b]->J == c[0]->J,
+                  "tsr_haar_recompress_batched: handle %d has K=%d J=%d, handle 0 K=%d J=%d", b, c[b]->K, c[b]->J,
+                  c[0]->K, c[0]->J);
   }
   tsr_status st = require_device();
   for (int b = 0; b < n_mesh && st == TSR_OK; ++b) st = require_same_device(c[b]->device, "tsr_haar_recompress_batched");
   if (st != TSR_OK) return st;
-  cudaStream_t s = as_stream(stream);
-  const long long total = offsets[n_mesh];
-  Scratch mw;   // one wavelet buffer, reused mesh after mesh (stream order)
-  st = mw.alloc(sizeof(float) * mw_max, s);
-  if (st != TSR_OK) return st;
-  float *Mw = static_cast<float *>(mw.p);
-  for (int b = 0; b < n_mesh; ++b) {
-    st = haar_forward_ld(M + offsets[b], total, c[b]->K * c[b]->J, c[b]->nu, Mw, s);
-    if (st == TSR_OK) st = wavelet_compress_into(Mw, c[b], s);
-    if (st != TSR_OK) return st;
-  }
-  return TSR_OK;
+  return haar_recompress_many(n_mesh, offsets, M, c, as_stream(stream));
 }
 
 extern "C" tsr_status tsr_compressed_info(const tsr_compressed *c, int *K, int *J, int *nu, int64_t *nnz,

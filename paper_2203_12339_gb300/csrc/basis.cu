@@ -88,6 +88,86 @@ __global__ void jacobi_round_kernel(double *__restrict__ A, int n_cols, int n_r,
   if (threadIdx.x == 0) atomicAdd(rotations, 1u);
 }
 
+// The whole solve in one cooperative launch: block b owns pair b of every round of the
+// circle ordering, rounds are separated by a grid barrier, and after each sweep every
+// block reads that sweep's rotation count (rot[sweep], all blocks see the same value) and
+// stops when it is zero.  The barrier's waits are bounded: a block that gives up records
+// it in *status and the host reports a timeout.  status[1] receives the sweeps run.
+__device__ __forceinline__ bool jacobi_grid_barrier(unsigned *bar, unsigned target, unsigned *status) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int ok = 0;
+    for (uint32_t it = 0; it < TSR_WAIT_LIMIT; ++it) {
+      if (*reinterpret_cast<volatile unsigned *>(bar) >= target) {
+        ok = 1;
+        break;
+      }
+    }
+    if (!ok) atomicOr(status, 1u);
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(256) jacobi_solve_kernel(double *__restrict__ A, int n_cols, int n_r, double tol,
+                                                          int max_sweeps, unsigned *__restrict__ rot,
+                                                          unsigned *__restrict__ bar, unsigned *__restrict__ status) {
+  __shared__ double red[3 * 32];
+  const int idx = blockIdx.x, nb = gridDim.x;
+  const int nm1 = n_cols - 1;
+  unsigned n_bar = 0;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    for (int round = 0; round < nm1; ++round) {
+      int p, q;
+      if (idx == 0) {
+        p = nm1;
+        q = round;
+      } else {
+        p = (round + idx) % nm1;
+        q = (round - idx + nm1) % nm1;
+      }
+      double *ap = A + (size_t)p * n_r;
+      double *aq = A + (size_t)q * n_r;
+      double v[3] = {0.0, 0.0, 0.0};
+      for (int m = threadIdx.x; m < n_r; m += blockDim.x) {
+        const double x = __ldcg(ap + m), y = __ldcg(aq + m);   // through L2: other blocks rewrote the columns
+        v[0] += x * x;
+        v[1] += y * y;
+        v[2] += x * y;
+      }
+      block_sum<3>(v, red);
+      const double alpha = v[0], beta = v[1], gamma = v[2];
+      const bool rotate = !(gamma == 0.0 || alpha == 0.0 || beta == 0.0) &&
+                          !(fabs(gamma) <= tol * sqrt(alpha) * sqrt(beta));
+      if (rotate) {
+        const double zeta = (beta - alpha) / (2.0 * gamma);
+        const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t);
+        const double s = c * t;
+        for (int m = threadIdx.x; m < n_r; m += blockDim.x) {
+          const double x = __ldcg(ap + m), y = __ldcg(aq + m);
+          ap[m] = c * x - s * y;
+          aq[m] = s * x + c * y;
+        }
+        if (threadIdx.x == 0) atomicAdd(&rot[sweep], 1u);
+      }
+      if (!jacobi_grid_barrier(bar, (++n_bar) * (unsigned)nb, status)) return;
+    }
+    if (*reinterpret_cast<volatile unsigned *>(&rot[sweep]) == 0u) {
+      if (idx == 0 && threadIdx.x == 0) status[2] = 1u;   // converged
+      ++sweep;
+      break;
+    }
+  }
+  if (idx == 0 && threadIdx.x == 0) status[1] = (unsigned)sweep;
+}
+
 // Column norms (= singular values), ranks by descending norm (ties: lower column).
 __global__ void jacobi_rank_kernel(const double *__restrict__ A, int n_cols, int n_r, int n_sv,
                                    double *__restrict__ norms, int *__restrict__ col_of_rank,
@@ -457,26 +537,53 @@ extern "C" tsr_status tsr_fit_pca_basis(int n_mat, const double *sigma_a, const 
   FIT_CUDA(cudaMalloc(&A, sizeof(double) * (size_t)n_cols * n_r));
   FIT_CUDA(cudaMalloc(&norms, sizeof(double) * n_cols));
   FIT_CUDA(cudaMalloc(&col_of_rank, sizeof(int) * n_cols));
-  FIT_CUDA(cudaMalloc(&rot, sizeof(unsigned)));
+  constexpr int kMaxSweeps = 60;
+  FIT_CUDA(cudaMalloc(&rot, sizeof(unsigned) * (kMaxSweeps + 4)));   // per-sweep counts | barrier | status[3]
 
   jacobi_build_kernel<<<n_cols, 256, 0, s>>>(sigma_a, sigma_s, eta, n_mat, n_cols, n_r, dr, A); ::tsr::count_launch();
   FIT_CUDA(cudaGetLastError());
   const double tol = 1e-14;
   bool converged = false;
-  for (int sweep = 0; sweep < 60 && !converged; ++sweep) {
-    FIT_CUDA(cudaMemsetAsync(rot, 0, sizeof(unsigned), s));
-    for (int r = 0; r < n_cols - 1; ++r) {
-      jacobi_round_kernel<<<n_cols / 2, 256, 0, s>>>(A, n_cols, n_r, r, tol, rot);
+  // the whole solve in one cooperative launch (all n_cols / 2 blocks resident: the grid
+  // barrier between rounds needs it); one launch per round where that is not possible
+  FIT_CUDA(cudaMemsetAsync(rot, 0, sizeof(unsigned) * (kMaxSweeps + 4), s));
+  {
+    unsigned *bar = rot + kMaxSweeps, *status = rot + kMaxSweeps + 1;
+    int nc = n_cols, nr = n_r, ms = kMaxSweeps;
+    double tl = tol;
+    void *kargs[] = {&A, &nc, &nr, &tl, &ms, &rot, &bar, &status};
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->device);
+    cudaError_t le = coop ? cudaLaunchCooperativeKernel((const void *)jacobi_solve_kernel, dim3(n_cols / 2), dim3(256),
+                                                        kargs, 0, s)
+                          : cudaErrorNotSupported;
+    if (le == cudaSuccess) {
       ::tsr::count_launch();
+      unsigned h[3] = {0u, 0u, 0u};
+      FIT_CUDA(cudaMemcpyAsync(h, status, sizeof(unsigned) * 3, cudaMemcpyDeviceToHost, s));
+      FIT_CUDA(cudaStreamSynchronize(s));
+      if (h[0] & 1u) {
+        set_error("tsr_fit_pca_basis: a grid barrier of the Jacobi solve gave up its bounded wait");
+        return fail(TSR_ERR_TIMEOUT);
+      }
+      converged = h[2] != 0u;
+    } else {
+      (void)cudaGetLastError();   // clear the refused cooperative launch
+      for (int sweep = 0; sweep < kMaxSweeps && !converged; ++sweep) {
+        for (int r = 0; r < n_cols - 1; ++r) {
+          jacobi_round_kernel<<<n_cols / 2, 256, 0, s>>>(A, n_cols, n_r, r, tol, rot + sweep);
+          ::tsr::count_launch();
+        }
+        FIT_CUDA(cudaGetLastError());
+        unsigned h = 0;
+        FIT_CUDA(cudaMemcpyAsync(&h, rot + sweep, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        FIT_CUDA(cudaStreamSynchronize(s));
+        converged = (h == 0);
+      }
     }
-    FIT_CUDA(cudaGetLastError());
-    unsigned h = 0;
-    FIT_CUDA(cudaMemcpyAsync(&h, rot, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    FIT_CUDA(cudaStreamSynchronize(s));
-    converged = (h == 0);
   }
   if (!converged) {
-    set_error("tsr_fit_pca_basis: Jacobi SVD did not converge in 60 sweeps");
+    set_error("tsr_fit_pca_basis: Jacobi SVD did not converge in %d sweeps", kMaxSweeps);
     return fail(TSR_ERR_CUDA);
   }
   const int n_sv = std::min(n_mat, n_r);

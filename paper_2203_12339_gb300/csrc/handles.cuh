@@ -126,6 +126,12 @@ tsr_status spatial_inverse_transpose(int wavelet, const float *X, int rows, int 
 tsr_status wavelet_compress(const float *Mw, int K, int J, int nu, double p, tsr_compressed **out,
                             cudaStream_t s);
 tsr_status wavelet_compress_into(const float *Mw, tsr_compressed *c, cudaStream_t s);
+// Step 2 of n meshes whose columns of M start at M + offsets[b] (row stride offsets[n]): fill
+// existing top-p Haar handles, or create and fill them.  One launch per stage and 32 meshes.
+tsr_status haar_recompress_many(int n, const int64_t *offsets, const float *M, tsr_compressed *const *c,
+                                cudaStream_t s);
+tsr_status haar_compress_many(int n, const int64_t *offsets, const float *M, int K, int J, double p,
+                              tsr_compressed **out, cudaStream_t s);
 tsr_status wavelet_compress_energy(const float *Mw, int K, int J, int nu, double energy, tsr_compressed **out,
                                    cudaStream_t s);
 tsr_status relight(const tsr_compressed *c, int n_edit, const float *g, const float *l, float *B,

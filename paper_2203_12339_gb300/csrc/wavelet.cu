@@ -37,13 +37,11 @@ constexpr int HAAR_SEG_THREADS = 256;
 // approximations ping-pong in shared memory, the details of each level are final
 // and go straight to their global positions; the run's approximation goes to
 // A[row][d][seg] (or, for a whole chart, to Xw position 0 with the poles).
-__global__ void __launch_bounds__(1024) haar_forward_kernel(const float *__restrict__ X, int nu, int P, long long ldx,
-                                                           int NW, int seg_len, float *__restrict__ Xw,
-                                                           float *__restrict__ A) {
-  extern __shared__ float sh[];
+__device__ __forceinline__ void haar_forward_block(const float *__restrict__ X, int nu, int P, long long ldx, int NW,
+                                                   int seg_len, float *__restrict__ Xw, float *__restrict__ A, int seg,
+                                                   int d, int row, float *sh) {
   float *b0 = sh, *b1 = sh + seg_len;
   const int P2 = P * P, nseg = P2 / seg_len;
-  const int seg = blockIdx.x % nseg, d = (blockIdx.x / nseg) % 10, row = blockIdx.x / (nseg * 10);
   const float *x = X + (size_t)row * ldx + (size_t)d * nu * nu;
   float *out = Xw + (size_t)row * NW + (size_t)d * P2;
   for (int q = threadIdx.x; q < seg_len; q += blockDim.x) {
@@ -80,11 +78,20 @@ __global__ void __launch_bounds__(1024) haar_forward_kernel(const float *__restr
   }
 }
 
+__global__ void __launch_bounds__(1024) haar_forward_kernel(const float *__restrict__ X, int nu, int P, long long ldx,
+                                                           int NW, int seg_len, float *__restrict__ Xw,
+                                                           float *__restrict__ A) {
+  extern __shared__ float sh[];
+  const int nseg = P * P / seg_len;
+  haar_forward_block(X, nu, P, ldx, NW, seg_len, Xw, A, blockIdx.x % nseg, (blockIdx.x / nseg) % 10,
+                     blockIdx.x / (nseg * 10), sh);
+}
+
 // The levels above the runs: block per (row, chart) over its nseg approximations.
-__global__ void haar_forward_top_kernel(const float *__restrict__ X, const float *__restrict__ A, int nu, int P,
-                                        long long ldx, int NW, int nseg, float *__restrict__ Xw) {
+__device__ __forceinline__ void haar_forward_top_block(const float *__restrict__ X, const float *__restrict__ A, int nu,
+                                                       int P, long long ldx, int NW, int nseg, float *__restrict__ Xw,
+                                                       int d, int row) {
   __shared__ float b[2][HAAR_SEG];
-  const int d = blockIdx.x % 10, row = blockIdx.x / 10;
   const int P2 = P * P;
   float *out = Xw + (size_t)row * NW + (size_t)d * P2;
   for (int q = threadIdx.x; q < nseg; q += blockDim.x) b[0][q] = A[((size_t)row * 10 + d) * nseg + q];
@@ -108,6 +115,11 @@ __global__ void haar_forward_top_kernel(const float *__restrict__ X, const float
       Xw[(size_t)row * NW + 10 * (size_t)P2 + 1] = X[(size_t)row * ldx + 10 * (size_t)nu * nu + 1];
     }
   }
+}
+
+__global__ void haar_forward_top_kernel(const float *__restrict__ X, const float *__restrict__ A, int nu, int P,
+                                        long long ldx, int NW, int nseg, float *__restrict__ Xw) {
+  haar_forward_top_block(X, A, nu, P, ldx, NW, nseg, Xw, blockIdx.x % 10, blockIdx.x / 10);
 }
 
 // ---------------------------------------------------------------- Haar inverse
@@ -331,13 +343,12 @@ __device__ void keep_pass(const float *__restrict__ c, int n_coef, unsigned tau,
 // flight), then, in index order, the keep flags and the column list: every larger
 // value, and the first (n_keep - #larger) values equal to it.  Both poles are kept
 // and end the column list.
-__global__ void __launch_bounds__(SEL_NT) select_kernel(const float *__restrict__ Mw, int n_coef, int NW, int n_keep,
-                                                       uint8_t *__restrict__ keep, int32_t *__restrict__ cidx,
-                                                       float *__restrict__ cval) {
+__device__ __forceinline__ void select_block(const float *__restrict__ Mw, int n_coef, int NW, int n_keep,
+                                             uint8_t *__restrict__ keep, int32_t *__restrict__ cidx,
+                                             float *__restrict__ cval, int rowi) {
   __shared__ unsigned hist[256];
   __shared__ unsigned s_sel, s_cum, s_eq;
   __shared__ unsigned wsum[SEL_NT / 32];
-  const int rowi = blockIdx.x;
   const float *c = Mw + (size_t)rowi * NW;
   uint8_t *kp = keep + (size_t)rowi * NW;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -400,6 +411,12 @@ __global__ void __launch_bounds__(SEL_NT) select_kernel(const float *__restrict_
   // prefix = key of the n_keep-th largest; keep `remaining` of its n_eq equal keys (lowest index first)
   keep_pass(c, n_coef, prefix, remaining, remaining >= n_eq, n_keep, kp, cidx + (size_t)rowi * (n_keep + 2),
             cval + (size_t)rowi * (n_keep + 2), wsum);
+}
+
+__global__ void __launch_bounds__(SEL_NT) select_kernel(const float *__restrict__ Mw, int n_coef, int NW, int n_keep,
+                                                       uint8_t *__restrict__ keep, int32_t *__restrict__ cidx,
+                                                       float *__restrict__ cval) {
+  select_block(Mw, n_coef, NW, n_keep, keep, cidx, cval, blockIdx.x);
 }
 
 // Energy rule: per (k, j) row the smallest n >= 1 whose n largest |c| (ties: lower
@@ -586,11 +603,11 @@ __global__ void __launch_bounds__(SEL_NT) keep_energy_kernel(const float *__rest
 //         tile offset and a scan of the 32 row counts, the warp writes its entries
 //         (kj ascending within each row) and row_ptr.
 constexpr int ROW_TILE = 32;
-__global__ void __launch_bounds__(256) count_kernel(const uint8_t *__restrict__ keep, int KJ, int NW,
-                                                    int64_t *__restrict__ tsum) {
+__device__ __forceinline__ void count_block(const uint8_t *__restrict__ keep, int KJ, int NW,
+                                            int64_t *__restrict__ tsum, int tile) {
   __shared__ int part[8][ROW_TILE];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int w = blockIdx.x * ROW_TILE + lane;
+  const int w = tile * ROW_TILE + lane;
   int n = 0;
   if (w < NW)
     for (int kj = warp; kj < KJ; kj += 8) n += keep[(size_t)kj * NW + w];
@@ -602,12 +619,17 @@ __global__ void __launch_bounds__(256) count_kernel(const uint8_t *__restrict__ 
     for (int q = 0; q < 8; ++q) t += part[q][lane];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) tsum[blockIdx.x] = t;
+    if (lane == 0) tsum[tile] = t;
   }
 }
 
+__global__ void __launch_bounds__(256) count_kernel(const uint8_t *__restrict__ keep, int KJ, int NW,
+                                                    int64_t *__restrict__ tsum) {
+  count_block(keep, KJ, NW, tsum, blockIdx.x);
+}
+
 // exclusive scan of v[0..n) in place; v[n] = total (single block; n = tiles, a few thousand)
-__global__ void __launch_bounds__(1024) scan_kernel(int64_t *__restrict__ v, int n) {
+__device__ __forceinline__ void scan_block(int64_t *__restrict__ v, int n) {
   __shared__ int64_t warp_sum[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int per = (n + blockDim.x - 1) / blockDim.x;
@@ -639,14 +661,15 @@ __global__ void __launch_bounds__(1024) scan_kernel(int64_t *__restrict__ v, int
   if (threadIdx.x == blockDim.x - 1) v[n] = run;
 }
 
-__global__ void __launch_bounds__(256) fill_kernel(const float *__restrict__ Mw, const uint8_t *__restrict__ keep,
-                                                   int KJ, int NW, const int64_t *__restrict__ toff,
-                                                   int64_t *__restrict__ row_ptr, uint16_t *__restrict__ col,
-                                                   float *__restrict__ val) {
+__global__ void __launch_bounds__(1024) scan_kernel(int64_t *__restrict__ v, int n) { scan_block(v, n); }
+
+__device__ __forceinline__ void fill_block(const float *__restrict__ Mw, const uint8_t *__restrict__ keep, int KJ,
+                                           int NW, const int64_t *__restrict__ toff, int64_t *__restrict__ row_ptr,
+                                           uint16_t *__restrict__ col, float *__restrict__ val, int tile) {
   __shared__ int part[8][ROW_TILE];
   __shared__ int64_t rbase[ROW_TILE];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int w = blockIdx.x * ROW_TILE + lane;
+  const int w = tile * ROW_TILE + lane;
   const int kb = warp * KJ / 8, ke = (warp + 1) * KJ / 8;
   int n = 0;
   if (w < NW)
@@ -663,7 +686,7 @@ __global__ void __launch_bounds__(256) fill_kernel(const float *__restrict__ Mw,
       const int y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += y;
     }
-    const int64_t rb = toff[blockIdx.x] + (incl - t);
+    const int64_t rb = toff[tile] + (incl - t);
     rbase[lane] = rb;
     if (w < NW) row_ptr[w] = rb;
     if (w == NW - 1) row_ptr[NW] = rb + t;
@@ -679,6 +702,13 @@ __global__ void __launch_bounds__(256) fill_kernel(const float *__restrict__ Mw,
       ++p;
     }
   }
+}
+
+__global__ void __launch_bounds__(256) fill_kernel(const float *__restrict__ Mw, const uint8_t *__restrict__ keep,
+                                                   int KJ, int NW, const int64_t *__restrict__ toff,
+                                                   int64_t *__restrict__ row_ptr, uint16_t *__restrict__ col,
+                                                   float *__restrict__ val) {
+  fill_block(Mw, keep, KJ, NW, toff, row_ptr, col, val, blockIdx.x);
 }
 
 static int keep_count(double p, int n_coef) {
@@ -808,6 +838,179 @@ tsr_status wavelet_compress_energy(const float *Mw, int K, int J, int nu, double
   }
   *out = c;
   return TSR_OK;
+}
+
+
+// ---------------------------------------------------------------- Step 2 of many meshes
+// Haar analysis, top-p selection and CSR packing of up to TSR_CB_MAX meshes per launch of
+// each stage, from a descriptor table passed by value (no host copies: capturable in a
+// CUDA graph).  Mesh b's columns of the concatenated M start at X (row stride ldx); its
+// wavelet coefficients, keep flags and tile counts live in stream-ordered scratch.  Every
+// block does exactly what the per-mesh kernels do for the same (mesh, row, ...), so the
+// handles are bit-identical to compressing each mesh alone.
+constexpr int TSR_CB_MAX = 32;
+struct CompressMesh {
+  const float *X;
+  float *Mw, *A;
+  uint8_t *keep;
+  int64_t *tcnt;
+  int64_t *row_ptr;
+  uint16_t *col;
+  float *val;
+  int32_t *cidx;
+  float *cval;
+  int nu, P, NW, n_keep, seg_len, nseg, row_tiles;
+  int b_haar, b_top, b_tile;   // first block of the mesh in the Haar, top-level and row-tile launches
+};
+struct CompressBatch {
+  int n, KJ;
+  long long ldx;
+  CompressMesh m[TSR_CB_MAX];
+};
+
+// the mesh whose first block (field B) is the largest one <= blk
+#define TSR_CB_FIND(cb, field, blk)                                      \
+  ([&]() {                                                              \
+    int b_ = 0;                                                         \
+    while (b_ + 1 < (cb).n && (cb).m[b_ + 1].field <= (blk)) ++b_;      \
+    return b_;                                                          \
+  }())
+
+__global__ void __launch_bounds__(HAAR_SEG_THREADS) haar_forward_batched_kernel(const __grid_constant__ CompressBatch cb) {
+  extern __shared__ float sh[];
+  const int blk = blockIdx.x;
+  const int b = TSR_CB_FIND(cb, b_haar, blk);
+  const CompressMesh &m = cb.m[b];
+  const int local = blk - m.b_haar;
+  haar_forward_block(m.X, m.nu, m.P, cb.ldx, m.NW, m.seg_len, m.Mw, m.A, local % m.nseg, (local / m.nseg) % 10,
+                     local / (m.nseg * 10), sh);
+}
+
+__global__ void haar_forward_top_batched_kernel(const __grid_constant__ CompressBatch cb) {
+  const int blk = blockIdx.x;
+  const int b = TSR_CB_FIND(cb, b_top, blk);
+  const CompressMesh &m = cb.m[b];
+  const int local = blk - m.b_top;
+  haar_forward_top_block(m.X, m.A, m.nu, m.P, cb.ldx, m.NW, m.nseg, m.Mw, local % 10, local / 10);
+}
+
+__global__ void __launch_bounds__(SEL_NT) select_batched_kernel(const __grid_constant__ CompressBatch cb) {
+  const CompressMesh &m = cb.m[blockIdx.x / cb.KJ];
+  select_block(m.Mw, m.NW - 2, m.NW, m.n_keep, m.keep, m.cidx, m.cval, blockIdx.x % cb.KJ);
+}
+
+__global__ void __launch_bounds__(256) count_batched_kernel(const __grid_constant__ CompressBatch cb) {
+  const int b = TSR_CB_FIND(cb, b_tile, (int)blockIdx.x);
+  const CompressMesh &m = cb.m[b];
+  count_block(m.keep, cb.KJ, m.NW, m.tcnt, blockIdx.x - m.b_tile);
+}
+
+__global__ void __launch_bounds__(1024) scan_batched_kernel(const __grid_constant__ CompressBatch cb) {
+  scan_block(cb.m[blockIdx.x].tcnt, cb.m[blockIdx.x].row_tiles);
+}
+
+__global__ void __launch_bounds__(256) fill_batched_kernel(const __grid_constant__ CompressBatch cb) {
+  const int b = TSR_CB_FIND(cb, b_tile, (int)blockIdx.x);
+  const CompressMesh &m = cb.m[b];
+  fill_block(m.Mw, m.keep, cb.KJ, m.NW, m.tcnt, m.row_ptr, m.col, m.val, blockIdx.x - m.b_tile);
+}
+
+// Step 2 (Haar, top-p selection, packing) of n meshes into their existing top-p Haar handles
+// c[b] (K, J, nu and n_keep fixed); mesh b's columns of M start at M + offsets[b], row stride
+// offsets[n].  One launch per stage and group of TSR_CB_MAX meshes.
+tsr_status haar_recompress_many(int n, const int64_t *offsets, const float *M, tsr_compressed *const *c,
+                                cudaStream_t s) {
+  const long long ldx = offsets[n];
+  const int KJ = c[0]->K * c[0]->J;
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  for (int b0 = 0; b0 < n; b0 += TSR_CB_MAX) {
+    const int nb = std::min(TSR_CB_MAX, n - b0);
+    CompressBatch cb{};
+    cb.n = nb;
+    cb.KJ = KJ;
+    cb.ldx = ldx;
+    size_t bytes = 0;
+    int n_haar = 0, n_top = 0, n_tile = 0;
+    for (int q = 0; q < nb; ++q) {
+      const tsr_compressed *h = c[b0 + q];
+      CompressMesh &m = cb.m[q];
+      m.nu = h->nu;
+      m.P = h->P;
+      m.NW = h->n_rows;
+      m.n_keep = h->n_keep;
+      m.seg_len = std::min(m.P * m.P, HAAR_SEG);
+      m.nseg = m.P * m.P / m.seg_len;
+      m.row_tiles = (m.NW + ROW_TILE - 1) / ROW_TILE;
+      m.b_haar = n_haar;
+      m.b_top = n_top;
+      m.b_tile = n_tile;
+      n_haar += KJ * 10 * m.nseg;
+      n_top += m.nseg > 1 ? KJ * 10 : 0;
+      n_tile += m.row_tiles;
+      bytes += al(sizeof(float) * (size_t)KJ * m.NW) + al(sizeof(float) * (size_t)KJ * 10 * m.nseg) +
+               al((size_t)KJ * m.NW) + al(sizeof(int64_t) * (m.row_tiles + 1));
+    }
+    Scratch sc;
+    tsr_status st = sc.alloc(bytes, s);
+    if (st != TSR_OK) return st;
+    uint8_t *p = static_cast<uint8_t *>(sc.p);
+    for (int q = 0; q < nb; ++q) {
+      const tsr_compressed *h = c[b0 + q];
+      CompressMesh &m = cb.m[q];
+      m.X = M + offsets[b0 + q];
+      m.Mw = reinterpret_cast<float *>(p);
+      p += al(sizeof(float) * (size_t)KJ * m.NW);
+      m.A = reinterpret_cast<float *>(p);
+      p += al(sizeof(float) * (size_t)KJ * 10 * m.nseg);
+      m.keep = p;
+      p += al((size_t)KJ * m.NW);
+      m.tcnt = reinterpret_cast<int64_t *>(p);
+      p += al(sizeof(int64_t) * (m.row_tiles + 1));
+      m.row_ptr = h->row_ptr;
+      m.col = h->col;
+      m.val = h->val;
+      m.cidx = h->cidx;
+      m.cval = h->cval;
+    }
+    haar_forward_batched_kernel<<<n_haar, HAAR_SEG_THREADS, sizeof(float) * 2 * HAAR_SEG, s>>>(cb);
+    ::tsr::count_launch();
+    if (n_top > 0) {
+      haar_forward_top_batched_kernel<<<n_top, 256, 0, s>>>(cb);
+      ::tsr::count_launch();
+    }
+    select_batched_kernel<<<nb * KJ, SEL_NT, 0, s>>>(cb); ::tsr::count_launch();
+    count_batched_kernel<<<n_tile, 256, 0, s>>>(cb); ::tsr::count_launch();
+    scan_batched_kernel<<<nb, 1024, 0, s>>>(cb); ::tsr::count_launch();
+    fill_batched_kernel<<<n_tile, 256, 0, s>>>(cb); ::tsr::count_launch();
+    TSR_CUDA(cudaGetLastError());
+  }
+  return TSR_OK;
+}
+
+// The top-p Haar handles of n meshes: sized on the host (n_keep is fixed by p and the
+// chart size), then filled by haar_recompress_many.
+tsr_status haar_compress_many(int n, const int64_t *offsets, const float *M, int K, int J, double p,
+                              tsr_compressed **out, cudaStream_t s) {
+  for (int b = 0; b < n; ++b) out[b] = nullptr;
+  tsr_status st = TSR_OK;
+  for (int b = 0; b < n && st == TSR_OK; ++b) {
+    const long long nv = offsets[b + 1] - offsets[b];
+    int nu = 1;
+    while (10LL * nu * nu + 2 < nv) ++nu;
+    const int P = chart_side(nu), n_coef = 10 * P * P, n_keep = keep_count(p, n_coef);
+    st = compressed_alloc(K, J, nu, std::vector<int>(K * J, n_keep), &out[b]);
+    if (st == TSR_OK) {
+      out[b]->n_keep = n_keep;
+      out[b]->keep_rule = 0;
+    }
+  }
+  if (st == TSR_OK) st = haar_recompress_many(n, offsets, M, out, s);
+  if (st != TSR_OK)
+    for (int b = 0; b < n; ++b) {
+      tsr_compressed_destroy(out[b]);
+      out[b] = nullptr;
+    }
+  return st;
 }
 
 }  // namespace tsr
