@@ -768,6 +768,9 @@ static tsr_status compressed_alloc(int K, int J, int nu, const std::vector<int> 
   const size_t nnz4 = ((size_t)c->nnz + 3) & ~(size_t)3;
   if (e == cudaSuccess) e = cudaMalloc(&c->col, sizeof(uint16_t) * nnz4);
   if (e == cudaSuccess) e = cudaMalloc(&c->val, sizeof(float) * nnz4);
+  // the padding holds column 0 and value 0, so every entry of a group is a valid term
+  if (e == cudaSuccess && nnz4 > (size_t)c->nnz) e = cudaMemset(c->col + c->nnz, 0, sizeof(uint16_t) * (nnz4 - c->nnz));
+  if (e == cudaSuccess && nnz4 > (size_t)c->nnz) e = cudaMemset(c->val + c->nnz, 0, sizeof(float) * (nnz4 - c->nnz));
   if (e == cudaSuccess) e = cudaMalloc(&c->cidx, sizeof(int32_t) * c->nnz);
   if (e == cudaSuccess) e = cudaMalloc(&c->cval, sizeof(float) * c->nnz);
   if (e == cudaSuccess) e = cudaMalloc(&c->col_ptr, sizeof(int64_t) * (KJ + 1));

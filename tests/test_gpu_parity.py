@@ -508,6 +508,26 @@ def test_relight_one_edit_large_charts(torch_cuda, tsr, nu, K, J, p):
         assert _relight_err(B, B_ref) <= 2e-6, (E, _relight_err(B, B_ref))
 
 
+@pytest.mark.parametrize("p", [1.0, 0.6])
+def test_relight_dense_runs_many_windows(torch_cuda, tsr, p):
+    """Every (p = 1) or most coefficients kept at K = 16, J = 25 on 64^2-position charts: a run's rows hold
+    up to 1,023 x 400 entries, so the fused kernel cuts each run's entry stream into several head-bitmap
+    windows and chains rows across them.  One and two edits (3 and 6 vectors) and five edits (the
+    16 basis images + combine) against the oracle."""
+    torch = torch_cuda
+    nu, K, J = 64, 16, 25
+    comp, kept = _compressed_case(torch, tsr, nu, K, J, p, 64)
+    rng = np.random.default_rng(5)
+    light = rng.standard_normal(J).astype(np.float32)
+    for E in (1, 2, 5):
+        g = rng.standard_normal((E, 3, K)).astype(np.float32)
+        B = tsr.relight(comp, _dev(torch, g), _dev(torch, light)).cpu().numpy()
+        B_ref = O.relight(kept, nu, g.astype(np.float64), light.astype(np.float64))
+        assert _relight_err(B, B_ref) <= 2e-6, (E, _relight_err(B, B_ref))
+        Bm = tsr.relight_many([comp], _dev(torch, g[None]), _dev(torch, light))[0].cpu().numpy()
+        assert _relight_err(Bm, B_ref) <= 2e-6, (E, _relight_err(Bm, B_ref))
+
+
 def test_relight_many_uneven_copies(torch_cuda, tsr):
     """tsr_relight_many over uneven copies (1 to 40 vertices per chart side, Haar and CDF 9/7): every
     copy against the oracle's relight of its own kept coefficients, for 1, 2 and 3 edits (fused launch,
