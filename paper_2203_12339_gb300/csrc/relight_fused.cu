@@ -36,14 +36,15 @@
 namespace tsr {
 
 constexpr int RF_THREADS = 256;
-constexpr int RF_SEG = 1024;                               // Morton positions per run
-constexpr int RF_MAX_LGN = 4;                              // up to 16 runs per chart (P <= 128, the library's nu <= 128)
+constexpr int RF_LGSEG = 10;
+constexpr int RF_SEG = 1 << RF_LGSEG;                      // Morton positions per run
+constexpr int RF_MAX_LGN = 14 - RF_LGSEG;                  // log2 of the runs of a 128^2 chart (the library's nu <= 128)
 constexpr int RF_MAX_TOP = 1 + RF_MAX_LGN;                 // path rows
 constexpr int RF_MAX_ROWS = RF_MAX_TOP + RF_SEG - 1 + 2;   // + run details + the two poles
 constexpr int RF_BW = (RF_MAX_ROWS + 3) & ~3;              // b^w row stride in shared memory
 constexpr int RF_MAXC = 32;                                // copies per launch (kernel parameter space)
 constexpr int RF_WARPS = RF_THREADS / 32;
-__host__ __device__ constexpr int rf_units(int VV) { return VV <= 3 ? 4 : 8; }   // groups of 4 entries per lane unit
+__host__ __device__ constexpr int rf_units(int) { return 8; }   // groups of 4 entries per lane unit
 
 struct RelightCopy {
   const int64_t *row_ptr;
@@ -155,7 +156,7 @@ __device__ __forceinline__ void rf_fma(const float *lt, const float4 *gs4, unsig
 }
 
 template <int VV>
-__global__ void __launch_bounds__(RF_THREADS, VV <= 3 ? 4 : (VV <= 6 ? 3 : 2)) relight_fused_kernel(const __grid_constant__ RelightBatch bt, int K,
+__global__ void __launch_bounds__(RF_THREADS, VV <= 6 ? 3 : 2) relight_fused_kernel(const __grid_constant__ RelightBatch bt, int K,
                                                                   int J, unsigned m2J, const float *__restrict__ l) {
   constexpr int VQ = (VV + 3) / 4;   // float4s per c row
   constexpr bool XDYN = VV > 6;      // b^w in dynamic shared memory (above 24 KB)
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(RF_THREADS, VV <= 3 ? 4 : (VV <= 6 ? 3 : 2)) r
   const RelightCopy &cp = bt.c[ci];
   const int nu = cp.nu, lgP = cp.lgP;
   const int lgP2 = 2 * lgP, P2 = 1 << lgP2;
-  const int lgL = min(lgP2, 10), L = 1 << lgL;
+  const int lgL = min(lgP2, RF_LGSEG), L = 1 << lgL;
   const int lgn = lgP2 - lgL;   // log2(runs per chart)
   const int local = (int)blockIdx.x - cp.item0;
   const int d = local >> lgn, s = local & ((1 << lgn) - 1);
@@ -439,14 +440,15 @@ __global__ void __launch_bounds__(RF_THREADS, VV <= 3 ? 4 : (VV <= 6 ? 3 : 2)) r
   for (int it = tid; it < (nv << ls); it += RF_THREADS) {
     const int v = it >> ls, p = it & ((1 << ls) - 1);
     const float *xv = &bw[v][T - 1];   // the run's details by local position
+    // a right child takes a - d: d with its sign bit flipped (a + (-d) is a - d exactly)
     float a = bw[v][0];
     for (int lv = 0; lv < lgn; ++lv) {
-      const float dd = bw[v][1 + lv];
-      a = ((s >> (lgn - 1 - lv)) & 1) ? (a - dd) * rs2 : (a + dd) * rs2;
+      const unsigned flip = (unsigned)((s >> (lgn - 1 - lv)) & 1) << 31;
+      a = (a + __uint_as_float(__float_as_uint(bw[v][1 + lv]) ^ flip)) * rs2;
     }
     for (int ln = 0; ln < ls; ++ln) {   // approximation index p >> (ls - ln) at level 2^ln
-      const float dd = xv[(1 << ln) + (p >> (ls - ln))];
-      a = ((p >> (ls - ln - 1)) & 1) ? (a - dd) * rs2 : (a + dd) * rs2;
+      const unsigned flip = (unsigned)((p >> (ls - ln - 1)) & 1) << 31;
+      a = (a + __uint_as_float(__float_as_uint(xv[(1 << ln) + (p >> (ls - ln))]) ^ flip)) * rs2;
     }
     float o[16];
     o[0] = a;
@@ -465,11 +467,17 @@ __global__ void __launch_bounds__(RF_THREADS, VV <= 3 ? 4 : (VV <= 6 ? 3 : 2)) r
     const unsigned mb = (unsigned)p << D;   // first Morton position of the subtree in the run
     const int rb = r0 + (int)rf_compact(mb >> 1), cb = c0 + (int)rf_compact(mb);
     float *__restrict__ Bv = B + (size_t)v * N + (size_t)d * nu * nu;
+    if (D == 4 && rb + 3 < nu && cb + 3 < nu) {   // the whole 4 x 4 square inside the chart
+      float *__restrict__ Bs = Bv + rb * nu + cb;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      if (i < (1 << D)) {
-        const int r = rb + (((i >> 1) & 1) | ((i >> 2) & 2)), c = cb + ((i & 1) | ((i >> 1) & 2));
-        if (r < nu && c < nu) Bv[r * nu + c] = o[i];
+      for (int i = 0; i < 16; ++i) Bs[(((i >> 1) & 1) | ((i >> 2) & 2)) * nu + ((i & 1) | ((i >> 1) & 2))] = o[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        if (i < (1 << D)) {
+          const int r = rb + (((i >> 1) & 1) | ((i >> 2) & 2)), c = cb + ((i & 1) | ((i >> 1) & 2));
+          if (r < nu && c < nu) Bv[r * nu + c] = o[i];
+        }
       }
     }
   }
@@ -484,7 +492,7 @@ bool relight_fusable(const tsr_compressed *c, int n_edit) {
 }
 
 bool relight_fusable_basis(const tsr_compressed *c) {
-  return c->wavelet == 0 && c->P <= (1 << (RF_MAX_LGN / 2 + 5)) && c->nnz < (1ll << 31);
+  return c->wavelet == 0 && c->P <= (1 << ((RF_MAX_LGN + RF_LGSEG) / 2)) && c->nnz < (1ll << 31);
 }
 
 // Dynamic shared memory of relight_fused_kernel<VV>: b^w when VV > 6.

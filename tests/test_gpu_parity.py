@@ -511,9 +511,9 @@ def test_relight_one_edit_large_charts(torch_cuda, tsr, nu, K, J, p):
 @pytest.mark.parametrize("p", [1.0, 0.6])
 def test_relight_dense_runs_many_windows(torch_cuda, tsr, p):
     """Every (p = 1) or most coefficients kept at K = 16, J = 25 on 64^2-position charts: a run's rows hold
-    up to 1,023 x 400 entries, so the fused kernel cuts each run's entry stream into several head-bitmap
-    windows and chains rows across them.  One and two edits (3 and 6 vectors) and five edits (the
-    16 basis images + combine) against the oracle."""
+    up to 1,023 x 400 entries, so the fused kernel's rows take up to 13 lane units each, span warp steps
+    and cross the eight warp ranges, whose partial sums are chained.  One and two edits (3 and 6 vectors)
+    and five edits (the 16 basis images + combine) against the oracle."""
     torch = torch_cuda
     nu, K, J = 64, 16, 25
     comp, kept = _compressed_case(torch, tsr, nu, K, J, p, 64)
