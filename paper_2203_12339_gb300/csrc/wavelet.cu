@@ -33,58 +33,120 @@ constexpr int HAAR_SEG = 1024;
 constexpr int HAAR_SEG_THREADS = 256;
 
 // ---------------------------------------------------------------- Haar forward
-// Levels on positions [seg S, (seg+1) S) of chart d of `row` (S = seg_len): the
-// approximations ping-pong in shared memory, the details of each level are final
-// and go straight to their global positions; the run's approximation goes to
-// A[row][d][seg] (or, for a whole chart, to Xw position 0 with the poles).
-__device__ __forceinline__ void haar_forward_block(const float *__restrict__ X, int nu, int P, long long ldx, int NW,
-                                                   int seg_len, float *__restrict__ Xw, float *__restrict__ A, int seg,
-                                                   int d, int row, float *sh) {
-  float *b0 = sh, *b1 = sh + seg_len;
-  const int P2 = P * P, nseg = P2 / seg_len;
+// A problem is positions [seg S, (seg + 1) S) of chart d of a row (S = min(P^2, HAAR_SEG),
+// a power of 4).  A thread takes Q = min(16, S) consecutive Morton positions (a square of the
+// chart) and does the first log2 Q levels in registers; the next levels pair lanes of its
+// warp through shuffles; a problem wider than a warp (S = 1024) finishes its last level in
+// its first warp after one barrier.  Problems are packed HF_THREADS / (S / Q) to a logical
+// block, and a persistent grid loops over the logical blocks.  Each level maps the pair
+// (a, b) to (a + b) / sqrt2 and the detail (a - b) / sqrt2 (rounded adds and multiplies, no
+// contraction); details are final and go straight to their global positions; the problem's
+// approximation goes to A[row][d][seg] (or, for a whole chart, to Xw position 0, with the
+// poles).
+constexpr int HF_THREADS = 256;
+constexpr int HF_GRID = 2048;   // persistent grid (logical blocks beyond it loop)
+__host__ __device__ inline int hf_per_thread(int S) { return S < 16 ? S : 16; }
+__host__ __device__ inline int hf_problems_per_block(int S) { return HF_THREADS / (S / hf_per_thread(S)); }
+
+__device__ __forceinline__ void haar_forward_problems(const float *__restrict__ X, int nu, int P, long long ldx, int NW,
+                                                      int S, float *__restrict__ Xw, float *__restrict__ A, int p0,
+                                                      int n_prob, float *part) {
+  const float rs2 = 0.70710678118654752440f;
+  const int Q = hf_per_thread(S), T = S / Q;   // positions per thread, threads per problem
+  const int P2 = P * P, nseg = P2 / S;
+  const int slot = threadIdx.x / T, t = threadIdx.x - slot * T;
+  const int p = p0 + slot;
+  const bool act = p < n_prob;
+  const int seg = act ? p % nseg : 0, d = act ? (p / nseg) % 10 : 0, row = act ? p / (nseg * 10) : 0;
   const float *x = X + (size_t)row * ldx + (size_t)d * nu * nu;
   float *out = Xw + (size_t)row * NW + (size_t)d * P2;
-  for (int q = threadIdx.x; q < seg_len; q += blockDim.x) {
-    const unsigned m = (unsigned)(seg * seg_len + q);
-    const int r = (int)compact_bits(m >> 1), c = (int)compact_bits(m);
-    b0[q] = (r < nu && c < nu) ? x[r * nu + c] : 0.0f;
-  }
-  __syncthreads();
-  const float rs2 = 0.70710678118654752440f;
-  float *src = b0, *dst = b1;
-  int ng = P2;   // current length of the whole chart's approximation
-  for (int n = seg_len; n > 1; n >>= 1, ng >>= 1) {
-    const int h = n >> 1;
-    for (int t = threadIdx.x; t < h; t += blockDim.x) {
-      const float a = src[2 * t], b = src[2 * t + 1];
-      dst[t] = (a + b) * rs2;
-      out[(ng >> 1) + seg * h + t] = (a - b) * rs2;
+  float v[16];
+  {
+    const unsigned m0 = (unsigned)(seg * S + Q * t);
+    const int r0 = (int)compact_bits(m0 >> 1), c0 = (int)compact_bits(m0);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      v[i] = 0.0f;
+      const int r = r0 + (((i >> 1) & 1) | ((i >> 2) & 2)), c = c0 + ((i & 1) | ((i >> 1) & 2));
+      if (i < Q && act && r < nu && c < nu) v[i] = x[r * nu + c];
     }
-    __syncthreads();
-    float *tmp = src;
-    src = dst;
-    dst = tmp;
   }
-  if (threadIdx.x == 0) {
+  int n = S, ng = P2;   // the problem's and the whole chart's current approximation lengths
+#pragma unroll
+  for (int len = 16; len > 1; len >>= 1) {
+    if (len <= Q) {
+      const int h = len >> 1;
+      float dd[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (j < h) {
+          dd[j] = __fmul_rn(__fsub_rn(v[2 * j], v[2 * j + 1]), rs2);
+          v[j] = __fmul_rn(__fadd_rn(v[2 * j], v[2 * j + 1]), rs2);
+        }
+      }
+      if (act) {
+        float *o = out + (ng >> 1) + seg * (n >> 1) + h * t;   // h consecutive details, 8-byte aligned for h >= 2
+        if (h >= 2) {
+#pragma unroll
+          for (int j = 0; j < 8; j += 2)
+            if (j < h) *reinterpret_cast<float2 *>(o + j) = make_float2(dd[j], dd[j + 1]);
+        } else {
+          o[0] = dd[0];
+        }
+      }
+      n >>= 1;
+      ng >>= 1;
+    }
+  }
+  // thread t now holds approximation t of the problem's n = T
+  float a = v[0];
+  const int TW = T < 32 ? T : 32;
+  for (int w = 1; w < TW; w <<= 1) {
+    const float o = __shfl_down_sync(0xffffffffu, a, w);
+    if ((t & (2 * w - 1)) == 0) {
+      if (act) out[(ng >> 1) + seg * (n >> 1) + t / (2 * w)] = __fmul_rn(__fsub_rn(a, o), rs2);
+      a = __fmul_rn(__fadd_rn(a, o), rs2);
+    }
+    n >>= 1;
+    ng >>= 1;
+  }
+  if (T > 32) {   // uniform: W = T / 32 warps per problem, one value each
+    const int W = T / 32;
+    if ((t & 31) == 0) part[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (t < 32) {   // the problem's first warp
+      a = t < W ? part[(threadIdx.x >> 5) + t] : 0.0f;
+      for (int w = 1; w < W; w <<= 1) {
+        const float o = __shfl_down_sync(0xffffffffu, a, w);
+        if ((t & (2 * w - 1)) == 0 && t < W) {
+          if (act) out[(ng >> 1) + seg * (n >> 1) + t / (2 * w)] = __fmul_rn(__fsub_rn(a, o), rs2);
+          a = __fmul_rn(__fadd_rn(a, o), rs2);
+        }
+        n >>= 1;
+        ng >>= 1;
+      }
+    }
+    __syncthreads();   // part is reused by the next logical block
+  }
+  if (t == 0 && act) {
     if (nseg == 1) {
-      out[0] = src[0];
+      out[0] = a;
       if (d == 0) {
         Xw[(size_t)row * NW + 10 * (size_t)P2] = X[(size_t)row * ldx + 10 * (size_t)nu * nu];
         Xw[(size_t)row * NW + 10 * (size_t)P2 + 1] = X[(size_t)row * ldx + 10 * (size_t)nu * nu + 1];
       }
     } else {
-      A[((size_t)row * 10 + d) * nseg + seg] = src[0];
+      A[((size_t)row * 10 + d) * nseg + seg] = a;
     }
   }
 }
 
-__global__ void __launch_bounds__(1024) haar_forward_kernel(const float *__restrict__ X, int nu, int P, long long ldx,
-                                                           int NW, int seg_len, float *__restrict__ Xw,
-                                                           float *__restrict__ A) {
-  extern __shared__ float sh[];
-  const int nseg = P * P / seg_len;
-  haar_forward_block(X, nu, P, ldx, NW, seg_len, Xw, A, blockIdx.x % nseg, (blockIdx.x / nseg) % 10,
-                     blockIdx.x / (nseg * 10), sh);
+__global__ void __launch_bounds__(HF_THREADS) haar_forward_kernel(const float *__restrict__ X, int nu, int P,
+                                                                 long long ldx, int NW, int S, float *__restrict__ Xw,
+                                                                 float *__restrict__ A, int n_prob, int n_lb) {
+  __shared__ float part[HF_THREADS / 32];   // the warps' approximations (S = 1024)
+  for (int lb = blockIdx.x; lb < n_lb; lb += gridDim.x)
+    haar_forward_problems(X, nu, P, ldx, NW, S, Xw, A, lb * hf_problems_per_block(S), n_prob, part);
 }
 
 // The levels above the runs: block per (row, chart) over its nseg approximations.
@@ -192,20 +254,21 @@ tsr_status haar_forward(const float *X, int rows, int nu, float *Xw, cudaStream_
 tsr_status haar_forward_ld(const float *X, long long ldx, int rows, int nu, float *Xw, cudaStream_t s) {
   const int P = chart_side(nu), P2 = P * P;
   const int NW = 10 * P2 + 2;
-  if (P2 <= HAAR_SEG) {
-    const size_t smem = sizeof(float) * (size_t)P2 * 2;
-    haar_forward_kernel<<<rows * 10, haar_threads(P2), smem, s>>>(X, nu, P, ldx, NW, P2, Xw, nullptr);
+  const int S = std::min(P2, HAAR_SEG), nseg = P2 / S;
+  const int n_prob = rows * 10 * nseg, npb = hf_problems_per_block(S);
+  if (n_prob == 0) return TSR_OK;
+  const int n_lb = (n_prob + npb - 1) / npb, grid = std::min(n_lb, HF_GRID);
+  if (nseg == 1) {
+    haar_forward_kernel<<<grid, HF_THREADS, 0, s>>>(X, nu, P, ldx, NW, S, Xw, nullptr, n_prob, n_lb);
     ::tsr::count_launch();
     TSR_CUDA(cudaGetLastError());
     return TSR_OK;
   }
-  const int nseg = P2 / HAAR_SEG;
   Scratch as;
   tsr_status st = as.alloc(sizeof(float) * (size_t)rows * 10 * nseg, s);
   if (st != TSR_OK) return st;
   float *A = static_cast<float *>(as.p);
-  const size_t smem = sizeof(float) * HAAR_SEG * 2;
-  haar_forward_kernel<<<rows * 10 * nseg, HAAR_SEG_THREADS, smem, s>>>(X, nu, P, ldx, NW, HAAR_SEG, Xw, A);
+  haar_forward_kernel<<<grid, HF_THREADS, 0, s>>>(X, nu, P, ldx, NW, S, Xw, A, n_prob, n_lb);
   ::tsr::count_launch();
   haar_forward_top_kernel<<<rows * 10, 256, 0, s>>>(X, A, nu, P, ldx, NW, nseg, Xw); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
@@ -367,6 +430,7 @@ __device__ __forceinline__ void select_block(const float *__restrict__ Mw, int n
       for (int q = 0; q < 4; ++q) {
         const int w = base + q * SEL_NT + threadIdx.x;
         const bool in = (w < n_coef) && ((u[q] & mask) == prefix);
+        if (__ballot_sync(0xffffffffu, in) == 0u) continue;   // after the first digit few keys share the prefix
         const unsigned digit = in ? ((u[q] >> shift) & 255u) : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, digit);
         if (in && lane == __ffs(peers) - 1) atomicAdd(&hist[digit], (unsigned)__popc(peers));
@@ -413,10 +477,166 @@ __device__ __forceinline__ void select_block(const float *__restrict__ Mw, int n
             cval + (size_t)rowi * (n_keep + 2), wsum);
 }
 
+// The same selection for a row of at most SEL_WARP_MAX coefficients by one warp: the four
+// radix digits histogrammed in the warp's own 256 bins, the keep flags and the column list
+// placed by warp scans.  Same keys, same digits, same tie rule: the same keep set and list.
+#ifndef TSR_SEL_WARP_MAX
+#define TSR_SEL_WARP_MAX (10 * 256)
+#endif
+constexpr int SEL_WARP_MAX = TSR_SEL_WARP_MAX;
+__device__ __forceinline__ unsigned warp_excl_scan(unsigned x, unsigned &total) {
+  const int lane = threadIdx.x & 31;
+  unsigned incl = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  total = __shfl_sync(0xffffffffu, incl, 31);
+  return incl - x;
+}
+
+__device__ void select_warp(const float *__restrict__ c, int n_coef, int n_keep, uint8_t *__restrict__ kp,
+                            int32_t *__restrict__ ci, float *__restrict__ cv, unsigned *hist) {
+  const int lane = threadIdx.x & 31;
+  unsigned prefix = 0, mask = 0, remaining = (unsigned)n_keep, n_eq = 0;
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int q = lane; q < 256; q += 32) hist[q] = 0;
+    __syncwarp();
+    for (int base = 0; base < n_coef; base += 4 * 32) {
+      unsigned u[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int w = base + q * 32 + lane;
+        u[q] = (w < n_coef) ? (__float_as_uint(c[w]) & 0x7FFFFFFFu) : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int w = base + q * 32 + lane;
+        const bool in = (w < n_coef) && ((u[q] & mask) == prefix);
+        if (__ballot_sync(0xffffffffu, in) == 0u) continue;
+        const unsigned digit = in ? ((u[q] >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, digit);
+        if (in && lane == __ffs(peers) - 1) atomicAdd(&hist[digit], (unsigned)__popc(peers));
+      }
+    }
+    __syncwarp();
+    // lane l holds digits 255 - 8 l down to 248 - 8 l; the digit where the running count
+    // from the top reaches `remaining`
+    unsigned h[8], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      h[q] = hist[255 - 8 * lane - q];
+      sum += h[q];
+    }
+    unsigned incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const unsigned hit = __ballot_sync(0xffffffffu, incl >= remaining);
+    const int ldr = __ffs(hit) - 1;
+    unsigned sel = 0, cum = incl - sum, eq = 0;
+    {
+      int q = 0;
+      for (; q < 7; ++q) {
+        if (cum + h[q] >= remaining) break;
+        cum += h[q];
+      }
+      sel = (unsigned)(255 - 8 * lane - q);
+      eq = h[q];
+    }
+    sel = __shfl_sync(0xffffffffu, sel, ldr);
+    cum = __shfl_sync(0xffffffffu, cum, ldr);
+    eq = __shfl_sync(0xffffffffu, eq, ldr);
+    remaining -= cum;
+    prefix |= sel << shift;
+    mask |= 255u << shift;
+    n_eq = eq;
+    __syncwarp();
+  }
+  // keep flags and column list in index order: chunks of 256 coefficients, 8 per lane
+  const unsigned tau = prefix;
+  const bool all_eq = remaining >= n_eq;
+  unsigned written = 0, eq_seen = 0;
+  for (int base = 0; base < n_coef; base += 8 * 32) {
+    const int w0 = base + 8 * lane;
+    float v[8];
+    unsigned u[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      v[q] = (w0 + q < n_coef) ? c[w0 + q] : 0.f;
+      u[q] = __float_as_uint(v[q]) & 0x7FFFFFFFu;
+    }
+    unsigned er = 0, eq_tot = 0;
+    if (!all_eq) {
+      unsigned neq = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) neq += (w0 + q < n_coef && u[q] == tau) ? 1u : 0u;
+      er = eq_seen + warp_excl_scan(neq, eq_tot);
+    }
+    unsigned kmask = 0, nk = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      bool k = false;
+      if (w0 + q < n_coef) {
+        if (u[q] > tau) {
+          k = true;
+        } else if (u[q] == tau) {
+          k = all_eq || er < remaining;
+          ++er;
+        }
+      }
+      kmask |= (k ? 1u : 0u) << q;
+      nk += k ? 1u : 0u;
+    }
+    unsigned k_tot;
+    unsigned pos = written + warp_excl_scan(nk, k_tot);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (w0 + q < n_coef) kp[w0 + q] = (uint8_t)((kmask >> q) & 1u);
+      if (((kmask >> q) & 1u) && pos < (unsigned)n_keep) {
+        ci[pos] = w0 + q;
+        cv[pos] = v[q];
+        ++pos;
+      }
+    }
+    written += k_tot;
+    eq_seen += eq_tot;
+  }
+  if (lane == 0) {
+    kp[n_coef] = 1;
+    kp[n_coef + 1] = 1;
+    ci[n_keep] = n_coef;
+    cv[n_keep] = c[n_coef];
+    ci[n_keep + 1] = n_coef + 1;
+    cv[n_keep + 1] = c[n_coef + 1];
+  }
+}
+
+// Rows per select block: SEL_NT / 32 rows by warps when the row has at most SEL_WARP_MAX
+// coefficients, else one row by the whole block.
+__host__ __device__ inline int sel_rows_per_block(int n_coef) { return n_coef <= SEL_WARP_MAX ? SEL_NT / 32 : 1; }
+
+__device__ __forceinline__ void select_rows(const float *__restrict__ Mw, int n_coef, int NW, int n_keep, int rows,
+                                            uint8_t *__restrict__ keep, int32_t *__restrict__ cidx,
+                                            float *__restrict__ cval, int blk, unsigned (*whist)[256]) {
+  if (n_coef <= SEL_WARP_MAX) {
+    const int warp = threadIdx.x >> 5, rowi = blk * (SEL_NT / 32) + warp;
+    if (rowi < rows)
+      select_warp(Mw + (size_t)rowi * NW, n_coef, n_keep, keep + (size_t)rowi * NW, cidx + (size_t)rowi * (n_keep + 2),
+                  cval + (size_t)rowi * (n_keep + 2), whist[warp]);
+  } else {
+    select_block(Mw, n_coef, NW, n_keep, keep, cidx, cval, blk);
+  }
+}
+
 __global__ void __launch_bounds__(SEL_NT) select_kernel(const float *__restrict__ Mw, int n_coef, int NW, int n_keep,
-                                                       uint8_t *__restrict__ keep, int32_t *__restrict__ cidx,
-                                                       float *__restrict__ cval) {
-  select_block(Mw, n_coef, NW, n_keep, keep, cidx, cval, blockIdx.x);
+                                                       int rows, uint8_t *__restrict__ keep,
+                                                       int32_t *__restrict__ cidx, float *__restrict__ cval) {
+  __shared__ unsigned whist[SEL_NT / 32][256];
+  select_rows(Mw, n_coef, NW, n_keep, rows, keep, cidx, cval, blockIdx.x, whist);
 }
 
 // Energy rule: per (k, j) row the smallest n >= 1 whose n largest |c| (ties: lower
@@ -744,7 +964,9 @@ tsr_status wavelet_compress_into(const float *Mw, tsr_compressed *c, cudaStream_
   tsr_status st = keep_s.alloc((size_t)KJ * NW, s);
   if (st != TSR_OK) return st;
   uint8_t *keep = static_cast<uint8_t *>(keep_s.p);
-  select_kernel<<<KJ, SEL_NT, 0, s>>>(Mw, n_coef, NW, c->n_keep, keep, c->cidx, c->cval); ::tsr::count_launch();
+  const int rpb = sel_rows_per_block(n_coef);
+  select_kernel<<<(KJ + rpb - 1) / rpb, SEL_NT, 0, s>>>(Mw, n_coef, NW, c->n_keep, KJ, keep, c->cidx, c->cval);
+  ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
   return csr_from_keep(Mw, keep, c, s);
 }
@@ -863,7 +1085,7 @@ struct CompressMesh {
   int32_t *cidx;
   float *cval;
   int nu, P, NW, n_keep, seg_len, nseg, row_tiles;
-  int b_haar, b_top, b_tile;   // first block of the mesh in the Haar, top-level and row-tile launches
+  int b_haar, b_top, b_sel, b_tile;   // first block of the mesh in the Haar, top-level, selection and row-tile launches
 };
 struct CompressBatch {
   int n, KJ;
@@ -879,14 +1101,15 @@ struct CompressBatch {
     return b_;                                                          \
   }())
 
-__global__ void __launch_bounds__(HAAR_SEG_THREADS) haar_forward_batched_kernel(const __grid_constant__ CompressBatch cb) {
-  extern __shared__ float sh[];
-  const int blk = blockIdx.x;
-  const int b = TSR_CB_FIND(cb, b_haar, blk);
-  const CompressMesh &m = cb.m[b];
-  const int local = blk - m.b_haar;
-  haar_forward_block(m.X, m.nu, m.P, cb.ldx, m.NW, m.seg_len, m.Mw, m.A, local % m.nseg, (local / m.nseg) % 10,
-                     local / (m.nseg * 10), sh);
+__global__ void __launch_bounds__(HF_THREADS) haar_forward_batched_kernel(const __grid_constant__ CompressBatch cb,
+                                                                         int n_lb) {
+  __shared__ float part[HF_THREADS / 32];
+  for (int lb = blockIdx.x; lb < n_lb; lb += gridDim.x) {
+    const int b = TSR_CB_FIND(cb, b_haar, lb);
+    const CompressMesh &m = cb.m[b];
+    haar_forward_problems(m.X, m.nu, m.P, cb.ldx, m.NW, m.seg_len, m.Mw, m.A,
+                          (lb - m.b_haar) * hf_problems_per_block(m.seg_len), cb.KJ * 10 * m.nseg, part);
+  }
 }
 
 __global__ void haar_forward_top_batched_kernel(const __grid_constant__ CompressBatch cb) {
@@ -898,8 +1121,10 @@ __global__ void haar_forward_top_batched_kernel(const __grid_constant__ Compress
 }
 
 __global__ void __launch_bounds__(SEL_NT) select_batched_kernel(const __grid_constant__ CompressBatch cb) {
-  const CompressMesh &m = cb.m[blockIdx.x / cb.KJ];
-  select_block(m.Mw, m.NW - 2, m.NW, m.n_keep, m.keep, m.cidx, m.cval, blockIdx.x % cb.KJ);
+  __shared__ unsigned whist[SEL_NT / 32][256];
+  const int b = TSR_CB_FIND(cb, b_sel, (int)blockIdx.x);
+  const CompressMesh &m = cb.m[b];
+  select_rows(m.Mw, m.NW - 2, m.NW, m.n_keep, cb.KJ, m.keep, m.cidx, m.cval, blockIdx.x - m.b_sel, whist);
 }
 
 __global__ void __launch_bounds__(256) count_batched_kernel(const __grid_constant__ CompressBatch cb) {
@@ -933,7 +1158,7 @@ tsr_status haar_recompress_many(int n, const int64_t *offsets, const float *M, t
     cb.KJ = KJ;
     cb.ldx = ldx;
     size_t bytes = 0;
-    int n_haar = 0, n_top = 0, n_tile = 0;
+    int n_haar = 0, n_top = 0, n_sel = 0, n_tile = 0;
     for (int q = 0; q < nb; ++q) {
       const tsr_compressed *h = c[b0 + q];
       CompressMesh &m = cb.m[q];
@@ -946,10 +1171,12 @@ tsr_status haar_recompress_many(int n, const int64_t *offsets, const float *M, t
       m.row_tiles = (m.NW + ROW_TILE - 1) / ROW_TILE;
       m.b_haar = n_haar;
       m.b_top = n_top;
+      m.b_sel = n_sel;
       m.b_tile = n_tile;
-      n_haar += KJ * 10 * m.nseg;
+      n_haar += (KJ * 10 * m.nseg + hf_problems_per_block(m.seg_len) - 1) / hf_problems_per_block(m.seg_len);
       n_top += m.nseg > 1 ? KJ * 10 : 0;
       n_tile += m.row_tiles;
+      n_sel += (KJ + sel_rows_per_block(m.NW - 2) - 1) / sel_rows_per_block(m.NW - 2);
       bytes += al(sizeof(float) * (size_t)KJ * m.NW) + al(sizeof(float) * (size_t)KJ * 10 * m.nseg) +
                al((size_t)KJ * m.NW) + al(sizeof(int64_t) * (m.row_tiles + 1));
     }
@@ -975,13 +1202,13 @@ tsr_status haar_recompress_many(int n, const int64_t *offsets, const float *M, t
       m.cidx = h->cidx;
       m.cval = h->cval;
     }
-    haar_forward_batched_kernel<<<n_haar, HAAR_SEG_THREADS, sizeof(float) * 2 * HAAR_SEG, s>>>(cb);
+    haar_forward_batched_kernel<<<std::min(n_haar, HF_GRID), HF_THREADS, 0, s>>>(cb, n_haar);
     ::tsr::count_launch();
     if (n_top > 0) {
       haar_forward_top_batched_kernel<<<n_top, 256, 0, s>>>(cb);
       ::tsr::count_launch();
     }
-    select_batched_kernel<<<nb * KJ, SEL_NT, 0, s>>>(cb); ::tsr::count_launch();
+    select_batched_kernel<<<n_sel, SEL_NT, 0, s>>>(cb); ::tsr::count_launch();
     count_batched_kernel<<<n_tile, 256, 0, s>>>(cb); ::tsr::count_launch();
     scan_batched_kernel<<<nb, 1024, 0, s>>>(cb); ::tsr::count_launch();
     fill_batched_kernel<<<n_tile, 256, 0, s>>>(cb); ::tsr::count_launch();
