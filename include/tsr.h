@@ -135,7 +135,7 @@ tsr_status tsr_fault_inject(int kind, int n);
  * tsr_basis_info: K, n_r and r_max of a handle (host out-pointers, any may be NULL).
  * tsr_basis_far_series: the far-field series the BF16 transfer evaluates
  *   instead of the table (Section 3, Eq. 6-7; see tsr_precompute_transfer):
- *   *rel_err = max_k max over r in [3/40 r_max, r_max] of
+ *   *rel_err = max_k max over r in [r_max / 16, r_max] of
  *   |sum_{p<12} c_kp T_p(x(r)) - r^2 f_k(r)| / max_r |r^2 f_k(r)|, computed on the
  *   device when the handle was made; *used = 1 when rel_err <= 2e-3 (the BF16
  *   transfer then uses the series, else the table).  Out-pointers may be NULL.
@@ -186,11 +186,11 @@ tsr_status tsr_project_material_backward(const tsr_basis *basis, int n, const do
  * Precisions:
  *   TSR_FP32   CUDA cores, FP32 table of f_k, Kahan-compensated sums.
  *   TSR_BF16   tensor cores (BF16 x BF16 -> FP32) for the far pairs, those with
- *              r^2 >= r_e^2, r_e = max(3/40 r_max, 2 h), h^2 = sum(A)/N; the near
+ *              r^2 >= r_e^2, r_e = max(r_max / 16, 2 h), h^2 = sum(A)/N; the near
  *              pairs r^2 < r_e^2 (the self pair among them) are summed exactly in
  *              FP32 and added.  The far kernel values come from the 12-term
  *              series f_k(r) = sum_p c_kp T_p(x) / r^2 (x linear in log r on
- *              [3/40 r_max, r_max]) when tsr_basis_far_series reports it accurate,
+ *              [r_max / 16, r_max]) when tsr_basis_far_series reports it accurate,
  *              else from the BF16 table.
  *   TSR_BF16X3 split BF16 (hi + lo of both operands, three products) for every
  *              pair from the table, the self pair replaced in FP32.

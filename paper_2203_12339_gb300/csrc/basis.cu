@@ -350,8 +350,8 @@ tsr_status basis_build_tables(tsr_basis *b, cudaStream_t s) {
   const int n = (b->n_r + 1) * b->KP;
   build_tables_kernel<<<(n + 255) / 256, 256, 0, s>>>(b->f64, b->K, b->KP, b->n_r, b->tab32, b->tab16); ::tsr::count_launch();
   TSR_CUDA(cudaGetLastError());
-  // far-field series on [r_near, r_max], r_near = 3/40 r_max
-  b->r_near = 0.075 * b->r_max;
+  // far-field series on [r_near, r_max], r_near = r_max / 16 (2.5 mm at r_max = 40 mm)
+  b->r_near = 0.0625 * b->r_max;
   const double lo = std::log(b->r_near), hi = std::log(b->r_max);
   b->x_alpha = (float)(std::log(2.0) / (hi - lo));
   b->x_beta = (float)(-1.0 - 2.0 * lo / (hi - lo));

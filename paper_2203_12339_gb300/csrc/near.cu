@@ -7,7 +7,7 @@
 // here in FP32, with the FP32 table of f_k and T'[j][i] = A_i T[j][i] in FP32:
 //     M[k][j][o] += sum_{i : r_oi^2 < r_e^2, r_oi^2 <= r_max^2} A_i f_k(r_oi) T[j][i],
 // r_e = max(r_floor, 2 h), h^2 = (sum_i A_i) / N the mean cell area of the mesh
-// (r_floor is the lower end of the far-field series, 3/40 r_max).  The split is
+// (r_floor is the lower end of the far-field series, r_max / 16).  The split is
 // decided on the FP32 squared distance of the definition (pair_r2), computed the
 // same way on both sides, so every pair is counted exactly once.
 //

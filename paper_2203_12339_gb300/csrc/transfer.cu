@@ -507,6 +507,37 @@ __device__ __forceinline__ float fast_lg2(float x) {
   return y;
 }
 
+// Two FP32 lanes per instruction (add/sub/mul/fma .rn.f32x2): each lane rounds exactly as
+// the scalar instruction, so results are bit-identical to the scalar code.
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
 // Decodes unit u.  One mesh: u = tile * S + split, stages over all records (or
 // over the tile's near-chunk list); batched: the unit table.
 __device__ __forceinline__ Unit decode_unit(int u, int S, int SPT, int N, const int4 *units, const int *mesh_N,
@@ -785,6 +816,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
         tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(C::ACC_COLS + ih * NWD);
     const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
     const float r2max = args.r2max, xa_alpha = args.x_alpha, xa_beta = args.x_beta;
+    const uint64_t alpha2 = f2_pack(xa_alpha, xa_alpha), beta2 = f2_pack(xa_beta, xa_beta);
     // Ring state of this group's steps (steps grp, grp + CONC, ...): A slot sa (phase pa),
     // record slot sr (phase pr); `own` counts down to this group's next step.
     int sa = grp % NS, sr = grp % C::NR, own = grp;
@@ -814,6 +846,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
       const float xo = o_ok ? pos_m[o] : 0.f;
       const float yo = o_ok ? pos_m[stride + o] : 0.f;
       const float zo = o_ok ? pos_m[2 * stride + o] : 0.f;
+      const uint64_t xo2 = f2_pack(xo, xo), yo2 = f2_pack(yo, yo), zo2 = f2_pack(zo, zo);
       const float rlo2 = args.rn2 ? args.rn2[un.mesh] : 0.f;   // below: the exact near field
       bool ok = true;
       int seg_pos = 0, seg_count = 0;
@@ -837,17 +870,29 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
                         za[4] = {zs.x, zs.y, zs.z, zs.w};
             float sv[4], xsv[4], x2v[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float r2 = pair_r2(xo, yo, zo, xa[q], ya[q], za[q]);
-              const bool far = r2 >= rlo2 && r2 <= r2max;
-              // lg2 and rcp run on every pair (no branch); a pair outside the far field
-              // gets s = 0, which zeroes all of its terms whatever x is
-              const float rf = far ? r2 : 1.f;
-              const float lg = fast_lg2(rf), rc = rcp_approx(rf);
-              const float x = fmaf(xa_alpha, lg, xa_beta);
-              sv[q] = far ? rc : 0.f;
-              xsv[q] = x * sv[q];
-              x2v[q] = x + x;
+            for (int e2 = 0; e2 < 2; ++e2) {   // two i per packed instruction, as pair_r2 rounds
+              const int q0 = 2 * e2;
+              const uint64_t dx = f2_sub(xo2, f2_pack(xa[q0], xa[q0 + 1]));
+              const uint64_t dy = f2_sub(yo2, f2_pack(ya[q0], ya[q0 + 1]));
+              const uint64_t dz = f2_sub(zo2, f2_pack(za[q0], za[q0 + 1]));
+              float r2[2];
+              f2_unpack(f2_add(f2_add(f2_mul(dx, dx), f2_mul(dy, dy)), f2_mul(dz, dz)), r2[0], r2[1]);
+              bool far[2];
+              float lg[2], rc[2];
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                far[e] = r2[e] >= rlo2 && r2[e] <= r2max;
+                // lg2 and rcp run on every pair (no branch); a pair outside the far field
+                // gets s = 0, which zeroes all of its terms whatever x is
+                const float rf = far[e] ? r2[e] : 1.f;
+                lg[e] = fast_lg2(rf);
+                rc[e] = rcp_approx(rf);
+              }
+              const uint64_t x = f2_fma(alpha2, f2_pack(lg[0], lg[1]), beta2);
+              const uint64_t s2 = f2_pack(far[0] ? rc[0] : 0.f, far[1] ? rc[1] : 0.f);
+              f2_unpack(s2, sv[q0], sv[q0 + 1]);
+              f2_unpack(f2_mul(x, s2), xsv[q0], xsv[q0 + 1]);
+              f2_unpack(f2_add(x, x), x2v[q0], x2v[q0 + 1]);
             }
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
