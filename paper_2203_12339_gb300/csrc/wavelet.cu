@@ -430,7 +430,6 @@ __device__ __forceinline__ void select_block(const float *__restrict__ Mw, int n
       for (int q = 0; q < 4; ++q) {
         const int w = base + q * SEL_NT + threadIdx.x;
         const bool in = (w < n_coef) && ((u[q] & mask) == prefix);
-        if (__ballot_sync(0xffffffffu, in) == 0u) continue;   // after the first digit few keys share the prefix
         const unsigned digit = in ? ((u[q] >> shift) & 255u) : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, digit);
         if (in && lane == __ffs(peers) - 1) atomicAdd(&hist[digit], (unsigned)__popc(peers));
