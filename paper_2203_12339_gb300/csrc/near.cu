@@ -12,9 +12,9 @@
 // same way on both sides, so every pair is counted exactly once.
 //
 // GB300 layout: vertices are Morton-sorted (mesh index above the 30 Morton bits for
-// batched meshes), so 128 consecutive sorted vertices form a compact patch ("tile")
-// and 16 form a compact "chunk".  One block per half tile (64 output rows x the
-// basis pairs) scans the chunk boxes of its mesh range, keeps the chunks whose box
+// batched meshes), so NEAR_ROWS consecutive sorted vertices form a compact patch
+// ("tile") and 16 form a compact "chunk".  One block per tile (NEAR_ROWS output rows x
+// the basis pairs) scans the chunk boxes of its mesh range, keeps the chunks whose box
 // is within r_e of the tile box, stages their positions and T' in shared memory
 // and accumulates two bases x J products per thread; results are added to M at the
 // rows' original indices.  Everything is deterministic (fixed orders, no atomics).
@@ -204,11 +204,18 @@ __global__ void near_box_kernel(const float *__restrict__ pos_s, long long np, l
   }
 }
 
-constexpr int NEAR_ROWS = 64;     // output rows per block
+#ifndef TSR_NEAR_ROWS
+#define TSR_NEAR_ROWS 32
+#endif
+constexpr int NEAR_ROWS = TSR_NEAR_ROWS;   // output rows per block (a divisor of 128)
 constexpr int NEAR_SCAN = 256;    // chunk boxes tested per pass
-constexpr int NEAR_BATCH = 4;     // listed chunks staged per barrier (64 candidates)
+#ifndef TSR_NEAR_BATCH
+#define TSR_NEAR_BATCH 12
+#endif
+constexpr int NEAR_BATCH = TSR_NEAR_BATCH;   // listed chunks staged per barrier (16 candidates each)
 
-// One block per 64 sorted output rows.  Per batch of up to 64 staged candidates i:
+// One block per NEAR_ROWS sorted output rows (two or more blocks per SM interleave their
+// phases).  Per batch of up to 16 NEAR_BATCH staged candidates i:
 //  phase A: the block tests every (row, i) pair once (a warp covers 32 consecutive i of
 //           one row) and records the near pairs as bit masks plus x = r / dr;
 //  phase B: thread (row, kg) owns bases 2 kg, 2 kg + 1 and walks its row's set bits in
@@ -220,7 +227,7 @@ __global__ void __launch_bounds__(512) near_field_kernel(
     const float *__restrict__ chunk_box, int n_mesh, const long long *__restrict__ voff,
     const float *__restrict__ rn2, const float4 *__restrict__ tab, int KG, int n_r, float inv_dr, float r2max,
     int K, int J, float *__restrict__ M, long long stride) {
-  constexpr int NC = NEAR_BATCH * 16;   // candidates per batch (64)
+  constexpr int NC = NEAR_BATCH * 16;   // candidates per batch
   __shared__ __align__(16) float sT[NC * JP];
   __shared__ float sx[NC], sy[NC], sz[NC];
   __shared__ int sm[NC];
@@ -233,7 +240,7 @@ __global__ void __launch_bounds__(512) near_field_kernel(
   __shared__ float s_tb[6];
   __shared__ int s_range[2];
   __shared__ float s_rn2m;
-  const int tile = blockIdx.x >> 1;   // 128-row tile of the sorted order
+  const int tile = blockIdx.x;   // the block's rows of the sorted order, with their box
   const int kg = threadIdx.x % KG;
   const int ol = threadIdx.x / KG;
   const long long os = (long long)blockIdx.x * NEAR_ROWS + ol;
@@ -250,7 +257,7 @@ __global__ void __launch_bounds__(512) near_field_kernel(
   }
   if (threadIdx.x == 0) {
     // meshes of the tile's first and last rows; the chunks of those meshes (sorted blocks)
-    const long long t0 = (long long)tile * 128, t1 = min(total, t0 + 128) - 1;
+    const long long t0 = (long long)tile * NEAR_ROWS, t1 = min(total, t0 + NEAR_ROWS) - 1;
     const int m0 = mesh_s[t0], m1 = mesh_s[t1];
     const long long c0 = (n_mesh > 1 ? voff[m0] : 0) / 16;
     const long long c1 = ((n_mesh > 1 ? voff[m1 + 1] : total) + 15) / 16;
@@ -375,7 +382,7 @@ tsr_status near_setup(NearField &nf, const tsr_basis *b, int n_mesh, const long 
   nf.J = J;
   nf.JP = (J + 3) & ~3;
   nf.np = (total + 127) / 128 * 128;
-  nf.n_tiles = (int)(nf.np / 128);
+  nf.n_tiles = (int)(nf.np / NEAR_ROWS);   // row blocks of the near-field kernel
   nf.n_chunks = (int)(nf.np / 16);
   size_t sort_bytes = 0;
   TSR_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, (unsigned long long *)nullptr,
@@ -427,7 +434,8 @@ tsr_status near_setup(NearField &nf, const tsr_basis *b, int n_mesh, const long 
                                                                       nf.JP, n_mesh, d_voff, nf.pos_s, nf.tq,
                                                                       nf.mesh_s);
   ::tsr::count_launch();
-  near_box_kernel<<<(nf.n_tiles + 127) / 128, 128, 0, s>>>(nf.pos_s, nf.np, total, 128, nf.n_tiles, nf.tile_box);
+  near_box_kernel<<<(nf.n_tiles + 127) / 128, 128, 0, s>>>(nf.pos_s, nf.np, total, NEAR_ROWS, nf.n_tiles,
+                                                          nf.tile_box);
   ::tsr::count_launch();
   near_box_kernel<<<(nf.n_chunks + 127) / 128, 128, 0, s>>>(nf.pos_s, nf.np, total, 16, nf.n_chunks, nf.chunk_box);
   ::tsr::count_launch();
@@ -441,7 +449,7 @@ static void launch_near(const NearField &nf, const tsr_basis *b, float *M, long 
   const int threads = NEAR_ROWS * KG;
   const float inv_dr = static_cast<float>((b->n_r - 1) / b->r_max);
   const float r2max = static_cast<float>(b->r_max * b->r_max);
-  near_field_kernel<JP><<<2 * nf.n_tiles, threads, 0, s>>>(
+  near_field_kernel<JP><<<nf.n_tiles, threads, 0, s>>>(
       nf.pos_s, nf.tq, nf.mesh_s, nf.perm, nf.np, nf.total, nf.tile_box, nf.chunk_box, nf.n_mesh, nf.voff, nf.rn2,
       reinterpret_cast<const float4 *>(b->tab32), KG, b->n_r, inv_dr, r2max, b->K, nf.J, M, stride);
   ::tsr::count_launch();
