@@ -132,8 +132,13 @@ def test_project_material_backward(torch_cuda, tsr, oracle_basis16):
 
 # ------------------------------------------------------------------ Eq. 6-7 transfer
 def _scene_arrays(nu, K, J, amp, seed):
-    sc = scene.make_scene(nu, K=K, J=J, amp=amp, seed=seed)
-    return sc, sc.mesh.pos.astype(np.float32), sc.mesh.area.astype(np.float32), sc.T.astype(np.float32)
+    """The scene's arrays; J beyond the 25 coefficients of four SH bands (the library takes up to 32)
+    repeats the first transport rows, so every row keeps the statistics of real transport."""
+    sc = scene.make_scene(nu, K=K, J=min(J, 25), amp=amp, seed=seed)
+    T = sc.T.astype(np.float32)
+    if J > 25:
+        T = np.concatenate([T, T[:J - 25]])
+    return sc, sc.mesh.pos.astype(np.float32), sc.mesh.area.astype(np.float32), T
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "bf16x3"])
@@ -150,11 +155,12 @@ def test_transfer_full_small(torch_cuda, tsr, oracle_basis16, precision, nu, K, 
     _check_M(M.cpu().numpy(), M_ref, precision)
 
 
-@pytest.mark.parametrize("nu,K,J,seed", [(1, 8, 9, 0), (2, 8, 9, 3), (4, 8, 9, 1), (4, 16, 25, 2), (6, 12, 16, 3),
-                                         (7, 12, 16, 4), (8, 12, 16, 5)])
+@pytest.mark.parametrize("nu,K,J,seed", [(1, 8, 9, 0), (2, 8, 9, 3), (4, 8, 9, 1), (4, 16, 25, 2), (4, 16, 32, 6),
+                                         (6, 12, 16, 3), (7, 12, 16, 4), (8, 12, 16, 5)])
 def test_transfer_bf16_coarse_meshes(torch_cuda, tsr, oracle_basis16, nu, K, J, seed):
     """BF16 on coarse meshes (12 to 642 vertices), where a few close pairs carry much of M: the
-    near pairs (r < max(3 mm, 2h)) are summed exactly in FP32, so the bound holds with margin."""
+    near pairs (r < max(r_max / 16, 2h)) are summed exactly in FP32, so the bound holds with margin;
+    J = 32 takes the widest records, accumulators and near-field staging."""
     torch = torch_cuda
     f_ref, _ = oracle_basis16
     sc, pos, area, T = _scene_arrays(nu, K, J, 0.1 if nu > 1 else 0.0, seed)
