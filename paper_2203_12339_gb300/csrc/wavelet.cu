@@ -400,76 +400,132 @@ __device__ void keep_pass(const float *__restrict__ c, int n_coef, unsigned tau,
   }
 }
 
-// One block per (k, j) row.  Radix select (4 x 8 bits) of the n_keep-th largest
-// |c| over the chart coefficients (histograms with warp-aggregated shared atomics:
-// lanes holding the same digit add once; four independent loads per thread in
-// flight), then, in index order, the keep flags and the column list: every larger
-// value, and the first (n_keep - #larger) values equal to it.  Both poles are kept
-// and end the column list.
+// One radix digit of `width` bits at `shift` (bins = 2^width <= 4096) over the n keys of
+// src (|c| bits: the sign is masked off) whose bits above the digit equal `prefix` under
+// `mask`: a histogram (warp-aggregated shared atomics: lanes holding the same digit add
+// once; four independent loads per thread in flight), then the digit where the count of
+// larger keys, taken from the top, reaches `remaining`.  Out: the digit, the count of keys
+// in larger digits and the count in the digit.  src may be global or shared memory.
+__device__ void sel_digit(const unsigned *src, int n, int shift, int width, unsigned prefix, unsigned mask,
+                          unsigned remaining, unsigned *hist, unsigned *wsum, unsigned *s_out, unsigned &sel,
+                          unsigned &cum, unsigned &eq) {
+  const int bins = 1 << width, lane = threadIdx.x & 31;
+  for (int q = threadIdx.x; q < bins; q += SEL_NT) hist[q] = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += 4 * SEL_NT) {
+    unsigned u[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int w = base + q * SEL_NT + threadIdx.x;
+      u[q] = (w < n) ? (src[w] & 0x7FFFFFFFu) : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int w = base + q * SEL_NT + threadIdx.x;
+      const bool in = (w < n) && ((u[q] & mask) == prefix);
+      const unsigned digit = in ? ((u[q] >> shift) & (unsigned)(bins - 1)) : (unsigned)bins;
+      const unsigned peers = __match_any_sync(0xffffffffu, digit);
+      if (in && lane == __ffs(peers) - 1) atomicAdd(&hist[digit], (unsigned)__popc(peers));
+    }
+  }
+  __syncthreads();
+  // thread t holds the `per` digits just below bins - per t; a block scan from the top finds
+  // the thread, then the digit, where the running count reaches `remaining`
+  const int per = bins > SEL_NT ? bins / SEL_NT : 1;
+  const int top = bins - per * (int)threadIdx.x;   // the thread's digits: [top - per, top)
+  unsigned h[8] = {0, 0, 0, 0, 0, 0, 0, 0}, sum = 0;
+  if (top > 0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q < per) {
+        h[q] = hist[top - 1 - q];
+        sum += h[q];
+      }
+  }
+  unsigned total;
+  const unsigned before = block_excl_scan(sum, wsum, total);
+  if (top > 0 && before < remaining && before + sum >= remaining) {
+    unsigned c0 = before;
+    int q = 0;
+    for (; q < per - 1; ++q) {
+      if (c0 + h[q] >= remaining) break;
+      c0 += h[q];
+    }
+    s_out[0] = (unsigned)(top - 1 - q);
+    s_out[1] = c0;
+    s_out[2] = h[q];
+  }
+  __syncthreads();
+  sel = s_out[0];
+  cum = s_out[1];
+  eq = s_out[2];
+  __syncthreads();
+}
+
+// One block per (k, j) row: the n_keep-th largest |c| over the chart coefficients, then, in
+// index order, the keep flags and the column list (every larger value, and the first
+// (n_keep - #larger) values equal to it; both poles kept and ending the list).  The key is
+// found digit by digit: the top 12 bits over the row; then, when the keys sharing those bits
+// fit the 4,096-word scratch (big), they are gathered there and the last 19 bits are two
+// digits over the gathered keys; otherwise three more digits over the row.  The key and the
+// number of its equals are the same either way, so the keep set does not depend on the path.
 __device__ __forceinline__ void select_block(const float *__restrict__ Mw, int n_coef, int NW, int n_keep,
                                              uint8_t *__restrict__ keep, int32_t *__restrict__ cidx,
-                                             float *__restrict__ cval, int rowi) {
-  __shared__ unsigned hist[256];
-  __shared__ unsigned s_sel, s_cum, s_eq;
+                                             float *__restrict__ cval, int rowi, unsigned *big) {
+  __shared__ unsigned hist[1024];
+  __shared__ unsigned s_out[3], s_n;
   __shared__ unsigned wsum[SEL_NT / 32];
   const float *c = Mw + (size_t)rowi * NW;
+  const unsigned *keys = reinterpret_cast<const unsigned *>(c);
   uint8_t *kp = keep + (size_t)rowi * NW;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned prefix = 0, mask = 0, remaining = (unsigned)n_keep, n_eq = 0;
-  for (int shift = 24; shift >= 0; shift -= 8) {
-    for (int q = threadIdx.x; q < 256; q += SEL_NT) hist[q] = 0;
+  unsigned remaining = (unsigned)n_keep, sel, cum, eq;
+  sel_digit(keys, n_coef, 19, 12, 0u, 0u, remaining, big, wsum, s_out, sel, cum, eq);
+  remaining -= cum;
+  unsigned prefix = sel << 19, mask = 0xFFFu << 19, n_eq = eq;
+  if (n_eq <= 4096u) {
+    // gather the keys of the chosen 12-bit digit (in any order: only counts depend on them)
+    if (threadIdx.x == 0) s_n = 0;
     __syncthreads();
+    const int lane = threadIdx.x & 31;
     for (int base = 0; base < n_coef; base += 4 * SEL_NT) {
       unsigned u[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int q = 0; q < 4; ++q) {   // four independent loads per thread in flight
         const int w = base + q * SEL_NT + threadIdx.x;
-        u[q] = (w < n_coef) ? (__float_as_uint(c[w]) & 0x7FFFFFFFu) : 0u;
+        u[q] = w < n_coef ? (keys[w] & 0x7FFFFFFFu) : 0u;
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int w = base + q * SEL_NT + threadIdx.x;
-        const bool in = (w < n_coef) && ((u[q] & mask) == prefix);
-        const unsigned digit = in ? ((u[q] >> shift) & 255u) : 256u;
-        const unsigned peers = __match_any_sync(0xffffffffu, digit);
-        if (in && lane == __ffs(peers) - 1) atomicAdd(&hist[digit], (unsigned)__popc(peers));
+        const bool in = w < n_coef && (u[q] & mask) == prefix;
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        if (bal == 0u) continue;
+        unsigned at = 0;
+        if (lane == __ffs(bal) - 1) at = atomicAdd(&s_n, (unsigned)__popc(bal));
+        at = __shfl_sync(0xffffffffu, at, __ffs(bal) - 1);
+        if (in) big[at + __popc(bal & ((1u << lane) - 1u))] = u[q];
       }
     }
     __syncthreads();
-    if (warp == 0) {
-      // lane l holds digits 255 - 8 l down to 248 - 8 l; a scan from the top finds the
-      // digit where the running count reaches `remaining` (the histogram holds >= remaining)
-      unsigned h[8], sum = 0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        h[q] = hist[255 - 8 * lane - q];
-        sum += h[q];
-      }
-      unsigned incl = sum;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const unsigned hit = __ballot_sync(0xffffffffu, incl >= remaining);
-      if (hit != 0u && lane == __ffs(hit) - 1) {
-        unsigned cum = incl - sum;
-        int q = 0;
-        for (; q < 7; ++q) {
-          if (cum + h[q] >= remaining) break;
-          cum += h[q];
-        }
-        s_sel = (unsigned)(255 - 8 * lane - q);
-        s_cum = cum;
-        s_eq = h[q];
-      }
+    const int ng = (int)s_n;
+    sel_digit(big, ng, 9, 10, prefix, mask, remaining, hist, wsum, s_out, sel, cum, eq);
+    remaining -= cum;
+    prefix |= sel << 9;
+    mask |= 0x3FFu << 9;
+    sel_digit(big, ng, 0, 9, prefix, mask, remaining, hist, wsum, s_out, sel, cum, eq);
+    remaining -= cum;
+    prefix |= sel;
+    mask |= 0x1FFu;
+    n_eq = eq;
+  } else {
+    const int shifts[3] = {11, 3, 0}, widths[3] = {8, 8, 3};
+    for (int d = 0; d < 3; ++d) {
+      sel_digit(keys, n_coef, shifts[d], widths[d], prefix, mask, remaining, hist, wsum, s_out, sel, cum, eq);
+      remaining -= cum;
+      prefix |= sel << shifts[d];
+      mask |= ((1u << widths[d]) - 1u) << shifts[d];
+      n_eq = eq;
     }
-    __syncthreads();
-    remaining -= s_cum;
-    prefix |= s_sel << shift;
-    mask |= 255u << shift;
-    n_eq = s_eq;
-    __syncthreads();
   }
   // prefix = key of the n_keep-th largest; keep `remaining` of its n_eq equal keys (lowest index first)
   keep_pass(c, n_coef, prefix, remaining, remaining >= n_eq, n_keep, kp, cidx + (size_t)rowi * (n_keep + 2),
@@ -627,7 +683,7 @@ __device__ __forceinline__ void select_rows(const float *__restrict__ Mw, int n_
       select_warp(Mw + (size_t)rowi * NW, n_coef, n_keep, keep + (size_t)rowi * NW, cidx + (size_t)rowi * (n_keep + 2),
                   cval + (size_t)rowi * (n_keep + 2), whist[warp]);
   } else {
-    select_block(Mw, n_coef, NW, n_keep, keep, cidx, cval, blk);
+    select_block(Mw, n_coef, NW, n_keep, keep, cidx, cval, blk, &whist[0][0]);
   }
 }
 
