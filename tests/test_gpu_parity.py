@@ -393,6 +393,28 @@ def test_select_and_pack_exact(torch_cuda, tsr, nu, p):
             assert val[q] == Mw.reshape(K * J, n_rows)[col[q], w]
 
 
+@pytest.mark.parametrize("data", ["spread", "zeros"])
+def test_select_large_rows_exact(torch_cuda, tsr, data):
+    """Rows of 40,960 chart coefficients (nu = 40: 64 x 64 charts) take the block selection: a 12-bit
+    first digit over the row, then the gathered keys of that digit in shared memory (values spread over
+    many binades) or more digits over the row (90 % exact zeros and eighths: more than 4,096 equal keys
+    and ties everywhere).  Bit-exact against the oracle's top-p mask (ties by lower index)."""
+    torch = torch_cuda
+    nu, K, J, p = 40, 2, 3, 0.1
+    P = O.chart_side(nu)
+    n_rows = 10 * P * P + 2
+    rng = np.random.default_rng(7)
+    if data == "spread":
+        Mw = rng.standard_normal((K, J, n_rows)) * np.exp(rng.uniform(-12.0, 3.0, (K, J, n_rows)))
+    else:
+        Mw = np.where(rng.random((K, J, n_rows)) < 0.9, 0.0, np.round(rng.standard_normal((K, J, n_rows)) * 8) / 8)
+    Mw = Mw.astype(np.float32)
+    comp = tsr.wavelet_compress(_dev(torch, Mw), nu, p)
+    row_ptr, col, val = (t.cpu().numpy() for t in comp.export())
+    got = _mask_from_csr(row_ptr, col, n_rows, K * J).reshape(K, J, n_rows)
+    assert np.array_equal(got, O.select_top(Mw, nu, p))
+
+
 def _energy_boundary_ok(row, e, n_gpu):
     """True if n_gpu reaches the energy threshold and n_gpu - 1 does not, both within FP64
     rounding of the summation order (the two sides add the same exact squares in different orders)."""
