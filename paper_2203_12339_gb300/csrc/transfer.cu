@@ -372,10 +372,15 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 //    takes the steps s with s mod CONC = g), each thread a run of 4 CONC
 //    consecutive i of one row, so that a step's A tile is written while the tensor
 //    core consumes the previous one.
+//  * MODE_CHEB_S:    the same terms written to shared memory (canonical K-major layout, one
+//    16-byte store per term and thread) for the MMA to read from there, so that tensor
+//    memory holds only the accumulators: at J_pad = 32 (12 x 32 accumulator columns) two A
+//    slots fit, and two groups of 8 warps, 8 i per thread, write alternate steps.
 // Table modes take the pairs with rn2 <= r^2 <= r_max^2 (rn2 = 0 when no separate
 // near field is added: the self pair is then replaced in FP32 by the epilogue);
-// MODE_CHEB takes the same far pairs, whose near complement near.cu adds in FP32.
-enum { MODE_NEAR = 0, MODE_CHEB = 1, MODE_NEAR_TMEM = 2 };
+// the series modes take the same far pairs, whose near complement near.cu adds in FP32.
+enum { MODE_NEAR = 0, MODE_CHEB = 1, MODE_NEAR_TMEM = 2, MODE_CHEB_S = 3 };
+__host__ __device__ constexpr bool is_series(int mode) { return mode == MODE_CHEB || mode == MODE_CHEB_S; }
 
 struct TcArgs {
   int N;             // vertices (rows o and columns i)
@@ -428,7 +433,7 @@ struct Unit {
 template <int MODE, int CB, int JP, bool SPLIT, int NS>
 struct TcCfg {
   static constexpr int LOOKAHEAD = 8;                      // records in flight ahead of the generators
-  static constexpr int CONC = (MODE == MODE_CHEB) ? NS : 1;   // generator groups (steps in flight)
+  static constexpr int CONC = is_series(MODE) ? NS : 1;   // generator groups (steps in flight)
   static constexpr int NR = NS + LOOKAHEAD;                // record slots
   static constexpr int REC = rec_bytes(JP, SPLIT);
   static constexpr bool ATMEM = (MODE == MODE_NEAR_TMEM || MODE == MODE_CHEB);
@@ -448,7 +453,7 @@ struct TcCfg {
   static_assert(USED_COLS <= 512, "tensor memory holds 512 columns");
   static size_t smem_bytes(int n_r, int K) {
     return 1024 + (size_t)NS * A_STAGE + (size_t)NR * REC_STAGE + (size_t)(n_r + 1) * CB * TAB_ELEM +
-           (MODE == MODE_CHEB ? (size_t)K * CB * sizeof(float) : 0) + 512;
+           (is_series(MODE) ? (size_t)K * CB * sizeof(float) : 0) + 512;
   }
 };
 
@@ -579,7 +584,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
   uint8_t *sTab = sRec + (size_t)C::NR * C::REC_STAGE;  // (n_r+1) * CB * TAB_ELEM   (MODE_NEAR)
   float *sC = reinterpret_cast<float *>(sTab + (size_t)(args.n_r + 1) * CB * C::TAB_ELEM);   // [K][CB] (MODE_CHEB)
   uint64_t *bar = reinterpret_cast<uint64_t *>(
-      reinterpret_cast<uint8_t *>(sC) + (MODE == MODE_CHEB ? (((size_t)args.K * CB * 4 + 15) / 16) * 16 : 0));
+      reinterpret_cast<uint8_t *>(sC) + (is_series(MODE) ? (((size_t)args.K * CB * 4 + 15) / 16) * 16 : 0));
   uint64_t *bar_tma = bar;                        // [NR] records landed
   uint64_t *bar_full = bar + C::NR;               // [NS] A stage written by its generator group
   uint64_t *bar_mma = bar + C::NR + NS;           // [NS] MMAs of a stage completed
@@ -796,7 +801,7 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
         }
         umma_commit_elect(&bar_mma[sa]);     // the A slot may be rewritten
         umma_commit_elect(&bar_rfree[sr]);   // the record slot may be refilled
-        if (MODE == MODE_CHEB && seg_end) umma_commit_elect(bar_seg);   // the segment's accumulators are final
+        if (is_series(MODE) && seg_end) umma_commit_elect(bar_seg);   // the segment's accumulators are final
         if (++sa == NS) {
           sa = 0;
           pa ^= 1u;
@@ -805,15 +810,21 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
       }
     }
     __syncwarp();
-  } else if constexpr (MODE == MODE_CHEB) {
+  } else if constexpr (is_series(MODE)) {
     // ------------------------------------------------------------ generator warps, far-field series
     // Warp w: TMEM lane quarter w mod 4 (rows 32 (w mod 4) + lane), group w / GW (the
     // steps s with s mod CONC = group), run (w mod GW) / 4 of IPT consecutive i of the step.
     constexpr int CONC = C::CONC, GW = 16 / CONC, IPT = 4 * CONC, NWD = IPT / 2;
+    constexpr bool SMEM_A = MODE == MODE_CHEB_S;
+    static_assert(!SMEM_A || NWD == 4, "shared-memory A: 8 i per thread (two generator groups)");
     const int quarter = warp & 3, grp = warp / GW, ih = (warp % GW) >> 2;
     const int orow = quarter * 32 + lane;
     const uint32_t a_tmem_row =
         tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(C::ACC_COLS + ih * NWD);
+    // shared-memory A: the thread's row and 8-i K chunk in the canonical K-major layout (8 x 16 B
+    // core matrices, K chunks 128 B apart, 8-row groups 256 B apart), one 16-byte store per term
+    const uint32_t a_smem_row =
+        smem_u32(sA) + (uint32_t)((orow >> 3) * 256 + ih * 128 + (orow & 7) * 16);
     const uint32_t lane_base = tmem_base + ((uint32_t)(quarter * 32) << 16);
     const float r2max = args.r2max, xa_alpha = args.x_alpha, xa_beta = args.x_beta;
     const uint64_t alpha2 = f2_pack(xa_alpha, xa_alpha), beta2 = f2_pack(xa_beta, xa_beta);
@@ -903,7 +914,29 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
             }
           }
           const uint32_t a_slot = a_tmem_row + (uint32_t)(sa * C::A_COLS);
-          if constexpr (NS >= 2) {
+          if constexpr (SMEM_A) {
+            // the slot's previous MMAs (CONC steps back) completed long ago: wait, then store
+            // the terms as the recurrence produces them
+            if (!first_use && __any_sync(0xffffffffu, !wait_or_abort(&bar_mma[sa], pa ^ 1u, abort_flag))) {
+              ok = false;
+              break;
+            }
+            const uint32_t a_st = a_smem_row + (uint32_t)(sa * C::A_STAGE);
+            st_shared_v4(a_st, w0[0], w0[1], w0[2], w0[3]);
+            st_shared_v4(a_st + C::A_TILE, w1[0], w1[1], w1[2], w1[3]);
+#pragma unroll
+            for (int p = 2; p < CB; ++p) {
+              uint32_t w2[NWD];
+#pragma unroll
+              for (int h = 0; h < NWD; ++h) w2[h] = bf16x2_fma((p & 1) ? mp[h] : mn[h], w1[h], w0[h]);
+              st_shared_v4(a_st + (uint32_t)(p * C::A_TILE), w2[0], w2[1], w2[2], w2[3]);
+#pragma unroll
+              for (int h = 0; h < NWD; ++h) {
+                w0[h] = w1[h];
+                w1[h] = w2[h];
+              }
+            }
+          } else if constexpr (NS >= 2) {
             // the slot's previous MMAs (CONC steps back) completed long ago: wait, then stream
             // the terms to TMEM as the recurrence produces them (few live registers)
             if (!first_use && __any_sync(0xffffffffu, !wait_or_abort(&bar_mma[sa], pa ^ 1u, abort_flag))) {
@@ -946,8 +979,12 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
 #pragma unroll
             for (int p = 0; p < CB; ++p) tmem_st_run<NWD>(a_slot + (uint32_t)(p * 8), feat[p]);
           }
-          tmem_st_wait();
-          tc_fence_before();
+          if constexpr (SMEM_A) {
+            fence_proxy_async_smem();   // the stores, before the tensor core reads them
+          } else {
+            tmem_st_wait();
+            tc_fence_before();
+          }
           mbar_arrive(&bar_full[sa]);
           // advance this group's ring by CONC steps
           sa += CONC;
@@ -1328,7 +1365,7 @@ static tsr_status launch_tc(const TcArgs &a0, int n_cols, const CUtensorMap &tma
   TcArgs a = a0;
   // The tensor-core FP32 accumulation does not round to nearest, so long sums are cut
   // into segments that the epilogue adds with round-to-nearest FP32 adds.
-  a.seg_stages = (MODE == MODE_CHEB ? 16384 : 4096) / 16;
+  a.seg_stages = (is_series(MODE) ? 16384 : 4096) / 16;
   a.n_groups = (n_cols + CB - 1) / CB;
   const size_t smem = C::smem_bytes(a.n_r, a.K);
   if (smem > 232448) {
@@ -1364,7 +1401,7 @@ static tsr_status launch_tc(const TcArgs &a0, int n_cols, const CUtensorMap &tma
   TSR_CUDA(cudaGetLastError());
   if (streamk) {
     streamk_fixup_kernel<<<G * a.streamk_P, 1024, 0, s>>>(a.M, a.slots, a.n_otiles, a.n_steps, a.streamk_P,
-                                                          MODE == MODE_CHEB ? a.K : CB, a.K, a.J, a.N, a.stride);
+                                                          is_series(MODE) ? a.K : CB, a.K, a.J, a.N, a.stride);
     ::tsr::count_launch();
     TSR_CUDA(cudaGetLastError());
   }
@@ -1418,8 +1455,9 @@ static tsr_status dispatch_table(const TcArgs &a, int JP, bool split, const CUte
 }
 
 // The far-field series generator (TSR_CHEB_BF16 terms).  conc: generator groups (steps
-// written concurrently); with J_pad = 32 the accumulators take 384 of the 512 TMEM
-// columns, which leaves room for one A slot only.
+// written concurrently).  With J_pad = 32 the accumulators take 384 of the 512 TMEM
+// columns, which leaves room for one A slot in TMEM only: there the A tiles go to shared
+// memory instead (two slots, two groups; TSR_CHEB_SMEM=0 keeps the single TMEM slot).
 static tsr_status dispatch_cheb(const TcArgs &a, int JP, const CUtensorMap &tmap, bool allow_split, cudaStream_t s,
                                 int conc = 0) {
   if (conc == 0) {
@@ -1430,7 +1468,9 @@ static tsr_status dispatch_cheb(const TcArgs &a, int JP, const CUtensorMap &tmap
     if (conc == 1) return launch_tc<MODE_CHEB, TSR_CHEB_BF16, 16, false, 1>(a, TSR_CHEB_BF16, tmap, allow_split, s);
     return launch_tc<MODE_CHEB, TSR_CHEB_BF16, 16, false, 2>(a, TSR_CHEB_BF16, tmap, allow_split, s);
   }
-  return launch_tc<MODE_CHEB, TSR_CHEB_BF16, 32, false, 1>(a, TSR_CHEB_BF16, tmap, allow_split, s);
+  const char *e = std::getenv("TSR_CHEB_SMEM");   // diagnostic: "0" keeps the single TMEM A slot
+  if (e && e[0] == '0') return launch_tc<MODE_CHEB, TSR_CHEB_BF16, 32, false, 1>(a, TSR_CHEB_BF16, tmap, allow_split, s);
+  return launch_tc<MODE_CHEB_S, TSR_CHEB_BF16, 32, false, 2>(a, TSR_CHEB_BF16, tmap, allow_split, s);
 }
 
 // "table": the BF16 transfer uses the table generator even where the series is accurate
