@@ -210,9 +210,20 @@ __global__ void near_box_kernel(const float *__restrict__ pos_s, long long np, l
 constexpr int NEAR_ROWS = TSR_NEAR_ROWS;   // output rows per block (a divisor of 128)
 constexpr int NEAR_SCAN = 256;    // chunk boxes tested per pass
 #ifndef TSR_NEAR_BATCH
-#define TSR_NEAR_BATCH 12
+#define TSR_NEAR_BATCH 4
 #endif
 constexpr int NEAR_BATCH = TSR_NEAR_BATCH;   // listed chunks staged per barrier (16 candidates each)
+
+// Asynchronous global -> shared copies (cp.async): the next candidate batch lands while the
+// current one is tested and summed, without holding registers.
+__device__ __forceinline__ void near_cp16(void *smem, const void *gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void near_cp4(void *smem, const void *gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void near_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void near_cp_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // One block per NEAR_ROWS sorted output rows (two or more blocks per SM interleave their
 // phases).  Per batch of up to 16 NEAR_BATCH staged candidates i:
@@ -228,9 +239,9 @@ __global__ void __launch_bounds__(512) near_field_kernel(
     const float *__restrict__ rn2, const float4 *__restrict__ tab, int KG, int n_r, float inv_dr, float r2max,
     int K, int J, float *__restrict__ M, long long stride) {
   constexpr int NC = NEAR_BATCH * 16;   // candidates per batch
-  __shared__ __align__(16) float sT[NC * JP];
-  __shared__ float sx[NC], sy[NC], sz[NC];
-  __shared__ int sm[NC];
+  __shared__ __align__(16) float sTb[2][NC * JP];   // two batches: one staged while the other is summed
+  __shared__ float sxb[2][NC], syb[2][NC], szb[2][NC];
+  __shared__ int smb[2][NC];
   __shared__ float s_xv[NEAR_ROWS][NC + 1];       // r / dr of the near pairs (+1: no bank conflicts)
   __shared__ unsigned s_mask[NEAR_ROWS][NC / 32];
   __shared__ float s_row[NEAR_ROWS][4];           // x, y, z, r_e^2 of the block's rows
@@ -298,26 +309,34 @@ __global__ void __launch_bounds__(512) near_field_kernel(
     }
     if (keep) s_list[before + __popc(bal & ((1u << lane) - 1u))] = c;
     __syncthreads();
-    for (int lb = 0; lb < n_list; lb += NEAR_BATCH) {
-      // stage up to NEAR_BATCH listed chunks (16 i each); the rest of the batch is empty
+    // stage up to NEAR_BATCH listed chunks (16 i each) into buffer bs; the rest of the batch is empty
+    auto stage = [&](int lb, int bs) {
       const int nb = min(NEAR_BATCH, n_list - lb);
       for (int q = threadIdx.x; q < nb * 16 * JP / 4; q += blockDim.x) {
         const int cc = q / (16 * JP / 4), w = q % (16 * JP / 4);
-        reinterpret_cast<float4 *>(sT)[q] =
-            reinterpret_cast<const float4 *>(tq + (size_t)s_list[lb + cc] * 16 * JP)[w];
+        near_cp16(reinterpret_cast<float4 *>(sTb[bs]) + q,
+                  reinterpret_cast<const float4 *>(tq + (size_t)s_list[lb + cc] * 16 * JP) + w);
       }
       for (int q = threadIdx.x; q < NC; q += blockDim.x) {
         if (q < nb * 16) {
           const long long i = (long long)s_list[lb + q / 16] * 16 + (q % 16);
-          sx[q] = pos_s[i];
-          sy[q] = pos_s[np + i];
-          sz[q] = pos_s[2 * np + i];
-          sm[q] = mesh_s[i];
+          near_cp4(&sxb[bs][q], pos_s + i);
+          near_cp4(&syb[bs][q], pos_s + np + i);
+          near_cp4(&szb[bs][q], pos_s + 2 * np + i);
+          near_cp4(&smb[bs][q], mesh_s + i);
         } else {
-          sm[q] = -1;   // no candidate
+          smb[bs][q] = -1;   // no candidate
         }
       }
-      __syncthreads();
+      near_cp_commit();
+    };
+    if (n_list > 0) stage(0, 0);
+    for (int lb = 0, bs = 0; lb < n_list; lb += NEAR_BATCH, bs ^= 1) {
+      near_cp_wait();
+      __syncthreads();   // batch lb is in buffer bs; the other buffer's last batch has been summed
+      if (lb + NEAR_BATCH < n_list) stage(lb + NEAR_BATCH, bs ^ 1);
+      const float *sT = sTb[bs], *sx = sxb[bs], *sy = syb[bs], *sz = szb[bs];
+      const int *sm = smb[bs];
       // phase A: warp w takes 32 consecutive candidates of one row per turn
       for (int item = warp; item < NEAR_ROWS * (NC / 32); item += n_warps) {
         const int r = item / (NC / 32), wd = item % (NC / 32), ii = wd * 32 + lane;
@@ -357,7 +376,7 @@ __global__ void __launch_bounds__(512) near_field_kernel(
           }
         }
       }
-      __syncthreads();
+      // (the next batch's barrier, after its copies landed, orders this phase B before its phase A)
     }
     __syncthreads();   // s_warp and s_list are rewritten by the next pass
   }
