@@ -216,8 +216,9 @@ tsr_status tsr_precompute_transfer(const tsr_basis *basis, int N, const float *p
  * a plan).  For repeated or graph-captured use, build a plan once:
  *   tsr_batch_plan_create   uploads the unit and mesh tables (synchronous);
  *   tsr_batch_plan_autotune times each generator configuration of the BF16
- *                           transfer (the far-field series with one or two 16-i
- *                           steps in flight; the table with 4, 8, 12 or 16 bases
+ *                           transfer (the far-field series with three or two
+ *                           16-i steps in flight, and one at J <= 16; the table
+ *                           with 4, 8, 12 or 16 bases
  *                           per CTA group) on the caller's data, keeps the
  *                           fastest, returns its time in *best_ms (synchronises;
  *                           outside any capture);

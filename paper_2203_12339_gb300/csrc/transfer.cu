@@ -443,8 +443,10 @@ struct TcCfg {
   static constexpr int REC_STAGE = REC;
   static constexpr int TAB_ELEM = TABLE ? (SPLIT ? 8 : 4) : 0;
   static constexpr int U = TABLE ? CB * TAB_ELEM / 16 : 1;   // 16-byte units per table row
-  static constexpr int NGEN = 512;                         // generator threads (warps 0-15)
+  // generator threads: 16 warps, or for the series modes with NS >= 2 one group of 8 warps per A slot
+  static constexpr int NGEN = (is_series(MODE) && NS >= 2) ? 256 * NS : 512;
   static constexpr int NTHREADS = NGEN + 64;               // + the MMA-issue warp and the TMA warp
+  static_assert(NTHREADS <= 1024, "at most 1024 threads per block");
   static constexpr int ACC_COLS = CB * JP;                 // FP32 accumulators
   static constexpr int A_COLS = ATMEM ? CB * 8 : 0;        // A tile of one stage in TMEM (16 BF16 per row = 8 columns)
   static constexpr int USED_COLS = ACC_COLS + NS * A_COLS;
@@ -814,7 +816,8 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
     // ------------------------------------------------------------ generator warps, far-field series
     // Warp w: TMEM lane quarter w mod 4 (rows 32 (w mod 4) + lane), group w / GW (the
     // steps s with s mod CONC = group), run (w mod GW) / 4 of IPT consecutive i of the step.
-    constexpr int CONC = C::CONC, GW = 16 / CONC, IPT = 4 * CONC, NWD = IPT / 2;
+    // One group: 16 warps, 4 i per thread; two or three groups: 8 warps each, 8 i per thread.
+    constexpr int CONC = C::CONC, GW = CONC >= 2 ? 8 : 16, IPT = 64 / GW, NWD = IPT / 2;
     constexpr bool SMEM_A = MODE == MODE_CHEB_S;
     static_assert(!SMEM_A || NWD == 4, "shared-memory A: 8 i per thread (two generator groups)");
     const int quarter = warp & 3, grp = warp / GW, ih = (warp % GW) >> 2;
@@ -1455,21 +1458,31 @@ static tsr_status dispatch_table(const TcArgs &a, int JP, bool split, const CUte
 }
 
 // The far-field series generator (TSR_CHEB_BF16 terms).  conc: generator groups (steps
-// written concurrently).  With J_pad = 32 the accumulators take 384 of the 512 TMEM
-// columns, which leaves room for one A slot in TMEM only: there the A tiles go to shared
-// memory instead (two slots, two groups; TSR_CHEB_SMEM=0 keeps the single TMEM slot).
+// written concurrently; three groups of 8 warps by default, 24 generator warps at 72
+// registers).  With J_pad = 32 the accumulators take 384 of the 512 TMEM columns, which
+// leaves room for one A slot in TMEM only: there the A tiles go to shared memory instead
+// (one slot per group; TSR_CHEB_SMEM=0 keeps the single TMEM slot).  With J_pad = 16 the
+// A slots sit in TMEM beside the accumulators (TSR_CHEB_SMEM=1: in shared memory).
 static tsr_status dispatch_cheb(const TcArgs &a, int JP, const CUtensorMap &tmap, bool allow_split, cudaStream_t s,
                                 int conc = 0) {
   if (conc == 0) {
-    const char *e = std::getenv("TSR_CHEB_CONC");   // diagnostic: "1" or "2" steps in flight (J_pad = 16)
-    conc = (e && e[0] == '1') ? 1 : 2;
+    const char *e = std::getenv("TSR_CHEB_CONC");   // diagnostic: "1", "2" or "3" steps in flight
+    conc = (e && e[0] >= '1' && e[0] <= '3') ? e[0] - '0' : 3;
   }
+  const char *e = std::getenv("TSR_CHEB_SMEM");   // diagnostic: "0" A in TMEM, "1" A in shared memory
+  const int smem_a = (e && (e[0] == '0' || e[0] == '1')) ? e[0] - '0' : -1;
   if (JP == 16) {
     if (conc == 1) return launch_tc<MODE_CHEB, TSR_CHEB_BF16, 16, false, 1>(a, TSR_CHEB_BF16, tmap, allow_split, s);
+    if (smem_a == 1) {
+      if (conc == 3) return launch_tc<MODE_CHEB_S, TSR_CHEB_BF16, 16, false, 3>(a, TSR_CHEB_BF16, tmap, allow_split, s);
+      return launch_tc<MODE_CHEB_S, TSR_CHEB_BF16, 16, false, 2>(a, TSR_CHEB_BF16, tmap, allow_split, s);
+    }
+    if (conc == 3) return launch_tc<MODE_CHEB, TSR_CHEB_BF16, 16, false, 3>(a, TSR_CHEB_BF16, tmap, allow_split, s);
     return launch_tc<MODE_CHEB, TSR_CHEB_BF16, 16, false, 2>(a, TSR_CHEB_BF16, tmap, allow_split, s);
   }
-  const char *e = std::getenv("TSR_CHEB_SMEM");   // diagnostic: "0" keeps the single TMEM A slot
-  if (e && e[0] == '0') return launch_tc<MODE_CHEB, TSR_CHEB_BF16, 32, false, 1>(a, TSR_CHEB_BF16, tmap, allow_split, s);
+  if (smem_a == 0 || conc == 1)
+    return launch_tc<MODE_CHEB, TSR_CHEB_BF16, 32, false, 1>(a, TSR_CHEB_BF16, tmap, allow_split, s);
+  if (conc == 3) return launch_tc<MODE_CHEB_S, TSR_CHEB_BF16, 32, false, 3>(a, TSR_CHEB_BF16, tmap, allow_split, s);
   return launch_tc<MODE_CHEB_S, TSR_CHEB_BF16, 32, false, 2>(a, TSR_CHEB_BF16, tmap, allow_split, s);
 }
 
@@ -1642,7 +1655,7 @@ tsr_status batch_plan_run(const tsr_batch_plan *p, const float *pos, const float
 }
 
 // Times every generator configuration once on the caller's data and keeps the fastest
-// in the plan: the far-field series with one or two steps in flight (J_pad = 16), and the
+// in the plan: the far-field series with three or two steps in flight (and one at J_pad = 16), and the
 // table with 4, 8, 12 or 16 bases per CTA group.  Synchronises the stream; not for use
 // inside a capture.
 tsr_status batch_plan_autotune(tsr_batch_plan *p, const float *pos, const float *area, const float *T, float *M,
@@ -1654,6 +1667,7 @@ tsr_status batch_plan_autotune(tsr_batch_plan *p, const float *pos, const float 
   struct Cand { int gen, conc, kb; };
   std::vector<Cand> cands;
   if (p->basis->cheb_ok) {
+    cands.push_back({0, 3, 0});
     cands.push_back({0, 2, 0});
     if (p->J <= 16) cands.push_back({0, 1, 0});
   }

@@ -56,7 +56,7 @@ def test_plan_autotune_and_graph_capture(env):
     best = plan.autotune(d["pos"], d["area"], d["T"], out=M)
     info = plan.info()
     assert best > 0
-    assert (info["generator"], info["param"]) in [("series", 1), ("series", 2)] + [("table", kb) for kb in (4, 8, 12, 16)]
+    assert (info["generator"], info["param"]) in [("series", 1), ("series", 2), ("series", 3)] + [("table", kb) for kb in (4, 8, 12, 16)]
     assert info["units"] == sum((offs[b + 1] - offs[b] + 127) // 128 for b in range(len(NUS)))
     plan.run(d["pos"], d["area"], d["T"], out=M)           # warm (allocator pools, function attributes)
     torch.cuda.synchronize()
