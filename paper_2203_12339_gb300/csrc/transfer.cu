@@ -376,11 +376,22 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 //    16-byte store per term and thread) for the MMA to read from there, so that tensor
 //    memory holds only the accumulators: at J_pad = 32 (12 x 32 accumulator columns) two A
 //    slots fit, and two groups of 8 warps, 8 i per thread, write alternate steps.
+//  * MODE_CHEB_H:    hybrid: the first PT terms of a step in the tensor-memory columns
+//    left beside the accumulators, the other CB - PT in shared memory, so that the
+//    shared-memory data path carries only part of the A traffic (written once by the
+//    generators, read once by the MMAs).
 // Table modes take the pairs with rn2 <= r^2 <= r_max^2 (rn2 = 0 when no separate
 // near field is added: the self pair is then replaced in FP32 by the epilogue);
 // the series modes take the same far pairs, whose near complement near.cu adds in FP32.
-enum { MODE_NEAR = 0, MODE_CHEB = 1, MODE_NEAR_TMEM = 2, MODE_CHEB_S = 3 };
-__host__ __device__ constexpr bool is_series(int mode) { return mode == MODE_CHEB || mode == MODE_CHEB_S; }
+enum { MODE_NEAR = 0, MODE_CHEB = 1, MODE_NEAR_TMEM = 2, MODE_CHEB_S = 3, MODE_CHEB_H = 4 };
+__host__ __device__ constexpr bool is_series(int mode) {
+  return mode == MODE_CHEB || mode == MODE_CHEB_S || mode == MODE_CHEB_H;
+}
+// Terms per A slot that the hybrid layout keeps in tensor memory: what the 512 columns hold
+// beside CB x JP accumulators for NS slots of 8 columns per term.
+__host__ __device__ constexpr int hybrid_terms(int CB, int JP, int NS) {
+  return (512 - CB * JP) / (8 * NS) < CB ? (512 - CB * JP) / (8 * NS) : CB;
+}
 
 struct TcArgs {
   int N;             // vertices (rows o and columns i)
@@ -437,9 +448,11 @@ struct TcCfg {
   static constexpr int NR = NS + LOOKAHEAD;                // record slots
   static constexpr int REC = rec_bytes(JP, SPLIT);
   static constexpr bool ATMEM = (MODE == MODE_NEAR_TMEM || MODE == MODE_CHEB);
+  static constexpr bool HYB = MODE == MODE_CHEB_H;
+  static constexpr int PT = HYB ? hybrid_terms(CB, JP, NS) : (ATMEM ? CB : 0);   // A terms in TMEM
   static constexpr bool TABLE = (MODE == MODE_NEAR || MODE == MODE_NEAR_TMEM);
   static constexpr int A_TILE = 128 * 16 * 2;              // one (column, 16-i step) BF16 tile
-  static constexpr int A_STAGE = ATMEM ? 0 : CB * (SPLIT ? 2 : 1) * A_TILE;
+  static constexpr int A_STAGE = ATMEM ? 0 : (CB - PT) * (SPLIT ? 2 : 1) * A_TILE;
   static constexpr int REC_STAGE = REC;
   static constexpr int TAB_ELEM = TABLE ? (SPLIT ? 8 : 4) : 0;
   static constexpr int U = TABLE ? CB * TAB_ELEM / 16 : 1;   // 16-byte units per table row
@@ -448,7 +461,7 @@ struct TcCfg {
   static constexpr int NTHREADS = NGEN + 64;               // + the MMA-issue warp and the TMA warp
   static_assert(NTHREADS <= 1024, "at most 1024 threads per block");
   static constexpr int ACC_COLS = CB * JP;                 // FP32 accumulators
-  static constexpr int A_COLS = ATMEM ? CB * 8 : 0;        // A tile of one stage in TMEM (16 BF16 per row = 8 columns)
+  static constexpr int A_COLS = PT * 8;                    // A tiles of one stage in TMEM (16 BF16 per row = 8 columns)
   static constexpr int USED_COLS = ACC_COLS + NS * A_COLS;
   static constexpr int TMEM_COLS = (USED_COLS <= 32) ? 32 : (USED_COLS <= 64) ? 64 : (USED_COLS <= 128) ? 128
                                  : (USED_COLS <= 256) ? 256 : 512;
@@ -786,6 +799,14 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
           const uint32_t a0 = tmem_base + (uint32_t)(C::ACC_COLS + sa * C::A_COLS);
 #pragma unroll
           for (int cb = 0; cb < CB; cb += 4) umma4_ta<JP>(tmem_base + (uint32_t)(cb * JP), a0 + (uint32_t)(cb * 8), dbh, idesc, first);
+        } else if constexpr (C::HYB) {
+          const uint32_t a0 = tmem_base + (uint32_t)(C::ACC_COLS + sa * C::A_COLS);
+#pragma unroll
+          for (int cb = 0; cb < CB; ++cb) {
+            const uint32_t d = tmem_base + (uint32_t)(cb * JP);
+            if (cb < C::PT) umma_bf16_ta_elect(d, a0 + (uint32_t)(cb * 8), dbh, idesc, first);
+            else umma_bf16_elect(d, da + (uint64_t)(((cb - C::PT) * C::A_TILE) >> 4), dbh, idesc, first);
+          }
         } else {
 #pragma unroll
           for (int cb = 0; cb < CB; ++cb) {
@@ -818,8 +839,9 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
     // steps s with s mod CONC = group), run (w mod GW) / 4 of IPT consecutive i of the step.
     // One group: 16 warps, 4 i per thread; two or three groups: 8 warps each, 8 i per thread.
     constexpr int CONC = C::CONC, GW = CONC >= 2 ? 8 : 16, IPT = 64 / GW, NWD = IPT / 2;
-    constexpr bool SMEM_A = MODE == MODE_CHEB_S;
-    static_assert(!SMEM_A || NWD == 4, "shared-memory A: 8 i per thread (two generator groups)");
+    constexpr bool SMEM_A = MODE == MODE_CHEB_S, HYB = C::HYB;
+    constexpr int PT = C::PT;
+    static_assert(!(SMEM_A || HYB) || NWD == 4, "shared-memory A: 8 i per thread (two or three generator groups)");
     const int quarter = warp & 3, grp = warp / GW, ih = (warp % GW) >> 2;
     const int orow = quarter * 32 + lane;
     const uint32_t a_tmem_row =
@@ -863,10 +885,12 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
       const uint64_t xo2 = f2_pack(xo, xo), yo2 = f2_pack(yo, yo), zo2 = f2_pack(zo, zo);
       const float rlo2 = args.rn2 ? args.rn2[un.mesh] : 0.f;   // below: the exact near field
       bool ok = true;
-      int seg_pos = 0, seg_count = 0;
-      for (int sidx = sb; sidx < se; ++sidx) {
-        if (own == 0) {
-          own = CONC;
+      int seg_count = 0;
+      for (int s0 = sb; s0 < se; s0 += seg_stages) {
+        // accumulation segment [s0, s0 + n_seg): this group's steps s0 + own, s0 + own + CONC, ...
+        const int n_seg = min(se - s0, seg_stages);
+        int q = own;
+        for (; q < n_seg; q += CONC) {
           if (__any_sync(0xffffffffu, !wait_or_abort(&bar_tma[sr], pr, abort_flag))) {
             ok = false;
             break;
@@ -917,7 +941,34 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
             }
           }
           const uint32_t a_slot = a_tmem_row + (uint32_t)(sa * C::A_COLS);
-          if constexpr (SMEM_A) {
+          if constexpr (HYB) {
+            // terms p < PT to tensor memory, the others to shared memory, as the recurrence
+            // produces them (the slot's previous MMAs completed CONC steps back)
+            if (!first_use && __any_sync(0xffffffffu, !wait_or_abort(&bar_mma[sa], pa ^ 1u, abort_flag))) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a_st = a_smem_row + (uint32_t)(sa * C::A_STAGE) - (uint32_t)(PT * C::A_TILE);
+            auto put = [&](int p, const uint32_t (&w)[NWD]) {
+              if (p < PT) tmem_st_run<NWD>(a_slot + (uint32_t)(p * 8), w);
+              else st_shared_v4(a_st + (uint32_t)(p * C::A_TILE), w[0], w[1], w[2], w[3]);
+            };
+            put(0, w0);
+            put(1, w1);
+#pragma unroll
+            for (int p = 2; p < CB; ++p) {
+              uint32_t w2[NWD];
+#pragma unroll
+              for (int h = 0; h < NWD; ++h) w2[h] = bf16x2_fma((p & 1) ? mp[h] : mn[h], w1[h], w0[h]);
+              put(p, w2);
+#pragma unroll
+              for (int h = 0; h < NWD; ++h) {
+                w0[h] = w1[h];
+                w1[h] = w2[h];
+              }
+            }
+          } else if constexpr (SMEM_A) {
             // the slot's previous MMAs (CONC steps back) completed long ago: wait, then store
             // the terms as the recurrence produces them
             if (!first_use && __any_sync(0xffffffffu, !wait_or_abort(&bar_mma[sa], pa ^ 1u, abort_flag))) {
@@ -982,7 +1033,11 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
 #pragma unroll
             for (int p = 0; p < CB; ++p) tmem_st_run<NWD>(a_slot + (uint32_t)(p * 8), feat[p]);
           }
-          if constexpr (SMEM_A) {
+          if constexpr (HYB) {
+            fence_proxy_async_smem();   // the shared-memory stores, before the tensor core reads them
+            tmem_st_wait();
+            tc_fence_before();
+          } else if constexpr (SMEM_A) {
             fence_proxy_async_smem();   // the stores, before the tensor core reads them
           } else {
             tmem_st_wait();
@@ -1002,12 +1057,11 @@ __global__ void __launch_bounds__(TcCfg<MODE, CB, JP, SPLIT, NS>::NTHREADS, 1)
             pr ^= 1u;
           }
         }
-        --own;
-        if (++seg_pos != seg_stages && sidx + 1 != se) continue;
+        if (!ok) break;
+        own = q - n_seg;   // steps of the next segment before this group's next one
         // End of an accumulation segment (every warp): M[k][j] (+)= sum_p c_kp G[p][j] for
         // 2 k x 8 j per item, G read from TMEM two terms at a time.
         const bool first_seg = seg_count == 0;
-        seg_pos = 0;
         ++seg_count;
         const bool e_ok = wait_or_abort(bar_seg, (uint32_t)(seg_done & 1), abort_flag);
         ++seg_done;
@@ -1460,9 +1514,11 @@ static tsr_status dispatch_table(const TcArgs &a, int JP, bool split, const CUte
 // The far-field series generator (TSR_CHEB_BF16 terms).  conc: generator groups (steps
 // written concurrently; three groups of 8 warps by default, 24 generator warps at 72
 // registers).  With J_pad = 32 the accumulators take 384 of the 512 TMEM columns, which
-// leaves room for one A slot in TMEM only: there the A tiles go to shared memory instead
-// (one slot per group; TSR_CHEB_SMEM=0 keeps the single TMEM slot).  With J_pad = 16 the
-// A slots sit in TMEM beside the accumulators (TSR_CHEB_SMEM=1: in shared memory).
+// leaves room for one whole A slot in TMEM only: there each group's slot holds its first
+// terms in the 128 free TMEM columns (5 of 12 with three slots) and the rest in shared
+// memory (TSR_CHEB_HYB=0: every term in shared memory; TSR_CHEB_SMEM=0: the single TMEM
+// slot).  With J_pad = 16 the A slots sit in TMEM beside the accumulators
+// (TSR_CHEB_SMEM=1: in shared memory).
 static tsr_status dispatch_cheb(const TcArgs &a, int JP, const CUtensorMap &tmap, bool allow_split, cudaStream_t s,
                                 int conc = 0) {
   if (conc == 0) {
@@ -1482,6 +1538,11 @@ static tsr_status dispatch_cheb(const TcArgs &a, int JP, const CUtensorMap &tmap
   }
   if (smem_a == 0 || conc == 1)
     return launch_tc<MODE_CHEB, TSR_CHEB_BF16, 32, false, 1>(a, TSR_CHEB_BF16, tmap, allow_split, s);
+  const char *h = std::getenv("TSR_CHEB_HYB");   // diagnostic: "0" every A term in shared memory
+  if (!(h && h[0] == '0')) {
+    if (conc == 3) return launch_tc<MODE_CHEB_H, TSR_CHEB_BF16, 32, false, 3>(a, TSR_CHEB_BF16, tmap, allow_split, s);
+    return launch_tc<MODE_CHEB_H, TSR_CHEB_BF16, 32, false, 2>(a, TSR_CHEB_BF16, tmap, allow_split, s);
+  }
   if (conc == 3) return launch_tc<MODE_CHEB_S, TSR_CHEB_BF16, 32, false, 3>(a, TSR_CHEB_BF16, tmap, allow_split, s);
   return launch_tc<MODE_CHEB_S, TSR_CHEB_BF16, 32, false, 2>(a, TSR_CHEB_BF16, tmap, allow_split, s);
 }

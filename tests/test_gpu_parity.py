@@ -205,22 +205,25 @@ def test_transfer_bf16_generators_and_series_fallback(torch_cuda, tsr, oracle_ba
 @pytest.mark.parametrize("K,J", [(12, 16), (16, 25)])
 def test_transfer_series_generator_layouts(torch_cuda, tsr, oracle_basis16, monkeypatch, K, J):
     """Every layout of the far-field series generator on a 4,002-vertex mesh: one group of 16 warps,
-    two or three groups of 8 warps, A operand in tensor memory or in shared memory.  They form the
-    same BF16 products and issue the same MMAs in the same order, so M is bit-identical across
-    them, and within the BF16 bound of the oracle."""
+    two or three groups of 8 warps; the A operand in tensor memory, in shared memory, or split
+    between them (the first terms of a slot in tensor memory).  They form the same BF16 products and
+    issue the same MMAs in the same order, so M is bit-identical across them, and within the BF16
+    bound of the oracle."""
     torch = torch_cuda
     f_ref, _ = oracle_basis16
     sc, pos, area, T = _scene_arrays(20, K, J, 0.1, 3)
     args = (_dev(torch, pos.T), _dev(torch, area), _dev(torch, T))
     basis = tsr.basis_create(f_ref[:K])
     assert basis.far_series()[1]
-    layouts = [("1", "0"), ("2", "0"), ("3", "0"), ("2", "1"), ("3", "1")] if J <= 16 else \
-              [("1", "0"), ("2", "1"), ("3", "1")]
+    # (groups, A in shared memory, hybrid)
+    layouts = [("1", "0", "0"), ("2", "0", "0"), ("3", "0", "0"), ("2", "1", "0"), ("3", "1", "0")] if J <= 16 else \
+              [("1", "0", "0"), ("2", "1", "0"), ("3", "1", "0"), ("2", "1", "1"), ("3", "1", "1")]
     out = {}
-    for conc, smem in layouts:
+    for conc, smem, hyb in layouts:
         monkeypatch.setenv("TSR_CHEB_CONC", conc)
         monkeypatch.setenv("TSR_CHEB_SMEM", smem)
-        out[(conc, smem)] = tsr.precompute_transfer(basis, *args, "bf16").cpu().numpy()
+        monkeypatch.setenv("TSR_CHEB_HYB", hyb)
+        out[(conc, smem, hyb)] = tsr.precompute_transfer(basis, *args, "bf16").cpu().numpy()
     tsr.stream_status()
     first = out[layouts[0]]
     for key, M in out.items():
