@@ -222,6 +222,21 @@ __device__ __forceinline__ void near_cp16(void *smem, const void *gmem) {
 __device__ __forceinline__ void near_cp4(void *smem, const void *gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
+// Two FP32 lanes per instruction (fma.rn.f32x2): each lane rounds exactly as fmaf, so the
+// sums are bit-identical to the scalar form.
+__device__ __forceinline__ uint64_t near_f2_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void near_f2_unpack(uint64_t v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t near_f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
 __device__ __forceinline__ void near_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void near_cp_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
@@ -281,9 +296,9 @@ __global__ void __launch_bounds__(512) near_field_kernel(
     for (int q = 0; q < 6; ++q) s_tb[q] = tile_box[tile * 6 + q];
   }
   __syncthreads();
-  float acc0[JP], acc1[JP];
+  uint64_t acc0[JP / 2], acc1[JP / 2];   // sums for (j, j + 1), two lanes per fma.rn.f32x2
 #pragma unroll
-  for (int j = 0; j < JP; ++j) acc0[j] = acc1[j] = 0.f;
+  for (int j2 = 0; j2 < JP / 2; ++j2) acc0[j2] = acc1[j2] = 0ull;   // +0.0f in both lanes
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = (int)(blockDim.x >> 5);
   const int scan = min(NEAR_SCAN, (int)blockDim.x);   // chunk boxes tested per pass (a multiple of 32)
   for (int base = s_range[0]; base < s_range[1]; base += scan) {
@@ -360,18 +375,16 @@ __global__ void __launch_bounds__(512) near_field_kernel(
             const float t = x - static_cast<float>(m);
             const float4 tb = __ldg(tab + (size_t)m * KG + kg);
             const float F0 = fmaf(t, tb.y, tb.x), F1 = fmaf(t, tb.w, tb.z);
+            const uint64_t F0p = near_f2_pack(F0, F0), F1p = near_f2_pack(F1, F1);
             const float4 *tv = reinterpret_cast<const float4 *>(sT + ii * JP);
 #pragma unroll
             for (int j4 = 0; j4 < JP / 4; ++j4) {
               const float4 v = tv[j4];
-              acc0[4 * j4] = fmaf(F0, v.x, acc0[4 * j4]);
-              acc0[4 * j4 + 1] = fmaf(F0, v.y, acc0[4 * j4 + 1]);
-              acc0[4 * j4 + 2] = fmaf(F0, v.z, acc0[4 * j4 + 2]);
-              acc0[4 * j4 + 3] = fmaf(F0, v.w, acc0[4 * j4 + 3]);
-              acc1[4 * j4] = fmaf(F1, v.x, acc1[4 * j4]);
-              acc1[4 * j4 + 1] = fmaf(F1, v.y, acc1[4 * j4 + 1]);
-              acc1[4 * j4 + 2] = fmaf(F1, v.z, acc1[4 * j4 + 2]);
-              acc1[4 * j4 + 3] = fmaf(F1, v.w, acc1[4 * j4 + 3]);
+              const uint64_t va = near_f2_pack(v.x, v.y), vb = near_f2_pack(v.z, v.w);
+              acc0[2 * j4] = near_f2_fma(F0p, va, acc0[2 * j4]);
+              acc0[2 * j4 + 1] = near_f2_fma(F0p, vb, acc0[2 * j4 + 1]);
+              acc1[2 * j4] = near_f2_fma(F1p, va, acc1[2 * j4]);
+              acc1[2 * j4 + 1] = near_f2_fma(F1p, vb, acc1[2 * j4 + 1]);
             }
           }
         }
@@ -384,10 +397,17 @@ __global__ void __launch_bounds__(512) near_field_kernel(
     const long long o = perm[os];
     const int k0 = 2 * kg, k1 = 2 * kg + 1;
 #pragma unroll
-    for (int j = 0; j < JP; ++j) {
-      if (j < J) {
-        if (k0 < K) M[((size_t)k0 * J + j) * stride + o] += acc0[j];
-        if (k1 < K) M[((size_t)k1 * J + j) * stride + o] += acc1[j];
+    for (int j2 = 0; j2 < JP / 2; ++j2) {
+      float a0[2], a1[2];
+      near_f2_unpack(acc0[j2], a0[0], a0[1]);
+      near_f2_unpack(acc1[j2], a1[0], a1[1]);
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int j = 2 * j2 + e;
+        if (j < J) {
+          if (k0 < K) M[((size_t)k0 * J + j) * stride + o] += a0[e];
+          if (k1 < K) M[((size_t)k1 * J + j) * stride + o] += a1[e];
+        }
       }
     }
   }
