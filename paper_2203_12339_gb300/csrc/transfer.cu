@@ -368,18 +368,18 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 //  * MODE_CHEB:      A[o][i] = W_p(r_oi), p < CB = 12, the scaled Chebyshev terms of
 //    the far field, in tensor memory; the accumulators hold
 //    G[p][j] = sum_i W_p(r_oi) T'[j][i] and the epilogue forms M[k][j] = sum_p c_kp G[p][j].
-//    The warps form CONC groups that fill the A slots of alternate steps (group g
-//    takes the steps s with s mod CONC = g), each thread a run of 4 CONC
-//    consecutive i of one row, so that a step's A tile is written while the tensor
-//    core consumes the previous one.
+//    The warps form CONC = NS groups, one per A slot (group g takes the steps s with
+//    s mod CONC = g and visits only those), so that steps are written while the tensor
+//    core consumes earlier ones: one group of 16 warps with 4 i per thread, or two or
+//    three groups of 8 warps with 8 i per thread (three: 24 generator warps at 72
+//    registers, the default);
 //  * MODE_CHEB_S:    the same terms written to shared memory (canonical K-major layout, one
 //    16-byte store per term and thread) for the MMA to read from there, so that tensor
-//    memory holds only the accumulators: at J_pad = 32 (12 x 32 accumulator columns) two A
-//    slots fit, and two groups of 8 warps, 8 i per thread, write alternate steps.
+//    memory holds only the accumulators (at J_pad = 32, 12 x 32 accumulator columns);
 //  * MODE_CHEB_H:    hybrid: the first PT terms of a step in the tensor-memory columns
 //    left beside the accumulators, the other CB - PT in shared memory, so that the
 //    shared-memory data path carries only part of the A traffic (written once by the
-//    generators, read once by the MMAs).
+//    generators, read once by the MMAs); the default at J_pad = 32.
 // Table modes take the pairs with rn2 <= r^2 <= r_max^2 (rn2 = 0 when no separate
 // near field is added: the self pair is then replaced in FP32 by the epilogue);
 // the series modes take the same far pairs, whose near complement near.cu adds in FP32.
